@@ -1,0 +1,29 @@
+"""Nonequispaced Fourier matrix and direct sums (Sec. 1-2, eq:matrix_A, eq:nfft, eq:nfft*)."""
+import numpy as np
+
+
+def freqs(M):
+    """k = -M/2 .. M/2-1 (M even, eq:trig_polynomial)."""
+    return np.arange(-(M // 2), M // 2)
+
+
+def matrix_A(x, M):
+    """A = (exp(2 pi i k x_j))_{j, k}  in C^{N x M}  (eq:matrix_A)."""
+    return np.exp(2j * np.pi * np.outer(np.asarray(x, np.float64), freqs(M)))
+
+
+def nfft_direct(x, fhat):
+    """f_j = sum_k fhat_k exp(2 pi i k x_j)  (eq:nfft), O(NM)."""
+    return matrix_A(x, len(fhat)) @ np.asarray(fhat, np.complex128)
+
+
+def nfft_adjoint_direct(x, f, M):
+    """h_k = sum_j f_j exp(-2 pi i k x_j)  (eq:nfft*), O(NM)."""
+    return matrix_A(x, M).conj().T @ np.asarray(f, np.complex128)
+
+
+def dense_lsq_inverse(x, f, M):
+    """Least-squares solution of A fhat = f (eq:problem_infft) by LAPACK's
+    SVD-based solver: the exact comparator for small overdetermined problems."""
+    sol, *_ = np.linalg.lstsq(matrix_A(x, M), np.asarray(f, np.complex128), rcond=None)
+    return sol

@@ -1,0 +1,94 @@
+"""The synthetic workloads (sizes, node families, data) and the test-data generator.
+
+Seeds: stream ``CONFIG_SEED_BASE + c`` for workload ``c``; sub-streams are
+derived by adding fixed offsets (nodes, coefficients, noise).
+"""
+from dataclasses import dataclass
+import numpy as np
+
+from .rng import complex_normal
+from .nodes import iid_uniform, jittered, chebyshev_jittered
+
+CONFIG_SEED_BASE = 1811053350
+_NODES, _COEF, _NOISE = 1, 2, 3
+
+
+def trig_poly_eval(x, fhat, block=256):
+    """f_j = sum_{k=-M/2}^{M/2-1} fhat_k exp(2 pi i k x_j)  (eq:trig_polynomial).
+
+    Evaluated in fp64 with the frequency split k = -M/2 + block*q + r so the sum
+    becomes one complex matrix product; every exponential is formed directly
+    from its own argument.  Accuracy is a few 1e-12 relative at M = 2^16, far
+    below the 1e-8 noise the large workload adds.  This is input generation,
+    not part of the inversion method."""
+    x = np.asarray(x, dtype=np.float64)
+    fhat = np.asarray(fhat, dtype=np.complex128)
+    M = fhat.shape[0]
+    if M % block != 0:
+        block = M
+    Q = M // block
+    r = np.arange(block, dtype=np.float64)
+    q = np.arange(Q, dtype=np.float64)
+    out = np.empty(x.shape[0], dtype=np.complex128)
+    F = fhat.reshape(Q, block)              # F[q, r] = fhat at k = -M/2 + block q + r
+    for s in range(0, x.shape[0], 8192):
+        xs = x[s:s + 8192]
+        # reduce x*k modulo 1 before forming the angle to keep it small
+        a1 = np.outer(xs, r)
+        a1 -= np.round(a1)
+        E1 = np.exp(2j * np.pi * a1)                    # (n, block)
+        a2 = np.outer(xs, block * q - M / 2)
+        a2 -= np.round(a2)
+        E2 = np.exp(2j * np.pi * a2)                    # (n, Q)
+        T = E1 @ F.T                                    # (n, Q): sum over r
+        out[s:s + 8192] = np.sum(E2 * T, axis=1)
+    return out
+
+
+@dataclass
+class Problem:
+    name: str
+    M: int
+    N: int
+    sigma: float
+    m: int
+    x: np.ndarray
+    fhat: np.ndarray
+    f: np.ndarray
+
+
+def make_problem(config, m=None, M=None, N=None, with_data=True, noise_rel=None, seed=None):
+    """Workload ``config`` in {1, 2, 5} (1-D single-problem forms).
+
+    1: M=64, N=128, i.i.d. uniform nodes, exact data, sigma=2, m=4.
+    2: M=2^16, N=2^18 jittered nodes, data plus 1e-8 relative complex noise, sigma=2, m in {4,6,8}.
+    5: M=2^14, N=2^16 i.i.d. uniform nodes, exact data, sigma=2, m=4.
+    M, N override the sizes (same recipe, smaller problem for fast tests)."""
+    seed = CONFIG_SEED_BASE + config if seed is None else seed
+    if config == 1:
+        M = M or 64; N = N or 128; m = m or 4
+        x = iid_uniform(seed * 16 + _NODES, N)
+        noise_rel = 0.0 if noise_rel is None else noise_rel
+    elif config == 2:
+        M = M or 2 ** 16; N = N or 2 ** 18; m = m or 4
+        x = jittered(seed * 16 + _NODES, N)
+        noise_rel = 1e-8 if noise_rel is None else noise_rel
+    elif config == 5:
+        M = M or 2 ** 14; N = N or 2 ** 16; m = m or 4
+        x = iid_uniform(seed * 16 + _NODES, N)
+        noise_rel = 0.0 if noise_rel is None else noise_rel
+    elif config == "cheb":
+        M = M or 1024; N = N or 3 * 1024; m = m or 6
+        x = chebyshev_jittered(seed * 16 + _NODES, N)
+        noise_rel = 0.0 if noise_rel is None else noise_rel
+    else:
+        raise ValueError(f"unknown workload {config!r}")
+    fhat = complex_normal(seed * 16 + _COEF, M)
+    f = None
+    if with_data:
+        f = trig_poly_eval(x, fhat)
+        if noise_rel:
+            eta = complex_normal(seed * 16 + _NOISE, N)
+            eta *= noise_rel * np.linalg.norm(f) / np.linalg.norm(eta)
+            f = f + eta
+    return Problem(f"config{config}", M, N, 2.0, m, x, fhat, f)
