@@ -1,0 +1,380 @@
+"""Benchmark of the GB300 direct inverse NFFT (overdetermined case, Sec. 3.2.2).
+
+A step is one pass of the whole path on one synthetic problem shaped like the
+paper's reconstruction experiment (Dirichlet kernel, sigma = 2, jittered nodes):
+the pattern of I(l) (eq:set_l), the fp64 least-squares precompute of B_opt
+(eq:opt_ansatz2 .. eq:solution_ansatz2) and the modified adjoint NFFT
+fhat = D^* F^* B_opt^* f (eq:approx_ansatz2).  Workload: M = 2^16, N = 2^18,
+m = 4 (override with --M/--N/--m).  Inputs live in HBM before the timed region;
+the L2 cache is flushed (a 256 MiB write) before every timed step, outside the
+step's CUDA events.
+
+Output: one JSON line (rank 0).  Multi-GPU (torchrun): every rank solves its own
+independent problem (replicas; the method does not shard a single problem), the
+time is the max over ranks and `value` sums the nodes of all ranks.
+
+--impl reference runs the FP64 CPU oracle instead (the only reference that exists:
+the paper ships no code), on rank 0, on a bounded sample of the same workload.
+"""
+import os
+
+# the CPU oracle legs are timed single-threaded; pin BLAS/OpenMP before numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import make_problem  # noqa: E402
+
+METRIC = "iNFFT nodes/s at M=2^16,N=2^18 (rel.err≤1e-5 vs FP64), % HBM roofline"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--M", type=int, default=2 ** 16)
+    ap.add_argument("--N", type=int, default=2 ** 18)
+    ap.add_argument("--m", type=int, default=4)
+    ap.add_argument("--apply-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"1D jittered iNFFT M={a.M} N={a.N} sigma=2 m={a.m} (Dirichlet full kernel)"
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ---------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------- roofline model
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    except (OSError, ValueError):
+        return 6800.0, 2070.0, "fallback"
+
+
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_PER_SM = 4          # 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
+KAPPA_FLOPS = 40                       # fp64 flops of one closed-form kernel value
+
+
+def lsq_flops(counts):
+    """Algorithmic fp64 flops of the B_opt precompute: per column of n nodes, the
+    Cholesky factorisation n^3/3, the two triangular solves 2n^2, and the
+    n(n-1)/2 + n closed-form kernel values of Re G_l and Re r_l."""
+    n = counts.astype(np.float64)
+    return float(np.sum(n ** 3 / 3 + 2 * n ** 2 + (n * (n - 1) / 2 + n) * KAPPA_FLOPS))
+
+
+def apply_bytes(N, M, nnz):
+    """Algorithmic HBM bytes of one modified adjoint NFFT: read f (8N), read the
+    fp32 weights (4 nnz), write fhat (8M); the grid stays in L2."""
+    return 8 * N + 4 * nnz + 8 * M
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+    import paper_1811_05335_gb300 as g
+
+    rank, local, world = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    p = make_problem(2, M=a.M, N=a.N, m=a.m, with_data=False, seed=1811053352 + 1000 * rank)
+    f_host = (np.random.default_rng(7 + rank).standard_normal((a.N, 2)).astype(np.float32)
+              .view(np.complex64).ravel())            # timing data: the values do not change the work
+    x = torch.tensor(p.x, dtype=torch.float64, device=dev)
+    f = torch.tensor(f_host, device=dev)
+    fhat = torch.empty(a.M, dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    plan = g.infft_plan_create(a.M, a.N, 2.0, a.m)
+
+    def step():
+        g.infft_set_nodes(plan, x, stream)
+        g.infft_precompute(plan, stream)
+        g.infft_apply(plan, f, fhat, stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = g.infft_get_info(plan)
+    counts = g.infft_copy_plan_data(plan, weights=False)["col_count"]
+
+    # ---- timed region: K whole-path steps, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index_for(local)) if rank == 0 else None
+    launches0 = g.infft_launch_count()
+    g.infft_profile(plan, True)
+    for i in range(a.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    g.infft_profile(plan, False)
+    launches = g.infft_launch_count() - launches0
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        dist.barrier()
+    kernels = g.infft_profile_read(plan)
+    ms_total = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    value = world * a.N * a.steps / (ms_total / 1e3)
+
+    # ---- apply only (fixed plan): the paper's "fixed nodes, several problems" regime
+    g.infft_profile(plan, True)
+    k_app = a.apply_steps
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k_app)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k_app)]
+    for i in range(k_app):
+        flush.fill_(float(i))
+        s_ev[i].record(stream)
+        g.infft_apply(plan, f, fhat, stream)
+        e_ev[i].record(stream)
+    torch.cuda.synchronize()
+    g.infft_profile(plan, False)
+    app_kernels = g.infft_profile_read(plan)
+    app_ms = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) / k_app
+
+    # cuFFT on the same grid length, for comparison with the own FFT passes
+    grid = torch.randn(plan.M_sigma, dtype=torch.complex64, device=dev)
+    for _ in range(5):
+        torch.fft.fft(grid)
+    c_s = [torch.cuda.Event(enable_timing=True) for _ in range(50)]
+    c_e = [torch.cuda.Event(enable_timing=True) for _ in range(50)]
+    for i in range(50):
+        flush.fill_(float(i))
+        c_s[i].record(stream)
+        torch.fft.fft(grid)
+        c_e[i].record(stream)
+    torch.cuda.synchronize()
+    cufft_ms = sum(s.elapsed_time(e) for s, e in zip(c_s, c_e)) / 50
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        xh = torch.tensor(p.x, dtype=torch.float64).pin_memory().numpy()
+        fh_ = torch.tensor(f_host).pin_memory().numpy()
+        outh = torch.empty(a.M, dtype=torch.complex64).pin_memory().numpy()
+        plan_h = g.infft_plan_create(a.M, a.N, 2.0, a.m)
+
+        def step_host():
+            g.infft_set_nodes(plan_h, xh, 0)
+            g.infft_precompute(plan_h, 0)
+            g.infft_apply(plan_h, fh_, outh, 0)    # returns once fhat is in host memory
+
+        for _ in range(a.warmup):
+            step_host()
+        wall = 0.0
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            wall += time.perf_counter() - t0
+        tw = torch.tensor([wall], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tw, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * a.N * a.steps / float(tw.item()), "unit": "nodes/s",
+               "h2d_bytes_per_step": int(xh.nbytes + fh_.nbytes), "d2h_bytes_per_step": int(outh.nbytes)}
+        plan_h.close()
+
+    # ---- roofline of the dominant kernel and of the apply
+    hbm, sm_max, src = peaks()
+    ktab = {name: (n, ms) for name, n, ms in kernels}
+    dom = max(ktab, key=lambda k: ktab[k][1])
+    dom_n, dom_ms = ktab[dom]
+    dom_avg_s = dom_ms / dom_n / 1e3
+    roofline = None
+    if dom.startswith("lsq"):
+        # all columns are solved by the warp tiers at this workload (|I(l)| <= 64)
+        fl = lsq_flops(counts)
+        lsq_ms = sum(ms for name, (n, ms) in ktab.items() if name.startswith("lsq")) / dom_n
+        peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+        ach = fl / (lsq_ms / 1e3) / 1e12
+        roofline = {"kernel": "lsq (B_opt precompute, all tiers)", "bound": "alu", "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 4 fp64 flop/clk x max SM clock"}
+    app_tab = {name: ms for name, n, ms in app_kernels}
+    app_kernel_ms = sum(app_tab.values()) / k_app
+    ab = apply_bytes(a.N, a.M, info["nnz"])
+    ach_app = ab / (app_kernel_ms / 1e3) / 1e9
+    roofline_apply = {"kernel": "spread + fft passes (one apply)", "bound": "hbm", "achieved": ach_app,
+                      "peak": hbm, "unit": "GB/s", "frac": ach_app / hbm, "traffic": None,
+                      "peak_source": src, "algorithmic_bytes": ab}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "M": a.M, "N": a.N, "sigma": 2.0, "m": a.m,
+                   "step": "pattern + fp64 B_opt precompute + fp32 apply", "l2_flush": "256 MiB write before each step",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+        "roofline_apply": roofline_apply,
+        "apply_only": {"value": world * a.N / (app_ms / 1e3), "unit": "nodes/s", "ms_per_apply": app_ms,
+                       "kernel_ms_per_apply": app_kernel_ms, "steps": k_app},
+        "fft_vs_cufft": {"own_fft_ms": sum(v for k, v in app_tab.items() if k.startswith("fft")) / k_app,
+                         "cufft_ms": cufft_ms, "length": plan.M_sigma},
+        "kernels": {name: {"launches": n, "ms_total": ms} for name, n, ms in kernels},
+        "plan": {"nnz": info["nnz"], "max_column": info["max_column"], "fallback_columns": info["fallback_columns"]},
+        "cpu_baseline": cpu,
+    }
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------- CPU oracle legs
+
+
+def oracle_step(p, f):
+    import oracle
+    B = oracle.bopt.bopt_closed(p.x, p.M, 2.0, p.m)
+    return oracle.infft.infft_apply(B, f)
+
+
+def cpu_baseline(a):
+    """The oracle as it stands, single-threaded, on one full problem of the workload."""
+    p = make_problem(2, M=a.M, N=a.N, m=a.m, with_data=False)
+    f = np.random.default_rng(7).standard_normal(a.N) + 0j
+    t0 = time.perf_counter()
+    oracle_step(p, f)
+    dt = time.perf_counter() - t0
+    return {"value": a.N / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full problem of the workload (M={a.M}, N={a.N}, m={a.m}): pattern, closed-form "
+                      f"fp64 B_opt and D^*F^*B^*f, {dt:.1f} s"}
+
+
+def run_reference(a):
+    rank, _, world = dist_info()
+    if rank != 0:
+        return
+    # bounded sample: the same recipe at 1/16 of the nodes and coefficients per step
+    M, N = max(a.M // 16, 64), max(a.N // 16, 256)
+    p = make_problem(2, M=M, N=N, m=a.m, with_data=False)
+    f = np.random.default_rng(7).standard_normal(N) + 0j
+    for _ in range(a.warmup):
+        oracle_step(p, f)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle_step(p, f)
+    dt = time.perf_counter() - t0
+    v = N * a.steps / dt
+    sample = f"per step the workload's recipe at M={M}, N={N}, m={a.m} (1/16 of the nodes)"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "nodes/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(a), "M": a.M, "N": a.N, "sigma": 2.0, "m": a.m},
+           "cpu_baseline": {"value": v, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)

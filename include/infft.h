@@ -1,0 +1,181 @@
+/*
+ * infft.h -- C ABI of the GB300 direct inverse NFFT (overdetermined case).
+ *
+ * Method: Kircheis & Potts, "Direct inversion of the nonequispaced fast Fourier
+ * transform", Sec. 3.2.2.  Given N nodes x_j in [-1/2, 1/2) and samples
+ * f_j = f(x_j) of a trigonometric polynomial of degree M (eq:trig_polynomial),
+ * the Fourier coefficients are approximated by a modified adjoint NFFT
+ *
+ *     fhat ~ D^* F^* B_opt^* f                               (eq:approx_ansatz2)
+ *
+ * where B_opt is the (2m+1)-sparse real matrix whose column l solves the
+ * least-squares problem min ||L_l b - e_l|| (eq:opt_ansatz2 .. eq:solution_ansatz2)
+ * with the Dirichlet choice of Remark remark:Dirichlet_ansatz2.
+ *
+ * Conventions used by every entry point:
+ *   - Frequencies k = -M/2 .. M/2-1 are stored at index k + M/2.
+ *   - Grid points l = -M_sigma/2 .. M_sigma/2-1 (M_sigma = sigma*M) at l + M_sigma/2.
+ *   - Complex arrays are interleaved (re, im) float pairs (complex64), i.e. a
+ *     length-n complex array is 2n floats; double-complex arrays likewise.
+ *   - Array pointers may be host or device memory unless stated otherwise; the
+ *     library detects which (cudaPointerGetAttributes) and stages host data
+ *     through plan-owned device buffers.  Device pointers must be on the plan's
+ *     device and 8-byte aligned (16 for double complex).
+ *   - `stream` is a CUDA stream handle (cudaStream_t); NULL means the legacy
+ *     default stream.  All device work is enqueued on it; calls return before
+ *     it finishes unless stated otherwise.  Results in device memory are valid
+ *     once the stream has reached the call; results written to HOST memory are
+ *     valid when the call returns.
+ *   - Every entry point returns an infft_status.  On failure nothing further
+ *     is enqueued and infft_last_error() describes the failure (thread-local).
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the
+ *     caller, and at most one stream should use a plan at a time.
+ *
+ * There is no CPU fallback: every step runs in CUDA kernels for sm_103a.
+ */
+#ifndef INFFT_GB300_H
+#define INFFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque plan: owns a copy of the nodes, the sparsity pattern, the weights
+ * of B_opt and every work buffer.  Created by infft_plan / infft_plan_create,
+ * released by plan_destroy. */
+typedef struct infft_plan_s* infft_plan_t;
+
+/* Same layout as cudaStream_t (a pointer to the driver's stream object). */
+typedef struct CUstream_st* infft_stream_t;
+
+typedef enum {
+    INFFT_OK = 0,
+    INFFT_EINVAL = 1,        /* invalid argument (sizes, sigma, m, nodes, NULL pointers) */
+    INFFT_ENOMEM = 2,        /* device or pinned-host allocation failed */
+    INFFT_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    INFFT_ENOTREADY = 4,     /* apply before set_nodes/precompute */
+    INFFT_EUNSUPPORTED = 5,  /* valid by the paper but not built here (e.g. a column too large) */
+    INFFT_ENUMERIC = 6       /* precompute finished but some columns needed the fallback */
+} infft_status;
+
+/* Kernel choice of Remark remark:Dirichlet_ansatz2 (w_hat(k) = 1 on the kept
+ * frequencies, D = diag(c_k / M_sigma), eq:matrix_D):
+ *   INFFT_KERNEL_FULL: all k = -M/2 .. M/2-1 kept (default);
+ *   INFFT_KERNEL_SYM : the remark's literal choice, D's k = -M/2 entry set to 0. */
+enum { INFFT_KERNEL_FULL = 0, INFFT_KERNEL_SYM = 1 };
+
+/* Diagnostic counters of a plan (infft_get_info synchronises the plan's last stream). */
+typedef struct {
+    int64_t M, N, M_sigma;
+    int32_t m, kernel;
+    double sigma, tau;
+    int64_t nnz;             /* sum over l of |I(l)|, eq:set_l */
+    int32_t max_column;      /* max |I(l)| */
+    int32_t empty_columns;   /* columns with I(l) empty (b_l empty, J_l = 1) */
+    int32_t bad_nodes;       /* device-checked nodes that were not finite or not in [-1/2, 1/2) */
+    int32_t fallback_columns;/* columns whose Cholesky needed a larger regularisation */
+    int32_t unsupported_columns; /* columns larger than the largest solver tier */
+    int32_t nodes_set;       /* 1 once infft_set_nodes ran */
+    int32_t precomputed;     /* 1 once infft_precompute ran after the last set_nodes */
+    double objective;        /* sum_l J_l = ||F D A^* B_opt - I||_F^2 (eq:matrixnorm_opt_ansatz2 squared) */
+} infft_info;
+
+/* ---- the five calls of the method ------------------------------------- */
+
+/* Creates a plan for M coefficients (M even, >= 2), N >= 1 nodes x (fp64,
+ * length N, host or device, each in [-1/2, 1/2), eq:trig_polynomial), oversampling
+ * sigma >= 1 with M_sigma = sigma*M an even integer (Sec. 2.1) and cut-off m >= 1
+ * with 2m < M_sigma (eq:set_l); kernel FULL, tau = 1e-12.  Runs the pattern step
+ * (infft_set_nodes) and waits for it.  *out receives the plan (NULL on failure).
+ * The caller keeps ownership of x; the plan copies it. */
+infft_status infft_plan(int64_t M, int64_t N, const double* x, double sigma, int m,
+                        infft_plan_t* out);
+
+/* Fills B_opt: for every grid point l, the Tikhonov-regularised normal
+ * equations (Re G_l + mu I) b_l = Re r_l of min ||L_l b - e_l||^2 over real b
+ * (eq:opt_ansatz2, eq:matrix_Ll, eq:solution_ansatz2), with G_l = L_l^* L_l and
+ * r_l = L_l^* e_l in closed form and mu = tau * (Re G_l)_{jj}, solved in fp64.
+ * Requires infft_set_nodes.  Asynchronous on `stream`; columns that needed the
+ * fallback (a larger mu) or exceed the largest solver are reported by infft_get_info. */
+infft_status infft_precompute(infft_plan_t plan, infft_stream_t stream);
+
+/* The inverse NFFT (eq:approx_ansatz2): fhat = D^* F^* B_opt^* f.
+ *   f    : N complex64 samples in the caller's node order (host or device), read only;
+ *   fhat : M complex64 coefficients, k = -M/2 .. M/2-1 at k + M/2 (host or device), written.
+ * Steps: spreading g = B_opt^* f onto the M_sigma grid (Sec. 3.2.2), a length-M_sigma
+ * FFT F^* (eq:matrix_F) keeping the M central frequencies, and the diagonal D^*
+ * (eq:matrix_D) fused into the FFT's last pass.  fp32 arithmetic, fp32 accumulation.
+ * Requires infft_precompute. */
+infft_status infft_apply(infft_plan_t plan, const float* f, float* fhat, infft_stream_t stream);
+
+/* The modified NFFT f = B_opt F D fhat (Remark remark:ansatz2_adj), the exact
+ * adjoint of infft_apply: <infft_apply(f), g> = <f, nfft_apply(g)>.
+ *   fhat : M complex64 (k + M/2 layout), read;  f : N complex64 in node order, written.
+ * Requires infft_precompute. */
+infft_status nfft_apply(infft_plan_t plan, const float* fhat, float* f, infft_stream_t stream);
+
+/* Releases the plan and every buffer it owns (waits for the device to finish
+ * work that uses them).  NULL is accepted. */
+infft_status plan_destroy(infft_plan_t plan);
+
+/* ---- finer-grained control ------------------------------------------- */
+
+/* Creates a plan without nodes: validates the sizes (as infft_plan), picks the
+ * kernel (INFFT_KERNEL_FULL or INFFT_KERNEL_SYM) and the Tikhonov factor tau
+ * (0 <= tau < 1; 1e-12 is the default reading) and allocates every device
+ * buffer for the worst case nnz <= (2m+1) N, so later calls allocate nothing.
+ * Requires N * (2m+1) < 2^31 and M_sigma <= 2^24 a power of two. */
+infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int kernel,
+                               double tau, infft_plan_t* out);
+
+/* The pattern step (eq:set_l): copies x (N fp64, host or device), sorts the
+ * nodes by grid cell and derives, for every grid point l, I(l) as a contiguous
+ * (wrapping) range of sorted nodes.  A node belongs to I(l) iff
+ * ceil(u) - m <= l <= floor(u) + m (mod M_sigma), decided exactly on
+ * u = fl(M_sigma x).  Host x is validated on the host (INFFT_EINVAL); device x is
+ * validated on the device and reported by infft_get_info (bad_nodes).
+ * Invalidates an earlier precompute. */
+infft_status infft_set_nodes(infft_plan_t plan, const double* x, infft_stream_t stream);
+
+/* fp64 variants of the two applies (weights, spreading, FFT and accumulation in
+ * fp64; double-complex arrays).  For accuracy checks against the oracle. */
+infft_status infft_apply_z(infft_plan_t plan, const double* f, double* fhat, infft_stream_t stream);
+infft_status nfft_apply_z(infft_plan_t plan, const double* fhat, double* f, infft_stream_t stream);
+
+/* Synchronises the plan's last stream and fills *info. */
+infft_status infft_get_info(infft_plan_t plan, infft_info* info);
+
+/* Copies the pattern and B_opt to HOST arrays (synchronous).  Any pointer may
+ * be NULL to skip it.  perm[i] = caller index of the i-th sorted node (N);
+ * col_start[p] = first sorted position of I(l), col_count[p] = |I(l)| (M_sigma
+ * each, p = l + M_sigma/2; the range wraps modulo N); col_offset[p] = offset of
+ * column p's weights (M_sigma + 1); weights[col_offset[p] + i] = b_{l, perm[(col_start[p] + i) mod N]}
+ * in fp64 (nnz); objective[p] = J_l = ||L_l b_l - e_l||^2 (M_sigma). */
+infft_status infft_copy_plan_data(infft_plan_t plan, int32_t* perm, int32_t* col_start,
+                                  int32_t* col_count, int32_t* col_offset, double* weights,
+                                  double* objective);
+
+/* Per-kernel device timing.  infft_profile(plan, 1) makes every later launch of
+ * this plan record a CUDA event pair on its stream; infft_profile_read
+ * synchronises and returns, per internal kernel, its name, launch count and
+ * summed milliseconds (up to `cap` entries; *n receives the number written),
+ * then clears the record.  infft_profile(plan, 0) stops recording. */
+infft_status infft_profile(infft_plan_t plan, int enable);
+infft_status infft_profile_read(infft_plan_t plan, int cap, const char** names,
+                                int64_t* launches, double* milliseconds, int* n);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t infft_launch_count(void);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* infft_last_error(void);
+
+/* Library version string. */
+const char* infft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INFFT_GB300_H */

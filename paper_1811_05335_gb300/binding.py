@@ -1,0 +1,254 @@
+"""ctypes binding of libinfft_gb300.so (same names as the C ABI in include/infft.h).
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed to the
+library as raw pointers (the library detects host vs device memory).  Complex data
+is complex64 (infft_apply / nfft_apply) or complex128 (the _z variants); nodes
+are float64.  ``stream`` is a torch.cuda.Stream, a raw cudaStream_t integer, or
+None for torch's current stream when a CUDA tensor is involved (else the legacy
+default stream)."""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KERNEL_FULL, KERNEL_SYM = 0, 1
+_KERNELS = {"full": KERNEL_FULL, "sym": KERNEL_SYM, KERNEL_FULL: KERNEL_FULL, KERNEL_SYM: KERNEL_SYM}
+_STATUS = {0: "INFFT_OK", 1: "INFFT_EINVAL", 2: "INFFT_ENOMEM", 3: "INFFT_ECUDA", 4: "INFFT_ENOTREADY",
+           5: "INFFT_EUNSUPPORTED", 6: "INFFT_ENUMERIC"}
+
+EXPORTED_SYMBOLS = (
+    "infft_plan", "infft_precompute", "infft_apply", "nfft_apply", "plan_destroy", "infft_plan_create",
+    "infft_set_nodes", "infft_apply_z", "nfft_apply_z", "infft_get_info", "infft_copy_plan_data",
+    "infft_profile", "infft_profile_read", "infft_launch_count", "infft_last_error", "infft_version",
+)
+
+
+class InfftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("M_sigma", ctypes.c_int64),
+                ("m", ctypes.c_int32), ("kernel", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("tau", ctypes.c_double), ("nnz", ctypes.c_int64), ("max_column", ctypes.c_int32),
+                ("empty_columns", ctypes.c_int32), ("bad_nodes", ctypes.c_int32),
+                ("fallback_columns", ctypes.c_int32), ("unsupported_columns", ctypes.c_int32),
+                ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32), ("objective", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library():
+    """Loads the built library (raises InfftError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise InfftError(-1, f"{path} is not built; run __graft_entry__.build() (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D, VP = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "infft_plan": [I64, I64, VP, D, I32, ctypes.POINTER(P)],
+        "infft_plan_create": [I64, I64, D, I32, I32, D, ctypes.POINTER(P)],
+        "infft_set_nodes": [P, VP, VP],
+        "infft_precompute": [P, VP],
+        "infft_apply": [P, VP, VP, VP],
+        "nfft_apply": [P, VP, VP, VP],
+        "infft_apply_z": [P, VP, VP, VP],
+        "nfft_apply_z": [P, VP, VP, VP],
+        "plan_destroy": [P],
+        "infft_get_info": [P, ctypes.POINTER(_Info)],
+        "infft_copy_plan_data": [P, VP, VP, VP, VP, VP, VP],
+        "infft_profile": [P, I32],
+        "infft_profile_read": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(I64),
+                               ctypes.POINTER(D), ctypes.POINTER(I32)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.infft_launch_count.restype = ctypes.c_int64
+    lib.infft_launch_count.argtypes = []
+    lib.infft_last_error.restype = ctypes.c_char_p
+    lib.infft_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        raise InfftError(code, library().infft_last_error().decode())
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _as_ptr(a, kind, keep):
+    """Raw pointer of a contiguous array of the wanted element kind."""
+    if _is_torch(a):
+        import torch
+        want = {"c64": torch.complex64, "c128": torch.complex128, "f64": torch.float64}[kind]
+        if a.dtype != want:
+            raise TypeError(f"expected a {want} tensor, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        keep.append(a)
+        return a.data_ptr()
+    want = {"c64": np.complex64, "c128": np.complex128, "f64": np.float64}[kind]
+    arr = np.ascontiguousarray(a, dtype=want)
+    keep.append(arr)
+    return arr.ctypes.data
+
+
+def _stream(stream, *arrays):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    for a in arrays:
+        if _is_torch(a) and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return 0
+
+
+def _empty_like(ref, n, kind):
+    if _is_torch(ref):
+        import torch
+        dt = {"c64": torch.complex64, "c128": torch.complex128}[kind]
+        return torch.empty(n, dtype=dt, device=ref.device)
+    return np.empty(n, dtype={"c64": np.complex64, "c128": np.complex128}[kind])
+
+
+class Plan:
+    """Owner of an infft_plan_t handle (released by plan_destroy or close())."""
+
+    def __init__(self, handle, M, N, Ms, m):
+        self.handle, self.M, self.N, self.M_sigma, self.m = handle, M, N, Ms, m
+
+    def close(self):
+        if self.handle:
+            _check(library().plan_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ms(M, sigma):
+    return int(round(sigma * M))
+
+
+def infft_plan(M, N, x, sigma, m):
+    """Creates a plan for nodes x (kernel full, tau = 1e-12) and runs the pattern step."""
+    keep = []
+    h = ctypes.c_void_p()
+    _check(library().infft_plan(M, N, _as_ptr(x, "f64", keep), float(sigma), int(m), ctypes.byref(h)))
+    return Plan(h.value, M, N, _ms(M, sigma), m)
+
+
+def infft_plan_create(M, N, sigma, m, kernel="full", tau=1e-12):
+    h = ctypes.c_void_p()
+    k = _KERNELS.get(kernel, kernel) if isinstance(kernel, (str, int)) else kernel
+    _check(library().infft_plan_create(M, N, float(sigma), int(m), int(k), float(tau), ctypes.byref(h)))
+    return Plan(h.value, M, N, _ms(M, sigma), m)
+
+
+def infft_set_nodes(plan, x, stream=None):
+    keep = []
+    _check(library().infft_set_nodes(plan.handle, _as_ptr(x, "f64", keep), _stream(stream, x)))
+
+
+def infft_precompute(plan, stream=None):
+    _check(library().infft_precompute(plan.handle, _stream(stream)))
+
+
+def _apply(fn, plan, src, out, n_out, kind, stream):
+    keep = []
+    if out is None:
+        out = _empty_like(src, n_out, kind)
+    _check(fn(plan.handle, _as_ptr(src, kind, keep), _as_ptr(out, kind, keep), _stream(stream, src, out)))
+    return out
+
+
+def infft_apply(plan, f, out=None, stream=None):
+    """fhat = D^* F^* B_opt^* f (complex64)."""
+    return _apply(library().infft_apply, plan, f, out, plan.M, "c64", stream)
+
+
+def nfft_apply(plan, fhat, out=None, stream=None):
+    """f = B_opt F D fhat (complex64), the adjoint of infft_apply."""
+    return _apply(library().nfft_apply, plan, fhat, out, plan.N, "c64", stream)
+
+
+def infft_apply_z(plan, f, out=None, stream=None):
+    return _apply(library().infft_apply_z, plan, f, out, plan.M, "c128", stream)
+
+
+def nfft_apply_z(plan, fhat, out=None, stream=None):
+    return _apply(library().nfft_apply_z, plan, fhat, out, plan.N, "c128", stream)
+
+
+def plan_destroy(plan):
+    plan.close()
+
+
+def infft_get_info(plan):
+    info = _Info()
+    _check(library().infft_get_info(plan.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in _Info._fields_}
+
+
+def infft_copy_plan_data(plan, weights=True):
+    """Pattern and B_opt as host numpy arrays (see include/infft.h)."""
+    info = infft_get_info(plan)
+    N, Ms, nnz = plan.N, plan.M_sigma, int(info["nnz"])
+    perm = np.empty(N, np.int32)
+    start = np.empty(Ms, np.int32)
+    count = np.empty(Ms, np.int32)
+    off = np.empty(Ms + 1, np.int32)
+    w = np.empty(max(nnz, 1), np.float64) if weights else None
+    J = np.empty(Ms, np.float64) if weights else None
+    ptr = lambda a: a.ctypes.data if a is not None else None
+    _check(library().infft_copy_plan_data(plan.handle, ptr(perm), ptr(start), ptr(count), ptr(off), ptr(w),
+                                          ptr(J)))
+    out = dict(perm=perm, col_start=start, col_count=count, col_offset=off)
+    if weights:
+        out.update(weights=w[:nnz], objective=J)
+    return out
+
+
+def infft_profile(plan, enable=True):
+    _check(library().infft_profile(plan.handle, 1 if enable else 0))
+
+
+def infft_profile_read(plan):
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    launches = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = ctypes.c_int()
+    _check(library().infft_profile_read(plan.handle, cap, names, launches, ms, ctypes.byref(n)))
+    return [(names[i].decode(), int(launches[i]), float(ms[i])) for i in range(n.value)]
+
+
+def infft_launch_count():
+    return int(library().infft_launch_count())
+
+
+def infft_version():
+    return library().infft_version().decode()

@@ -1,0 +1,384 @@
+// C ABI of the GB300 direct inverse NFFT: plan lifecycle, argument checks,
+// host/device staging and the per-kernel profiler.  The numerical steps live in
+// pattern.cu (index sets), lsq.cu (B_opt), spread.cu and fft.cu (the applies).
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "plan.h"
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+thread_local std::string g_error;
+
+infft_status fail(infft_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return st;
+}
+
+infft_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? INFFT_ENOMEM : INFFT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_pointer(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of an unknown host pointer
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_plan_buffers(Plan* p) {
+    void* bufs[] = {p->x, p->xs, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist, p->col_start,
+                    p->col_count, p->col_off, p->big_list, p->mid_list, p->counters, p->w64, p->w32, p->J, p->grid,
+                    p->work, p->stage_in, p->stage_out};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+}
+
+template <typename X> cudaError_t dalloc(X** ptr, size_t count) {
+    return cudaMalloc((void**)ptr, count * sizeof(X) + 16);
+}
+
+infft_status validate_sizes(int64_t M, int64_t N, double sigma, int m, int kernel, double tau, int64_t* Ms_out,
+                            int* logMs_out) {
+    if (M < 2 || (M & 1)) return fail(INFFT_EINVAL, "M must be even and >= 2 (got %lld)", (long long)M);
+    if (N < 1) return fail(INFFT_EINVAL, "N must be >= 1 (got %lld)", (long long)N);
+    if (!std::isfinite(sigma) || sigma < 1.0) return fail(INFFT_EINVAL, "sigma must be >= 1 (got %g)", sigma);
+    const double msd = sigma * (double)M;
+    if (msd > (double)(1 << 30) || msd != std::floor(msd) || ((int64_t)msd & 1))
+        return fail(INFFT_EINVAL, "sigma*M must be an even integer (got %.17g)", msd);
+    const int64_t Ms = (int64_t)msd;
+    if (m < 1 || 2 * (int64_t)m >= Ms)
+        return fail(INFFT_EINVAL, "need m >= 1 and 2m < M_sigma (m = %d, M_sigma = %lld)", m, (long long)Ms);
+    if (kernel != INFFT_KERNEL_FULL && kernel != INFFT_KERNEL_SYM)
+        return fail(INFFT_EINVAL, "kernel must be INFFT_KERNEL_FULL or INFFT_KERNEL_SYM (got %d)", kernel);
+    if (!(tau >= 0.0 && tau < 1.0)) return fail(INFFT_EINVAL, "tau must be in [0, 1) (got %g)", tau);
+    if ((double)N * (2.0 * m + 1.0) >= 2147483647.0)
+        return fail(INFFT_EINVAL, "N (2m+1) must be < 2^31 (N = %lld, m = %d)", (long long)N, m);
+    if (Ms > (1 << 24) || (Ms & (Ms - 1)))
+        return fail(INFFT_EUNSUPPORTED, "M_sigma = %lld: this build supports powers of two up to 2^24",
+                    (long long)Ms);
+    int lg = 0;
+    while ((int64_t(1) << lg) < Ms) ++lg;
+    *Ms_out = Ms;
+    *logMs_out = lg;
+    return INFFT_OK;
+}
+
+template <typename T> infft_status apply_impl(infft_plan_t p, const T* f, T* fhat, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_apply before infft_precompute");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    const size_t csz = 2 * sizeof(T);
+    const void* fin = f;
+    cudaError_t e;
+    if (!is_device_pointer(f)) {
+        if ((e = cudaMemcpyAsync(p->stage_in, f, p->N * csz, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "copy f to device");
+        fin = p->stage_in;
+    }
+    const bool host_out = !is_device_pointer(fhat);
+    void* fout = host_out ? p->stage_out : (void*)fhat;
+    if ((e = run_spread<T>(p, fin, s)) != cudaSuccess) return cuda_fail(e, "spread");
+    if ((e = run_fft_adjoint<T>(p, fout, s)) != cudaSuccess) return cuda_fail(e, "fft");
+    if (host_out) {
+        if ((e = cudaMemcpyAsync(fhat, p->stage_out, p->M * csz, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "copy fhat to host");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    }
+    return INFFT_OK;
+}
+
+template <typename T> infft_status nfft_impl(infft_plan_t p, const T* fhat, T* f, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !fhat) return fail(INFFT_EINVAL, "fhat and f must not be NULL");
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "nfft_apply before infft_precompute");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    const size_t csz = 2 * sizeof(T);
+    const void* in = fhat;
+    cudaError_t e;
+    if (!is_device_pointer(fhat)) {
+        if ((e = cudaMemcpyAsync(p->stage_in, fhat, p->M * csz, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "copy fhat to device");
+        in = p->stage_in;
+    }
+    const bool host_out = !is_device_pointer(f);
+    void* out = host_out ? p->stage_out : (void*)f;
+    if ((e = run_fft_forward<T>(p, in, s)) != cudaSuccess) return cuda_fail(e, "fft");
+    if ((e = run_interp<T>(p, out, s)) != cudaSuccess) return cuda_fail(e, "interpolate");
+    if (host_out) {
+        if ((e = cudaMemcpyAsync(f, p->stage_out, p->N * csz, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "copy f to host");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    }
+    return INFFT_OK;
+}
+
+}  // namespace
+
+void launch_begin(Plan* p, const char* name, cudaStream_t s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!p->profiling) return;
+    ProfileRec r;
+    r.name = name;
+    cudaEventCreate(&r.start);
+    cudaEventCreate(&r.stop);
+    cudaEventRecord(r.start, s);
+    p->prof.push_back(r);
+}
+
+void launch_end(Plan* p, cudaStream_t s) {
+    if (!p->profiling || p->prof.empty()) return;
+    cudaEventRecord(p->prof.back().stop, s);
+}
+
+extern "C" {
+
+infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int kernel, double tau,
+                               infft_plan_t* out) {
+    if (!out) return fail(INFFT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int64_t Ms = 0;
+    int logMs = 0;
+    infft_status st = validate_sizes(M, N, sigma, m, kernel, tau, &Ms, &logMs);
+    if (st != INFFT_OK) return st;
+    Plan* p = new Plan();
+    cudaGetDevice(&p->device);
+    p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
+    p->logMs = logMs;
+    p->key_bits = logMs + 1;   // keys < 2 M_sigma
+    p->nnz_cap = N * (2 * (int64_t)m + 1);
+    const int64_t tiles = (N + 2047) / 2048;
+    const int64_t stage = (N > M ? N : M);
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, cnt) if (e == cudaSuccess) e = dalloc(&(ptr), (size_t)(cnt))
+    ALLOC(p->x, N); ALLOC(p->xs, N);
+    ALLOC(p->keys[0], N); ALLOC(p->keys[1], N); ALLOC(p->vals[0], N); ALLOC(p->vals[1], N);
+    ALLOC(p->hist, 256 * tiles + 1);
+    ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->mid_list, Ms);
+    ALLOC(p->counters, CNT_N);
+    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms);
+    double2 *grid = nullptr, *work = nullptr, *sin_ = nullptr, *sout = nullptr;
+    ALLOC(grid, Ms); ALLOC(work, Ms); ALLOC(sin_, stage); ALLOC(sout, stage);
+#undef ALLOC
+    p->grid = grid; p->work = work; p->stage_in = sin_; p->stage_out = sout;
+    if (e == cudaSuccess) e = cudaMemset(p->counters, 0, CNT_N * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        free_plan_buffers(p);
+        delete p;
+        return cuda_fail(e, "allocate plan buffers");
+    }
+    const int passes = (p->key_bits + 7) / 8;
+    p->skey = p->keys[passes & 1];
+    p->perm = p->vals[passes & 1];
+    *out = p;
+    return INFFT_OK;
+}
+
+infft_status infft_set_nodes(infft_plan_t p, const double* x, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!x) return fail(INFFT_EINVAL, "x is NULL");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e;
+    if (is_device_pointer(x)) {
+        e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    } else {
+        for (int64_t j = 0; j < p->N; ++j) {
+            if (!(std::isfinite(x[j]) && x[j] >= -0.5 && x[j] < 0.5))
+                return fail(INFFT_EINVAL, "node x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
+        }
+        e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy nodes");
+    p->precomputed = 0;
+    if ((e = run_pattern(p, s)) != cudaSuccess) return cuda_fail(e, "pattern");
+    p->nodes_set = 1;
+    return INFFT_OK;
+}
+
+infft_status infft_plan(int64_t M, int64_t N, const double* x, double sigma, int m, infft_plan_t* out) {
+    infft_status st = infft_plan_create(M, N, sigma, m, INFFT_KERNEL_FULL, 1e-12, out);
+    if (st != INFFT_OK) return st;
+    st = infft_set_nodes(*out, x, nullptr);
+    if (st == INFFT_OK) {
+        DeviceGuard g((*out)->device);
+        cudaError_t e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) st = cuda_fail(e, "synchronize");
+    }
+    if (st != INFFT_OK) {
+        std::string keep = g_error;
+        plan_destroy(*out);
+        *out = nullptr;
+        g_error = keep;
+    }
+    return st;
+}
+
+infft_status infft_precompute(infft_plan_t p, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_precompute before infft_set_nodes");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = run_precompute(p, s);
+    if (e != cudaSuccess) return cuda_fail(e, "precompute");
+    p->precomputed = 1;
+    return INFFT_OK;
+}
+
+infft_status infft_apply(infft_plan_t p, const float* f, float* fhat, infft_stream_t stream) {
+    return apply_impl<float>(p, f, fhat, stream);
+}
+infft_status infft_apply_z(infft_plan_t p, const double* f, double* fhat, infft_stream_t stream) {
+    return apply_impl<double>(p, f, fhat, stream);
+}
+infft_status nfft_apply(infft_plan_t p, const float* fhat, float* f, infft_stream_t stream) {
+    return nfft_impl<float>(p, fhat, f, stream);
+}
+infft_status nfft_apply_z(infft_plan_t p, const double* fhat, double* f, infft_stream_t stream) {
+    return nfft_impl<double>(p, fhat, f, stream);
+}
+
+infft_status plan_destroy(infft_plan_t p) {
+    if (!p) return INFFT_OK;
+    {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        for (auto& r : p->prof) { cudaEventDestroy(r.start); cudaEventDestroy(r.stop); }
+        free_plan_buffers(p);
+    }
+    delete p;
+    return INFFT_OK;
+}
+
+infft_status infft_get_info(infft_plan_t p, infft_info* info) {
+    if (!p || !info) return fail(INFFT_EINVAL, "plan and info must not be NULL");
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    int32_t cnt[CNT_N];
+    if ((e = cudaMemcpy(cnt, p->counters, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "read counters");
+    std::memset(info, 0, sizeof *info);
+    info->M = p->M; info->N = p->N; info->M_sigma = p->Ms; info->m = p->m; info->kernel = p->kernel;
+    info->sigma = p->sigma; info->tau = p->tau;
+    info->nodes_set = p->nodes_set;
+    info->precomputed = p->precomputed;
+    if (p->nodes_set) {
+        int32_t nnz = 0;
+        if ((e = cudaMemcpy(&nnz, p->col_off + p->Ms, sizeof nnz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "read nnz");
+        info->nnz = nnz;
+        info->max_column = cnt[CNT_MAX_COLUMN];
+        info->empty_columns = cnt[CNT_EMPTY];
+        info->bad_nodes = cnt[CNT_BAD_NODES];
+    }
+    if (p->precomputed) {
+        info->fallback_columns = cnt[CNT_FALLBACK];
+        info->unsupported_columns = cnt[CNT_UNSUPPORTED];
+        std::string buf(p->Ms * sizeof(double), '\0');
+        if ((e = cudaMemcpy(&buf[0], p->J, p->Ms * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "read objective");
+        const double* J = (const double*)buf.data();
+        double sum = 0.0;
+        for (int64_t i = 0; i < p->Ms; ++i) sum += J[i];
+        info->objective = sum;
+    }
+    return INFFT_OK;
+}
+
+infft_status infft_copy_plan_data(infft_plan_t p, int32_t* perm, int32_t* col_start, int32_t* col_count,
+                                  int32_t* col_offset, double* weights, double* objective) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!p->nodes_set) return fail(INFFT_ENOTREADY, "no nodes set");
+    if ((weights || objective) && !p->precomputed) return fail(INFFT_ENOTREADY, "not precomputed");
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    int32_t nnz = 0;
+    e = cudaMemcpy(&nnz, p->col_off + p->Ms, sizeof nnz, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && perm) e = cudaMemcpy(perm, p->perm, p->N * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && col_start) e = cudaMemcpy(col_start, p->col_start, p->Ms * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && col_count) e = cudaMemcpy(col_count, p->col_count, p->Ms * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && col_offset) e = cudaMemcpy(col_offset, p->col_off, (p->Ms + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && weights) e = cudaMemcpy(weights, p->w64, (size_t)nnz * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && objective) e = cudaMemcpy(objective, p->J, p->Ms * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "copy plan data");
+    return INFFT_OK;
+}
+
+infft_status infft_profile(infft_plan_t p, int enable) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    p->profiling = enable != 0;
+    return INFFT_OK;
+}
+
+infft_status infft_profile_read(infft_plan_t p, int cap, const char** names, int64_t* launches,
+                                double* milliseconds, int* n) {
+    if (!p || !n) return fail(INFFT_EINVAL, "plan and n must not be NULL");
+    DeviceGuard g(p->device);
+    std::map<std::string, std::pair<int64_t, double>> agg;
+    std::map<std::string, const char*> keep;
+    for (auto& r : p->prof) {
+        cudaEventSynchronize(r.stop);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.start, r.stop);
+        auto& a = agg[r.name];
+        a.first += 1;
+        a.second += ms;
+        keep[r.name] = r.name;
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    p->prof.clear();
+    int i = 0;
+    for (auto& kv : agg) {
+        if (i >= cap) break;
+        if (names) names[i] = keep[kv.first];
+        if (launches) launches[i] = kv.second.first;
+        if (milliseconds) milliseconds[i] = kv.second.second;
+        ++i;
+    }
+    *n = i;
+    return INFFT_OK;
+}
+
+int64_t infft_launch_count(void) { return g_launches.load(); }
+
+const char* infft_last_error(void) { return g_error.c_str(); }
+
+const char* infft_version(void) { return "infft-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Length-M_sigma FFT with the diagonal D fused into its last pass.
+//
+// Adjoint direction (the inverse NFFT, eq:approx_ansatz2):
+//   fhat_k = conj(d_k) * sum_{l} g_l exp(-2 pi i k l / M_sigma),  k = -M/2 .. M/2-1,
+// with l = p - M_sigma/2, i.e. fhat_k = d_k (-1)^k DFT(g)[k mod M_sigma] (d_k real).
+// Forward direction (the modified NFFT, Remark remark:ansatz2_adj):
+//   g_l = sum_k exp(2 pi i k l / M_sigma) d_k fhat_k,
+// i.e. g_p = sum_q Ghat_q exp(+2 pi i q p / M_sigma), Ghat_{k mod M_sigma} = (-1)^k d_k fhat_k.
+// d_k = 1/M_sigma (kernel full); kernel sym sets d_{-M/2} = 0 (eq:matrix_D with
+// Remark remark:Dirichlet_ansatz2).
+//
+// Transforms are radix-2 Stockham passes in shared memory (Govindaraju et al.,
+// "High performance discrete Fourier transforms on graphics processors", SC 2008).
+// M_sigma <= FFT_SMALL runs in one CTA; larger lengths use the four-step split
+// M_sigma = N1 * N2 (p = N2 p1 + p2, k = k1 + N1 k2): pass A transforms over p1 at
+// fixed p2 and applies the twiddle w^{p2 k1}; pass B transforms over p2 and writes
+// the pruned, deconvolved output.  Twiddles come from sincospi on exactly reduced
+// arguments.
+#include <climits>
+
+#include "plan.h"
+
+namespace {
+
+constexpr int FFT_THREADS = 256;
+constexpr int FFT_SMALL = 2048;
+
+template <typename T> INFFT_D cplx_t<T> czero() { return cmake((T)0, (T)0); }
+
+// Batched radix-2 Stockham FFTs of length n = 2^logn in shared memory.  a holds
+// `batch` transforms back to back; b is scratch of the same size.  Returns the
+// buffer that holds the result.  DIR = -1: exp(-2 pi i ...), +1: exp(+2 pi i ...).
+template <typename T, int DIR>
+INFFT_D cplx_t<T>* smem_fft(cplx_t<T>* a, cplx_t<T>* b, int logn, int batch) {
+    using C = cplx_t<T>;
+    const int n = 1 << logn, half = n >> 1;
+    const int total = batch * half;
+    for (int Ns = 1; Ns < n; Ns <<= 1) {
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int bi = t >> (logn - 1), j = t & (half - 1);
+            const C* src = a + bi * n;
+            C* dst = b + bi * n;
+            const int jm = j & (Ns - 1);
+            C v0 = src[j], v1 = src[j + half];
+            v1 = cmul(v1, expipi((T)(DIR * jm) / (T)Ns));
+            const int d = ((j - jm) << 1) + jm;
+            dst[d] = cadd(v0, v1);
+            dst[d + Ns] = csub(v0, v1);
+        }
+        __syncthreads();
+        C* tmp = a; a = b; b = tmp;
+    }
+    return a;
+}
+
+// frequency k of DFT bin q (or INT_MIN when q is pruned)
+INFFT_D int bin_to_k(int q, int Ms, int M) {
+    if (q < M / 2) return q;
+    if (q >= Ms - M / 2) return q - Ms;
+    return INT_MIN;
+}
+
+// (-1)^k d_k as a real factor (d_k = 1/M_sigma, 0 at k = -M/2 for kernel sym)
+template <typename T> INFFT_D T deconv(int k, int M, T inv_Ms, int sym) {
+    if (sym && k == -M / 2) return (T)0;
+    return (k & 1) ? -inv_Ms : inv_Ms;
+}
+
+// ---- single-CTA transform --------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_small_adjoint(const cplx_t<T>* __restrict__ g, cplx_t<T>* __restrict__ fhat, int logMs, int M, T inv_Ms,
+                    int sym) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* a = (C*)smem_raw;
+    const int Ms = 1 << logMs;
+    C* b = a + Ms;
+    for (int i = threadIdx.x; i < Ms; i += blockDim.x) a[i] = g[i];
+    __syncthreads();
+    C* res = smem_fft<T, -1>(a, b, logMs, 1);
+    for (int kk = threadIdx.x; kk < M; kk += blockDim.x) {
+        const int k = kk - M / 2;
+        fhat[kk] = cscale(res[k & (Ms - 1)], deconv<T>(k, M, inv_Ms, sym));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_small_forward(const cplx_t<T>* __restrict__ fhat, cplx_t<T>* __restrict__ g, int logMs, int M, T inv_Ms,
+                    int sym) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* a = (C*)smem_raw;
+    const int Ms = 1 << logMs;
+    C* b = a + Ms;
+    for (int q = threadIdx.x; q < Ms; q += blockDim.x) {
+        const int k = bin_to_k(q, Ms, M);
+        a[q] = (k == INT_MIN) ? czero<T>() : cscale(fhat[k + M / 2], deconv<T>(k, M, inv_Ms, sym));
+    }
+    __syncthreads();
+    C* res = smem_fft<T, +1>(a, b, logMs, 1);
+    for (int i = threadIdx.x; i < Ms; i += blockDim.x) g[i] = res[i];
+}
+
+// ---- four-step transform ---------------------------------------------------
+
+// Pass A: CTA owns p2 in [p2_0, p2_0 + CA); transforms over p1 (length N1 = 2^log1),
+// multiplies by w^{p2 k1} and stores Y[k1 * N2 + p2].  FORWARD_INPUT: the input
+// is built from fhat (forward direction) instead of read from g.
+template <typename T, int DIR, bool FORWARD_INPUT>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_passA(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ Y, int log1, int log2, int CA, int M,
+            T inv_Ms, int sym) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N1 = 1 << log1, N2 = 1 << log2, Ms = N1 * N2;
+    C* a = (C*)smem_raw;
+    C* b = a + CA * N1;
+    const int p2_0 = blockIdx.x * CA;
+    for (int t = threadIdx.x; t < CA * N1; t += blockDim.x) {
+        const int c = t % CA, p1 = t / CA;     // consecutive threads read consecutive p2
+        const int q = (p1 << log2) + p2_0 + c;
+        C v;
+        if (FORWARD_INPUT) {
+            const int k = bin_to_k(q, Ms, M);
+            v = (k == INT_MIN) ? czero<T>() : cscale(in[k + M / 2], deconv<T>(k, M, inv_Ms, sym));
+        } else {
+            v = in[q];
+        }
+        a[c * N1 + p1] = v;
+    }
+    __syncthreads();
+    C* res = smem_fft<T, DIR>(a, b, log1, CA);
+    for (int t = threadIdx.x; t < CA * N1; t += blockDim.x) {
+        const int c = t % CA, k1 = t / CA;
+        const int p2 = p2_0 + c;
+        const unsigned r = ((unsigned)p2 * (unsigned)k1) & (unsigned)(Ms - 1);   // exact reduction
+        const C w = expipi((T)(DIR * 2) * (T)r / (T)Ms);
+        Y[(k1 << log2) + p2] = cmul(res[c * N1 + k1], w);
+    }
+}
+
+// Pass B: CTA owns k1 in [k1_0, k1_0 + CB); transforms rows Y[k1][.] of length
+// N2 and writes X[k1 + N1 k2].  ADJOINT_OUTPUT: prune to the M central
+// frequencies and apply (-1)^k d_k; otherwise store all M_sigma grid values.
+template <typename T, int DIR, bool ADJOINT_OUTPUT>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_passB(const cplx_t<T>* __restrict__ Y, cplx_t<T>* __restrict__ out, int log1, int log2, int CB, int M,
+            T inv_Ms, int sym) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N1 = 1 << log1, N2 = 1 << log2, Ms = N1 * N2;
+    C* a = (C*)smem_raw;
+    C* b = a + CB * N2;
+    const int k1_0 = blockIdx.x * CB;
+    for (int t = threadIdx.x; t < CB * N2; t += blockDim.x) a[t] = Y[((k1_0 + t / N2) << log2) + (t % N2)];
+    __syncthreads();
+    C* res = smem_fft<T, DIR>(a, b, log2, CB);
+    for (int t = threadIdx.x; t < CB * N2; t += blockDim.x) {
+        const int c = t % CB, k2 = t / CB;     // consecutive threads write consecutive q
+        const int q = k1_0 + c + (k2 << log1);
+        const C v = res[c * N2 + k2];
+        if (ADJOINT_OUTPUT) {
+            const int k = bin_to_k(q, Ms, M);
+            if (k != INT_MIN) out[k + M / 2] = cscale(v, deconv<T>(k, M, inv_Ms, sym));
+        } else {
+            out[q] = v;
+        }
+    }
+}
+
+struct Split {
+    int log1, log2, CA, CB;
+};
+
+template <typename T> Split choose_split(int logMs) {
+    Split s;
+    s.log2 = logMs / 2;
+    s.log1 = logMs - s.log2;
+    const int N1 = 1 << s.log1, N2 = 1 << s.log2;
+    // aim for >= 128 CTAs per pass and <= 64 KB of shared memory per CTA
+    const int cap_bytes = 64 * 1024;
+    s.CA = N2 / 128; if (s.CA < 1) s.CA = 1; if (s.CA > 8) s.CA = 8;
+    while (s.CA > 1 && 2 * s.CA * N1 * (int)sizeof(cplx_t<T>) > cap_bytes) s.CA >>= 1;
+    s.CB = N1 / 128; if (s.CB < 1) s.CB = 1; if (s.CB > 8) s.CB = 8;
+    while (s.CB > 1 && 2 * s.CB * N2 * (int)sizeof(cplx_t<T>) > cap_bytes) s.CB >>= 1;
+    return s;
+}
+
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s) {
+    using C = cplx_t<T>;
+    const int Ms = (int)p->Ms, M = (int)p->M, logMs = p->logMs;
+    const T inv_Ms = (T)1 / (T)Ms;
+    const int sym = p->kernel == INFFT_KERNEL_SYM;
+    cudaError_t e;
+    if (Ms <= FFT_SMALL) {
+        const size_t smem = 2 * (size_t)Ms * sizeof(C);
+        if ((e = allow_smem(k_fft_small_adjoint<T>, smem)) != cudaSuccess) return e;
+        launch_begin(p, sizeof(T) == 4 ? "fft_small" : "fft_small_z", s);
+        k_fft_small_adjoint<T><<<1, FFT_THREADS, smem, s>>>((const C*)p->grid, (C*)fhat, logMs, M, inv_Ms, sym);
+        launch_end(p, s);
+        return cudaGetLastError();
+    }
+    const Split sp = choose_split<T>(logMs);
+    const size_t smemA = 2 * (size_t)sp.CA * ((size_t)1 << sp.log1) * sizeof(C);
+    const size_t smemB = 2 * (size_t)sp.CB * ((size_t)1 << sp.log2) * sizeof(C);
+    if ((e = allow_smem(k_fft_passA<T, -1, false>, smemA)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_fft_passB<T, -1, true>, smemB)) != cudaSuccess) return e;
+    launch_begin(p, sizeof(T) == 4 ? "fft_passA" : "fft_passA_z", s);
+    k_fft_passA<T, -1, false><<<(1 << sp.log2) / sp.CA, FFT_THREADS, smemA, s>>>(
+        (const C*)p->grid, (C*)p->work, sp.log1, sp.log2, sp.CA, M, inv_Ms, sym);
+    launch_end(p, s);
+    launch_begin(p, sizeof(T) == 4 ? "fft_passB_deconv" : "fft_passB_deconv_z", s);
+    k_fft_passB<T, -1, true><<<(1 << sp.log1) / sp.CB, FFT_THREADS, smemB, s>>>(
+        (const C*)p->work, (C*)fhat, sp.log1, sp.log2, sp.CB, M, inv_Ms, sym);
+    launch_end(p, s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s) {
+    using C = cplx_t<T>;
+    const int Ms = (int)p->Ms, M = (int)p->M, logMs = p->logMs;
+    const T inv_Ms = (T)1 / (T)Ms;
+    const int sym = p->kernel == INFFT_KERNEL_SYM;
+    cudaError_t e;
+    if (Ms <= FFT_SMALL) {
+        const size_t smem = 2 * (size_t)Ms * sizeof(C);
+        if ((e = allow_smem(k_fft_small_forward<T>, smem)) != cudaSuccess) return e;
+        launch_begin(p, sizeof(T) == 4 ? "fft_small_fwd" : "fft_small_fwd_z", s);
+        k_fft_small_forward<T><<<1, FFT_THREADS, smem, s>>>((const C*)fhat, (C*)p->grid, logMs, M, inv_Ms, sym);
+        launch_end(p, s);
+        return cudaGetLastError();
+    }
+    const Split sp = choose_split<T>(logMs);
+    const size_t smemA = 2 * (size_t)sp.CA * ((size_t)1 << sp.log1) * sizeof(C);
+    const size_t smemB = 2 * (size_t)sp.CB * ((size_t)1 << sp.log2) * sizeof(C);
+    if ((e = allow_smem(k_fft_passA<T, 1, true>, smemA)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_fft_passB<T, 1, false>, smemB)) != cudaSuccess) return e;
+    launch_begin(p, sizeof(T) == 4 ? "fft_fwd_passA_deconv" : "fft_fwd_passA_deconv_z", s);
+    k_fft_passA<T, 1, true><<<(1 << sp.log2) / sp.CA, FFT_THREADS, smemA, s>>>(
+        (const C*)fhat, (C*)p->work, sp.log1, sp.log2, sp.CA, M, inv_Ms, sym);
+    launch_end(p, s);
+    launch_begin(p, sizeof(T) == 4 ? "fft_fwd_passB" : "fft_fwd_passB_z", s);
+    k_fft_passB<T, 1, false><<<(1 << sp.log1) / sp.CB, FFT_THREADS, smemB, s>>>(
+        (const C*)p->work, (C*)p->grid, sp.log1, sp.log2, sp.CB, M, inv_Ms, sym);
+    launch_end(p, s);
+    return cudaGetLastError();
+}
+
+template cudaError_t run_fft_adjoint<float>(Plan*, void*, cudaStream_t);
+template cudaError_t run_fft_adjoint<double>(Plan*, void*, cudaStream_t);
+template cudaError_t run_fft_forward<float>(Plan*, const void*, cudaStream_t);
+template cudaError_t run_fft_forward<double>(Plan*, const void*, cudaStream_t);

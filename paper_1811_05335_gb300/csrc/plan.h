@@ -1,0 +1,94 @@
+// Internal plan object and the launch functions each translation unit provides.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/infft.h"
+#include "common.cuh"
+
+// device counters (int32), read back by infft_get_info
+enum {
+    CNT_BAD_NODES = 0,
+    CNT_FALLBACK = 1,
+    CNT_UNSUPPORTED = 2,
+    CNT_MAX_COLUMN = 3,
+    CNT_EMPTY = 4,
+    CNT_BIG_LIST = 5,      // number of columns queued for the CTA solver
+    CNT_MID_LIST = 6,      // number of columns queued for the 64-row warp solver
+    CNT_N = 8
+};
+
+// largest column handled by the two warp solver tiers, and by the CTA solver
+constexpr int LSQ_WARP_NMAX = 32;
+constexpr int LSQ_WARP2_NMAX = 64;
+constexpr int LSQ_CTA_NMAX = 224;
+
+struct ProfileRec {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
+struct infft_plan_s {
+    int device = 0;
+    int64_t M = 0, N = 0, Ms = 0;
+    int m = 0, kernel = INFFT_KERNEL_FULL;
+    double sigma = 2.0, tau = 1e-12;
+    int logMs = 0;
+    int64_t nnz_cap = 0;
+    int key_bits = 0;
+
+    // pattern (a1)
+    double* x = nullptr;        // nodes, caller order (N)
+    double* xs = nullptr;       // nodes, sorted (N)
+    uint32_t* keys[2] = {nullptr, nullptr};   // radix sort ping-pong (N)
+    int32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* skey = nullptr;   // sorted keys (points into keys[])
+    int32_t* perm = nullptr;    // sorted position -> caller index (points into vals[])
+    uint32_t* hist = nullptr;   // radix histograms (256 * tiles)
+    int32_t* col_start = nullptr;   // Ms
+    int32_t* col_count = nullptr;   // Ms
+    int32_t* col_off = nullptr;     // Ms + 1
+    int32_t* big_list = nullptr;    // Ms (columns for the CTA solver)
+    int32_t* mid_list = nullptr;    // Ms (columns for the 64-row warp solver)
+    int32_t* counters = nullptr;    // CNT_N
+
+    // B_opt (a2)
+    double* w64 = nullptr;      // nnz_cap
+    float* w32 = nullptr;       // nnz_cap
+    double* J = nullptr;        // Ms
+
+    // apply buffers (a3-a5)
+    void* grid = nullptr;       // Ms double2 (also used as float2)
+    void* work = nullptr;       // Ms double2 (FFT intermediate)
+    void* stage_in = nullptr;   // max(N, M) double2: host-input staging
+    void* stage_out = nullptr;  // max(N, M) double2: host-output staging
+
+    int nodes_set = 0, precomputed = 0;
+    cudaStream_t last_stream = nullptr;
+
+    bool profiling = false;
+    std::vector<ProfileRec> prof;
+};
+
+typedef infft_plan_s Plan;
+
+// Launch bookkeeping: counts launches and, when profiling, brackets each launch
+// with an event pair on its stream.
+void launch_begin(Plan* p, const char* name, cudaStream_t s);
+void launch_end(Plan* p, cudaStream_t s);
+
+// pattern.cu
+cudaError_t run_pattern(Plan* p, cudaStream_t s);
+cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s);
+// lsq.cu
+cudaError_t run_precompute(Plan* p, cudaStream_t s);
+// spread.cu: g = B_opt^* f onto p->grid (T = float or double, complex layout)
+template <typename T> cudaError_t run_spread(Plan* p, const void* f, cudaStream_t s);
+// spread.cu: f = B_opt g from p->grid, f in caller node order
+template <typename T> cudaError_t run_interp(Plan* p, void* f, cudaStream_t s);
+// fft.cu: fhat = D^* F^* grid (pruned to the M central frequencies)
+template <typename T> cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s);
+// fft.cu: grid = F D fhat
+template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s);
