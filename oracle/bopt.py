@@ -21,7 +21,8 @@ Two tiers compute the same b_l:
 * ``bopt_closed`` uses F^* F = M_sigma I_M (|k - k'| < M <= M_sigma), so
   G_l = M_sigma H_l^* D^* D H_l, whose real part has the closed form
   Re G_{jj'} = Re kappa(x_j - x_j'), and Re r_j = Re kappa(l/M_sigma - x_j)
-  (oracle.kernel); then (Re G_l + mu I) b = Re r_l by LAPACK LU.
+  (oracle.kernel, differences taken on the torus by torus_diff); then
+  (Re G_l + mu I) b = Re r_l by LAPACK LU.
 
 Both return the column structure (ptr, idx): I(l) = idx[ptr[p]:ptr[p+1]] with
 p = l + M_sigma/2, the coefficients b (aligned with idx) and the column
@@ -32,7 +33,7 @@ import numpy as np
 
 from .nfft import freqs
 from .pattern import index_sets_l, index_sets_l_fast
-from .kernel import diag_D, re_kappa_closed, gram_diag
+from .kernel import diag_D, re_kappa_closed, gram_diag, torus_diff
 
 TAU_DEFAULT = 1e-12
 
@@ -118,8 +119,8 @@ def bopt_naive(x, M, sigma, m, kernel="full", tau=TAU_DEFAULT):
 def column_system_closed(x, I, l, M, Ms, kernel, mu):
     """Re G_l + mu I and Re r_l for one column in closed form."""
     xI = x[I]
-    G = re_kappa_closed(xI[:, None] - xI[None, :], M, Ms, kernel) + mu * np.eye(len(I))
-    r = re_kappa_closed(l / Ms - xI, M, Ms, kernel)
+    G = re_kappa_closed(torus_diff(xI[:, None], xI[None, :]), M, Ms, kernel) + mu * np.eye(len(I))
+    r = re_kappa_closed(torus_diff(l / Ms, xI), M, Ms, kernel)
     return G, r
 
 
@@ -142,8 +143,8 @@ def bopt_closed(x, M, sigma, m, kernel="full", tau=TAU_DEFAULT, chunk=8192):
             I = idx[ptr[pc][:, None] + np.arange(n)[None, :]]          # (C, n)
             xI = x[I]
             l = (pc - Ms // 2).astype(np.float64)
-            Gre = re_kappa_closed(xI[:, :, None] - xI[:, None, :], M, Ms, kernel)
-            r = re_kappa_closed(l[:, None] / Ms - xI, M, Ms, kernel)
+            Gre = re_kappa_closed(torus_diff(xI[:, :, None], xI[:, None, :]), M, Ms, kernel)
+            r = re_kappa_closed(torus_diff(l[:, None] / Ms, xI), M, Ms, kernel)
             bc = np.linalg.solve(Gre + mu * np.eye(n)[None], r[:, :, None])[:, :, 0]
             b[ptr[pc][:, None] + np.arange(n)[None, :]] = bc
             # J_l = ||L b - e_l||^2 = b^T Re G b - 2 Re r . b + 1  (b real)

@@ -39,6 +39,20 @@ def kappa_sum(t, M, Ms, kernel):
     return (np.exp(2j * np.pi * np.multiply.outer(t, freqs(M))) @ c) / Ms
 
 
+def torus_diff(a, b):
+    """a - b as the representative in [-1/2, 1/2] of the difference on the torus
+    R/Z ("observing the periodicity", Sec. 3.2.2).  When a - b leaves [-1/2, 1/2]
+    the +-1/2 shifts are applied to each operand first, so two nodes that are
+    close across the seam x = +-1/2 get their small difference to full relative
+    precision (a plain a - b near +-1 loses it before the wrap)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = a - b
+    d = np.where(d > 0.5, (a - 0.5) - (b + 0.5), d)
+    d = np.where(d < -0.5, (a + 0.5) - (b - 0.5), d)
+    return d
+
+
 def _wrap(t):
     t = np.asarray(t, dtype=np.float64)
     return t - np.floor(t + 0.5)

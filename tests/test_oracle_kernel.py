@@ -57,3 +57,33 @@ def test_diag_D_and_gram_diag():
     assert d[0] == 0 and np.all(d[1:] == 1 / 16)
     assert kernel.gram_diag(8, 16, "full") == 0.5
     assert kernel.gram_diag(8, 16, "sym") == 7 / 16
+
+
+def test_torus_diff_exact_rational():
+    """torus_diff returns the representative in [-1/2, 1/2] of a - b mod 1, correctly
+    rounded (checked in exact rational arithmetic), including pairs straddling the seam."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    a = np.concatenate([uniform(1, 300, -0.5, 0.5), 0.5 - rng.uniform(0, 1e-4, 100), [np.nextafter(0.5, 0)]])
+    b = np.concatenate([uniform(2, 300, -0.5, 0.5), -0.5 + rng.uniform(0, 1e-4, 100), [-0.5]])
+    for ai, bi in [(a, b), (b, a)]:
+        d = kernel.torus_diff(ai, bi)
+        for x, y, got in zip(ai, bi, d):
+            ex = Fraction(float(x)) - Fraction(float(y))
+            while ex > Fraction(1, 2):
+                ex -= 1
+            while ex < Fraction(-1, 2):
+                ex += 1
+            assert float(ex) == got, (x, y)
+
+
+def test_torus_diff_seam_precision():
+    """Nodes 2e-7 apart across the seam: torus_diff keeps full relative precision,
+    where subtracting first and wrapping afterwards is off by ~1e-17 (1e-11 relative)."""
+    from fractions import Fraction
+    a, b = 0.4999999123456789, -0.4999998765432101
+    exact = Fraction(a) - Fraction(b) - 1
+    assert abs(Fraction(float(kernel.torus_diff(a, b))) - exact) < Fraction(1, 10 ** 21)
+    assert abs(Fraction(float(kernel.torus_diff(b, a))) + exact) < Fraction(1, 10 ** 21)
+    naive = (a - b) - 1.0
+    assert abs(Fraction(naive) - exact) > Fraction(1, 10 ** 18)
