@@ -54,7 +54,7 @@ bool is_device_pointer(const void* ptr) {
 
 void free_plan_buffers(Plan* p) {
     void* bufs[] = {p->x, p->xs, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist, p->col_start,
-                    p->col_count, p->col_off, p->big_list, p->mid_list, p->counters, p->w64, p->w32, p->J, p->grid,
+                    p->col_count, p->col_off, p->big_list, p->mid_list, p->counters, p->w64, p->w32, p->J, p->wide, p->grid,
                     p->work, p->stage_in, p->stage_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -187,7 +187,7 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
     ALLOC(p->hist, 256 * tiles + 1);
     ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->mid_list, Ms);
     ALLOC(p->counters, CNT_N);
-    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms);
+    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms); ALLOC(p->wide, Ms);
     double2 *grid = nullptr, *work = nullptr, *sin_ = nullptr, *sout = nullptr;
     ALLOC(grid, Ms); ALLOC(work, Ms); ALLOC(sin_, stage); ALLOC(sout, stage);
 #undef ALLOC

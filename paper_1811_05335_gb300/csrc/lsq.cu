@@ -24,9 +24,14 @@ struct KernelParams {
     int sym;         // 0: full, 1: sym
 };
 
-INFFT_D double re_kappa(double t, const KernelParams& kp) {
-    if (t >= 0.5) t -= 1.0;          // both kernels are 1-periodic; evaluate near 0
-    else if (t < -0.5) t += 1.0;
+// Re kappa(a - b) with a - b taken on the torus R/Z (both kernels are 1-periodic).
+// Shifting each operand by 1/2 before subtracting keeps the difference of two
+// points that are close across the seam x = +-1/2 exact; subtracting first and
+// wrapping afterwards would lose ~11 digits and can make Re G_l + mu I indefinite.
+INFFT_D double re_kappa(double a, double b, const KernelParams& kp) {
+    double t = a - b;
+    if (t > 0.5) t = (a - 0.5) - (b + 0.5);
+    else if (t < -0.5) t = (a + 0.5) - (b - 0.5);
     if (t == 0.0) return kp.diag;
     double s, c;
     sincospi(t, &s, &c);
@@ -52,7 +57,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
            const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
            KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-           double* __restrict__ Jout, const int32_t* __restrict__ list, int list_counter,
+           double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ list,
+           int list_counter,
            int32_t* __restrict__ next_list, int next_counter, int32_t* __restrict__ counters) {
     constexpr int ROWS = NMAX / 32;
     constexpr int LD = NMAX + 1;     // padded row stride: conflict-free column access
@@ -66,7 +72,7 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         const int p = list ? list[it] : it;
         const int n = col_count[p];
         if (n == 0) {
-            if (lane == 0) Jout[p] = 1.0;
+            if (lane == 0) { Jout[p] = 1.0; wide[p] = 0; }
             continue;
         }
         if (n > NMAX) {
@@ -85,11 +91,11 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         double mu = mu0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-            for (int i = lane; i < n; i += 32) r[i] = re_kappa(tl - xl[i], kp);
+            for (int i = lane; i < n; i += 32) r[i] = re_kappa(tl, xl[i], kp);
             for (int e = lane; e < ntri; e += 32) {
                 int i, j;
                 tri_index(e, i, j);
-                A[i * LD + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i] - xl[j], kp);
+                A[i * LD + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], kp);
             }
             __syncwarp();
             ok = true;
@@ -123,7 +129,7 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         }
         if (!ok) {   // give up: empty contribution, counted as a fallback
             for (int i = lane; i < n; i += 32) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
-            if (lane == 0) { Jout[p] = 1.0; atomicAdd(&counters[CNT_FALLBACK], 1); }
+            if (lane == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_FALLBACK], 1); }
             continue;
         }
         if (lane == 0 && mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
@@ -153,16 +159,23 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
             }
             __syncwarp();
         }
-        double bsq = 0.0;
+        double bsq = 0.0, babs = 0.0;
         for (int i = lane; i < n; i += 32) {
             const double b = r[i];
             w64[off + i] = b;
             w32[off + i] = (float)b;
             bsq += b * b;
+            babs += fabs(b);
         }
-        for (int o = 16; o; o >>= 1) bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+        for (int o = 16; o; o >>= 1) {
+            bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+            babs += __shfl_xor_sync(0xffffffffu, babs, o);
+        }
         // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
-        if (lane == 0) Jout[p] = 1.0 - ysq - mu * bsq;
+        if (lane == 0) {
+            Jout[p] = 1.0 - ysq - mu * bsq;
+            wide[p] = babs > WIDE_COLUMN_L1;
+        }
         __syncwarp();
     }
 }
@@ -179,20 +192,21 @@ __global__ void __launch_bounds__(CTA_THREADS)
 k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
           const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
           KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-          double* __restrict__ Jout, const int32_t* __restrict__ big_list, int32_t* __restrict__ counters) {
+          double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ big_list,
+          int32_t* __restrict__ counters) {
     extern __shared__ double smem[];
     double* A = smem;                 // CN (CN + 1) / 2, packed rows
     double* r = A + CN * (CN + 1) / 2; // CN
     double* xl = r + CN;              // CN
     __shared__ int s_ok;
-    __shared__ double s_red[CTA_THREADS / 32];
+    __shared__ double s_red[2 * (CTA_THREADS / 32)];
     const int total = counters[CNT_BIG_LIST];   // filled by the warp tiers
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int p = big_list[it];
         const int n = col_count[p], s = col_start[p], off = col_off[p];
         if (n > CN) {
             for (int i = threadIdx.x; i < n; i += CTA_THREADS) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
-            if (threadIdx.x == 0) { Jout[p] = 1.0; atomicAdd(&counters[CNT_UNSUPPORTED], 1); }
+            if (threadIdx.x == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_UNSUPPORTED], 1); }
             continue;
         }
         const double tl = (double)(p - Ms / 2) / (double)Ms;
@@ -206,11 +220,11 @@ k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         double mu = mu0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-            for (int i = threadIdx.x; i < n; i += CTA_THREADS) r[i] = re_kappa(tl - xl[i], kp);
+            for (int i = threadIdx.x; i < n; i += CTA_THREADS) r[i] = re_kappa(tl, xl[i], kp);
             for (int e = threadIdx.x; e < ntri; e += CTA_THREADS) {
                 int i, j;
                 tri_index(e, i, j);
-                A[trow(i) + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i] - xl[j], kp);
+                A[trow(i) + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], kp);
             }
             if (threadIdx.x == 0) s_ok = 1;
             __syncthreads();
@@ -242,7 +256,7 @@ k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         }
         if (!ok) {
             for (int i = threadIdx.x; i < n; i += CTA_THREADS) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
-            if (threadIdx.x == 0) { Jout[p] = 1.0; atomicAdd(&counters[CNT_FALLBACK], 1); }
+            if (threadIdx.x == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_FALLBACK], 1); }
             __syncthreads();
             continue;
         }
@@ -263,20 +277,25 @@ k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
             for (int i = threadIdx.x; i < k; i += CTA_THREADS) r[i] -= A[trow(k) + i] * bk;
             __syncthreads();
         }
-        double bsq = 0.0;
+        double bsq = 0.0, babs = 0.0;
         for (int i = threadIdx.x; i < n; i += CTA_THREADS) {
             double b = r[i];
             w64[off + i] = b;
             w32[off + i] = (float)b;
             bsq += b * b;
+            babs += fabs(b);
         }
-        for (int o = 16; o; o >>= 1) bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = bsq;
+        for (int o = 16; o; o >>= 1) {
+            bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+            babs += __shfl_xor_sync(0xffffffffu, babs, o);
+        }
+        if ((threadIdx.x & 31) == 0) { s_red[threadIdx.x >> 5] = bsq; s_red[CTA_THREADS / 32 + (threadIdx.x >> 5)] = babs; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < CTA_THREADS / 32; ++w) t += s_red[w];
+            double t = 0.0, a = 0.0;
+            for (int w = 0; w < CTA_THREADS / 32; ++w) { t += s_red[w]; a += s_red[CTA_THREADS / 32 + w]; }
             Jout[p] = 1.0 - ysq - mu * t;
+            wide[p] = a > WIDE_COLUMN_L1;
         }
         __syncthreads();
     }
@@ -314,21 +333,21 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     // tier 1: every column, |I(l)| <= 32; larger ones go to the mid list
     launch_begin(p, "lsq_warp32", s);
     k1<<<(Ms + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                               p->w64, p->w32, p->J, nullptr, 0, p->mid_list, CNT_MID_LIST,
+                                               p->w64, p->w32, p->J, p->wide, nullptr, 0, p->mid_list, CNT_MID_LIST,
                                                p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // tier 2: the mid list, |I(l)| <= 64; larger ones go to the big list
     launch_begin(p, "lsq_warp64", s);
     k2<<<2 * sms, W2 * 32, s2, s>>>(p->xs, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
-                                    p->w32, p->J, p->mid_list, CNT_MID_LIST, p->big_list, CNT_BIG_LIST,
+                                    p->w32, p->J, p->wide, p->mid_list, CNT_MID_LIST, p->big_list, CNT_BIG_LIST,
                                     p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // tier 3: the big list, one CTA per column, |I(l)| <= 224
     launch_begin(p, "lsq_cta", s);
     k_lsq_cta<<<sms, CTA_THREADS, s3, s>>>(p->xs, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
-                                           p->w32, p->J, p->big_list, p->counters);
+                                           p->w32, p->J, p->wide, p->big_list, p->counters);
     launch_end(p, s);
     return cudaGetLastError();
 }

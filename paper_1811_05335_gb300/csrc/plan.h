@@ -25,6 +25,11 @@ constexpr int LSQ_WARP_NMAX = 32;
 constexpr int LSQ_WARP2_NMAX = 64;
 constexpr int LSQ_CTA_NMAX = 224;
 
+// Columns whose ||b_l||_1 exceeds this are spread and interpolated with fp64
+// weights and fp64 accumulation: their terms cancel, and fp32 rounding of
+// O(||b_l||_1 |f|) terms would dominate the result.
+constexpr double WIDE_COLUMN_L1 = 32.0;
+
 struct ProfileRec {
     const char* name;
     cudaEvent_t start, stop;
@@ -58,6 +63,7 @@ struct infft_plan_s {
     double* w64 = nullptr;      // nnz_cap
     float* w32 = nullptr;       // nnz_cap
     double* J = nullptr;        // Ms
+    uint8_t* wide = nullptr;    // Ms: 1 if column l uses fp64 weights in the fp32 applies
 
     // apply buffers (a3-a5)
     void* grid = nullptr;       // Ms double2 (also used as float2)

@@ -3,7 +3,7 @@ compare it with the FP64 oracle on the same seeded inputs."""
 import numpy as np
 
 import oracle
-from oracle.kernel import re_kappa_closed, gram_diag
+from oracle.kernel import re_kappa_closed, gram_diag, torus_diff
 
 EPS = np.finfo(np.float64).eps
 
@@ -68,8 +68,8 @@ def regularised_excess(data, x, M, Ms, kernel, tau, cols=None):
         xI = x[node[ent]]
         b = w[ent]
         l = (ps - Ms // 2).astype(np.float64)
-        G = re_kappa_closed(xI[:, :, None] - xI[:, None, :], M, Ms, kernel)
-        r = re_kappa_closed(l[:, None] / Ms - xI, M, Ms, kernel)
+        G = re_kappa_closed(torus_diff(xI[:, :, None], xI[:, None, :]), M, Ms, kernel)
+        r = re_kappa_closed(torus_diff(l[:, None] / Ms, xI), M, Ms, kernel)
         Greg = G + mu * np.eye(n)[None]
         bo = np.linalg.solve(Greg, r[:, :, None])[:, :, 0]
         phi = lambda c: np.einsum("ci,cij,cj->c", c, Greg, c) - 2 * np.sum(r * c, axis=1) + 1.0

@@ -6,9 +6,15 @@ Tolerances:
   objective Phi_l within 1e-12 relative (plus evaluation rounding); b itself is not
   compared, because the normal matrix has condition ~ 1/tau and b is ill-determined
   along near-null directions of L_l that do not affect fhat for data in range(A);
-* fhat, fp32 path: rel l2 <= 1e-5 against the oracle's fp64 fhat;
+* fhat, fp32 path: rel l2 <= 1e-5 against the oracle's fp64 fhat on the same complex64
+  input values (the fp32 path's input is complex64; rounding the data itself moves
+  fhat by up to ~2e-5 on i.i.d. uniform nodes, where ||b_l||_1 reaches 1e4);
 * fhat, fp64 path: rel l2 <= 1e-9, the bound that the fp64 solve supports:
-  eps / (2 sqrt(mu)) ~ 7e-11 with mu = tau/sigma, tau = 1e-12 (times a margin).
+  eps / (2 sqrt(mu)) ~ 7e-11 with mu = tau/sigma, tau = 1e-12 (times a margin); on
+  i.i.d. uniform nodes with N = 2M, 4x the disagreement of the oracle's two tiers;
+* nfft_apply (B_opt F D): adjoint identity with infft_apply on random probes (1e-5 fp32,
+  1e-11 fp64), element-wise oracle parity where B_opt is well determined (sigma = 1
+  equispaced), and fp32 = fp64 on the same B_opt.
 """
 import numpy as np
 import pytest
@@ -62,6 +68,11 @@ CASES = ["cfg1", "jit_small", "jit_fourstep", "jit_m8", "cheb", "cheb_big", "rag
 _cache = {}
 
 
+def c64(a):
+    """The complex64 values the fp32 path receives, as exact complex128."""
+    return np.asarray(a, np.complex64).astype(np.complex128)
+
+
 def solved(name):
     if name not in _cache:
         x, f, M, sigma, m, kernel = problem(name)
@@ -96,25 +107,76 @@ def test_bopt_attains_regularised_minimum(name):
 @pytest.mark.parametrize("name", CASES)
 def test_infft_apply_fp32(name):
     x, f, M, sigma, m, kernel, B, ghat, (plan, fhat, back, data, info) = solved(name)
-    want = oracle.infft.infft_apply(B, f)
+    want = oracle.infft.infft_apply(B, c64(f))
     err = oracle.infft.rel_l2(fhat, want)
     assert err <= FP32_TOL, f"{name}: rel l2 {err:.3e}"
 
 
+def run_probes(name, z, k=6):
+    """Adjoint-identity probes: <infft_apply(f_r), g_r> vs <f_r, nfft_apply(g_r)> on the GPU."""
+    import torch
+    import paper_1811_05335_gb300 as g
+    x, f, M, sigma, m, kernel, B, ghat, _ = solved(name)
+    dev = torch.device("cuda:0")
+    ct = torch.complex128 if z else torch.complex64
+    plan = g.infft_plan_create(M, len(x), sigma, m, kernel=kernel)
+    g.infft_set_nodes(plan, torch.tensor(x, dtype=torch.float64, device=dev))
+    g.infft_precompute(plan)
+    apply, nfft = (g.infft_apply_z, g.nfft_apply_z) if z else (g.infft_apply, g.nfft_apply)
+    errs = []
+    for r in range(k):
+        fr = torch.tensor(complex_normal(1000 + r, len(x)), dtype=ct, device=dev)
+        gr = torch.tensor(complex_normal(2000 + r, M), dtype=ct, device=dev)
+        a = torch.vdot(gr, apply(plan, fr)).item()
+        b = torch.vdot(nfft(plan, gr), fr).item()
+        scale = (torch.linalg.vector_norm(apply(plan, fr)) * torch.linalg.vector_norm(gr)).item()
+        errs.append(abs(a - b) / scale)
+    plan.close()
+    return max(errs)
+
+
 @pytest.mark.parametrize("name", CASES)
-def test_nfft_apply_fp32(name):
+def test_nfft_apply_is_adjoint_fp32(name):
+    """B_opt F D is the exact adjoint of D^* F^* B_opt^* (Remark remark:ansatz2_adj), probed
+    with random vectors.  nfft_apply is not compared element by element with the oracle:
+    it applies the weights b_l directly, and b_l is determined only to ~eps/mu along
+    near-null directions of L_l (see test_bopt_attains_regularised_minimum), which
+    infft_apply never sees for data in range(A) but nfft_apply does."""
+    assert run_probes(name, z=False) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["cfg1", "jit_small", "jit_fourstep", "cheb", "sym"])
+def test_nfft_apply_is_adjoint_fp64(name):
+    assert run_probes(name, z=True) <= 1e-11
+
+
+@pytest.mark.parametrize("M,z", [(256, False), (256, True), (4096, False), (4096, True)])
+def test_nfft_apply_equispaced_elementwise(M, z):
+    """sigma = 1, M = N, x_j = j/M: Re G_l = I, so B_opt is well determined (= I/(1+tau))
+    and nfft_apply matches the oracle element by element."""
+    from workloads import equispaced
+    x = equispaced(M)
+    ghat = complex_normal(31, M)
+    B = oracle.bopt.bopt_closed(x, M, 1.0, 2)
+    _, _, back, _, info = run_gpu(x, complex_normal(32, M), M, 1.0, 2, fhat_in=ghat, z=z)
+    want = oracle.infft.nfft_apply(B, ghat if z else c64(ghat))
+    assert oracle.infft.rel_l2(back, want) <= (FP64_TOL if z else FP32_TOL)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "jit_small", "cheb"])
+def test_nfft_fp32_matches_fp64(name):
+    """Same (deterministic) B_opt: the fp32 adjoint equals the fp64 adjoint to fp32 rounding."""
     x, f, M, sigma, m, kernel, B, ghat, (plan, fhat, back, data, info) = solved(name)
-    want = oracle.infft.nfft_apply(B, ghat)
-    err = oracle.infft.rel_l2(back, want)
-    assert err <= FP32_TOL, f"{name}: rel l2 {err:.3e}"
+    _, _, back64, _, _ = run_gpu(x, f, M, sigma, m, kernel, fhat_in=c64(ghat), z=True)
+    assert oracle.infft.rel_l2(back, back64) <= FP32_TOL
 
 
 @pytest.mark.parametrize("name", ["cfg1", "jit_small", "jit_fourstep", "sym"])
 def test_adjoint_identity_gpu(name):
     """<infft_apply(f), g> = <f, nfft_apply(g)> with both sides computed on the GPU."""
     x, f, M, sigma, m, kernel, B, ghat, (plan, fhat, back, data, info) = solved(name)
-    lhs = np.vdot(ghat, fhat)
-    rhs = np.vdot(back, f)
+    lhs = np.vdot(c64(ghat), fhat)
+    rhs = np.vdot(back, c64(f))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
@@ -123,9 +185,16 @@ def test_fp64_apply(name):
     x, f, M, sigma, m, kernel, B, ghat, _ = solved(name)
     plan, fhat, back, data, info = run_gpu(x, f, M, sigma, m, kernel, fhat_in=ghat, z=True)
     err = oracle.infft.rel_l2(fhat, oracle.infft.infft_apply(B, f))
-    err_b = oracle.infft.rel_l2(back, oracle.infft.nfft_apply(B, ghat))
-    print(f"{name}: fp64 fhat rel l2 {err:.3e}, nfft {err_b:.3e}")
-    assert err <= FP64_TOL and err_b <= FP64_TOL
+    tol = FP64_TOL
+    if name == "cfg1":
+        # i.i.d. uniform nodes with N = 2M: columns are much worse conditioned
+        # (||b_l||_1 up to 2.5e4); the bound is the oracle's own ambiguity, the
+        # disagreement of its two exact tiers, times a margin of 4
+        Bn = oracle.bopt.bopt_naive(x, M, sigma, m, kernel)
+        amb = oracle.infft.rel_l2(oracle.infft.infft_apply(Bn, f, "direct"), oracle.infft.infft_apply(B, f))
+        tol = max(tol, 4 * amb)
+    print(f"{name}: fp64 fhat rel l2 {err:.3e} (tolerance {tol:.1e})")
+    assert err <= tol
 
 
 def test_host_pointers_match_device():
@@ -173,7 +242,7 @@ def test_empty_columns_and_duplicates():
     assert_pattern_equal(data, B)
     assert info["empty_columns"] > 0 and info["fallback_columns"] == 0
     assert np.all(data["objective"][data["col_count"] == 0] == 1.0)
-    assert oracle.infft.rel_l2(fhat, oracle.infft.infft_apply(B, f)) <= FP32_TOL
+    assert oracle.infft.rel_l2(fhat, oracle.infft.infft_apply(B, c64(f))) <= FP32_TOL
 
 
 def test_boundary_nodes():
@@ -188,7 +257,7 @@ def test_boundary_nodes():
     B = oracle.bopt.bopt_closed(x, 32, 2.0, 4)
     plan, fhat, back, data, info = run_gpu(x, f, 32, 2.0, 4)
     assert_pattern_equal(data, B)
-    assert oracle.infft.rel_l2(fhat, oracle.infft.infft_apply(B, f)) <= FP32_TOL
+    assert oracle.infft.rel_l2(fhat, oracle.infft.infft_apply(B, c64(f))) <= FP32_TOL
 
 
 def test_single_node_and_smallest_sizes():
@@ -229,7 +298,7 @@ def test_full_size_config2(m):
     cols = rng.choice(B.Ms, 4096, replace=False)
     excess, tol, jdiff = regularised_excess(data, p.x, p.M, B.Ms, "full", 1e-12, cols)
     assert np.all(np.abs(excess) <= tol) and np.all(jdiff <= 1.0)
-    want = oracle.infft.infft_apply(B, p.f)
+    want = oracle.infft.infft_apply(B, c64(p.f))
     err = oracle.infft.rel_l2(fhat, want)
     print(f"config2 m={m}: fp32 rel l2 vs oracle {err:.3e}; vs truth {oracle.infft.rel_l2(fhat, p.fhat):.3e}")
     assert err <= FP32_TOL
