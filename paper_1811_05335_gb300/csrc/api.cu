@@ -1,6 +1,7 @@
 // C ABI of the GB300 direct inverse NFFT: plan lifecycle, argument checks,
 // host/device staging and the per-kernel profiler.  The numerical steps live in
 // pattern.cu (index sets), lsq.cu (B_opt), spread.cu and fft.cu (the applies).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -54,7 +55,8 @@ bool is_device_pointer(const void* ptr) {
 
 void free_plan_buffers(Plan* p) {
     void* bufs[] = {p->x, p->xs, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist, p->col_start,
-                    p->col_count, p->col_off, p->big_list, p->mid_list, p->counters, p->w64, p->w32, p->J, p->wide, p->grid,
+                    p->col_count, p->col_off, p->list_a, p->list_b, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
+                    p->w32, p->J, p->wide, p->grid,
                     p->work, p->stage_in, p->stage_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -185,7 +187,9 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
     ALLOC(p->x, N); ALLOC(p->xs, N);
     ALLOC(p->keys[0], N); ALLOC(p->keys[1], N); ALLOC(p->vals[0], N); ALLOC(p->vals[1], N);
     ALLOC(p->hist, 256 * tiles + 1);
-    ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->mid_list, Ms);
+    ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->list_a, Ms); ALLOC(p->list_b, Ms);
+    ALLOC(p->scan_sums, (std::max<int64_t>(256 * tiles, Ms + 1) + 4095) / 4096 + 2);
+    ALLOC(p->phase, N);
     ALLOC(p->counters, CNT_N);
     ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms); ALLOC(p->wide, Ms);
     double2 *grid = nullptr, *work = nullptr, *sin_ = nullptr, *sout = nullptr;

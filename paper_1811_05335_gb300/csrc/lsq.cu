@@ -6,13 +6,27 @@
 // normal matrix has the closed form Re G_{jj'} = Re kappa(x_j - x_j') and the
 // right-hand side Re r_j = Re kappa(l/M_sigma - x_j), where
 //   full: Re kappa(t) = cos(pi t) sin(pi M t) / (M_sigma sin(pi t)),
-//   sym : Re kappa(t) = sin(pi (M-1) t) / (M_sigma sin(pi t))   (eq:kernel_Dirichlet).
+//   sym : Re kappa(t) = sin(pi (M-1) t) / (M_sigma sin(pi t))   (eq:kernel_Dirichlet)
+//                     = full - cos(pi M t) / M_sigma.
 // mu = tau * Re kappa(0) (Tikhonov; the paper assumes full rank).  The systems
-// are solved in fp64 by Cholesky; a failed pivot retries with mu * 1e3 (twice)
-// and is counted as a fallback column.
+// are solved in fp64 by Cholesky with reciprocal pivots; a failed pivot retries
+// with mu * 1e3 (twice) and is counted as a fallback column.
 //
-// Columns with |I(l)| <= 32 are solved by one warp each (lanes own rows);
-// larger columns go to a device-side list consumed by a CTA-per-column kernel.
+// GB300 executes fp64 at 1/64 of the fp32 rate, so the kernels are organised to
+// minimise fp64 warp instructions:
+//   * tier 1: one THREAD per column (|I(l)| <= 18), a private packed triangle in
+//     shared memory (lane-interleaved), no synchronisation at all;
+//   * tier 2/3: one warp per column, lanes own rows (|I(l)| <= 32 / 64);
+//   * tier 4: one CTA per column (|I(l)| <= 224), packed triangle.
+// Columns too large for a tier go to a device-side work list for the next one.
+//
+// Kernel values avoid library transcendentals on the common path: with per-node
+// phases (sin, cos)(pi M x_j), sin(pi M (a - b)) follows by angle addition, and
+// for |a - b| <= 1/32 the remaining factor cot(pi t) comes from the Taylor series
+// of u cot u (coefficients 2^{2k} |B_{2k}| / (2k)!, B = Bernoulli numbers) and a
+// Newton-Raphson reciprocal; pairs closer than a quarter period of sin(pi M t)
+// use the Taylor series of sin(z)/z and cos(z) instead of the phases, so the
+// cancellation in the angle addition never meets a tiny denominator.
 #include "plan.h"
 
 namespace {
@@ -24,19 +38,98 @@ struct KernelParams {
     int sym;         // 0: full, 1: sym
 };
 
-// Re kappa(a - b) with a - b taken on the torus R/Z (both kernels are 1-periodic).
-// Shifting each operand by 1/2 before subtracting keeps the difference of two
-// points that are close across the seam x = +-1/2 exact; subtracting first and
-// wrapping afterwards would lose ~11 digits and can make Re G_l + mu I indefinite.
-INFFT_D double re_kappa(double a, double b, const KernelParams& kp) {
+constexpr double PI = 3.141592653589793238462643383279502884;
+constexpr double SMALL_T = 1.0 / 32.0;    // Taylor path for cot(pi t) below this |t|
+
+// (sin, cos)(pi M z) with M z reduced modulo 2 exactly: M z = p + e with
+// p = fl(M z) and e = fma(M, z, -p); p - 2 rint(p/2) is exact.
+INFFT_D double2 phase_of(double M, double z) {
+    const double p = M * z;
+    const double e = fma(M, z, -p);
+    const double r = p - 2.0 * rint(0.5 * p);
+    double s, c;
+    sincospi(r + e, &s, &c);
+    return make_double2(s, c);
+}
+
+// 1/u to full fp64 precision: fp32 seed, two Newton-Raphson steps r <- r (2 - u r).
+INFFT_D double recip(double u) {
+    double r = (double)__frcp_rn((float)u);
+    double e = fma(-u, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-u, r, 1.0);
+    return fma(r, e, r);
+}
+
+// Torus difference a - b in [-1/2, 1/2]: shifting each operand by 1/2 before
+// subtracting keeps the difference of two points close across the seam x = +-1/2
+// exact (subtracting first and wrapping afterwards loses ~11 digits there and
+// can make Re G_l + mu I indefinite).
+INFFT_D double torus_diff(double a, double b) {
     double t = a - b;
     if (t > 0.5) t = (a - 0.5) - (b + 0.5);
     else if (t < -0.5) t = (a + 0.5) - (b - 0.5);
-    if (t == 0.0) return kp.diag;
+    return t;
+}
+
+// Re kappa(t) with library transcendentals (any t in [-1/2, 1/2]).
+INFFT_D double re_kappa_general(double t, const KernelParams& kp) {
     double s, c;
     sincospi(t, &s, &c);
     if (kp.sym) return sinpi((kp.M - 1.0) * t) / s * kp.inv_Ms;
     return c * sinpi(kp.M * t) / s * kp.inv_Ms;
+}
+
+// Re kappa(a - b); pa, pb = (sin, cos)(pi M a), (sin, cos)(pi M b).
+INFFT_D double re_kappa(double a, double b, double2 pa, double2 pb, const KernelParams& kp) {
+    const double t = torus_diff(a, b);
+    if (t == 0.0) return kp.diag;
+    if (fabs(t) > SMALL_T) return re_kappa_general(t, kp);
+    const double u = PI * t;
+    const double w = u * u;
+    // u cot u = 1 - w/3 - w^2/45 - 2w^3/945 - w^4/4725 - 2w^5/93555 - 1382 w^6/638512875
+    double xc = fma(w, -1382.0 / 638512875.0, -2.0 / 93555.0);
+    xc = fma(w, xc, -1.0 / 4725.0);
+    xc = fma(w, xc, -2.0 / 945.0);
+    xc = fma(w, xc, -1.0 / 45.0);
+    xc = fma(w, xc, -1.0 / 3.0);
+    xc = fma(w, xc, 1.0);
+    const double y = kp.M * t;
+    double s_over_u, cm = 0.0;
+    if (fabs(y) <= 0.25) {
+        // sin(pi M t)/(pi t) = M sin(z)/z and cos(z), z = pi M t, |z| <= pi/4
+        const double z = PI * y;
+        const double v = z * z;
+        double sz = fma(v, 1.0 / 355687428096000.0, -1.0 / 1307674368000.0);
+        sz = fma(v, sz, 1.0 / 6227020800.0);
+        sz = fma(v, sz, -1.0 / 39916800.0);
+        sz = fma(v, sz, 1.0 / 362880.0);
+        sz = fma(v, sz, -1.0 / 5040.0);
+        sz = fma(v, sz, 1.0 / 120.0);
+        sz = fma(v, sz, -1.0 / 6.0);
+        sz = fma(v, sz, 1.0);
+        s_over_u = kp.M * sz;
+        if (kp.sym) {
+            double cz = fma(v, -1.0 / 6402373705728000.0, 1.0 / 20922789888000.0);
+            cz = fma(v, cz, -1.0 / 87178291200.0);
+            cz = fma(v, cz, 1.0 / 479001600.0);
+            cz = fma(v, cz, -1.0 / 3628800.0);
+            cz = fma(v, cz, 1.0 / 40320.0);
+            cz = fma(v, cz, -1.0 / 720.0);
+            cz = fma(v, cz, 1.0 / 24.0);
+            cz = fma(v, cz, -0.5);
+            cm = fma(v, cz, 1.0);
+        }
+    } else {
+        // sin(pi M (a - b)) = sin A cos B - cos A sin B; M is even, so the torus wrap of
+        // t changes neither sin(pi M t) nor cos(pi M t)
+        const double sm = fma(pa.x, pb.y, -pa.y * pb.x);
+        s_over_u = sm * recip(u);
+        if (kp.sym) cm = fma(pa.y, pb.y, pa.x * pb.x);
+    }
+    double g = xc * s_over_u;        // cot(pi t) sin(pi M t)
+    if (kp.sym) g -= cm;             // sin(pi (M-1) t) / sin(pi t)
+    return g * kp.inv_Ms;
 }
 
 // (i, j), j <= i, of the e-th entry of a row-major lower triangle
@@ -48,66 +141,176 @@ INFFT_D void tri_index(int e, int& i, int& j) {
     j = e - r * (r + 1) / 2;
 }
 
-// One warp per column; lane t owns rows t, t + 32, ... (NMAX / 32 rows).  The
-// column comes from `list` (a device work list) or, when list == nullptr, is the
-// warp's global index.  Columns too large for this tier are pushed to `next_list`
-// (count at counters[next_counter]).
+INFFT_D int trow(int i) { return i * (i + 1) / 2; }   // packed lower-triangle row start
+
+// Per sorted node: (sin, cos)(pi M x).
+__global__ void k_node_phase(const double* __restrict__ xs, int N, double M, double2* __restrict__ ph) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) ph[i] = phase_of(M, xs[i]);
+}
+
+INFFT_D double col_t(int p, int Ms) { return (double)(p - Ms / 2) / (double)Ms; }   // l / M_sigma
+
+// ---------------------------------------------------------------- tier 1: thread per column
+
+template <int NMAX> constexpr int thread_tier_doubles() { return NMAX * (NMAX + 1) / 2 + NMAX; }
+
+// One thread per column.  Shared memory per warp: a packed lower triangle and the
+// right-hand side for each lane, stored lane-interleaved (element e of lane t at
+// [e * 32 + t]) so that the 32 threads of a warp never collide on a bank.
 template <int NMAX, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
+k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
+             const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
+             KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
+             double* __restrict__ Jout, uint8_t* __restrict__ wide, int32_t* __restrict__ next_list,
+             int next_counter, int32_t* __restrict__ counters) {
+    extern __shared__ double lsq_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* base = lsq_smem + (size_t)wid * 32 * thread_tier_doubles<NMAX>() + lane;
+    double* T = base;                                   // T[e * 32]
+    double* R = base + 32 * (NMAX * (NMAX + 1) / 2);    // R[i * 32]
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Ms) return;
+    const int n = col_count[p];
+    if (n == 0) {
+        Jout[p] = 1.0;
+        wide[p] = 0;
+        return;
+    }
+    if (n > NMAX) {
+        next_list[atomicAdd(&counters[next_counter], 1)] = p;
+        return;
+    }
+    const int s = col_start[p], off = col_off[p];
+    const double tl = col_t(p, Ms);
+    const double2 pl = phase_of(kp.M, tl);
+    double mu = mu0;
+    bool ok = false;
+    for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+        // Re G_l + mu I (lower triangle) and Re r_l
+        int qi = s;
+        for (int i = 0; i < n; ++i) {
+            const double xi = xs[qi];
+            const double2 pi = ph[qi];
+            R[i * 32] = re_kappa(tl, xi, pl, pi, kp);
+            int qj = s;
+            for (int j = 0; j < i; ++j) {
+                T[(trow(i) + j) * 32] = re_kappa(xi, xs[qj], pi, ph[qj], kp);
+                if (++qj == N) qj = 0;
+            }
+            T[(trow(i) + i) * 32] = kp.diag + mu;
+            if (++qi == N) qi = 0;
+        }
+        // right-looking Cholesky; the diagonal keeps the reciprocal pivot 1/L_kk
+        ok = true;
+        for (int k = 0; k < n; ++k) {
+            const double akk = T[(trow(k) + k) * 32];
+            if (!(akk > 0.0) || !isfinite(akk)) { ok = false; break; }
+            const double rp = rsqrt(akk);
+            T[(trow(k) + k) * 32] = rp;
+            for (int i = k + 1; i < n; ++i) T[(trow(i) + k) * 32] *= rp;
+            for (int i = k + 1; i < n; ++i) {
+                const double lik = T[(trow(i) + k) * 32];
+                const int ri = trow(i);
+                for (int j = k + 1; j <= i; ++j) T[(ri + j) * 32] = fma(-lik, T[(trow(j) + k) * 32], T[(ri + j) * 32]);
+            }
+        }
+        if (!ok) mu *= 1e3;
+    }
+    if (!ok) {
+        for (int i = 0; i < n; ++i) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
+        Jout[p] = 1.0;
+        wide[p] = 0;
+        atomicAdd(&counters[CNT_FALLBACK], 1);
+        return;
+    }
+    if (mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
+    // forward: y = L^{-1} r; ||y||^2 = r . b
+    double ysq = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double acc = R[k * 32];
+        const int rk = trow(k);
+        for (int j = 0; j < k; ++j) acc = fma(-T[(rk + j) * 32], R[j * 32], acc);
+        acc *= T[(rk + k) * 32];
+        R[k * 32] = acc;
+        ysq = fma(acc, acc, ysq);
+    }
+    // backward: L^T b = y
+    double bsq = 0.0, babs = 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+        double acc = R[k * 32];
+        for (int i = k + 1; i < n; ++i) acc = fma(-T[(trow(i) + k) * 32], R[i * 32], acc);
+        acc *= T[(trow(k) + k) * 32];
+        R[k * 32] = acc;
+        w64[off + k] = acc;
+        w32[off + k] = (float)acc;
+        bsq = fma(acc, acc, bsq);
+        babs += fabs(acc);
+    }
+    // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
+    Jout[p] = 1.0 - ysq - mu * bsq;
+    wide[p] = babs > WIDE_COLUMN_L1;
+}
+
+// ---------------------------------------------------------------- tier 2/3: warp per column
+
+// One warp per column; lane t owns rows t, t + 32, ... (NMAX / 32 rows).  Columns
+// come from `list` (count at counters[list_counter]).
+template <int NMAX, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_lsq_warp(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
            const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
            KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
            double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ list,
-           int list_counter,
-           int32_t* __restrict__ next_list, int next_counter, int32_t* __restrict__ counters) {
+           int list_counter, int32_t* __restrict__ next_list, int next_counter, int32_t* __restrict__ counters) {
     constexpr int ROWS = NMAX / 32;
     constexpr int LD = NMAX + 1;     // padded row stride: conflict-free column access
     extern __shared__ double lsq_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double* A = lsq_smem + (size_t)wid * (NMAX * LD + 2 * NMAX);
+    double* A = lsq_smem + (size_t)wid * (NMAX * LD + 4 * NMAX);
     double* r = A + NMAX * LD;
     double* xl = r + NMAX;
-    const int total = list ? counters[list_counter] : Ms;
+    double2* pv = (double2*)(xl + NMAX);
+    const int total = counters[list_counter];
     for (int it = blockIdx.x * WARPS + wid; it < total; it += gridDim.x * WARPS) {
-        const int p = list ? list[it] : it;
+        const int p = list[it];
         const int n = col_count[p];
-        if (n == 0) {
-            if (lane == 0) { Jout[p] = 1.0; wide[p] = 0; }
-            continue;
-        }
         if (n > NMAX) {
             if (lane == 0) next_list[atomicAdd(&counters[next_counter], 1)] = p;
             continue;
         }
         const int s = col_start[p], off = col_off[p];
-        const double tl = (double)(p - Ms / 2) / (double)Ms;   // l / M_sigma
+        const double tl = col_t(p, Ms);
+        const double2 pl = phase_of(kp.M, tl);
         for (int i = lane; i < n; i += 32) {
             int q = s + i;
             if (q >= N) q -= N;
             xl[i] = xs[q];
+            pv[i] = ph[q];
         }
         __syncwarp();
         const int ntri = n * (n + 1) / 2;
         double mu = mu0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-            for (int i = lane; i < n; i += 32) r[i] = re_kappa(tl, xl[i], kp);
+            for (int i = lane; i < n; i += 32) r[i] = re_kappa(tl, xl[i], pl, pv[i], kp);
             for (int e = lane; e < ntri; e += 32) {
                 int i, j;
                 tri_index(e, i, j);
-                A[i * LD + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], kp);
+                A[i * LD + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kp);
             }
             __syncwarp();
             ok = true;
             for (int k = 0; k < n; ++k) {
                 const double akk = A[k * LD + k];
                 if (!(akk > 0.0) || !isfinite(akk)) { ok = false; break; }   // warp-uniform
-                const double dk = sqrt(akk);
+                const double rp = rsqrt(akk);
                 double lik[ROWS];
 #pragma unroll
                 for (int t = 0; t < ROWS; ++t) {
                     const int i = lane + 32 * t;
-                    lik[t] = (i > k && i < n) ? A[i * LD + k] / dk : 0.0;
+                    lik[t] = (i > k && i < n) ? A[i * LD + k] * rp : 0.0;
                 }
                 __syncwarp();
 #pragma unroll
@@ -115,47 +318,48 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
                     const int i = lane + 32 * t;
                     if (i > k && i < n) A[i * LD + k] = lik[t];
                 }
-                if (lane == (k & 31)) A[k * LD + k] = dk;
+                if (lane == (k & 31)) A[k * LD + k] = rp;
                 __syncwarp();
 #pragma unroll
                 for (int t = 0; t < ROWS; ++t) {
                     const int i = lane + 32 * t;
                     if (i > k && i < n)
-                        for (int j = k + 1; j <= i; ++j) A[i * LD + j] -= lik[t] * A[j * LD + k];
+                        for (int j = k + 1; j <= i; ++j) A[i * LD + j] = fma(-lik[t], A[j * LD + k], A[i * LD + j]);
                 }
                 __syncwarp();
             }
             if (!ok) mu *= 1e3;
         }
-        if (!ok) {   // give up: empty contribution, counted as a fallback
+        if (!ok) {
             for (int i = lane; i < n; i += 32) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
             if (lane == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_FALLBACK], 1); }
+            __syncwarp();
             continue;
         }
         if (lane == 0 && mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
         // forward: y = L^{-1} r (r overwritten by y); ||y||^2 = r . b
         double ysq = 0.0;
         for (int k = 0; k < n; ++k) {
-            const double yk = r[k] / A[k * LD + k];
-            ysq += yk * yk;
+            const double yk = r[k] * A[k * LD + k];
+            ysq = fma(yk, yk, ysq);
             __syncwarp();
             if (lane == (k & 31)) r[k] = yk;
 #pragma unroll
             for (int t = 0; t < ROWS; ++t) {
                 const int i = lane + 32 * t;
-                if (i > k && i < n) r[i] -= A[i * LD + k] * yk;
+                if (i > k && i < n) r[i] = fma(-A[i * LD + k], yk, r[i]);
             }
             __syncwarp();
         }
         // backward: L^T b = y (r overwritten by b)
         for (int k = n - 1; k >= 0; --k) {
-            const double bk = r[k] / A[k * LD + k];
+            const double bk = r[k] * A[k * LD + k];
             __syncwarp();
             if (lane == (k & 31)) r[k] = bk;
 #pragma unroll
             for (int t = 0; t < ROWS; ++t) {
                 const int i = lane + 32 * t;
-                if (i < k) r[i] -= A[k * LD + i] * bk;
+                if (i < k) r[i] = fma(-A[k * LD + i], bk, r[i]);
             }
             __syncwarp();
         }
@@ -164,14 +368,13 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
             const double b = r[i];
             w64[off + i] = b;
             w32[off + i] = (float)b;
-            bsq += b * b;
+            bsq = fma(b, b, bsq);
             babs += fabs(b);
         }
         for (int o = 16; o; o >>= 1) {
             bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
             babs += __shfl_xor_sync(0xffffffffu, babs, o);
         }
-        // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
         if (lane == 0) {
             Jout[p] = 1.0 - ysq - mu * bsq;
             wide[p] = babs > WIDE_COLUMN_L1;
@@ -181,23 +384,25 @@ k_lsq_warp(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
 }
 
 template <int NMAX, int WARPS> constexpr size_t warp_smem_bytes() {
-    return (size_t)WARPS * (NMAX * (NMAX + 1) + 2 * NMAX) * sizeof(double);
+    return (size_t)WARPS * (NMAX * (NMAX + 1) + 4 * NMAX) * sizeof(double);
 }
+
+// ---------------------------------------------------------------- tier 4: CTA per column
 
 constexpr int CTA_THREADS = 256;
 constexpr int CN = LSQ_CTA_NMAX;
-INFFT_D int trow(int i) { return i * (i + 1) / 2; }   // packed lower-triangle row start
 
 __global__ void __launch_bounds__(CTA_THREADS)
-k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
+k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
           const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
           KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
           double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ big_list,
           int32_t* __restrict__ counters) {
     extern __shared__ double smem[];
-    double* A = smem;                 // CN (CN + 1) / 2, packed rows
+    double* A = smem;                  // CN (CN + 1) / 2, packed rows
     double* r = A + CN * (CN + 1) / 2; // CN
-    double* xl = r + CN;              // CN
+    double* xl = r + CN;               // CN
+    double2* pv = (double2*)(xl + CN); // CN
     __shared__ int s_ok;
     __shared__ double s_red[2 * (CTA_THREADS / 32)];
     const int total = counters[CNT_BIG_LIST];   // filled by the warp tiers
@@ -209,43 +414,45 @@ k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
             if (threadIdx.x == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_UNSUPPORTED], 1); }
             continue;
         }
-        const double tl = (double)(p - Ms / 2) / (double)Ms;
+        const double tl = col_t(p, Ms);
+        const double2 pl = phase_of(kp.M, tl);
         for (int i = threadIdx.x; i < n; i += CTA_THREADS) {
             int q = s + i;
             if (q >= N) q -= N;
             xl[i] = xs[q];
+            pv[i] = ph[q];
         }
         __syncthreads();
         const int ntri = n * (n + 1) / 2;
         double mu = mu0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-            for (int i = threadIdx.x; i < n; i += CTA_THREADS) r[i] = re_kappa(tl, xl[i], kp);
+            for (int i = threadIdx.x; i < n; i += CTA_THREADS) r[i] = re_kappa(tl, xl[i], pl, pv[i], kp);
             for (int e = threadIdx.x; e < ntri; e += CTA_THREADS) {
                 int i, j;
                 tri_index(e, i, j);
-                A[trow(i) + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], kp);
+                A[trow(i) + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kp);
             }
             if (threadIdx.x == 0) s_ok = 1;
             __syncthreads();
             for (int k = 0; k < n; ++k) {
-                double akk = A[trow(k) + k];
+                const double akk = A[trow(k) + k];
                 if (!(akk > 0.0) || !isfinite(akk)) {   // block-uniform
                     if (threadIdx.x == 0) s_ok = 0;
                     break;
                 }
-                double dk = sqrt(akk);
+                const double rp = rsqrt(akk);
                 __syncthreads();
-                for (int i = k + 1 + threadIdx.x; i < n; i += CTA_THREADS) A[trow(i) + k] /= dk;
-                if (threadIdx.x == 0) A[trow(k) + k] = dk;
+                for (int i = k + 1 + threadIdx.x; i < n; i += CTA_THREADS) A[trow(i) + k] *= rp;
+                if (threadIdx.x == 0) A[trow(k) + k] = rp;
                 __syncthreads();
                 const int m2 = n - k - 1;
                 const int nt = m2 * (m2 + 1) / 2;
                 for (int e = threadIdx.x; e < nt; e += CTA_THREADS) {
                     int a, b;
                     tri_index(e, a, b);
-                    int i = k + 1 + a, j = k + 1 + b;
-                    A[trow(i) + j] -= A[trow(i) + k] * A[trow(j) + k];
+                    const int i = k + 1 + a, j = k + 1 + b;
+                    A[trow(i) + j] = fma(-A[trow(i) + k], A[trow(j) + k], A[trow(i) + j]);
                 }
                 __syncthreads();
             }
@@ -263,33 +470,36 @@ k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         if (threadIdx.x == 0 && mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
         double ysq = 0.0;
         for (int k = 0; k < n; ++k) {
-            double yk = r[k] / A[trow(k) + k];
-            ysq += yk * yk;
+            const double yk = r[k] * A[trow(k) + k];
+            ysq = fma(yk, yk, ysq);
             __syncthreads();
             if (threadIdx.x == 0) r[k] = yk;
-            for (int i = k + 1 + threadIdx.x; i < n; i += CTA_THREADS) r[i] -= A[trow(i) + k] * yk;
+            for (int i = k + 1 + threadIdx.x; i < n; i += CTA_THREADS) r[i] = fma(-A[trow(i) + k], yk, r[i]);
             __syncthreads();
         }
         for (int k = n - 1; k >= 0; --k) {
-            double bk = r[k] / A[trow(k) + k];
+            const double bk = r[k] * A[trow(k) + k];
             __syncthreads();
             if (threadIdx.x == 0) r[k] = bk;
-            for (int i = threadIdx.x; i < k; i += CTA_THREADS) r[i] -= A[trow(k) + i] * bk;
+            for (int i = threadIdx.x; i < k; i += CTA_THREADS) r[i] = fma(-A[trow(k) + i], bk, r[i]);
             __syncthreads();
         }
         double bsq = 0.0, babs = 0.0;
         for (int i = threadIdx.x; i < n; i += CTA_THREADS) {
-            double b = r[i];
+            const double b = r[i];
             w64[off + i] = b;
             w32[off + i] = (float)b;
-            bsq += b * b;
+            bsq = fma(b, b, bsq);
             babs += fabs(b);
         }
         for (int o = 16; o; o >>= 1) {
             bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
             babs += __shfl_xor_sync(0xffffffffu, babs, o);
         }
-        if ((threadIdx.x & 31) == 0) { s_red[threadIdx.x >> 5] = bsq; s_red[CTA_THREADS / 32 + (threadIdx.x >> 5)] = babs; }
+        if ((threadIdx.x & 31) == 0) {
+            s_red[threadIdx.x >> 5] = bsq;
+            s_red[CTA_THREADS / 32 + (threadIdx.x >> 5)] = babs;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0, a = 0.0;
@@ -299,6 +509,10 @@ k_lsq_cta(const double* __restrict__ xs, const int32_t* __restrict__ col_start,
         }
         __syncthreads();
     }
+}
+
+template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
@@ -314,40 +528,54 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
 
     // clear the precompute counters (fallback, unsupported, work lists), keep the pattern's
     cudaError_t e = cudaMemsetAsync(p->counters + CNT_FALLBACK, 0, 2 * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_BIG_LIST, 0, 2 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_LIST_A, 0, 3 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 148;
 
-    constexpr int W1 = 4, W2 = 4;
-    auto k1 = k_lsq_warp<LSQ_WARP_NMAX, W1>;
-    auto k2 = k_lsq_warp<LSQ_WARP2_NMAX, W2>;
-    const size_t s1 = warp_smem_bytes<LSQ_WARP_NMAX, W1>(), s2 = warp_smem_bytes<LSQ_WARP2_NMAX, W2>();
-    const size_t s3 = (size_t)(CN * (CN + 1) / 2 + 2 * CN) * sizeof(double);
-    if ((e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lsq_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) != cudaSuccess)
-        return e;
-
-    // tier 1: every column, |I(l)| <= 32; larger ones go to the mid list
-    launch_begin(p, "lsq_warp32", s);
-    k1<<<(Ms + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                               p->w64, p->w32, p->J, p->wide, nullptr, 0, p->mid_list, CNT_MID_LIST,
-                                               p->counters);
+    launch_begin(p, "node_phase", s);
+    k_node_phase<<<(N + 255) / 256, 256, 0, s>>>(p->xs, N, kp.M, p->phase);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // tier 2: the mid list, |I(l)| <= 64; larger ones go to the big list
-    launch_begin(p, "lsq_warp64", s);
-    k2<<<2 * sms, W2 * 32, s2, s>>>(p->xs, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
-                                    p->w32, p->J, p->wide, p->mid_list, CNT_MID_LIST, p->big_list, CNT_BIG_LIST,
+
+    constexpr int T1 = LSQ_THREAD_NMAX, W1 = 4, W2 = 4, W3 = 4;
+    auto k1 = k_lsq_thread<T1, W1>;
+    auto k2 = k_lsq_warp<LSQ_WARP_NMAX, W2>;
+    auto k3 = k_lsq_warp<LSQ_WARP2_NMAX, W3>;
+    const size_t s1 = (size_t)W1 * 32 * thread_tier_doubles<T1>() * sizeof(double);
+    const size_t s2 = warp_smem_bytes<LSQ_WARP_NMAX, W2>(), s3 = warp_smem_bytes<LSQ_WARP2_NMAX, W3>();
+    const size_t s4 = (size_t)(CN * (CN + 1) / 2 + 4 * CN) * sizeof(double);
+    if ((e = set_smem(k1, s1)) != cudaSuccess) return e;
+    if ((e = set_smem(k2, s2)) != cudaSuccess) return e;
+    if ((e = set_smem(k3, s3)) != cudaSuccess) return e;
+    if ((e = set_smem(k_lsq_cta, s4)) != cudaSuccess) return e;
+
+    // tier 1: every column, thread per column, |I(l)| <= 18; larger ones to list A
+    launch_begin(p, "lsq_thread", s);
+    k1<<<(Ms + W1 * 32 - 1) / (W1 * 32), W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off,
+                                                           N, Ms, kp, mu, p->w64, p->w32, p->J, p->wide,
+                                                           p->list_a, CNT_LIST_A, p->counters);
+    launch_end(p, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // tier 2: list A, warp per column, |I(l)| <= 32; larger ones to list B
+    launch_begin(p, "lsq_warp32", s);
+    k2<<<2 * sms, W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+                                    p->w64, p->w32, p->J, p->wide, p->list_a, CNT_LIST_A, p->list_b, CNT_LIST_B,
                                     p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // tier 3: the big list, one CTA per column, |I(l)| <= 224
+    // tier 3: list B, warp per column, |I(l)| <= 64; larger ones to the big list
+    launch_begin(p, "lsq_warp64", s);
+    k3<<<2 * sms, W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+                                    p->w64, p->w32, p->J, p->wide, p->list_b, CNT_LIST_B, p->big_list,
+                                    CNT_BIG_LIST, p->counters);
+    launch_end(p, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // tier 4: the big list, one CTA per column, |I(l)| <= 224
     launch_begin(p, "lsq_cta", s);
-    k_lsq_cta<<<sms, CTA_THREADS, s3, s>>>(p->xs, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
-                                           p->w32, p->J, p->wide, p->big_list, p->counters);
+    k_lsq_cta<<<sms, CTA_THREADS, s4, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+                                           p->w64, p->w32, p->J, p->wide, p->big_list, p->counters);
     launch_end(p, s);
     return cudaGetLastError();
 }

@@ -104,41 +104,66 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int32_t* __
     }
 }
 
-// Exclusive scan of n int32 values by one block (out may alias in; out has n+1
-// entries and out[n] receives the total).
-__global__ void k_scan_single(const int32_t* in, int32_t* out, int n) {
-    __shared__ int32_t wsum[32];
-    const int T = blockDim.x;
-    const int chunk = (n + T - 1) / T;
-    const int b = min(n, threadIdx.x * chunk), e = min(n, b + chunk);
+// Exclusive scan of n int32 values in two passes over blocks of SCAN_CHUNK: the
+// first reduces each block, the second adds the prefix of the block sums and
+// scans the block.  out may alias in; out has n + 1 entries, out[n] = total.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+INFFT_D int32_t block_sum(int32_t v, int32_t* red) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int32_t t = 0;
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t* __restrict__ in, int n,
+                                                              int32_t* __restrict__ sums) {
+    __shared__ int32_t red[SCAN_THREADS / 32];
+    const int b0 = blockIdx.x * SCAN_CHUNK;
     int32_t s = 0;
-    for (int i = b; i < e; ++i) s += in[i];
-    // block-wide exclusive scan of s
+    for (int i = threadIdx.x; i < SCAN_CHUNK; i += SCAN_THREADS)
+        if (b0 + i < n) s += in[b0 + i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t* in, int32_t* out, int n,
+                                                             const int32_t* __restrict__ sums) {
+    __shared__ int32_t red[SCAN_THREADS / 32];
+    __shared__ int32_t wsum[SCAN_THREADS / 32];
+    int32_t before = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_THREADS) before += sums[b];
+    before = block_sum(before, red);
+    const int b0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = (b0 + i < n) ? in[b0 + i] : 0;
+        loc += v[i];
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t inc = s;
+    int32_t inc = loc;
     for (int o = 1; o < 32; o <<= 1) {
         int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += t;
     }
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
-    if (w == 0) {
-        int32_t ws = (lane < (T >> 5)) ? wsum[lane] : 0;
-        int32_t wi = ws;
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < (T >> 5)) wsum[lane] = wi - ws;
+    int32_t wpre = 0;
+    for (int ww = 0; ww < w; ++ww) wpre += wsum[ww];
+    int32_t run = before + wpre + inc - loc;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (b0 + i < n) out[b0 + i] = run;
+        run += v[i];
     }
-    __syncthreads();
-    int32_t run = wsum[w] + inc - s;
-    for (int i = b; i < e; ++i) {
-        int32_t t = in[i];
-        out[i] = run;
-        run += t;
-    }
-    if (threadIdx.x == T - 1) out[n] = run;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
 }
 
 __global__ void k_gather_x(const double* __restrict__ x, const int32_t* __restrict__ perm, int N,
@@ -178,8 +203,12 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s) {
-    launch_begin(p, "scan", s);
-    k_scan_single<<<1, 1024, 0, s>>>(in, out, n);
+    const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK > 0 ? (n + SCAN_CHUNK - 1) / SCAN_CHUNK : 1;
+    launch_begin(p, "scan_reduce", s);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, p->scan_sums);
+    launch_end(p, s);
+    launch_begin(p, "scan_apply", s);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, p->scan_sums);
     launch_end(p, s);
     return cudaGetLastError();
 }

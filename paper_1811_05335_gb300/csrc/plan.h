@@ -15,12 +15,14 @@ enum {
     CNT_UNSUPPORTED = 2,
     CNT_MAX_COLUMN = 3,
     CNT_EMPTY = 4,
-    CNT_BIG_LIST = 5,      // number of columns queued for the CTA solver
-    CNT_MID_LIST = 6,      // number of columns queued for the 64-row warp solver
+    CNT_LIST_A = 5,        // columns queued for the 32-row warp solver
+    CNT_LIST_B = 6,        // columns queued for the 64-row warp solver
+    CNT_BIG_LIST = 7,      // columns queued for the CTA solver
     CNT_N = 8
 };
 
-// largest column handled by the two warp solver tiers, and by the CTA solver
+// largest column handled by the thread, warp and CTA solver tiers
+constexpr int LSQ_THREAD_NMAX = 18;
 constexpr int LSQ_WARP_NMAX = 32;
 constexpr int LSQ_WARP2_NMAX = 64;
 constexpr int LSQ_CTA_NMAX = 224;
@@ -55,11 +57,14 @@ struct infft_plan_s {
     int32_t* col_start = nullptr;   // Ms
     int32_t* col_count = nullptr;   // Ms
     int32_t* col_off = nullptr;     // Ms + 1
+    int32_t* list_a = nullptr;      // Ms (columns for the 32-row warp solver)
+    int32_t* list_b = nullptr;      // Ms (columns for the 64-row warp solver)
     int32_t* big_list = nullptr;    // Ms (columns for the CTA solver)
-    int32_t* mid_list = nullptr;    // Ms (columns for the 64-row warp solver)
+    int32_t* scan_sums = nullptr;   // per-block partial sums of the scans
     int32_t* counters = nullptr;    // CNT_N
 
     // B_opt (a2)
+    double2* phase = nullptr;   // N: (sin, cos)(pi M x) of the sorted nodes
     double* w64 = nullptr;      // nnz_cap
     float* w32 = nullptr;       // nnz_cap
     double* J = nullptr;        // Ms
