@@ -153,11 +153,42 @@ INFFT_D double col_t(int p, int Ms) { return (double)(p - Ms / 2) / (double)Ms; 
 
 // ---------------------------------------------------------------- tier 1: thread per column
 
-template <int NMAX> constexpr int thread_tier_doubles() { return NMAX * (NMAX + 1) / 2 + NMAX; }
+constexpr int TILE_UMAX = 128;   // largest union of nodes a warp tile shares in shared memory
 
-// One thread per column.  Shared memory per warp: a packed lower triangle and the
-// right-hand side for each lane, stored lane-interleaved (element e of lane t at
-// [e * 32 + t]) so that the 32 threads of a warp never collide on a bank.
+template <int NMAX> constexpr int thread_tier_doubles() { return NMAX * (NMAX + 1) / 2 + NMAX; }
+template <int NMAX> constexpr size_t tile_warp_bytes() {
+    return (size_t)32 * thread_tier_doubles<NMAX>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
+           64 * sizeof(int);
+}
+
+// Writes Re G_l + mu I (lower triangle) and Re r_l of one column into its private
+// triangle T / vector R (stride 32), evaluating every entry itself.
+template <int NMAX>
+INFFT_D void fill_column(double* T, double* R, const double* __restrict__ xs, const double2* __restrict__ ph,
+                         int s, int n, int N, double tl, double2 pl, double mu, const KernelParams& kp) {
+    int qi = s;
+    for (int i = 0; i < n; ++i) {
+        const double xi = xs[qi];
+        const double2 pi = ph[qi];
+        R[i * 32] = re_kappa(tl, xi, pl, pi, kp);
+        int qj = s;
+        for (int j = 0; j < i; ++j) {
+            T[(trow(i) + j) * 32] = re_kappa(xi, xs[qj], pi, ph[qj], kp);
+            if (++qj == N) qj = 0;
+        }
+        T[(trow(i) + i) * 32] = kp.diag + mu;
+        if (++qi == N) qi = 0;
+    }
+}
+
+// One thread per column; a warp owns 32 consecutive columns (a tile).  Shared
+// memory per warp: each lane's packed lower triangle and right-hand side,
+// lane-interleaved (element e of lane t at [e * 32 + t]) so the 32 threads never
+// collide on a bank, plus the tile's union of nodes.  Consecutive columns share
+// most of their nodes (I(l) and I(l+1) are overlapping ranges of sorted nodes),
+// so the lanes evaluate each node pair of the union once and scatter the value
+// into the triangle of every column that contains both nodes; a tile whose union
+// does not fit falls back to per-column evaluation.
 template <int NMAX, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
@@ -167,41 +198,81 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
              int next_counter, int32_t* __restrict__ counters) {
     extern __shared__ double lsq_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double* base = lsq_smem + (size_t)wid * 32 * thread_tier_doubles<NMAX>() + lane;
-    double* T = base;                                   // T[e * 32]
-    double* R = base + 32 * (NMAX * (NMAX + 1) / 2);    // R[i * 32]
+    double* wbase = (double*)((char*)lsq_smem + (size_t)wid * tile_warp_bytes<NMAX>());
+    double* T = wbase + lane;                                   // T[e * 32]
+    double* R = wbase + lane + 32 * (NMAX * (NMAX + 1) / 2);    // R[i * 32]
+    double* ux = wbase + 32 * thread_tier_doubles<NMAX>();      // union x      [TILE_UMAX]
+    double2* up = (double2*)(ux + TILE_UMAX);                   // union phases [TILE_UMAX]
+    int* crs = (int*)(up + TILE_UMAX);                          // tile-relative start per lane [32]
+    int* cnn = crs + 32;                                        // size per lane [32]
+
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= Ms) return;
-    const int n = col_count[p];
-    if (n == 0) {
-        Jout[p] = 1.0;
-        wide[p] = 0;
-        return;
-    }
+    const bool live = p < Ms;
+    int n = live ? col_count[p] : 0;
     if (n > NMAX) {
         next_list[atomicAdd(&counters[next_counter], 1)] = p;
-        return;
+        n = 0;                           // handled by a later tier
     }
-    const int s = col_start[p], off = col_off[p];
+    const int s = live ? col_start[p] : 0;
+    const int S = __shfl_sync(0xffffffffu, s, 0);
+    int rs = s - S;
+    if (rs < 0) rs += N;
+    const bool mine = live && n > 0;
+    // the union of the tile's ranges, in tile-relative positions [0, U)
+    int U = mine ? rs + n : 0;
+    bool fits = !mine || (rs + n <= TILE_UMAX);
+    for (int o = 16; o; o >>= 1) U = max(U, __shfl_xor_sync(0xffffffffu, U, o));
+    const bool tile_ok = __all_sync(0xffffffffu, fits) && U <= N;
+    int D = n;
+    for (int o = 16; o; o >>= 1) D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
+
     const double tl = col_t(p, Ms);
     const double2 pl = phase_of(kp.M, tl);
+    if (tile_ok && U > 0) {
+        crs[lane] = mine ? rs : 0;
+        cnn[lane] = mine ? n : 0;
+        for (int r = lane; r < U; r += 32) {
+            int q = S + r;
+            if (q >= N) q -= N;
+            ux[r] = xs[q];
+            up[r] = ph[q];
+        }
+        __syncwarp();
+        // every pair (a, a + d), 1 <= d < D, of the union, evaluated once
+        const int per = D - 1;
+        const int pairs = U * per;
+        for (int e = lane; e < pairs; e += 32) {
+            const int a = e / per, b = a + 1 + e % per;
+            if (b >= U) continue;
+            bool needed = false;
+            for (int c = 0; c < 32; ++c) needed |= (crs[c] <= a) & (b < crs[c] + cnn[c]);
+            if (!needed) continue;
+            const double v = re_kappa(ux[b], ux[a], up[b], up[a], kp);
+            for (int c = 0; c < 32; ++c) {
+                const int r0 = crs[c];
+                if (r0 <= a && b < r0 + cnn[c])
+                    wbase[(trow(b - r0) + (a - r0)) * 32 + c] = v;
+            }
+        }
+        if (mine) {
+            for (int i = 0; i < n; ++i) {
+                R[i * 32] = re_kappa(tl, ux[rs + i], pl, up[rs + i], kp);
+                T[(trow(i) + i) * 32] = kp.diag + mu0;
+            }
+        }
+        __syncwarp();
+    } else if (mine) {
+        fill_column<NMAX>(T, R, xs, ph, s, n, N, tl, pl, mu0, kp);
+    }
+    if (!live || n == 0) {
+        if (live && col_count[p] == 0) { Jout[p] = 1.0; wide[p] = 0; }
+        return;
+    }
+    const int off = col_off[p];
     double mu = mu0;
     bool ok = false;
     for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-        // Re G_l + mu I (lower triangle) and Re r_l
-        int qi = s;
-        for (int i = 0; i < n; ++i) {
-            const double xi = xs[qi];
-            const double2 pi = ph[qi];
-            R[i * 32] = re_kappa(tl, xi, pl, pi, kp);
-            int qj = s;
-            for (int j = 0; j < i; ++j) {
-                T[(trow(i) + j) * 32] = re_kappa(xi, xs[qj], pi, ph[qj], kp);
-                if (++qj == N) qj = 0;
-            }
-            T[(trow(i) + i) * 32] = kp.diag + mu;
-            if (++qi == N) qi = 0;
-        }
+        if (attempt > 0) fill_column<NMAX>(T, R, xs, ph, s, n, N, tl, pl, mu, kp);
         // right-looking Cholesky; the diagonal keeps the reciprocal pivot 1/L_kk
         ok = true;
         for (int k = 0; k < n; ++k) {
@@ -543,7 +614,7 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     auto k1 = k_lsq_thread<T1, W1>;
     auto k2 = k_lsq_warp<LSQ_WARP_NMAX, W2>;
     auto k3 = k_lsq_warp<LSQ_WARP2_NMAX, W3>;
-    const size_t s1 = (size_t)W1 * 32 * thread_tier_doubles<T1>() * sizeof(double);
+    const size_t s1 = (size_t)W1 * tile_warp_bytes<T1>();
     const size_t s2 = warp_smem_bytes<LSQ_WARP_NMAX, W2>(), s3 = warp_smem_bytes<LSQ_WARP2_NMAX, W3>();
     const size_t s4 = (size_t)(CN * (CN + 1) / 2 + 4 * CN) * sizeof(double);
     if ((e = set_smem(k1, s1)) != cudaSuccess) return e;

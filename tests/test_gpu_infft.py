@@ -177,7 +177,10 @@ def test_adjoint_identity_gpu(name):
     x, f, M, sigma, m, kernel, B, ghat, (plan, fhat, back, data, info) = solved(name)
     lhs = np.vdot(c64(ghat), fhat)
     rhs = np.vdot(back, c64(f))
-    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    # fp32 rounding of an inner product is bounded by the norms of its factors, not by
+    # the (possibly much smaller) result; on i.i.d. uniform nodes the weights cancel
+    scale = np.linalg.norm(ghat) * np.linalg.norm(fhat) + np.linalg.norm(back) * np.linalg.norm(f)
+    assert abs(lhs - rhs) <= 1e-5 * scale
 
 
 @pytest.mark.parametrize("name", ["cfg1", "jit_small", "jit_fourstep", "cheb", "sym"])
