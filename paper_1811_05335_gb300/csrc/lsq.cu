@@ -155,22 +155,20 @@ INFFT_D double col_t(int p, int Ms) { return (double)(p - Ms / 2) / (double)Ms; 
 
 constexpr int TILE_UMAX = 128;   // largest union of nodes a warp tile shares in shared memory
 
-template <int NMAX> constexpr int thread_tier_doubles() { return NMAX * (NMAX + 1) / 2 + NMAX; }
+template <int NMAX> constexpr int tri_doubles() { return NMAX * (NMAX + 1) / 2; }
 template <int NMAX> constexpr size_t tile_warp_bytes() {
-    return (size_t)32 * thread_tier_doubles<NMAX>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
+    return (size_t)32 * tri_doubles<NMAX>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
            64 * sizeof(int);
 }
 
-// Writes Re G_l + mu I (lower triangle) and Re r_l of one column into its private
-// triangle T / vector R (stride 32), evaluating every entry itself.
-template <int NMAX>
-INFFT_D void fill_column(double* T, double* R, const double* __restrict__ xs, const double2* __restrict__ ph,
-                         int s, int n, int N, double tl, double2 pl, double mu, const KernelParams& kp) {
+// Writes Re G_l + mu I (lower triangle) of one column into its private triangle T
+// (stride 32), evaluating every entry itself.
+INFFT_D void fill_gram(double* T, const double* __restrict__ xs, const double2* __restrict__ ph, int s, int n,
+                       int N, double mu, const KernelParams& kp) {
     int qi = s;
     for (int i = 0; i < n; ++i) {
         const double xi = xs[qi];
         const double2 pi = ph[qi];
-        R[i * 32] = re_kappa(tl, xi, pl, pi, kp);
         int qj = s;
         for (int j = 0; j < i; ++j) {
             T[(trow(i) + j) * 32] = re_kappa(xi, xs[qj], pi, ph[qj], kp);
@@ -181,14 +179,72 @@ INFFT_D void fill_column(double* T, double* R, const double* __restrict__ xs, co
     }
 }
 
+// Up-looking Cholesky of the packed triangle T (stride 32) fused with the forward
+// solve, then the backward solve, for n <= NMAX.  Fully unrolled: the current row
+// of L, the reciprocal pivots and the solution vectors stay in registers and the
+// shared-memory traffic is loads of earlier rows (rows of L overwrite rows of T).
+// Returns false on a non-positive pivot.
+template <int NMAX>
+INFFT_D bool chol_solve(double* T, int n, const double (&r)[NMAX], double (&b)[NMAX], double& ysq) {
+    double invd[NMAX], y[NMAX];
+    bool ok = true;
+    ysq = 0.0;
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        if (i < n) {
+            double li[NMAX];
+#pragma unroll
+            for (int j = 0; j < i; ++j) {
+                double a0 = T[(trow(i) + j) * 32], a1 = 0.0;
+#pragma unroll
+                for (int k = 0; k < j; k += 2) {
+                    a0 = fma(-li[k], T[(trow(j) + k) * 32], a0);
+                    if (k + 1 < j) a1 = fma(-li[k + 1], T[(trow(j) + k + 1) * 32], a1);
+                }
+                li[j] = (a0 + a1) * invd[j];
+                T[(trow(i) + j) * 32] = li[j];
+            }
+            double d0 = T[(trow(i) + i) * 32], d1 = 0.0, y0 = r[i], y1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < i; k += 2) {
+                d0 = fma(-li[k], li[k], d0);
+                y0 = fma(-li[k], y[k], y0);
+                if (k + 1 < i) {
+                    d1 = fma(-li[k + 1], li[k + 1], d1);
+                    y1 = fma(-li[k + 1], y[k + 1], y1);
+                }
+            }
+            const double d = d0 + d1;
+            ok = ok && (d > 0.0) && isfinite(d);
+            invd[i] = rsqrt(d);
+            T[(trow(i) + i) * 32] = invd[i];
+            y[i] = (y0 + y1) * invd[i];
+            ysq = fma(y[i], y[i], ysq);
+        }
+    }
+#pragma unroll
+    for (int k = NMAX - 1; k >= 0; --k) {
+        if (k < n) {
+            double a0 = y[k], a1 = 0.0;
+#pragma unroll
+            for (int i = k + 1; i < NMAX; i += 2) {
+                if (i < n) a0 = fma(-T[(trow(i) + k) * 32], b[i], a0);
+                if (i + 1 < NMAX && i + 1 < n) a1 = fma(-T[(trow(i + 1) + k) * 32], b[i + 1], a1);
+            }
+            b[k] = (a0 + a1) * invd[k];
+        }
+    }
+    return ok;
+}
+
 // One thread per column; a warp owns 32 consecutive columns (a tile).  Shared
-// memory per warp: each lane's packed lower triangle and right-hand side,
-// lane-interleaved (element e of lane t at [e * 32 + t]) so the 32 threads never
-// collide on a bank, plus the tile's union of nodes.  Consecutive columns share
-// most of their nodes (I(l) and I(l+1) are overlapping ranges of sorted nodes),
-// so the lanes evaluate each node pair of the union once and scatter the value
-// into the triangle of every column that contains both nodes; a tile whose union
-// does not fit falls back to per-column evaluation.
+// memory per warp: each lane's packed lower triangle, lane-interleaved (element e
+// of lane t at [e * 32 + t]) so the 32 threads never collide on a bank, plus the
+// tile's union of nodes.  Consecutive columns share most of their nodes (I(l) and
+// I(l+1) are overlapping ranges of sorted nodes), so the lanes evaluate each node
+// pair of the union once and scatter the value into the triangle of every column
+// that contains both nodes; a tile whose union does not fit falls back to
+// per-column evaluation.
 template <int NMAX, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
@@ -200,8 +256,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* wbase = (double*)((char*)lsq_smem + (size_t)wid * tile_warp_bytes<NMAX>());
     double* T = wbase + lane;                                   // T[e * 32]
-    double* R = wbase + lane + 32 * (NMAX * (NMAX + 1) / 2);    // R[i * 32]
-    double* ux = wbase + 32 * thread_tier_doubles<NMAX>();      // union x      [TILE_UMAX]
+    double* ux = wbase + 32 * tri_doubles<NMAX>();              // union x      [TILE_UMAX]
     double2* up = (double2*)(ux + TILE_UMAX);                   // union phases [TILE_UMAX]
     int* crs = (int*)(up + TILE_UMAX);                          // tile-relative start per lane [32]
     int* cnn = crs + 32;                                        // size per lane [32]
@@ -220,7 +275,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     const bool mine = live && n > 0;
     // the union of the tile's ranges, in tile-relative positions [0, U)
     int U = mine ? rs + n : 0;
-    bool fits = !mine || (rs + n <= TILE_UMAX);
+    const bool fits = !mine || (rs + n <= TILE_UMAX);
     for (int o = 16; o; o >>= 1) U = max(U, __shfl_xor_sync(0xffffffffu, U, o));
     const bool tile_ok = __all_sync(0xffffffffu, fits) && U <= N;
     int D = n;
@@ -228,66 +283,66 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
 
     const double tl = col_t(p, Ms);
     const double2 pl = phase_of(kp.M, tl);
+    double r[NMAX];
     if (tile_ok && U > 0) {
         crs[lane] = mine ? rs : 0;
         cnn[lane] = mine ? n : 0;
-        for (int r = lane; r < U; r += 32) {
-            int q = S + r;
-            if (q >= N) q -= N;
-            ux[r] = xs[q];
-            up[r] = ph[q];
+        for (int q = lane; q < U; q += 32) {
+            int g = S + q;
+            if (g >= N) g -= N;
+            ux[q] = xs[g];
+            up[q] = ph[g];
         }
         __syncwarp();
         // every pair (a, a + d), 1 <= d < D, of the union, evaluated once
         const int per = D - 1;
         const int pairs = U * per;
         for (int e = lane; e < pairs; e += 32) {
-            const int a = e / per, b = a + 1 + e % per;
-            if (b >= U) continue;
+            const int a = e / per, bb = a + 1 + e % per;
+            if (bb >= U) continue;
             bool needed = false;
-            for (int c = 0; c < 32; ++c) needed |= (crs[c] <= a) & (b < crs[c] + cnn[c]);
+            for (int c = 0; c < 32; ++c) needed |= (crs[c] <= a) & (bb < crs[c] + cnn[c]);
             if (!needed) continue;
-            const double v = re_kappa(ux[b], ux[a], up[b], up[a], kp);
+            const double v = re_kappa(ux[bb], ux[a], up[bb], up[a], kp);
             for (int c = 0; c < 32; ++c) {
                 const int r0 = crs[c];
-                if (r0 <= a && b < r0 + cnn[c])
-                    wbase[(trow(b - r0) + (a - r0)) * 32 + c] = v;
+                if (r0 <= a && bb < r0 + cnn[c]) wbase[(trow(bb - r0) + (a - r0)) * 32 + c] = v;
             }
         }
         if (mine) {
-            for (int i = 0; i < n; ++i) {
-                R[i * 32] = re_kappa(tl, ux[rs + i], pl, up[rs + i], kp);
-                T[(trow(i) + i) * 32] = kp.diag + mu0;
+#pragma unroll
+            for (int i = 0; i < NMAX; ++i) {
+                if (i < n) {
+                    r[i] = re_kappa(tl, ux[rs + i], pl, up[rs + i], kp);
+                    T[(trow(i) + i) * 32] = kp.diag + mu0;
+                }
             }
         }
         __syncwarp();
     } else if (mine) {
-        fill_column<NMAX>(T, R, xs, ph, s, n, N, tl, pl, mu0, kp);
+        fill_gram(T, xs, ph, s, n, N, mu0, kp);
     }
-    if (!live || n == 0) {
+    if (!mine) {
         if (live && col_count[p] == 0) { Jout[p] = 1.0; wide[p] = 0; }
         return;
     }
-    const int off = col_off[p];
-    double mu = mu0;
-    bool ok = false;
-    for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-        if (attempt > 0) fill_column<NMAX>(T, R, xs, ph, s, n, N, tl, pl, mu, kp);
-        // right-looking Cholesky; the diagonal keeps the reciprocal pivot 1/L_kk
-        ok = true;
-        for (int k = 0; k < n; ++k) {
-            const double akk = T[(trow(k) + k) * 32];
-            if (!(akk > 0.0) || !isfinite(akk)) { ok = false; break; }
-            const double rp = rsqrt(akk);
-            T[(trow(k) + k) * 32] = rp;
-            for (int i = k + 1; i < n; ++i) T[(trow(i) + k) * 32] *= rp;
-            for (int i = k + 1; i < n; ++i) {
-                const double lik = T[(trow(i) + k) * 32];
-                const int ri = trow(i);
-                for (int j = k + 1; j <= i; ++j) T[(ri + j) * 32] = fma(-lik, T[(trow(j) + k) * 32], T[(ri + j) * 32]);
+    if (!(tile_ok && U > 0)) {
+        int q = s;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+            if (i < n) {
+                r[i] = re_kappa(tl, xs[q], pl, ph[q], kp);
+                if (++q == N) q = 0;
             }
         }
-        if (!ok) mu *= 1e3;
+    }
+    const int off = col_off[p];
+    double mu = mu0, b[NMAX], ysq = 0.0;
+    bool ok = chol_solve<NMAX>(T, n, r, b, ysq);
+    for (int attempt = 1; attempt < 3 && !ok; ++attempt) {
+        mu *= 1e3;
+        fill_gram(T, xs, ph, s, n, N, mu, kp);
+        ok = chol_solve<NMAX>(T, n, r, b, ysq);
     }
     if (!ok) {
         for (int i = 0; i < n; ++i) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
@@ -297,27 +352,15 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
         return;
     }
     if (mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
-    // forward: y = L^{-1} r; ||y||^2 = r . b
-    double ysq = 0.0;
-    for (int k = 0; k < n; ++k) {
-        double acc = R[k * 32];
-        const int rk = trow(k);
-        for (int j = 0; j < k; ++j) acc = fma(-T[(rk + j) * 32], R[j * 32], acc);
-        acc *= T[(rk + k) * 32];
-        R[k * 32] = acc;
-        ysq = fma(acc, acc, ysq);
-    }
-    // backward: L^T b = y
     double bsq = 0.0, babs = 0.0;
-    for (int k = n - 1; k >= 0; --k) {
-        double acc = R[k * 32];
-        for (int i = k + 1; i < n; ++i) acc = fma(-T[(trow(i) + k) * 32], R[i * 32], acc);
-        acc *= T[(trow(k) + k) * 32];
-        R[k * 32] = acc;
-        w64[off + k] = acc;
-        w32[off + k] = (float)acc;
-        bsq = fma(acc, acc, bsq);
-        babs += fabs(acc);
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        if (i < n) {
+            w64[off + i] = b[i];
+            w32[off + i] = (float)b[i];
+            bsq = fma(b[i], b[i], bsq);
+            babs += fabs(b[i]);
+        }
     }
     // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
     Jout[p] = 1.0 - ysq - mu * bsq;
