@@ -14,10 +14,11 @@
 //
 // GB300 executes fp64 at 1/64 of the fp32 rate, so the kernels are organised to
 // minimise fp64 warp instructions:
-//   * tier 1: one THREAD per column (|I(l)| <= 18), a private packed triangle in
-//     shared memory (lane-interleaved), no synchronisation at all;
-//   * tier 2/3: one warp per column, lanes own rows (|I(l)| <= 32 / 64);
-//   * tier 4: one CTA per column (|I(l)| <= 224), packed triangle.
+//   * thread tiers: one THREAD per column (tiles whose largest |I(l)| is <= 17,
+//     25 or 33), a private packed triangle in shared memory (lane-interleaved),
+//     Gram entries shared across the 32 columns of a warp tile;
+//   * warp tier: one warp per column, lanes own rows (|I(l)| <= 64);
+//   * CTA tier: one CTA per column (|I(l)| <= 224), packed triangle.
 // Columns too large for a tier go to a device-side work list for the next one.
 //
 // Kernel values avoid library transcendentals on the common path: with per-node
@@ -27,6 +28,8 @@
 // Newton-Raphson reciprocal; pairs closer than a quarter period of sin(pi M t)
 // use the Taylor series of sin(z)/z and cos(z) instead of the phases, so the
 // cancellation in the angle addition never meets a tiny denominator.
+#include <cstring>
+
 #include "plan.h"
 
 namespace {
@@ -36,6 +39,13 @@ struct KernelParams {
     double inv_Ms;   // 1 / M_sigma
     double diag;     // Re kappa(0)
     int sym;         // 0: full, 1: sym
+    // near-pair evaluation of the full kernel (|t| <= 1/32), coefficients folded on the
+    // host: Re kappa(t) = cx(t^2) * sin(pi M t) / t  with cx(t^2) = (u cot u) / (pi M_sigma),
+    // u = pi t; and, for |M t| <= 1/4, Re kappa(t) = cx(t^2) * cs(t^2) with
+    // cs(t^2) = pi M sin(z)/z, z = pi M t.
+    double cx[7];
+    double cs[9];
+    unsigned long long near_bits;   // bit pattern of 0.25 / M (|t| below it: sin(z)/z series)
 };
 
 constexpr double PI = 3.141592653589793238462643383279502884;
@@ -153,12 +163,41 @@ INFFT_D double col_t(int p, int Ms) { return (double)(p - Ms / 2) / (double)Ms; 
 
 // ---------------------------------------------------------------- tier 1: thread per column
 
+// Re kappa(t) of the full kernel for a pair known to be near (|t| <= 1/32, t taken
+// without a seam): u cot u and sin(z)/z by their Taylor series (coefficients folded
+// on the host), sin(pi M t) by angle addition of the phases, branches decided on
+// the bit pattern of |t| so that no fp64 comparison is issued.
+INFFT_D double kappa_near(double t, double2 pa, double2 pb, const KernelParams& kp) {
+    const unsigned long long tb = (unsigned long long)__double_as_longlong(t) & 0x7fffffffffffffffULL;
+    if (tb == 0ULL) return kp.diag;
+    const double t2 = t * t;
+    double xc = fma(t2, kp.cx[6], kp.cx[5]);
+    xc = fma(t2, xc, kp.cx[4]);
+    xc = fma(t2, xc, kp.cx[3]);
+    xc = fma(t2, xc, kp.cx[2]);
+    xc = fma(t2, xc, kp.cx[1]);
+    xc = fma(t2, xc, kp.cx[0]);
+    if (tb <= kp.near_bits) {
+        double sz = fma(t2, kp.cs[8], kp.cs[7]);
+        sz = fma(t2, sz, kp.cs[6]);
+        sz = fma(t2, sz, kp.cs[5]);
+        sz = fma(t2, sz, kp.cs[4]);
+        sz = fma(t2, sz, kp.cs[3]);
+        sz = fma(t2, sz, kp.cs[2]);
+        sz = fma(t2, sz, kp.cs[1]);
+        sz = fma(t2, sz, kp.cs[0]);
+        return xc * sz;
+    }
+    const double sm = fma(pa.x, pb.y, -pa.y * pb.x);    // sin(pi M (a - b))
+    return xc * sm * recip(t);
+}
+
 constexpr int TILE_UMAX = 128;   // largest union of nodes a warp tile shares in shared memory
 
 template <int NMAX> constexpr int tri_doubles() { return NMAX * (NMAX + 1) / 2; }
 template <int NMAX> constexpr size_t tile_warp_bytes() {
     return (size_t)32 * tri_doubles<NMAX>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
-           64 * sizeof(int);
+           (64 + 2 * TILE_UMAX) * sizeof(int);
 }
 
 // Writes Re G_l + mu I (lower triangle) of one column into its private triangle T
@@ -181,12 +220,12 @@ INFFT_D void fill_gram(double* T, const double* __restrict__ xs, const double2* 
 
 // Up-looking Cholesky of the packed triangle T (stride 32) fused with the forward
 // solve, then the backward solve, for n <= NMAX.  Fully unrolled: the current row
-// of L, the reciprocal pivots and the solution vectors stay in registers and the
-// shared-memory traffic is loads of earlier rows (rows of L overwrite rows of T).
-// Returns false on a non-positive pivot.
+// of L, the reciprocal pivots and the right-hand side / solution (v: r, then y,
+// then b, in place) stay in registers; the shared-memory traffic is loads of
+// earlier rows (rows of L overwrite rows of T).  Returns false on a non-positive pivot.
 template <int NMAX>
-INFFT_D bool chol_solve(double* T, int n, const double (&r)[NMAX], double (&b)[NMAX], double& ysq) {
-    double invd[NMAX], y[NMAX];
+INFFT_D bool chol_solve(double* T, int n, double (&v)[NMAX], double& ysq) {
+    double invd[NMAX];
     bool ok = true;
     ysq = 0.0;
 #pragma unroll
@@ -201,46 +240,48 @@ INFFT_D bool chol_solve(double* T, int n, const double (&r)[NMAX], double (&b)[N
                     a0 = fma(-li[k], T[(trow(j) + k) * 32], a0);
                     if (k + 1 < j) a1 = fma(-li[k + 1], T[(trow(j) + k + 1) * 32], a1);
                 }
-                li[j] = (a0 + a1) * invd[j];
+                li[j] = (j > 1 ? a0 + a1 : a0) * invd[j];
                 T[(trow(i) + j) * 32] = li[j];
             }
-            double d0 = T[(trow(i) + i) * 32], d1 = 0.0, y0 = r[i], y1 = 0.0;
+            double d0 = T[(trow(i) + i) * 32], d1 = 0.0, y0 = v[i], y1 = 0.0;
 #pragma unroll
             for (int k = 0; k < i; k += 2) {
                 d0 = fma(-li[k], li[k], d0);
-                y0 = fma(-li[k], y[k], y0);
+                y0 = fma(-li[k], v[k], y0);
                 if (k + 1 < i) {
                     d1 = fma(-li[k + 1], li[k + 1], d1);
-                    y1 = fma(-li[k + 1], y[k + 1], y1);
+                    y1 = fma(-li[k + 1], v[k + 1], y1);
                 }
             }
-            const double d = d0 + d1;
+            const double d = i > 1 ? d0 + d1 : d0;
             ok = ok && (d > 0.0) && isfinite(d);
             invd[i] = rsqrt(d);
             T[(trow(i) + i) * 32] = invd[i];
-            y[i] = (y0 + y1) * invd[i];
-            ysq = fma(y[i], y[i], ysq);
+            v[i] = (i > 1 ? y0 + y1 : y0) * invd[i];
+            ysq = fma(v[i], v[i], ysq);
         }
     }
 #pragma unroll
     for (int k = NMAX - 1; k >= 0; --k) {
         if (k < n) {
-            double a0 = y[k], a1 = 0.0;
+            double a0 = v[k], a1 = 0.0;
 #pragma unroll
             for (int i = k + 1; i < NMAX; i += 2) {
-                if (i < n) a0 = fma(-T[(trow(i) + k) * 32], b[i], a0);
-                if (i + 1 < NMAX && i + 1 < n) a1 = fma(-T[(trow(i + 1) + k) * 32], b[i + 1], a1);
+                if (i < n) a0 = fma(-T[(trow(i) + k) * 32], v[i], a0);
+                if (i + 1 < NMAX && i + 1 < n) a1 = fma(-T[(trow(i + 1) + k) * 32], v[i + 1], a1);
             }
-            b[k] = (a0 + a1) * invd[k];
+            v[k] = (a0 + a1) * invd[k];
         }
     }
     return ok;
 }
 
-// One thread per column; a warp owns 32 consecutive columns (a tile).  Shared
-// memory per warp: each lane's packed lower triangle, lane-interleaved (element e
-// of lane t at [e * 32 + t]) so the 32 threads never collide on a bank, plus the
-// tile's union of nodes.  Consecutive columns share most of their nodes (I(l) and
+// One thread per column; a warp owns a tile of 32 consecutive columns.  The tile
+// is handled by the first tier whose NMAX covers its largest column (lo < max n <=
+// NMAX); the last tier pushes larger tiles' columns to `next_list`.  Shared memory
+// per warp: each lane's packed lower triangle, lane-interleaved (element e of lane
+// t at [e * 32 + t]) so the 32 threads never collide on a bank, plus the tile's
+// union of nodes.  Consecutive columns share most of their nodes (I(l) and
 // I(l+1) are overlapping ranges of sorted nodes), so the lanes evaluate each node
 // pair of the union once and scatter the value into the triangle of every column
 // that contains both nodes; a tile whose union does not fit falls back to
@@ -250,8 +291,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
              const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
              KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-             double* __restrict__ Jout, uint8_t* __restrict__ wide, int32_t* __restrict__ next_list,
-             int next_counter, int32_t* __restrict__ counters) {
+             double* __restrict__ Jout, uint8_t* __restrict__ wide, int lo, int push,
+             int32_t* __restrict__ next_list, int next_counter, int32_t* __restrict__ counters) {
     extern __shared__ double lsq_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* wbase = (double*)((char*)lsq_smem + (size_t)wid * tile_warp_bytes<NMAX>());
@@ -260,33 +301,36 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     double2* up = (double2*)(ux + TILE_UMAX);                   // union phases [TILE_UMAX]
     int* crs = (int*)(up + TILE_UMAX);                          // tile-relative start per lane [32]
     int* cnn = crs + 32;                                        // size per lane [32]
+    int* cfst = cnn + 32;                                       // per union node: first candidate column
+    int* clst = cfst + TILE_UMAX;                               // per union node: last candidate column
 
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = p < Ms;
-    int n = live ? col_count[p] : 0;
-    if (n > NMAX) {
-        next_list[atomicAdd(&counters[next_counter], 1)] = p;
-        n = 0;                           // handled by a later tier
+    const int n = live ? col_count[p] : 0;
+    int D = n;
+    for (int o = 16; o; o >>= 1) D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
+    if (D <= lo) return;                                        // an earlier tier took this tile
+    if (D > NMAX) {
+        if (push && n > 0) next_list[atomicAdd(&counters[next_counter], 1)] = p;
+        return;
     }
     const int s = live ? col_start[p] : 0;
     const int S = __shfl_sync(0xffffffffu, s, 0);
     int rs = s - S;
     if (rs < 0) rs += N;
-    const bool mine = live && n > 0;
+    const bool mine = n > 0;
     // the union of the tile's ranges, in tile-relative positions [0, U)
     int U = mine ? rs + n : 0;
     const bool fits = !mine || (rs + n <= TILE_UMAX);
     for (int o = 16; o; o >>= 1) U = max(U, __shfl_xor_sync(0xffffffffu, U, o));
-    const bool tile_ok = __all_sync(0xffffffffu, fits) && U <= N;
-    int D = n;
-    for (int o = 16; o; o >>= 1) D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
+    const bool tile_ok = __all_sync(0xffffffffu, fits) && U <= N && U > 0;
 
     const double tl = col_t(p, Ms);
     const double2 pl = phase_of(kp.M, tl);
-    double r[NMAX];
-    if (tile_ok && U > 0) {
+    double v[NMAX];
+    if (tile_ok) {
         crs[lane] = mine ? rs : 0;
-        cnn[lane] = mine ? n : 0;
+        cnn[lane] = n;
         for (int q = lane; q < U; q += 32) {
             int g = S + q;
             if (g >= N) g -= N;
@@ -294,26 +338,51 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
             up[q] = ph[g];
         }
         __syncwarp();
-        // every pair (a, a + d), 1 <= d < D, of the union, evaluated once
-        const int per = D - 1;
-        const int pairs = U * per;
-        for (int e = lane; e < pairs; e += 32) {
-            const int a = e / per, bb = a + 1 + e % per;
-            if (bb >= U) continue;
-            bool needed = false;
-            for (int c = 0; c < 32; ++c) needed |= (crs[c] <= a) & (bb < crs[c] + cnn[c]);
-            if (!needed) continue;
-            const double v = re_kappa(ux[bb], ux[a], up[bb], up[a], kp);
+        for (int q = lane; q < U; q += 32) {
+            int cf = 32, cl = -1;
             for (int c = 0; c < 32; ++c) {
-                const int r0 = crs[c];
-                if (r0 <= a && bb < r0 + cnn[c]) wbase[(trow(bb - r0) + (a - r0)) * 32 + c] = v;
+                if (cnn[c] > 0 && crs[c] + cnn[c] > q && cf == 32) cf = c;
+                if (cnn[c] > 0 && crs[c] <= q) cl = c;
+            }
+            cfst[q] = cf;
+            clst[q] = cl;
+        }
+        // the near path needs the union and the columns' grid points to lie within
+        // 1/64 of each other without crossing the seam
+        const double x0 = ux[0], x1 = ux[U - 1];
+        const bool near = !kp.sym && x1 >= x0 && x1 - x0 <= 1.0 / 64.0 &&
+                          __all_sync(0xffffffffu, !mine || (tl >= x0 - 1.0 / 64.0 && tl <= x1 + 1.0 / 64.0));
+        __syncwarp();
+        // every pair (a, b), a < b < a + D, of the union, evaluated once
+        const int per = D - 1;
+        if (per > 0) {
+            const int pairs = U * per;
+            const int qa = 32 / per, ra = 32 % per;
+            int a = lane / per, off = lane % per;
+            for (int e = lane; e < pairs; e += 32) {
+                const int b = a + 1 + off;
+                if (b < U) {
+                    const int c0 = cfst[b], c1 = clst[a];
+                    if (c0 <= c1) {
+                        const double val = near ? kappa_near(ux[b] - ux[a], up[b], up[a], kp)
+                                                : re_kappa(ux[b], ux[a], up[b], up[a], kp);
+                        for (int c = c0; c <= c1; ++c) {
+                            const int r0 = crs[c];
+                            if (r0 <= a && b < r0 + cnn[c]) wbase[(trow(b - r0) + (a - r0)) * 32 + c] = val;
+                        }
+                    }
+                }
+                a += qa;
+                off += ra;
+                if (off >= per) { off -= per; ++a; }
             }
         }
         if (mine) {
 #pragma unroll
             for (int i = 0; i < NMAX; ++i) {
                 if (i < n) {
-                    r[i] = re_kappa(tl, ux[rs + i], pl, up[rs + i], kp);
+                    v[i] = near ? kappa_near(tl - ux[rs + i], pl, up[rs + i], kp)
+                                : re_kappa(tl, ux[rs + i], pl, up[rs + i], kp);
                     T[(trow(i) + i) * 32] = kp.diag + mu0;
                 }
             }
@@ -321,28 +390,34 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
         __syncwarp();
     } else if (mine) {
         fill_gram(T, xs, ph, s, n, N, mu0, kp);
-    }
-    if (!mine) {
-        if (live && col_count[p] == 0) { Jout[p] = 1.0; wide[p] = 0; }
-        return;
-    }
-    if (!(tile_ok && U > 0)) {
         int q = s;
 #pragma unroll
         for (int i = 0; i < NMAX; ++i) {
             if (i < n) {
-                r[i] = re_kappa(tl, xs[q], pl, ph[q], kp);
+                v[i] = re_kappa(tl, xs[q], pl, ph[q], kp);
                 if (++q == N) q = 0;
             }
         }
     }
+    if (!mine) {
+        if (live) { Jout[p] = 1.0; wide[p] = 0; }
+        return;
+    }
     const int off = col_off[p];
-    double mu = mu0, b[NMAX], ysq = 0.0;
-    bool ok = chol_solve<NMAX>(T, n, r, b, ysq);
+    double mu = mu0, ysq = 0.0;
+    bool ok = chol_solve<NMAX>(T, n, v, ysq);
     for (int attempt = 1; attempt < 3 && !ok; ++attempt) {
         mu *= 1e3;
         fill_gram(T, xs, ph, s, n, N, mu, kp);
-        ok = chol_solve<NMAX>(T, n, r, b, ysq);
+        int q = s;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+            if (i < n) {
+                v[i] = re_kappa(tl, xs[q], pl, ph[q], kp);
+                if (++q == N) q = 0;
+            }
+        }
+        ok = chol_solve<NMAX>(T, n, v, ysq);
     }
     if (!ok) {
         for (int i = 0; i < n; ++i) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
@@ -356,10 +431,10 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
         if (i < n) {
-            w64[off + i] = b[i];
-            w32[off + i] = (float)b[i];
-            bsq = fma(b[i], b[i], bsq);
-            babs += fabs(b[i]);
+            w64[off + i] = v[i];
+            w32[off + i] = (float)v[i];
+            bsq = fma(v[i], v[i], bsq);
+            babs += fabs(v[i]);
         }
     }
     // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
@@ -638,6 +713,27 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     kp.inv_Ms = 1.0 / (double)Ms;
     kp.sym = (p->kernel == INFFT_KERNEL_SYM);
     kp.diag = (kp.sym ? (double)(p->M - 1) : (double)p->M) / (double)Ms;
+    {
+        // u cot u = sum_k c_k u^{2k} (Bernoulli numbers); folded: cx_k = c_k pi^{2k} / (pi M_sigma)
+        const double c[7] = {1.0, -1.0 / 3.0, -1.0 / 45.0, -2.0 / 945.0, -1.0 / 4725.0, -2.0 / 93555.0,
+                             -1382.0 / 638512875.0};
+        const double pi = 3.141592653589793238462643383279502884;
+        double pw = 1.0;
+        for (int k = 0; k < 7; ++k) {
+            kp.cx[k] = c[k] * pw / (pi * (double)Ms);
+            pw *= pi * pi;
+        }
+        // pi M sin(z)/z = pi M sum_k (-1)^k z^{2k} / (2k+1)!, z = pi M t
+        const double a = pi * (double)p->M;
+        double term = a, fact = 1.0;
+        for (int k = 0; k < 9; ++k) {
+            kp.cs[k] = term / fact;
+            term *= -a * a;
+            fact *= (double)(2 * k + 2) * (double)(2 * k + 3);
+        }
+        const double nb = 0.25 / (double)p->M;
+        memcpy(&kp.near_bits, &nb, sizeof nb);
+    }
     const double mu = p->tau * kp.diag;
 
     // clear the precompute counters (fallback, unsupported, work lists), keep the pattern's
@@ -653,42 +749,50 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    constexpr int T1 = LSQ_THREAD_NMAX, W1 = 4, W2 = 4, W3 = 4;
-    auto k1 = k_lsq_thread<T1, W1>;
-    auto k2 = k_lsq_warp<LSQ_WARP_NMAX, W2>;
-    auto k3 = k_lsq_warp<LSQ_WARP2_NMAX, W3>;
-    const size_t s1 = (size_t)W1 * tile_warp_bytes<T1>();
-    const size_t s2 = warp_smem_bytes<LSQ_WARP_NMAX, W2>(), s3 = warp_smem_bytes<LSQ_WARP2_NMAX, W3>();
-    const size_t s4 = (size_t)(CN * (CN + 1) / 2 + 4 * CN) * sizeof(double);
-    if ((e = set_smem(k1, s1)) != cudaSuccess) return e;
-    if ((e = set_smem(k2, s2)) != cudaSuccess) return e;
-    if ((e = set_smem(k3, s3)) != cudaSuccess) return e;
-    if ((e = set_smem(k_lsq_cta, s4)) != cudaSuccess) return e;
+    // thread tiers: a tile of 32 consecutive columns goes to the first tier whose
+    // NMAX covers its largest column; tiles above the last go to the warp tier
+    constexpr int A1 = LSQ_THREAD_NMAX1, A2 = LSQ_THREAD_NMAX2, A3 = LSQ_THREAD_NMAX3;
+    constexpr int W1 = 5, W2 = 2, W3 = 1, W4 = 4;
+    auto t1 = k_lsq_thread<A1, W1>;
+    auto t2 = k_lsq_thread<A2, W2>;
+    auto t3 = k_lsq_thread<A3, W3>;
+    auto k4 = k_lsq_warp<LSQ_WARP2_NMAX, W4>;
+    const size_t s1 = W1 * tile_warp_bytes<A1>(), s2 = W2 * tile_warp_bytes<A2>(), s3 = W3 * tile_warp_bytes<A3>();
+    const size_t s4 = warp_smem_bytes<LSQ_WARP2_NMAX, W4>();
+    const size_t s5 = (size_t)(CN * (CN + 1) / 2 + 4 * CN) * sizeof(double);
+    if ((e = set_smem(t1, s1)) != cudaSuccess) return e;
+    if ((e = set_smem(t2, s2)) != cudaSuccess) return e;
+    if ((e = set_smem(t3, s3)) != cudaSuccess) return e;
+    if ((e = set_smem(k4, s4)) != cudaSuccess) return e;
+    if ((e = set_smem(k_lsq_cta, s5)) != cudaSuccess) return e;
+    const int tiles = (Ms + 31) / 32;
 
-    // tier 1: every column, thread per column, |I(l)| <= 18; larger ones to list A
-    launch_begin(p, "lsq_thread", s);
-    k1<<<(Ms + W1 * 32 - 1) / (W1 * 32), W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off,
-                                                           N, Ms, kp, mu, p->w64, p->w32, p->J, p->wide,
-                                                           p->list_a, CNT_LIST_A, p->counters);
+    launch_begin(p, "lsq_thread17", s);
+    t1<<<(tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+                                                  kp, mu, p->w64, p->w32, p->J, p->wide, -1, 0, p->list_a,
+                                                  CNT_LIST_A, p->counters);
+    launch_end(p, s);
+    launch_begin(p, "lsq_thread25", s);
+    t2<<<(tiles + W2 - 1) / W2, W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+                                                  kp, mu, p->w64, p->w32, p->J, p->wide, A1, 0, p->list_a,
+                                                  CNT_LIST_A, p->counters);
+    launch_end(p, s);
+    launch_begin(p, "lsq_thread33", s);
+    t3<<<(tiles + W3 - 1) / W3, W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+                                                  kp, mu, p->w64, p->w32, p->J, p->wide, A2, 1, p->list_a,
+                                                  CNT_LIST_A, p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // tier 2: list A, warp per column, |I(l)| <= 32; larger ones to list B
-    launch_begin(p, "lsq_warp32", s);
-    k2<<<2 * sms, W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                    p->w64, p->w32, p->J, p->wide, p->list_a, CNT_LIST_A, p->list_b, CNT_LIST_B,
-                                    p->counters);
-    launch_end(p, s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // tier 3: list B, warp per column, |I(l)| <= 64; larger ones to the big list
+    // warp tier: columns of tiles whose largest column exceeds the thread tiers, |I(l)| <= 64
     launch_begin(p, "lsq_warp64", s);
-    k3<<<2 * sms, W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                    p->w64, p->w32, p->J, p->wide, p->list_b, CNT_LIST_B, p->big_list,
+    k4<<<2 * sms, W4 * 32, s4, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+                                    p->w64, p->w32, p->J, p->wide, p->list_a, CNT_LIST_A, p->big_list,
                                     CNT_BIG_LIST, p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // tier 4: the big list, one CTA per column, |I(l)| <= 224
+    // CTA tier: the big list, one CTA per column, |I(l)| <= 224
     launch_begin(p, "lsq_cta", s);
-    k_lsq_cta<<<sms, CTA_THREADS, s4, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+    k_lsq_cta<<<sms, CTA_THREADS, s5, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
                                            p->w64, p->w32, p->J, p->wide, p->big_list, p->counters);
     launch_end(p, s);
     return cudaGetLastError();

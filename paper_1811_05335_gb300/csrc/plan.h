@@ -15,15 +15,16 @@ enum {
     CNT_UNSUPPORTED = 2,
     CNT_MAX_COLUMN = 3,
     CNT_EMPTY = 4,
-    CNT_LIST_A = 5,        // columns queued for the 32-row warp solver
-    CNT_LIST_B = 6,        // columns queued for the 64-row warp solver
+    CNT_LIST_A = 5,        // columns queued for the warp solver
+    CNT_LIST_B = 6,        // (unused)
     CNT_BIG_LIST = 7,      // columns queued for the CTA solver
     CNT_N = 8
 };
 
 // largest column handled by the thread, warp and CTA solver tiers
-constexpr int LSQ_THREAD_NMAX = 18;
-constexpr int LSQ_WARP_NMAX = 32;
+constexpr int LSQ_THREAD_NMAX1 = 17;
+constexpr int LSQ_THREAD_NMAX2 = 25;
+constexpr int LSQ_THREAD_NMAX3 = 33;
 constexpr int LSQ_WARP2_NMAX = 64;
 constexpr int LSQ_CTA_NMAX = 224;
 
