@@ -311,7 +311,14 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     for (int o = 16; o; o >>= 1) D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
     if (D <= lo) return;                                        // an earlier tier took this tile
     if (D > NMAX) {
-        if (push && n > 0) next_list[atomicAdd(&counters[next_counter], 1)] = p;
+        if (push) {
+            if (n > 0) {
+                next_list[atomicAdd(&counters[next_counter], 1)] = p;
+            } else if (live) {             // empty columns of a pushed tile end here
+                Jout[p] = 1.0;
+                wide[p] = 0;
+            }
+        }
         return;
     }
     const int s = live ? col_start[p] : 0;
