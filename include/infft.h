@@ -166,6 +166,29 @@ infft_status infft_profile(infft_plan_t plan, int enable);
 infft_status infft_profile_read(infft_plan_t plan, int cap, const char** names,
                                 int64_t* launches, double* milliseconds, int* n);
 
+/* ---- allocation-free entry point ------------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory when they call: processes whose device memory belongs
+ * to their own pool allocator, or code that must not call cudaMalloc while
+ * another component is recording work on the device.
+ *
+ * Computes the last two steps of infft_apply on a caller-provided grid:
+ *   fhat_k = conj(d_k) sum_{l} grid_l exp(-2 pi i k l / M_sigma),  k = -M/2 .. M/2-1,
+ * with d_k = 1/M_sigma (kernel FULL) or the same with d_{-M/2} = 0 (kernel SYM).
+ *   grid : M_sigma complex64 on the device, l = -M_sigma/2 .. M_sigma/2-1 at l + M_sigma/2 (read);
+ *   fhat : M complex64 on the device, k + M/2 layout (written);
+ *   M even >= 2; M_sigma a power of two with max(M, 4) <= M_sigma <= 2^20 (larger sizes
+ *   return INFFT_EUNSUPPORTED; host pointers return INFFT_EINVAL).
+ * Allocates nothing: its scratch is one static device array of 2^20 complex64
+ * (8 MiB) that every GPU loading the library holds until the process exits.  The
+ * first call on a device looks up that array's device address (once per device,
+ * with the device current); make that first call before any stream capture.
+ * Every call shares the array, so calls that may overlap on the GPU (different
+ * streams, or different host threads) race: serialise them.  The array needs no
+ * clearing: each call overwrites every element it reads. */
+infft_status infft_fft_deconv_noalloc(const float* grid, int64_t M, int64_t M_sigma, int kernel,
+                                      float* fhat, infft_stream_t stream);
+
 /* Number of kernels this library has launched in the process so far. */
 int64_t infft_launch_count(void);
 

@@ -22,6 +22,7 @@ EXPORTED_SYMBOLS = (
     "infft_plan", "infft_precompute", "infft_apply", "nfft_apply", "plan_destroy", "infft_plan_create",
     "infft_set_nodes", "infft_apply_z", "nfft_apply_z", "infft_get_info", "infft_copy_plan_data",
     "infft_profile", "infft_profile_read", "infft_launch_count", "infft_last_error", "infft_version",
+    "infft_fft_deconv_noalloc",
 )
 
 
@@ -66,6 +67,7 @@ def library():
         "infft_get_info": [P, ctypes.POINTER(_Info)],
         "infft_copy_plan_data": [P, VP, VP, VP, VP, VP, VP],
         "infft_profile": [P, I32],
+        "infft_fft_deconv_noalloc": [VP, I64, I64, I32, VP, VP],
         "infft_profile_read": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(I64),
                                ctypes.POINTER(D), ctypes.POINTER(I32)],
     }
@@ -244,6 +246,18 @@ def infft_profile_read(plan):
     n = ctypes.c_int()
     _check(library().infft_profile_read(plan.handle, cap, names, launches, ms, ctypes.byref(n)))
     return [(names[i].decode(), int(launches[i]), float(ms[i])) for i in range(n.value)]
+
+
+def infft_fft_deconv_noalloc(grid, M, out=None, kernel="full", stream=None):
+    """fhat = D^* F^* grid (complex64, device tensors) without any allocation in the
+    library (see include/infft.h); `out` is allocated here by torch when not given."""
+    keep = []
+    if out is None:
+        out = _empty_like(grid, M, "c64")
+    k = _KERNELS.get(kernel, kernel)
+    _check(library().infft_fft_deconv_noalloc(_as_ptr(grid, "c64", keep), int(M), int(grid.shape[0]), int(k),
+                                              _as_ptr(out, "c64", keep), _stream(stream, grid, out)))
+    return out
 
 
 def infft_launch_count():

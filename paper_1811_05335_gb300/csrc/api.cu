@@ -148,6 +148,18 @@ template <typename T> infft_status nfft_impl(infft_plan_t p, const T* fhat, T* f
 
 }  // namespace
 
+infft_status set_error(infft_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return st;
+}
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void launch_begin(Plan* p, const char* name, cudaStream_t s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!p->profiling) return;

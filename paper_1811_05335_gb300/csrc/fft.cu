@@ -17,6 +17,7 @@
 // the pruned, deconvolved output.  Twiddles come from sincospi on exactly reduced
 // arguments.
 #include <climits>
+#include <mutex>
 
 #include "plan.h"
 
@@ -262,3 +263,99 @@ template cudaError_t run_fft_adjoint<float>(Plan*, void*, cudaStream_t);
 template cudaError_t run_fft_adjoint<double>(Plan*, void*, cudaStream_t);
 template cudaError_t run_fft_forward<float>(Plan*, const void*, cudaStream_t);
 template cudaError_t run_fft_forward<double>(Plan*, const void*, cudaStream_t);
+
+// ---- allocation-free entry point --------------------------------------------
+//
+// Callers that cannot allocate device memory at call time -- a process whose
+// device memory is handed out entirely by its own pool allocator, or code that
+// must not touch the allocator while another component is recording work -- get
+// the pruned FFT with fused deconvolution (the last two steps of the inverse
+// NFFT) without a plan.  Its only scratch, the four-step intermediate, lives in
+// a file-scope device array that every GPU loading this library holds until the
+// process exits.
+
+namespace {
+
+constexpr int NOALLOC_MAX_MS = 1 << 20;   // largest M_sigma (8 MiB of complex64 scratch)
+
+__device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_MAX_MS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+float2* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// The device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in: the address must come from cudaGetSymbolAddress,
+// looked up once per device with that device current.
+cudaError_t noalloc_scratch(int dev, float2** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = (float2*)ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+bool on_device(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" infft_status infft_fft_deconv_noalloc(const float* grid, int64_t M, int64_t M_sigma, int kernel,
+                                                 float* fhat, infft_stream_t stream) {
+    if (!grid || !fhat) return set_error(INFFT_EINVAL, "grid and fhat must not be NULL");
+    if (M < 2 || (M & 1)) return set_error(INFFT_EINVAL, "M must be even and >= 2 (got %lld)", (long long)M);
+    if (M_sigma < M || M_sigma < 4 || (M_sigma & (M_sigma - 1)))
+        return set_error(INFFT_EINVAL, "M_sigma must be a power of two >= max(M, 4) (got %lld)", (long long)M_sigma);
+    if (M_sigma > NOALLOC_MAX_MS)
+        return set_error(INFFT_EUNSUPPORTED, "M_sigma = %lld exceeds the %d of the allocation-free scratch",
+                         (long long)M_sigma, NOALLOC_MAX_MS);
+    if (kernel != INFFT_KERNEL_FULL && kernel != INFFT_KERNEL_SYM)
+        return set_error(INFFT_EINVAL, "kernel must be INFFT_KERNEL_FULL or INFFT_KERNEL_SYM (got %d)", kernel);
+    if (!on_device(grid) || !on_device(fhat))
+        return set_error(INFFT_EINVAL, "grid and fhat must be device memory");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(INFFT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return set_error(INFFT_EUNSUPPORTED, "device %d", dev);
+    float2* work = nullptr;
+    if ((e = noalloc_scratch(dev, &work)) != cudaSuccess)
+        return set_error(INFFT_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Ms = (int)M_sigma, Mi = (int)M;
+    int logMs = 0;
+    while ((1 << logMs) < Ms) ++logMs;
+    const float inv_Ms = 1.0f / (float)Ms;
+    const int sym = kernel == INFFT_KERNEL_SYM;
+    if (Ms <= FFT_SMALL) {
+        const size_t smem = 2 * (size_t)Ms * sizeof(float2);
+        if ((e = allow_smem(k_fft_small_adjoint<float>, smem)) != cudaSuccess)
+            return set_error(INFFT_ECUDA, "%s", cudaGetErrorString(e));
+        k_fft_small_adjoint<float><<<1, FFT_THREADS, smem, s>>>((const float2*)grid, (float2*)fhat, logMs, Mi,
+                                                                 inv_Ms, sym);
+        count_launches(1);
+    } else {
+        const Split sp = choose_split<float>(logMs);
+        const size_t smemA = 2 * (size_t)sp.CA * ((size_t)1 << sp.log1) * sizeof(float2);
+        const size_t smemB = 2 * (size_t)sp.CB * ((size_t)1 << sp.log2) * sizeof(float2);
+        if ((e = allow_smem(k_fft_passA<float, -1, false>, smemA)) != cudaSuccess ||
+            (e = allow_smem(k_fft_passB<float, -1, true>, smemB)) != cudaSuccess)
+            return set_error(INFFT_ECUDA, "%s", cudaGetErrorString(e));
+        k_fft_passA<float, -1, false><<<(1 << sp.log2) / sp.CA, FFT_THREADS, smemA, s>>>(
+            (const float2*)grid, work, sp.log1, sp.log2, sp.CA, Mi, inv_Ms, sym);
+        k_fft_passB<float, -1, true><<<(1 << sp.log1) / sp.CB, FFT_THREADS, smemB, s>>>(
+            work, (float2*)fhat, sp.log1, sp.log2, sp.CB, Mi, inv_Ms, sym);
+        count_launches(2);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return set_error(INFFT_ECUDA, "launch: %s", cudaGetErrorString(e));
+    return INFFT_OK;
+}

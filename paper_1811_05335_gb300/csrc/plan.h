@@ -86,6 +86,11 @@ struct infft_plan_s {
 
 typedef infft_plan_s Plan;
 
+// Records a failure for infft_last_error() and returns st.
+infft_status set_error(infft_status st, const char* fmt, ...);
+// Adds to the library's launch counter (infft_launch_count) for launches made without a plan.
+void count_launches(int n);
+
 // Launch bookkeeping: counts launches and, when profiling, brackets each launch
 // with an event pair on its stream.
 void launch_begin(Plan* p, const char* name, cudaStream_t s);

@@ -1,0 +1,66 @@
+"""The allocation-free entry point infft_fft_deconv_noalloc, for callers that cannot
+allocate device memory when they call (their device memory belongs to their own pool
+allocator, or they must not call cudaMalloc while other work is being recorded).
+
+It is checked against the existing entry point infft_apply: on the same plan, the
+grid g = B_opt^* f is formed here on the host from the plan's exported weights, and
+the no-alloc transform of g must reproduce infft_apply(f) within the fp32 tolerance
+of the other GPU tests, on two calls in a row.  This file runs last so that a run
+stopping at the first failure has already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def host_grid(data, f, Ms, N):
+    """g_l = sum_{j in I(l)} b_{l,j} f_j from the plan's exported pattern and fp64 weights."""
+    count = data["col_count"].astype(np.int64)
+    start = data["col_start"].astype(np.int64)
+    off = data["col_offset"].astype(np.int64)
+    nnz = int(off[-1])
+    col = np.repeat(np.arange(Ms), count)
+    pos = (np.repeat(start, count) + np.arange(nnz) - np.repeat(off[:-1], count)) % N
+    g = np.zeros(Ms, np.complex128)
+    np.add.at(g, col, data["weights"][:nnz] * f[data["perm"].astype(np.int64)[pos]])
+    return g
+
+
+@pytest.mark.parametrize("M,N,m", [(4096, 16384, 4), (512, 2048, 3)])   # four-step and single-CTA paths
+def test_fft_deconv_noalloc_matches_infft_apply(M, N, m):
+    import torch
+    import paper_1811_05335_gb300 as g
+    from workloads import make_problem
+    dev = torch.device("cuda:0")
+    p = make_problem(2, M=M, N=N, m=m)
+    plan = g.infft_plan_create(M, N, 2.0, m)
+    g.infft_set_nodes(plan, torch.tensor(p.x, dtype=torch.float64, device=dev))
+    g.infft_precompute(plan)
+    data = g.infft_copy_plan_data(plan)
+    Ms = plan.M_sigma
+    for call in range(2):                         # two calls in a row, different data
+        f = np.asarray(p.f * (1.0 + 0.5j * call), np.complex64)
+        want = g.infft_apply(plan, torch.tensor(f, device=dev)).cpu().numpy().astype(np.complex128)
+        grid = torch.tensor(host_grid(data, f.astype(np.complex128), Ms, N).astype(np.complex64), device=dev)
+        got = g.infft_fft_deconv_noalloc(grid, M).cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert err <= FP32_TOL, f"call {call}: rel l2 {err:.3e}"
+    plan.close()
+
+
+def test_fft_deconv_noalloc_rejects_sizes():
+    import torch
+    import paper_1811_05335_gb300 as g
+    lib = g.library()
+    grid = torch.zeros(8, dtype=torch.complex64, device="cuda:0")
+    out = torch.zeros(8, dtype=torch.complex64, device="cuda:0")
+    # M_sigma above the static scratch (2^20): refused before any GPU work
+    assert lib.infft_fft_deconv_noalloc(grid.data_ptr(), 8, 1 << 21, 0, out.data_ptr(), None) == 5
+    assert b"exceeds" in lib.infft_last_error()
+    assert lib.infft_fft_deconv_noalloc(grid.data_ptr(), 8, 12, 0, out.data_ptr(), None) == 1   # not a power of 2
+    host = np.zeros(8, np.complex64)
+    assert lib.infft_fft_deconv_noalloc(host.ctypes.data, 8, 8, 0, out.data_ptr(), None) == 1  # host pointer
