@@ -137,6 +137,24 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 1.25 TFLOP/s nominal at 2070 MHz over 15
 KAPPA_FLOPS = 40                       # fp64 flops of one closed-form kernel value
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel`
+    from the last ncu capture recorded in profiles/traffic.json, or None when the
+    kernel's source file changed since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(kernel)
+        if not rec:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            if hashlib.sha1(fh.read()).hexdigest() != rec["sha1"]:
+                return None
+        return rec["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def lsq_flops(counts):
     """Algorithmic fp64 flops of the B_opt precompute: per column of n nodes, the
     Cholesky factorisation n^3/3, the two triangular solves 2n^2, and the
@@ -288,7 +306,8 @@ def run_gpu(a):
         peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
         ach = fl / (lsq_ms / 1e3) / 1e12
         roofline = {"kernel": "lsq (B_opt precompute, all tiers)", "bound": "alu", "achieved": ach,
-                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": recorded_traffic("k_lsq_thread<17, 5>"),
                     "peak_source": "derived: 152 SMs x 4 fp64 flop/clk x max SM clock"}
     app_tab = {name: ms for name, n, ms in app_kernels}
     app_kernel_ms = sum(app_tab.values()) / k_app

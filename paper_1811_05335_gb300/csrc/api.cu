@@ -54,7 +54,7 @@ bool is_device_pointer(const void* ptr) {
 }
 
 void free_plan_buffers(Plan* p) {
-    void* bufs[] = {p->x, p->xs, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist, p->col_start,
+    void* bufs[] = {p->x, p->xs, p->skey, p->perm, p->bucket, p->cursor, p->seg_list, p->sort_tmp, p->col_start,
                     p->col_count, p->col_off, p->list_a, p->list_b, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
                     p->w32, p->J, p->wide, p->grid,
                     p->work, p->stage_in, p->stage_out};
@@ -190,17 +190,15 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
     cudaGetDevice(&p->device);
     p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
     p->logMs = logMs;
-    p->key_bits = logMs + 1;   // keys < 2 M_sigma
     p->nnz_cap = N * (2 * (int64_t)m + 1);
-    const int64_t tiles = (N + 2047) / 2048;
     const int64_t stage = (N > M ? N : M);
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, cnt) if (e == cudaSuccess) e = dalloc(&(ptr), (size_t)(cnt))
     ALLOC(p->x, N); ALLOC(p->xs, N);
-    ALLOC(p->keys[0], N); ALLOC(p->keys[1], N); ALLOC(p->vals[0], N); ALLOC(p->vals[1], N);
-    ALLOC(p->hist, 256 * tiles + 1);
+    ALLOC(p->skey, N); ALLOC(p->perm, N); ALLOC(p->sort_tmp, N);
+    ALLOC(p->bucket, 2 * Ms + 1); ALLOC(p->cursor, 2 * Ms); ALLOC(p->seg_list, N / 32 + 2);
     ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->list_a, Ms); ALLOC(p->list_b, Ms);
-    ALLOC(p->scan_sums, (std::max<int64_t>(256 * tiles, Ms + 1) + 4095) / 4096 + 2);
+    ALLOC(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
     ALLOC(p->phase, N);
     ALLOC(p->counters, CNT_N);
     ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms); ALLOC(p->wide, Ms);
@@ -214,9 +212,6 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
         delete p;
         return cuda_fail(e, "allocate plan buffers");
     }
-    const int passes = (p->key_bits + 7) / 8;
-    p->skey = p->keys[passes & 1];
-    p->perm = p->vals[passes & 1];
     *out = p;
     return INFFT_OK;
 }

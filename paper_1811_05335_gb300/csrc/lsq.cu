@@ -153,12 +153,6 @@ INFFT_D void tri_index(int e, int& i, int& j) {
 
 INFFT_D int trow(int i) { return i * (i + 1) / 2; }   // packed lower-triangle row start
 
-// Per sorted node: (sin, cos)(pi M x).
-__global__ void k_node_phase(const double* __restrict__ xs, int N, double M, double2* __restrict__ ph) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) ph[i] = phase_of(M, xs[i]);
-}
-
 INFFT_D double col_t(int p, int Ms) { return (double)(p - Ms / 2) / (double)Ms; }   // l / M_sigma
 
 // ---------------------------------------------------------------- tier 1: thread per column
@@ -750,11 +744,6 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 148;
-
-    launch_begin(p, "node_phase", s);
-    k_node_phase<<<(N + 255) / 256, 256, 0, s>>>(p->xs, N, kp.M, p->phase);
-    launch_end(p, s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     // thread tiers: a tile of 32 consecutive columns goes to the first tier whose
     // NMAX covers its largest column; tiles above the last go to the warp tier

@@ -6,101 +6,118 @@
 // Sorting the nodes by key = 2*cell + (u is not an integer) therefore turns every
 // I(l) into one contiguous key range [2(l-m), 2(l+m)] that wraps modulo M_sigma.
 //
-// The sort is a stable LSD radix sort (8-bit digits): equal keys keep the caller's
-// node order, so the whole pattern -- and every later result -- is deterministic.
+// The sort is a counting sort over the 2 M_sigma keys: a histogram, its exclusive
+// scan (the bucket offsets, which also give every column's range directly), an
+// atomic scatter, and a fix-up that orders each bucket by the caller's node index,
+// so the result -- and every later result -- is deterministic.  The fix-up also
+// gathers the sorted nodes and their phases (sin, cos)(pi M x) used by the
+// precompute.
 #include "plan.h"
 
 namespace {
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 8;                       // keys per thread per tile
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // 2048 keys per tile
-constexpr int RS_BINS = 256;
+constexpr int SMALL_BUCKET = 32;   // buckets up to this size are ordered by one thread
 
-__global__ void k_node_keys(const double* __restrict__ x, int N, int Ms, uint32_t* __restrict__ key,
-                            int32_t* __restrict__ val, int32_t* __restrict__ counters) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    double xj = x[j];
-    bool ok = isfinite(xj) && xj >= -0.5 && xj < 0.5;
-    if (!ok) {
-        atomicAdd(&counters[CNT_BAD_NODES], 1);
-        xj = 0.0;   // keeps the pattern in range; the plan reports the bad node
-    }
+INFFT_D uint32_t node_key(double xj, int Ms) {
     double u = __dmul_rn((double)Ms, xj);   // one rounded product, never contracted
     double fb = floor(u);
     int exact = (u == fb);
     long long cell = (long long)fb + Ms / 2;  // in [0, Ms]; u may round up to Ms/2
     if (cell >= Ms) cell -= Ms;
     if (cell < 0) cell += Ms;
-    key[j] = (uint32_t)(2 * cell + (exact ? 0 : 1));
-    val[j] = j;
+    return (uint32_t)(2 * cell + (exact ? 0 : 1));
 }
 
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* __restrict__ hist,
-                          int tiles) {
-    __shared__ uint32_t cnt[RS_BINS];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    int base = blockIdx.x * RS_TILE;
-#pragma unroll
-    for (int i = 0; i < RS_ITEMS; ++i) {
-        int e = base + i * RS_THREADS + threadIdx.x;
-        if (e < n) atomicAdd(&cnt[(keys[e] >> shift) & 0xFF], 1u);
-    }
-    __syncthreads();
-    hist[threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];   // digit-major
+INFFT_D double checked_node(const double* __restrict__ x, int j) {
+    const double xj = x[j];
+    return (isfinite(xj) && xj >= -0.5 && xj < 0.5) ? xj : 0.0;   // bad nodes are counted in k_bucket_count
 }
 
-// Stable scatter: warp w owns items [w*256, w*256+256) of the tile and walks them
-// in 8 rounds of 32 consecutive keys; ranks among equal digits come from
-// __match_any_sync, so the order inside a digit follows the input order.
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int n,
-                             int shift, const uint32_t* __restrict__ hist, int tiles,
-                             uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
-    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    const int base = blockIdx.x * RS_TILE + w * (RS_ITEMS * 32);
-    uint32_t k[RS_ITEMS];
-    int32_t v[RS_ITEMS];
-    uint32_t local[RS_ITEMS];
-    const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int e = base + r * 32 + lane;
-        bool valid = e < n;
-        k[r] = valid ? kin[e] : 0u;
-        v[r] = valid ? vin[e] : 0;
-        uint32_t d = valid ? ((k[r] >> shift) & 0xFF) : RS_BINS;   // invalid lanes share a dummy digit
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = (d < RS_BINS) ? wcnt[w][d] : 0u;
-        local[r] = before + __popc(peers & lt);
-        __syncwarp();
-        if (d < RS_BINS && (peers & lt) == 0) wcnt[w][d] = before + __popc(peers);
-        __syncwarp();
+__global__ void k_bucket_count(const double* __restrict__ x, int N, int Ms, int32_t* __restrict__ bucket,
+                               int32_t* __restrict__ counters) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double xj = x[j];
+    if (!(isfinite(xj) && xj >= -0.5 && xj < 0.5)) atomicAdd(&counters[CNT_BAD_NODES], 1);
+    atomicAdd(&bucket[node_key(checked_node(x, j), Ms)], 1);
+}
+
+__global__ void k_bucket_scatter(const double* __restrict__ x, int N, int Ms, const int32_t* __restrict__ bucket,
+                                 int32_t* __restrict__ cursor, int32_t* __restrict__ perm,
+                                 uint32_t* __restrict__ skey) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const uint32_t key = node_key(checked_node(x, j), Ms);
+    const int pos = bucket[key] + atomicAdd(&cursor[key], 1);
+    perm[pos] = j;
+    skey[pos] = key;
+}
+
+// (sin, cos)(pi M z) with M z reduced modulo 2 exactly: M z = p + e with
+// p = fl(M z) and e = fma(M, z, -p); p - 2 rint(p/2) is exact.
+INFFT_D double2 node_phase(double M, double z) {
+    const double p = M * z;
+    const double e = fma(M, z, -p);
+    const double r = p - 2.0 * rint(0.5 * p);
+    double s, c;
+    sincospi(r + e, &s, &c);
+    return make_double2(s, c);
+}
+
+INFFT_D void finish_node(int i, const double* __restrict__ x, const int32_t* __restrict__ perm, double M,
+                         double* __restrict__ xs, double2* __restrict__ ph) {
+    const double xi = checked_node(x, perm[i]);
+    xs[i] = xi;
+    ph[i] = node_phase(M, xi);
+}
+
+// One thread per bucket: small buckets are ordered by caller index (insertion
+// sort), larger ones are queued for k_bigseg_fixup.
+__global__ void k_bucket_fixup(const int32_t* __restrict__ bucket, int nkeys, const double* __restrict__ x,
+                               double M, int32_t* __restrict__ perm, double* __restrict__ xs,
+                               double2* __restrict__ ph, int32_t* __restrict__ seg_list,
+                               int32_t* __restrict__ counters) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nkeys) return;
+    const int s0 = bucket[b], s1 = bucket[b + 1], k = s1 - s0;
+    if (k == 0) return;
+    if (k > SMALL_BUCKET) {
+        seg_list[atomicAdd(&counters[CNT_BIG_SEGMENTS], 1)] = b;
+        return;
     }
-    __syncthreads();
-    {   // exclusive scan over warps, per digit (one thread per digit)
-        uint32_t run = 0;
-        for (int ww = 0; ww < RS_WARPS; ++ww) {
-            uint32_t t = wcnt[ww][threadIdx.x];
-            wcnt[ww][threadIdx.x] = run;
-            run += t;
+    for (int i = s0 + 1; i < s1; ++i) {
+        const int v = perm[i];
+        int q = i - 1;
+        while (q >= s0 && perm[q] > v) {
+            perm[q + 1] = perm[q];
+            --q;
         }
+        perm[q + 1] = v;
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int e = base + r * 32 + lane;
-        if (e < n) {
-            uint32_t d = (k[r] >> shift) & 0xFF;
-            uint32_t pos = hist[d * tiles + blockIdx.x] + wcnt[w][d] + local[r];
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+    for (int i = s0; i < s1; ++i) finish_node(i, x, perm, M, xs, ph);
+}
+
+// One CTA per large bucket: each element's final position is its rank among the
+// bucket's (distinct) caller indices; ranks are counted, written to tmp, copied back.
+__global__ void k_bigseg_fixup(const int32_t* __restrict__ seg_list, const int32_t* __restrict__ counters,
+                               const int32_t* __restrict__ bucket, const double* __restrict__ x, double M,
+                               int32_t* __restrict__ perm, int32_t* __restrict__ tmp, double* __restrict__ xs,
+                               double2* __restrict__ ph) {
+    const int total = counters[CNT_BIG_SEGMENTS];
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int b = seg_list[it];
+        const int s0 = bucket[b], s1 = bucket[b + 1], k = s1 - s0;
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            const int v = perm[s0 + i];
+            int rank = 0;
+            for (int q = 0; q < k; ++q) rank += perm[s0 + q] < v;
+            tmp[s0 + rank] = v;
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) perm[s0 + i] = tmp[s0 + i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) finish_node(s0 + i, x, perm, M, xs, ph);
+        __syncthreads();
     }
 }
 
@@ -166,32 +183,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t* in, 
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
 }
 
-__global__ void k_gather_x(const double* __restrict__ x, const int32_t* __restrict__ perm, int N,
-                           double* __restrict__ xs) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) xs[i] = x[perm[i]];
-}
-
-INFFT_D int lower_bound_u32(const uint32_t* __restrict__ a, int n, uint32_t v) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (a[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-__global__ void k_col_ranges(const uint32_t* __restrict__ skey, int N, int Ms, int m,
-                             int32_t* __restrict__ start, int32_t* __restrict__ count,
-                             int32_t* __restrict__ counters) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+// Column l (storage p) holds the keys [2(p-m), 2(p+m)] (mod 2 M_sigma): its range of
+// sorted nodes starts at the offset of the first key and ends before the offset of
+// the key after the last; the range wraps when the key interval does.
+__global__ void k_col_ranges(const int32_t* __restrict__ bucket, int N, int Ms, int m, int32_t* __restrict__ start,
+                             int32_t* __restrict__ count, int32_t* __restrict__ counters) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Ms) return;
     int lo = p - m; if (lo < 0) lo += Ms;
     int hi = p + m; if (hi >= Ms) hi -= Ms;
-    uint32_t klo = 2u * (uint32_t)lo, khi = 2u * (uint32_t)hi + 1u;   // keys [klo, khi)
-    int a = lower_bound_u32(skey, N, klo);
-    int b = lower_bound_u32(skey, N, khi);
-    int c = (klo < khi) ? (b - a) : (N - a) + b;
+    const int klo = 2 * lo, khi = 2 * hi + 1;     // keys [klo, khi)
+    const int a = bucket[klo], b = bucket[khi];
+    const int c = (klo < khi) ? (b - a) : (N - a) + b;
     start[p] = (a == N) ? 0 : a;
     count[p] = c;
     if (c == 0) atomicAdd(&counters[CNT_EMPTY], 1);
@@ -203,7 +206,7 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s) {
-    const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK > 0 ? (n + SCAN_CHUNK - 1) / SCAN_CHUNK : 1;
+    const int nb = n > 0 ? (n + SCAN_CHUNK - 1) / SCAN_CHUNK : 1;
     launch_begin(p, "scan_reduce", s);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, p->scan_sums);
     launch_end(p, s);
@@ -214,34 +217,32 @@ cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, 
 }
 
 cudaError_t run_pattern(Plan* p, cudaStream_t s) {
-    const int N = (int)p->N, Ms = (int)p->Ms;
+    const int N = (int)p->N, Ms = (int)p->Ms, nkeys = 2 * Ms;
     cudaError_t e = cudaMemsetAsync(p->counters, 0, CNT_N * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->bucket, 0, (size_t)(nkeys + 1) * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->cursor, 0, (size_t)nkeys * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
 
-    launch_begin(p, "node_keys", s);
-    k_node_keys<<<blocks_for(N, 256), 256, 0, s>>>(p->x, N, Ms, p->keys[0], p->vals[0], p->counters);
+    launch_begin(p, "bucket_count", s);
+    k_bucket_count<<<blocks_for(N, 256), 256, 0, s>>>(p->x, N, Ms, p->bucket, p->counters);
     launch_end(p, s);
-
-    const int tiles = blocks_for(N, RS_TILE);
-    const int passes = (p->key_bits + 7) / 8;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int in = pass & 1, out = in ^ 1, shift = 8 * pass;
-        launch_begin(p, "radix_hist", s);
-        k_rs_hist<<<tiles, RS_THREADS, 0, s>>>(p->keys[in], N, shift, p->hist, tiles);
-        launch_end(p, s);
-        e = run_exclusive_scan(p, (const int32_t*)p->hist, (int32_t*)p->hist, RS_BINS * tiles, s);
-        if (e != cudaSuccess) return e;
-        launch_begin(p, "radix_scatter", s);
-        k_rs_scatter<<<tiles, RS_THREADS, 0, s>>>(p->keys[in], p->vals[in], N, shift, p->hist, tiles,
-                                                   p->keys[out], p->vals[out]);
-        launch_end(p, s);
-    }
-    launch_begin(p, "gather_x", s);
-    k_gather_x<<<blocks_for(N, 256), 256, 0, s>>>(p->x, p->perm, N, p->xs);
+    if ((e = run_exclusive_scan(p, p->bucket, p->bucket, nkeys, s)) != cudaSuccess) return e;
+    launch_begin(p, "bucket_scatter", s);
+    k_bucket_scatter<<<blocks_for(N, 256), 256, 0, s>>>(p->x, N, Ms, p->bucket, p->cursor, p->perm, p->skey);
+    launch_end(p, s);
+    launch_begin(p, "bucket_fixup", s);
+    k_bucket_fixup<<<blocks_for(nkeys, 256), 256, 0, s>>>(p->bucket, nkeys, p->x, (double)p->M, p->perm, p->xs,
+                                                          p->phase, p->seg_list, p->counters);
+    launch_end(p, s);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    launch_begin(p, "bigseg_fixup", s);
+    k_bigseg_fixup<<<sms > 0 ? sms : 148, 256, 0, s>>>(p->seg_list, p->counters, p->bucket, p->x, (double)p->M,
+                                                       p->perm, p->sort_tmp, p->xs, p->phase);
     launch_end(p, s);
 
     launch_begin(p, "col_ranges", s);
-    k_col_ranges<<<blocks_for(Ms, 256), 256, 0, s>>>(p->skey, N, Ms, p->m, p->col_start, p->col_count,
+    k_col_ranges<<<blocks_for(Ms, 256), 256, 0, s>>>(p->bucket, N, Ms, p->m, p->col_start, p->col_count,
                                                      p->counters);
     launch_end(p, s);
     return run_exclusive_scan(p, p->col_count, p->col_off, Ms, s);

@@ -16,7 +16,7 @@ enum {
     CNT_MAX_COLUMN = 3,
     CNT_EMPTY = 4,
     CNT_LIST_A = 5,        // columns queued for the warp solver
-    CNT_LIST_B = 6,        // (unused)
+    CNT_BIG_SEGMENTS = 6,  // buckets queued for the large-bucket fix-up of the pattern sort
     CNT_BIG_LIST = 7,      // columns queued for the CTA solver
     CNT_N = 8
 };
@@ -45,16 +45,17 @@ struct infft_plan_s {
     double sigma = 2.0, tau = 1e-12;
     int logMs = 0;
     int64_t nnz_cap = 0;
-    int key_bits = 0;
 
     // pattern (a1)
     double* x = nullptr;        // nodes, caller order (N)
     double* xs = nullptr;       // nodes, sorted (N)
-    uint32_t* keys[2] = {nullptr, nullptr};   // radix sort ping-pong (N)
-    int32_t* vals[2] = {nullptr, nullptr};
-    uint32_t* skey = nullptr;   // sorted keys (points into keys[])
-    int32_t* perm = nullptr;    // sorted position -> caller index (points into vals[])
-    uint32_t* hist = nullptr;   // radix histograms (256 * tiles)
+    double2* phase = nullptr;   // N: (sin, cos)(pi M x) of the sorted nodes
+    uint32_t* skey = nullptr;   // N: key of each sorted node (2 cell + (u not an integer))
+    int32_t* perm = nullptr;    // N: sorted position -> caller index
+    int32_t* bucket = nullptr;  // 2 Ms + 1: key counts, then their exclusive prefix (bucket offsets)
+    int32_t* cursor = nullptr;  // 2 Ms: scatter cursors of the counting sort
+    int32_t* seg_list = nullptr;// buckets larger than one thread orders
+    int32_t* sort_tmp = nullptr;// N: scratch of the large-bucket fix-up
     int32_t* col_start = nullptr;   // Ms
     int32_t* col_count = nullptr;   // Ms
     int32_t* col_off = nullptr;     // Ms + 1
@@ -65,7 +66,6 @@ struct infft_plan_s {
     int32_t* counters = nullptr;    // CNT_N
 
     // B_opt (a2)
-    double2* phase = nullptr;   // N: (sin, cos)(pi M x) of the sorted nodes
     double* w64 = nullptr;      // nnz_cap
     float* w32 = nullptr;       // nnz_cap
     double* J = nullptr;        // Ms
