@@ -28,6 +28,7 @@
 // Newton-Raphson reciprocal; pairs closer than a quarter period of sin(pi M t)
 // use the Taylor series of sin(z)/z and cos(z) instead of the phases, so the
 // cancellation in the angle addition never meets a tiny denominator.
+#include <algorithm>
 #include <cstring>
 
 #include "plan.h"
@@ -298,12 +299,15 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     int* cfst = cnn + 32;                                       // per union node: first candidate column
     int* clst = cfst + TILE_UMAX;                               // per union node: last candidate column
 
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tiles = (Ms + 31) / 32;
+    for (int tile = blockIdx.x * WARPS + wid; tile < tiles; tile += gridDim.x * WARPS) {
+    __syncwarp();
+    const int p = tile * 32 + lane;
     const bool live = p < Ms;
     const int n = live ? col_count[p] : 0;
     int D = n;
     for (int o = 16; o; o >>= 1) D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
-    if (D <= lo) return;                                        // an earlier tier took this tile
+    if (D <= lo) continue;                                      // an earlier tier took this tile
     if (D > NMAX) {
         if (push) {
             if (n > 0) {
@@ -313,7 +317,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
                 wide[p] = 0;
             }
         }
-        return;
+        continue;
     }
     const int s = live ? col_start[p] : 0;
     const int S = __shfl_sync(0xffffffffu, s, 0);
@@ -402,7 +406,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     }
     if (!mine) {
         if (live) { Jout[p] = 1.0; wide[p] = 0; }
-        return;
+        continue;
     }
     const int off = col_off[p];
     double mu = mu0, ysq = 0.0;
@@ -425,7 +429,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
         Jout[p] = 1.0;
         wide[p] = 0;
         atomicAdd(&counters[CNT_FALLBACK], 1);
-        return;
+        continue;
     }
     if (mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
     double bsq = 0.0, babs = 0.0;
@@ -441,6 +445,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
     Jout[p] = 1.0 - ysq - mu * bsq;
     wide[p] = babs > WIDE_COLUMN_L1;
+    }
 }
 
 // ---------------------------------------------------------------- tier 2/3: warp per column
@@ -764,17 +769,17 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     const int tiles = (Ms + 31) / 32;
 
     launch_begin(p, "lsq_thread17", s);
-    t1<<<(tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+    t1<<<std::min((tiles + W1 - 1) / W1, sms), W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
                                                   kp, mu, p->w64, p->w32, p->J, p->wide, -1, 0, p->list_a,
                                                   CNT_LIST_A, p->counters);
     launch_end(p, s);
     launch_begin(p, "lsq_thread25", s);
-    t2<<<(tiles + W2 - 1) / W2, W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+    t2<<<std::min((tiles + W2 - 1) / W2, sms), W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
                                                   kp, mu, p->w64, p->w32, p->J, p->wide, A1, 0, p->list_a,
                                                   CNT_LIST_A, p->counters);
     launch_end(p, s);
     launch_begin(p, "lsq_thread33", s);
-    t3<<<(tiles + W3 - 1) / W3, W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+    t3<<<std::min((tiles + W3 - 1) / W3, sms), W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
                                                   kp, mu, p->w64, p->w32, p->J, p->wide, A2, 1, p->list_a,
                                                   CNT_LIST_A, p->counters);
     launch_end(p, s);

@@ -9,7 +9,7 @@
 // The sort is a counting sort over the 2 M_sigma keys: a histogram, its exclusive
 // scan (the bucket offsets, which also give every column's range directly), an
 // atomic scatter, and a fix-up that orders each bucket by the caller's node index,
-// so the result -- and every later result -- is deterministic.  The fix-up also
+// so the result -- and every later result -- is deterministic.  A last pass
 // gathers the sorted nodes and their phases (sin, cos)(pi M x) used by the
 // precompute.
 #include "plan.h"
@@ -64,8 +64,11 @@ INFFT_D double2 node_phase(double M, double z) {
     return make_double2(s, c);
 }
 
-INFFT_D void finish_node(int i, const double* __restrict__ x, const int32_t* __restrict__ perm, double M,
-                         double* __restrict__ xs, double2* __restrict__ ph) {
+// Per sorted node: its position and its phase (sin, cos)(pi M x).
+__global__ void k_gather_nodes(const double* __restrict__ x, const int32_t* __restrict__ perm, int N, double M,
+                               double* __restrict__ xs, double2* __restrict__ ph) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
     const double xi = checked_node(x, perm[i]);
     xs[i] = xi;
     ph[i] = node_phase(M, xi);
@@ -73,10 +76,8 @@ INFFT_D void finish_node(int i, const double* __restrict__ x, const int32_t* __r
 
 // One thread per bucket: small buckets are ordered by caller index (insertion
 // sort), larger ones are queued for k_bigseg_fixup.
-__global__ void k_bucket_fixup(const int32_t* __restrict__ bucket, int nkeys, const double* __restrict__ x,
-                               double M, int32_t* __restrict__ perm, double* __restrict__ xs,
-                               double2* __restrict__ ph, int32_t* __restrict__ seg_list,
-                               int32_t* __restrict__ counters) {
+__global__ void k_bucket_fixup(const int32_t* __restrict__ bucket, int nkeys, int32_t* __restrict__ perm,
+                               int32_t* __restrict__ seg_list, int32_t* __restrict__ counters) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nkeys) return;
     const int s0 = bucket[b], s1 = bucket[b + 1], k = s1 - s0;
@@ -94,15 +95,13 @@ __global__ void k_bucket_fixup(const int32_t* __restrict__ bucket, int nkeys, co
         }
         perm[q + 1] = v;
     }
-    for (int i = s0; i < s1; ++i) finish_node(i, x, perm, M, xs, ph);
 }
 
 // One CTA per large bucket: each element's final position is its rank among the
 // bucket's (distinct) caller indices; ranks are counted, written to tmp, copied back.
 __global__ void k_bigseg_fixup(const int32_t* __restrict__ seg_list, const int32_t* __restrict__ counters,
-                               const int32_t* __restrict__ bucket, const double* __restrict__ x, double M,
-                               int32_t* __restrict__ perm, int32_t* __restrict__ tmp, double* __restrict__ xs,
-                               double2* __restrict__ ph) {
+                               const int32_t* __restrict__ bucket, int32_t* __restrict__ perm,
+                               int32_t* __restrict__ tmp) {
     const int total = counters[CNT_BIG_SEGMENTS];
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int b = seg_list[it];
@@ -115,8 +114,6 @@ __global__ void k_bigseg_fixup(const int32_t* __restrict__ seg_list, const int32
         }
         __syncthreads();
         for (int i = threadIdx.x; i < k; i += blockDim.x) perm[s0 + i] = tmp[s0 + i];
-        __syncthreads();
-        for (int i = threadIdx.x; i < k; i += blockDim.x) finish_node(s0 + i, x, perm, M, xs, ph);
         __syncthreads();
     }
 }
@@ -231,14 +228,15 @@ cudaError_t run_pattern(Plan* p, cudaStream_t s) {
     k_bucket_scatter<<<blocks_for(N, 256), 256, 0, s>>>(p->x, N, Ms, p->bucket, p->cursor, p->perm, p->skey);
     launch_end(p, s);
     launch_begin(p, "bucket_fixup", s);
-    k_bucket_fixup<<<blocks_for(nkeys, 256), 256, 0, s>>>(p->bucket, nkeys, p->x, (double)p->M, p->perm, p->xs,
-                                                          p->phase, p->seg_list, p->counters);
+    k_bucket_fixup<<<blocks_for(nkeys, 256), 256, 0, s>>>(p->bucket, nkeys, p->perm, p->seg_list, p->counters);
     launch_end(p, s);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     launch_begin(p, "bigseg_fixup", s);
-    k_bigseg_fixup<<<sms > 0 ? sms : 148, 256, 0, s>>>(p->seg_list, p->counters, p->bucket, p->x, (double)p->M,
-                                                       p->perm, p->sort_tmp, p->xs, p->phase);
+    k_bigseg_fixup<<<sms > 0 ? sms : 148, 256, 0, s>>>(p->seg_list, p->counters, p->bucket, p->perm, p->sort_tmp);
+    launch_end(p, s);
+    launch_begin(p, "gather_nodes", s);
+    k_gather_nodes<<<blocks_for(N, 256), 256, 0, s>>>(p->x, p->perm, N, (double)p->M, p->xs, p->phase);
     launch_end(p, s);
 
     launch_begin(p, "col_ranges", s);
