@@ -55,7 +55,7 @@ bool is_device_pointer(const void* ptr) {
 
 void free_plan_buffers(Plan* p) {
     void* bufs[] = {p->x, p->xs, p->skey, p->perm, p->bucket, p->cursor, p->seg_list, p->sort_tmp, p->col_start,
-                    p->col_count, p->col_off, p->list_a, p->list_b, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
+                    p->col_count, p->col_off, p->list_a, p->tiles_mid, p->tiles_big, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
                     p->w32, p->J, p->wide, p->grid,
                     p->work, p->stage_in, p->stage_out};
     for (void* b : bufs)
@@ -197,7 +197,7 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
     ALLOC(p->x, N); ALLOC(p->xs, N);
     ALLOC(p->skey, N); ALLOC(p->perm, N); ALLOC(p->sort_tmp, N);
     ALLOC(p->bucket, 2 * Ms + 1); ALLOC(p->cursor, 2 * Ms); ALLOC(p->seg_list, N / 32 + 2);
-    ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->list_a, Ms); ALLOC(p->list_b, Ms);
+    ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->list_a, Ms); ALLOC(p->tiles_mid, Ms / 32 + 2); ALLOC(p->tiles_big, Ms / 32 + 2);
     ALLOC(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
     ALLOC(p->phase, N);
     ALLOC(p->counters, CNT_N);

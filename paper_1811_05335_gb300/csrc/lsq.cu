@@ -271,9 +271,9 @@ INFFT_D bool chol_solve(double* T, int n, double (&v)[NMAX], double& ysq) {
     return ok;
 }
 
-// One thread per column; a warp owns a tile of 32 consecutive columns.  The tile
-// is handled by the first tier whose NMAX covers its largest column (lo < max n <=
-// NMAX); the last tier pushes larger tiles' columns to `next_list`.  Shared memory
+// One thread per column; a warp owns a tile of 32 consecutive columns.  The first
+// tier visits every tile and routes those whose largest column exceeds its NMAX to
+// the tile lists of the larger thread tiers, or their columns to the warp tier.  Shared memory
 // per warp: each lane's packed lower triangle, lane-interleaved (element e of lane
 // t at [e * 32 + t]) so the 32 threads never collide on a bank, plus the tile's
 // union of nodes.  Consecutive columns share most of their nodes (I(l) and
@@ -286,8 +286,9 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
              const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
              KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-             double* __restrict__ Jout, uint8_t* __restrict__ wide, int lo, int push,
-             int32_t* __restrict__ next_list, int next_counter, int32_t* __restrict__ counters) {
+             double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ tiles_in,
+             int tiles_counter, int32_t* __restrict__ route_mid, int32_t* __restrict__ route_big,
+             int32_t* __restrict__ col_list, int32_t* __restrict__ counters) {
     extern __shared__ double lsq_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* wbase = (double*)((char*)lsq_smem + (size_t)wid * tile_warp_bytes<NMAX>());
@@ -299,23 +300,28 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     int* cfst = cnn + 32;                                       // per union node: first candidate column
     int* clst = cfst + TILE_UMAX;                               // per union node: last candidate column
 
-    const int tiles = (Ms + 31) / 32;
-    for (int tile = blockIdx.x * WARPS + wid; tile < tiles; tile += gridDim.x * WARPS) {
+    // tiles_in == nullptr: every tile, one per warp, routing the tiles this tier cannot
+    // take; otherwise the tiles of the list (persistent warps)
+    const int ntiles = tiles_in ? counters[tiles_counter] : (Ms + 31) / 32;
+    const int first = blockIdx.x * WARPS + wid, stride = tiles_in ? gridDim.x * WARPS : ntiles;
+    for (int it = first; it < ntiles; it += stride) {
     __syncwarp();
+    const int tile = tiles_in ? tiles_in[it] : it;
     const int p = tile * 32 + lane;
     const bool live = p < Ms;
     const int n = live ? col_count[p] : 0;
     int D = n;
     for (int o = 16; o; o >>= 1) D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
-    if (D <= lo) continue;                                      // an earlier tier took this tile
-    if (D > NMAX) {
-        if (push) {
-            if (n > 0) {
-                next_list[atomicAdd(&counters[next_counter], 1)] = p;
-            } else if (live) {             // empty columns of a pushed tile end here
-                Jout[p] = 1.0;
-                wide[p] = 0;
-            }
+    if (D > NMAX) {                        // only the routing tier meets such tiles
+        if (D <= LSQ_THREAD_NMAX2) {
+            if (lane == 0) route_mid[atomicAdd(&counters[CNT_TILES_MID], 1)] = tile;
+        } else if (D <= LSQ_THREAD_NMAX3) {
+            if (lane == 0) route_big[atomicAdd(&counters[CNT_TILES_BIG], 1)] = tile;
+        } else if (n > 0) {
+            col_list[atomicAdd(&counters[CNT_LIST_A], 1)] = p;
+        } else if (live) {                 // empty columns of a tile sent to the warp tier end here
+            Jout[p] = 1.0;
+            wide[p] = 0;
         }
         continue;
     }
@@ -744,7 +750,8 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
 
     // clear the precompute counters (fallback, unsupported, work lists), keep the pattern's
     cudaError_t e = cudaMemsetAsync(p->counters + CNT_FALLBACK, 0, 2 * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_LIST_A, 0, 3 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_LIST_A, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_BIG_LIST, 0, 3 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -769,19 +776,19 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     const int tiles = (Ms + 31) / 32;
 
     launch_begin(p, "lsq_thread17", s);
-    t1<<<std::min((tiles + W1 - 1) / W1, sms), W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
-                                                  kp, mu, p->w64, p->w32, p->J, p->wide, -1, 0, p->list_a,
-                                                  CNT_LIST_A, p->counters);
+    t1<<<(tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+                                                  kp, mu, p->w64, p->w32, p->J, p->wide, nullptr, 0, p->tiles_mid,
+                                                  p->tiles_big, p->list_a, p->counters);
     launch_end(p, s);
     launch_begin(p, "lsq_thread25", s);
-    t2<<<std::min((tiles + W2 - 1) / W2, sms), W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
-                                                  kp, mu, p->w64, p->w32, p->J, p->wide, A1, 0, p->list_a,
-                                                  CNT_LIST_A, p->counters);
+    t2<<<sms, W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
+                                p->w32, p->J, p->wide, p->tiles_mid, CNT_TILES_MID, nullptr, nullptr, nullptr,
+                                p->counters);
     launch_end(p, s);
     launch_begin(p, "lsq_thread33", s);
-    t3<<<std::min((tiles + W3 - 1) / W3, sms), W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
-                                                  kp, mu, p->w64, p->w32, p->J, p->wide, A2, 1, p->list_a,
-                                                  CNT_LIST_A, p->counters);
+    t3<<<sms, W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
+                                p->w32, p->J, p->wide, p->tiles_big, CNT_TILES_BIG, nullptr, nullptr, nullptr,
+                                p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // warp tier: columns of tiles whose largest column exceeds the thread tiers, |I(l)| <= 64

@@ -18,7 +18,9 @@ enum {
     CNT_LIST_A = 5,        // columns queued for the warp solver
     CNT_BIG_SEGMENTS = 6,  // buckets queued for the large-bucket fix-up of the pattern sort
     CNT_BIG_LIST = 7,      // columns queued for the CTA solver
-    CNT_N = 8
+    CNT_TILES_MID = 8,     // tiles routed to the 25-node thread tier
+    CNT_TILES_BIG = 9,     // tiles routed to the 33-node thread tier
+    CNT_N = 10
 };
 
 // largest column handled by the thread, warp and CTA solver tiers
@@ -60,7 +62,8 @@ struct infft_plan_s {
     int32_t* col_count = nullptr;   // Ms
     int32_t* col_off = nullptr;     // Ms + 1
     int32_t* list_a = nullptr;      // Ms (columns for the 32-row warp solver)
-    int32_t* list_b = nullptr;      // Ms (columns for the 64-row warp solver)
+    int32_t* tiles_mid = nullptr;   // Ms/32 + 1 (tiles for the 25-node thread tier)
+    int32_t* tiles_big = nullptr;   // Ms/32 + 1 (tiles for the 33-node thread tier)
     int32_t* big_list = nullptr;    // Ms (columns for the CTA solver)
     int32_t* scan_sums = nullptr;   // per-block partial sums of the scans
     int32_t* counters = nullptr;    // CNT_N

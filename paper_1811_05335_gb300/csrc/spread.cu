@@ -6,20 +6,22 @@
 
 namespace {
 
-// One thread per grid point: a segmented gather, deterministic and atomic-free.
-// In the fp32 path, "wide" columns (large ||b_l||_1, cancelling terms) use the
-// fp64 weights and an fp64 accumulator; the fp64 path always does.
+// Spreading of the fp32 path.  A CTA owns SPREAD_COLS consecutive grid points:
+// their weights are one contiguous block of B_opt's storage and their nodes one
+// contiguous (wrapping) range of sorted nodes, so both are staged in shared
+// memory with coalesced loads before each thread sums its own column.  Columns
+// with large ||b_l||_1 ("wide", cancelling terms) use the fp64 weights and an
+// fp64 accumulator.  A CTA whose block does not fit falls back to direct loads.
+constexpr int SPREAD_COLS = 256;
+constexpr int SPREAD_WMAX = 8192;     // staged weights per CTA (32 KB)
+constexpr int SPREAD_UMAX = 2048;     // staged node values per CTA (16 KB)
+
 template <typename T>
-__global__ void k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32,
-                         const double* __restrict__ w64, const uint8_t* __restrict__ wide,
-                         const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
-                         const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N,
-                         int Ms, cplx_t<T>* __restrict__ g) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= Ms) return;
-    const int n = col_count[p], s = col_start[p], off = col_off[p];
+INFFT_D cplx_t<T> spread_direct(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32,
+                                const double* __restrict__ w64, bool wide_col, const int32_t* __restrict__ perm,
+                                int n, int s, int off, int N) {
     int q = s;
-    if (sizeof(T) == 8 || wide[p]) {
+    if (sizeof(T) == 8 || wide_col) {
         double re = 0, im = 0;
         for (int i = 0; i < n; ++i) {
             const double wi = w64[off + i];
@@ -28,18 +30,90 @@ __global__ void k_spread(const cplx_t<T>* __restrict__ f, const float* __restric
             im += wi * (double)v.y;
             if (++q == N) q = 0;
         }
-        g[p] = cmake((T)re, (T)im);
-    } else {
-        float re = 0, im = 0;
-        for (int i = 0; i < n; ++i) {
-            const float wi = w32[off + i];
-            const cplx_t<T> v = f[perm[q]];
-            re += wi * (float)v.x;
-            im += wi * (float)v.y;
-            if (++q == N) q = 0;
-        }
-        g[p] = cmake((T)re, (T)im);
+        return cmake((T)re, (T)im);
     }
+    float re = 0, im = 0;
+    for (int i = 0; i < n; ++i) {
+        const float wi = w32[off + i];
+        const cplx_t<T> v = f[perm[q]];
+        re += wi * (float)v.x;
+        im += wi * (float)v.y;
+        if (++q == N) q = 0;
+    }
+    return cmake((T)re, (T)im);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SPREAD_COLS)
+k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32, const double* __restrict__ w64,
+         const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
+         const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
+         cplx_t<T>* __restrict__ g) {
+    __shared__ __align__(16) float ws[SPREAD_WMAX];
+    __shared__ cplx_t<T> fu[sizeof(T) == 4 ? SPREAD_UMAX : 1];
+    const int p0 = blockIdx.x * SPREAD_COLS;
+    const int p = p0 + threadIdx.x;
+    const int plast = min(p0 + SPREAD_COLS, Ms) - 1;
+    const bool live = p < Ms;
+    const int n = live ? col_count[p] : 0;
+    const int s = live ? col_start[p] : 0;
+    const int off = live ? col_off[p] : 0;
+    const bool wide_col = live && wide[p];
+    // the block's weights [w0, w1) and nodes [S, S + U) (mod N)
+    const int w0 = col_off[p0], w1 = col_off[plast + 1];
+    const int S = col_start[p0];
+    int U = 0;
+    {
+        int e = col_start[plast] + col_count[plast] - S;
+        if (e < 0) e += N;
+        U = e;
+    }
+    int r0 = s - S;
+    if (r0 < 0) r0 += N;
+    // every column's nodes must lie in the staged window (an empty first column need not bound it)
+    const int inside = !live || n == 0 || (r0 + n <= U);
+    const bool staged = __syncthreads_and(inside) && sizeof(T) == 4 && (w1 - w0) <= SPREAD_WMAX &&
+                        U <= SPREAD_UMAX && U <= N;
+    if (!staged) {
+        if (live) g[p] = spread_direct<T>(f, w32, w64, wide_col, perm, n, s, off, N);
+        return;
+    }
+    // weights: 16-byte vector loads of the aligned part, scalar edges
+    {
+        const int a0 = (w0 + 3) & ~3, a1 = w1 & ~3;
+        if (a0 < a1) {
+            const float4* src = (const float4*)(w32 + a0);
+            for (int v = threadIdx.x; v < (a1 - a0) / 4; v += SPREAD_COLS) {
+                const float4 t = src[v];
+                const int d = a0 - w0 + 4 * v;
+                ws[d] = t.x; ws[d + 1] = t.y; ws[d + 2] = t.z; ws[d + 3] = t.w;
+            }
+            for (int i = w0 + threadIdx.x; i < a0; i += SPREAD_COLS) ws[i - w0] = w32[i];
+            for (int i = a1 + threadIdx.x; i < w1; i += SPREAD_COLS) ws[i - w0] = w32[i];
+        } else {
+            for (int i = w0 + threadIdx.x; i < w1; i += SPREAD_COLS) ws[i - w0] = w32[i];
+        }
+    }
+    for (int q = threadIdx.x; q < U; q += SPREAD_COLS) {
+        int gq = S + q;
+        if (gq >= N) gq -= N;
+        fu[q] = f[perm[gq]];
+    }
+    __syncthreads();
+    if (!live) return;
+    if (wide_col) {
+        g[p] = spread_direct<T>(f, w32, w64, true, perm, n, s, off, N);
+        return;
+    }
+    const float* wc = ws + (off - w0);
+    float re = 0, im = 0;
+    for (int i = 0; i < n; ++i) {
+        const float wi = wc[i];
+        const cplx_t<T> v = fu[r0 + i];
+        re += wi * (float)v.x;
+        im += wi * (float)v.y;
+    }
+    g[p] = cmake((T)re, (T)im);
 }
 
 // One thread per sorted node: gathers from the 2m (or 2m+1) grid points of I(x_j).
@@ -81,7 +155,7 @@ template <typename T>
 cudaError_t run_spread(Plan* p, const void* f, cudaStream_t s) {
     const int Ms = (int)p->Ms;
     launch_begin(p, sizeof(T) == 4 ? "spread" : "spread_z", s);
-    k_spread<T><<<(Ms + 255) / 256, 256, 0, s>>>((const cplx_t<T>*)f, p->w32, p->w64, p->wide, p->perm, p->col_start,
+    k_spread<T><<<(Ms + SPREAD_COLS - 1) / SPREAD_COLS, SPREAD_COLS, 0, s>>>((const cplx_t<T>*)f, p->w32, p->w64, p->wide, p->perm, p->col_start,
                                                   p->col_count, p->col_off, (int)p->N, Ms,
                                                   (cplx_t<T>*)p->grid);
     launch_end(p, s);
