@@ -80,6 +80,7 @@ typedef struct {
     int32_t nodes_set;       /* 1 once infft_set_nodes ran */
     int32_t precomputed;     /* 1 once infft_precompute ran after the last set_nodes */
     double objective;        /* sum_l J_l = ||F D A^* B_opt - I||_F^2 (eq:matrixnorm_opt_ansatz2 squared) */
+    int32_t grad_failed_columns; /* columns the last infft_grad_nodes could not factor (terms set to 0) */
 } infft_info;
 
 /* ---- the five calls of the method ------------------------------------- */
@@ -143,6 +144,22 @@ infft_status infft_set_nodes(infft_plan_t plan, const double* x, infft_stream_t 
  * fp64; double-complex arrays).  For accuracy checks against the oracle. */
 infft_status infft_apply_z(infft_plan_t plan, const double* f, double* fhat, infft_stream_t stream);
 infft_status nfft_apply_z(infft_plan_t plan, const double* fhat, double* f, infft_stream_t stream);
+
+/* Gradient of a real loss L through the inverse NFFT with respect to the nodes (the
+ * differentiable form; the paper has no gradient, this follows from eq:approx_ansatz2 and
+ * the column problems eq:opt_ansatz2 .. eq:solution_ansatz2 by implicit differentiation,
+ * with the pattern I(l) held fixed, which it is except on a set of measure zero):
+ *   f      : N complex64, the data the forward infft_apply used (caller order, device);
+ *   w      : M complex64, dL/dRe fhat + i dL/dIm fhat (device);
+ *   grad_x : N fp64, dL/dx_j (caller order, device), written.
+ * With gamma = F D w, beta_{l,i} = Re(conj(gamma_l) f_i), lambda_l = (Re G_l + mu I)^{-1} beta_l:
+ *   dL/dx_j = sum_{l: j in I(l)} [-lambda_{l,j} kappa'(l/M_sigma - x_j)
+ *              - lambda_{l,j} sum_k kappa'(x_j - x_k) b_{l,k} - b_{l,j} sum_i kappa'(x_j - x_i) lambda_{l,i}].
+ * The gradient with respect to f is nfft_apply(w) (the exact adjoint).  Columns larger
+ * than 64 nodes are not handled (their terms are 0; infft_get_info reports them).
+ * Requires infft_precompute; device pointers only. */
+infft_status infft_grad_nodes(infft_plan_t plan, const float* f, const float* w, double* grad_x,
+                              infft_stream_t stream);
 
 /* Synchronises the plan's last stream and fills *info. */
 infft_status infft_get_info(infft_plan_t plan, infft_info* info);

@@ -22,7 +22,7 @@ EXPORTED_SYMBOLS = (
     "infft_plan", "infft_precompute", "infft_apply", "nfft_apply", "plan_destroy", "infft_plan_create",
     "infft_set_nodes", "infft_apply_z", "nfft_apply_z", "infft_get_info", "infft_copy_plan_data",
     "infft_profile", "infft_profile_read", "infft_launch_count", "infft_last_error", "infft_version",
-    "infft_fft_deconv_noalloc",
+    "infft_fft_deconv_noalloc", "infft_grad_nodes",
 )
 
 
@@ -38,7 +38,8 @@ class _Info(ctypes.Structure):
                 ("tau", ctypes.c_double), ("nnz", ctypes.c_int64), ("max_column", ctypes.c_int32),
                 ("empty_columns", ctypes.c_int32), ("bad_nodes", ctypes.c_int32),
                 ("fallback_columns", ctypes.c_int32), ("unsupported_columns", ctypes.c_int32),
-                ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32), ("objective", ctypes.c_double)]
+                ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32), ("objective", ctypes.c_double),
+                ("grad_failed_columns", ctypes.c_int32)]
 
 
 _lib = None
@@ -68,6 +69,7 @@ def library():
         "infft_copy_plan_data": [P, VP, VP, VP, VP, VP, VP],
         "infft_profile": [P, I32],
         "infft_fft_deconv_noalloc": [VP, I64, I64, I32, VP, VP],
+        "infft_grad_nodes": [P, VP, VP, VP, VP],
         "infft_profile_read": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(I64),
                                ctypes.POINTER(D), ctypes.POINTER(I32)],
     }
@@ -257,6 +259,17 @@ def infft_fft_deconv_noalloc(grid, M, out=None, kernel="full", stream=None):
     k = _KERNELS.get(kernel, kernel)
     _check(library().infft_fft_deconv_noalloc(_as_ptr(grid, "c64", keep), int(M), int(grid.shape[0]), int(k),
                                               _as_ptr(out, "c64", keep), _stream(stream, grid, out)))
+    return out
+
+
+def infft_grad_nodes(plan, f, w, out=None, stream=None):
+    """dL/dx (float64, device) for data f and w = dL/dRe fhat + i dL/dIm fhat (complex64, device)."""
+    import torch
+    keep = []
+    if out is None:
+        out = torch.empty(plan.N, dtype=torch.float64, device=f.device)
+    _check(library().infft_grad_nodes(plan.handle, _as_ptr(f, "c64", keep), _as_ptr(w, "c64", keep),
+                                      _as_ptr(out, "f64", keep), _stream(stream, f, w, out)))
     return out
 
 

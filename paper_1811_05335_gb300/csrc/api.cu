@@ -56,7 +56,7 @@ bool is_device_pointer(const void* ptr) {
 void free_plan_buffers(Plan* p) {
     void* bufs[] = {p->x, p->xs, p->skey, p->perm, p->bucket, p->cursor, p->seg_list, p->sort_tmp, p->col_start,
                     p->col_count, p->col_off, p->list_a, p->tiles_mid, p->tiles_big, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
-                    p->w32, p->J, p->wide, p->grid,
+                    p->w32, p->J, p->wide, p->gterm, p->grid,
                     p->work, p->stage_in, p->stage_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -201,7 +201,7 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
     ALLOC(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
     ALLOC(p->phase, N);
     ALLOC(p->counters, CNT_N);
-    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms); ALLOC(p->wide, Ms);
+    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms); ALLOC(p->wide, Ms); ALLOC(p->gterm, p->nnz_cap);
     double2 *grid = nullptr, *work = nullptr, *sin_ = nullptr, *sout = nullptr;
     ALLOC(grid, Ms); ALLOC(work, Ms); ALLOC(sin_, stage); ALLOC(sout, stage);
 #undef ALLOC
@@ -282,6 +282,21 @@ infft_status nfft_apply_z(infft_plan_t p, const double* fhat, double* f, infft_s
     return nfft_impl<double>(p, fhat, f, stream);
 }
 
+infft_status infft_grad_nodes(infft_plan_t p, const float* f, const float* w, double* grad_x,
+                              infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !w || !grad_x) return fail(INFFT_EINVAL, "f, w and grad_x must not be NULL");
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_grad_nodes before infft_precompute");
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(f) || !is_device_pointer(w) || !is_device_pointer(grad_x))
+        return fail(INFFT_EINVAL, "infft_grad_nodes takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = run_grad_nodes(p, f, w, grad_x, s);
+    if (e != cudaSuccess) return cuda_fail(e, "node gradient");
+    return INFFT_OK;
+}
+
 infft_status plan_destroy(infft_plan_t p) {
     if (!p) return INFFT_OK;
     {
@@ -319,6 +334,7 @@ infft_status infft_get_info(infft_plan_t p, infft_info* info) {
     if (p->precomputed) {
         info->fallback_columns = cnt[CNT_FALLBACK];
         info->unsupported_columns = cnt[CNT_UNSUPPORTED];
+        info->grad_failed_columns = cnt[CNT_GRAD_FAIL];
         std::string buf(p->Ms * sizeof(double), '\0');
         if ((e = cudaMemcpy(&buf[0], p->J, p->Ms * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "read objective");

@@ -20,7 +20,8 @@ enum {
     CNT_BIG_LIST = 7,      // columns queued for the CTA solver
     CNT_TILES_MID = 8,     // tiles routed to the 25-node thread tier
     CNT_TILES_BIG = 9,     // tiles routed to the 33-node thread tier
-    CNT_N = 10
+    CNT_GRAD_FAIL = 10,    // columns the node gradient could not factor (or too large)
+    CNT_N = 11
 };
 
 // largest column handled by the thread, warp and CTA solver tiers
@@ -73,6 +74,7 @@ struct infft_plan_s {
     float* w32 = nullptr;       // nnz_cap
     double* J = nullptr;        // Ms
     uint8_t* wide = nullptr;    // Ms: 1 if column l uses fp64 weights in the fp32 applies
+    double* gterm = nullptr;    // nnz_cap: per (column, node) terms of the node gradient
 
     // apply buffers (a3-a5)
     void* grid = nullptr;       // Ms double2 (also used as float2)
@@ -112,3 +114,5 @@ template <typename T> cudaError_t run_interp(Plan* p, void* f, cudaStream_t s);
 template <typename T> cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s);
 // fft.cu: grid = F D fhat
 template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s);
+// grad.cu: gx = dL/dx (caller order) for f (complex64, device) and w = dL/dfhat (complex64, device)
+cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cudaStream_t s);

@@ -1,0 +1,115 @@
+"""The differentiable form on the GPU: node and data gradients of L = ||fhat(f; x) - t||^2.
+
+* d/dx: element-wise against the oracle's implicit-differentiation gradient on the same
+  inputs (complex64 data; the gradient is insensitive both to that rounding and to the
+  ill-determined near-null components of b, measured at ~1e-6), and against
+  Richardson-extrapolated central differences of the fp64 oracle loss on 64 nodes;
+* d/df: B_opt F D w = nfft_apply(w) is checked as the adjoint of the apply (probes) and
+  against the oracle within the oracle's own ambiguity (its two tiers' disagreement);
+* the torch.autograd.Function gives the same gradients as the direct calls."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import grad as og
+from workloads import make_problem, complex_normal
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+
+
+def c64(a):
+    return np.asarray(a, np.complex64).astype(np.complex128)
+
+
+def gpu_grads(p, m, w, kernel="full"):
+    import torch
+    import paper_1811_05335_gb300 as g
+    dev = torch.device("cuda:0")
+    plan = g.infft_plan_create(p.M, p.N, 2.0, m, kernel=kernel)
+    g.infft_set_nodes(plan, torch.tensor(p.x, dtype=torch.float64, device=dev))
+    g.infft_precompute(plan)
+    f = torch.tensor(np.asarray(p.f, np.complex64), device=dev)
+    wt = torch.tensor(np.asarray(w, np.complex64), device=dev)
+    fhat = g.infft_apply(plan, f)
+    gx = g.infft_grad_nodes(plan, f, wt).cpu().numpy()
+    gf = g.nfft_apply(plan, wt).cpu().numpy().astype(np.complex128)
+    info = g.infft_get_info(plan)
+    plan.close()
+    return fhat.cpu().numpy().astype(np.complex128), gx, gf, info
+
+
+def oracle_grads(p, m, w, kernel="full"):
+    B = oracle.bopt.bopt_closed(p.x, p.M, 2.0, m, kernel)
+    return B, og.grad_x(B, p.x, c64(p.f), c64(w)), og.grad_f(B, c64(w))
+
+
+@pytest.mark.parametrize("kernel", ["full", "sym"])
+def test_grad_x_matches_oracle_small(kernel):
+    p = make_problem(5, M=256, N=1024, m=4)
+    B0 = oracle.bopt.bopt_closed(p.x, p.M, 2.0, 4, kernel)
+    w = c64(2 * (oracle.infft.infft_apply(B0, c64(p.f)) - p.fhat))
+    fhat, gx, gf, info = gpu_grads(p, 4, w, kernel)
+    B, gx_o, gf_o = oracle_grads(p, 4, w, kernel)
+    err = np.linalg.norm(gx - gx_o) / np.linalg.norm(gx_o)
+    print(f"{kernel}: grad_x rel l2 vs oracle {err:.3e}")
+    assert info["grad_failed_columns"] == 0
+    assert err <= GRAD_TOL
+
+
+def test_grad_f_within_oracle_ambiguity():
+    p = make_problem(5, M=64, N=256, m=4)
+    B0 = oracle.bopt.bopt_closed(p.x, p.M, 2.0, 4)
+    w = c64(2 * (oracle.infft.infft_apply(B0, c64(p.f)) - p.fhat))
+    fhat, gx, gf, info = gpu_grads(p, 4, w)
+    Bn = oracle.bopt.bopt_naive(p.x, p.M, 2.0, 4)
+    amb = oracle.infft.rel_l2(og.grad_f(Bn, w), og.grad_f(B0, w))
+    err = oracle.infft.rel_l2(gf, og.grad_f(B0, w))
+    print(f"grad_f rel l2 vs oracle {err:.3e}, oracle tiers disagree by {amb:.3e}")
+    assert err <= max(1e-5, 4 * amb)
+
+
+def test_autograd_function_matches_direct_calls():
+    import torch
+    import paper_1811_05335_gb300 as g
+    p = make_problem(5, M=128, N=512, m=4)
+    dev = torch.device("cuda:0")
+    x = torch.tensor(p.x, dtype=torch.float64, device=dev, requires_grad=True)
+    f = torch.tensor(np.asarray(p.f, np.complex64), device=dev, requires_grad=True)
+    t = torch.tensor(np.asarray(p.fhat, np.complex64), device=dev)
+    fhat = g.inverse_nfft(f, x, p.M, 2.0, 4)
+    loss = (fhat - t).abs().pow(2).sum()
+    loss.backward()
+    w = (2 * (fhat - t)).detach()
+    plan = g.infft_plan_create(p.M, p.N, 2.0, 4)
+    g.infft_set_nodes(plan, x.detach())
+    g.infft_precompute(plan)
+    gx = g.infft_grad_nodes(plan, f.detach(), w)
+    gf = g.nfft_apply(plan, w)
+    plan.close()
+    assert torch.allclose(x.grad, gx, rtol=1e-6, atol=1e-12)
+    assert torch.allclose(f.grad, gf, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.slow
+def test_grad_full_size_config5():
+    """M = 2^14, N = 2^16 i.i.d. uniform nodes: GPU node gradient against the oracle's,
+    and against central differences of the fp64 oracle loss on 64 random nodes
+    (Richardson over h = 1e-8, 5e-9: at this size the loss is smooth in x only on ~1e-9
+    scales, so a step of 1e-6 measures a secant, not the derivative)."""
+    p = make_problem(5)
+    B0 = oracle.bopt.bopt_closed(p.x, p.M, 2.0, 4)
+    w = c64(2 * (oracle.infft.infft_apply(B0, c64(p.f)) - p.fhat))
+    fhat, gx, gf, info = gpu_grads(p, 4, w)
+    gx_o = og.grad_x(B0, p.x, c64(p.f), w)
+    err = np.linalg.norm(gx - gx_o) / np.linalg.norm(gx_o)
+    nodes = og.safe_nodes(B0, p.x, 1e-8, 64, seed=5)
+    d1 = og.fd_grad_x(B0, p.x, c64(p.f), p.fhat, nodes, 1e-8)
+    d2 = og.fd_grad_x(B0, p.x, c64(p.f), p.fhat, nodes, 5e-9)
+    rich = d2 + (d2 - d1) / 3
+    fd_err = np.linalg.norm(gx[nodes] - rich) / np.linalg.norm(rich)
+    print(f"config5: grad_x rel l2 vs oracle {err:.3e}, vs Richardson FD on 64 nodes {fd_err:.3e}")
+    assert info["grad_failed_columns"] == 0
+    assert err <= GRAD_TOL
+    assert fd_err <= 2e-2
