@@ -8,6 +8,7 @@ from .binding import (  # noqa: F401
     InfftError, Plan, library, infft_plan, infft_plan_create, infft_set_nodes, infft_precompute,
     infft_apply, nfft_apply, infft_apply_z, nfft_apply_z, plan_destroy, infft_get_info,
     infft_copy_plan_data, infft_profile, infft_profile_read, infft_launch_count, infft_version,
-    infft_fft_deconv_noalloc,
+    infft_fft_deconv_noalloc, infft_grad_nodes,
     EXPORTED_SYMBOLS, KERNEL_FULL, KERNEL_SYM,
 )
+from .autograd import InverseNFFT, inverse_nfft  # noqa: F401
