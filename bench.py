@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--apply-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     return ap.parse_args()
 
 
@@ -310,6 +311,38 @@ def run_gpu(a):
                "h2d_bytes_per_step": int(xh.nbytes + fh_.nbytes), "d2h_bytes_per_step": int(outh.nbytes)}
         plan_h.close()
 
+    # ---- differentiable form (workload 5: M = 2^14, N = 2^16 i.i.d. uniform nodes, m = 4):
+    # forward (the plain single-problem path) and backward (d/df and d/dx) on the same GPU
+    diff = None
+    if not a.no_grad:
+        p5 = make_problem(5, with_data=False, seed=1811053355 + 1000 * rank)
+        x5 = torch.tensor(p5.x, dtype=torch.float64, device=dev)
+        f5 = torch.tensor(np.random.default_rng(11).standard_normal((p5.N, 2)).astype(np.float32)
+                          .view(np.complex64).ravel(), device=dev)
+        w5 = torch.tensor(np.random.default_rng(12).standard_normal((p5.M, 2)).astype(np.float32)
+                          .view(np.complex64).ravel(), device=dev)
+        plan5 = g.infft_plan_create(p5.M, p5.N, 2.0, 4)
+        fh5 = torch.empty(p5.M, dtype=torch.complex64, device=dev)
+        gf5 = torch.empty(p5.N, dtype=torch.complex64, device=dev)
+        gx5 = torch.empty(p5.N, dtype=torch.float64, device=dev)
+
+        def fwd():
+            g.infft_set_nodes(plan5, x5, stream)
+            g.infft_precompute(plan5, stream)
+            g.infft_apply(plan5, f5, fh5, stream)
+
+        def bwd():
+            g.nfft_apply(plan5, w5, gf5, stream)
+            g.infft_grad_nodes(plan5, f5, w5, gx5, stream)
+
+        fwd()
+        t_f = timed(fwd, reps=10)
+        t_b = timed(bwd, reps=10)
+        plan5.close()
+        diff = {"workload": f"1D i.i.d. uniform nodes M={p5.M} N={p5.N} sigma=2 m=4",
+                "forward_ms": t_f, "backward_ms": t_b, "backward_over_forward": t_b / t_f,
+                "unit_note": "forward: pattern + fp64 B_opt + apply; backward: nfft_apply + node gradient"}
+
     # ---- roofline of the dominant kernel and of the apply
     hbm, sm_max, src = peaks()
     ktab = {name: (n, ms) for name, n, ms in kernels}
@@ -353,6 +386,7 @@ def run_gpu(a):
                        "kernel_ms_per_apply": app_kernel_ms, "steps": k_app},
         "fft_vs_cufft": {"own_fft_deconv_ms": own_fft_ms, "cufft_ms": cufft_ms, "length": plan.M_sigma,
                          "note": "own: pruned length-M_sigma FFT with D fused (M outputs); cuFFT: full FFT"},
+        "differentiable": diff,
         "kernels": {name: {"launches": n, "ms_total": ms} for name, n, ms in kernels},
         "plan": {"nnz": info["nnz"], "max_column": info["max_column"], "fallback_columns": info["fallback_columns"]},
         "cpu_baseline": cpu,
