@@ -454,7 +454,370 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     }
 }
 
-// ---------------------------------------------------------------- tier 2/3: warp per column
+// ---------------------------------------------------------------- tiers 2/3: G lanes per column
+
+// A CTA of G warps owns a tile of 32 consecutive columns; G lanes share a column.
+// Thread-per-column triangles of |I(l)| = 25 or 33 leave room for one or two warps
+// per SM, which cannot keep the SM's fp64 pipes busy; with G lanes per column the
+// same shared memory serves G times as many warps.  The factorisation is
+// row-distributed and left-looking: for each pivot column j a lane forms the
+// entries of the rows it owns from row j (a broadcast within the group), the
+// pivot reaches the group by a shuffle, and no cross-lane sum is needed.  r is
+// stored as an extra last row (index NMAX), so its elimination is the forward
+// solve y = L^{-1} r.  The loops run to the warp's largest column Dw; columns of a
+// warp smaller than Dw are padded with identity rows, which leave their solution
+// unchanged, and rows Dw .. NMAX - 1 stay out of the system.  Lane g owns rows
+// NMAX - g - G t (slots t = 0, 1, ...), counted from the bottom: rows finished early
+// sit in the high slots, which drop out of the loop as j passes them, so few issued
+// multiply-adds fall on finished rows, and which lane and slot hold a row is known
+// at compile time.
+constexpr int GS = 33;   // element stride of the interleaved triangles (32 columns + 1 pad)
+
+template <int NMAX> constexpr int aug_doubles() { return (NMAX + 1) * (NMAX + 2) / 2; }
+// the triangles' region rounded up to 16 bytes, so that the double2 phases after it are aligned
+template <int NMAX> constexpr int group_tri_doubles() { return (aug_doubles<NMAX>() * GS + 1) & ~1; }
+template <int NMAX> constexpr size_t group_smem_bytes() {
+    return (size_t)group_tri_doubles<NMAX>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
+           (size_t)(64 + 2 * TILE_UMAX + 8) * sizeof(int);
+}
+
+// 1/sqrt(d) of a Cholesky pivot, and whether d is a positive number inside the fp32
+// normal range (otherwise the pivot counts as failed).  d is rounded to fp32 by
+// integer operations, the hardware fp32 reciprocal square root gives r with relative
+// error below 2^-21, and one Newton step with its second-order term,
+// r (1 - e)^{-1/2} ~ r (1 + e/2 + 3 e^2 / 8) with e = 1 - d r^2, leaves an error of
+// order 3 (e/2)^3 < 2^-60: below fp64 rounding.
+INFFT_D double rsqrt_pivot(double d, bool& ok) {
+    const long long bits = __double_as_longlong(d);
+    const int hi = (int)(bits >> 32);
+    const int ex = hi >> 20;                       // biased exponent (the sign is bit 31 of hi)
+    ok = hi > 0 && ex >= 1023 - 126 && ex <= 1023 + 127;
+    const int fb = ((ex - 1023 + 127) << 23) | ((hi & 0xfffff) << 3) | (int)((unsigned long long)bits >> 29 & 7);
+    const float rf = rsqrtf(__int_as_float(ok ? fb : 0x3f800000));
+    const int rb = __float_as_int(rf);
+    const int rhi = ((((rb >> 23) & 0xff) - 127 + 1023) << 20) | ((rb & 0x7fffff) >> 3);
+    double r = __hiloint2double(rhi, (int)((unsigned)rb << 29));
+    const double h = d * r;
+    const double e = fma(-h, r, 1.0);
+    const double t = fma(e, 0.375, 0.5);
+    return fma(r * e, t, r);
+}
+
+// Left-looking Cholesky of the augmented triangle (rows 0 .. Dw - 1 and the r row NMAX)
+// of one column, G lanes per column.  rowo[t]: element offset of row NMAX - g - G t
+// (row 0 where that is negative).  Rows of L overwrite the matrix, reciprocal pivots
+// the diagonal.  Returns false on a failed pivot (the same on all lanes of a group).
+template <int NMAX, int G, int R>
+INFFT_D bool group_factor(double* Tc, int g, int gbase, int Dw, const int (&rowo)[R]) {
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < Dw) {
+            double acc[R];
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (NMAX - G * t >= j) acc[t] = Tc[rowo[t] + j * GS];   // slot holds rows >= j
+#pragma unroll
+            for (int k = 0; k < j; ++k) {
+                const double ljk = Tc[(trow(j) + k) * GS];
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+                    if (NMAX - G * t >= j) acc[t] = fma(-Tc[rowo[t] + k * GS], ljk, acc[t]);
+            }
+            // row j: lane (NMAX - j) % G, slot (NMAX - j) / G
+            const double dj = __shfl_sync(0xffffffffu, acc[(NMAX - j) / G], gbase + (NMAX - j) % G);
+            bool okj;
+            const double rp = rsqrt_pivot(dj, okj);
+            ok = ok && okj;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                if (NMAX - G * t >= j) {
+                    const int i = NMAX - g - G * t;
+                    if (i > j) Tc[rowo[t] + j * GS] = acc[t] * rp;
+                }
+            }
+            if (g == (NMAX - j) % G) Tc[(trow(j) + j) * GS] = rp;
+            __syncwarp();
+        }
+    }
+    return ok;
+}
+
+// Backward solve L^T b = y by columns of L^T: bacc[t] holds y of row NMAX - g - G t
+// on entry and b on exit; colo[t] = max(NMAX - g - G t, 0) * GS.
+template <int NMAX, int G, int R>
+INFFT_D void group_backsolve(const double* Tc, int g, int gbase, int Dw, const int (&colo)[R], double (&bacc)[R]) {
+#pragma unroll
+    for (int i = NMAX - 1; i >= 0; --i) {
+        if (i < Dw) {
+            const double rp = Tc[(trow(i) + i) * GS];
+            const int ti = (NMAX - i) / G, gi = (NMAX - i) % G;
+            const double bi = __shfl_sync(0xffffffffu, bacc[ti] * rp, gbase + gi);
+            if (g == gi) bacc[ti] = bi;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                if (NMAX - G * t - (G - 1) < i) {                        // slot holds rows < i
+                    const int k = NMAX - g - G * t;
+                    if (k < i && k >= 0) bacc[t] = fma(-Tc[trow(i) * GS + colo[t]], bi, bacc[t]);
+                }
+            }
+        }
+    }
+}
+
+// A column's augmented system evaluated directly from the sorted nodes (tiles whose
+// union does not fit, and retries with a larger mu), rows and r entries split over
+// the G lanes: Re G_l + mu I for rows < n, identity rows for n <= i < Dw, r in row NMAX.
+template <int NMAX, int G>
+INFFT_D void group_fill_direct(double* Tc, int g, int n, int Dw, int s, const double* __restrict__ xs,
+                               const double2* __restrict__ ph, int N, double tl, double2 pl, double mu,
+                               const KernelParams& kp) {
+    for (int i = g; i < Dw; i += G) {
+        if (i < n) {
+            int qi = s + i;
+            if (qi >= N) qi -= N;
+            const double xi = xs[qi];
+            const double2 pi = ph[qi];
+            int qk = s;
+            for (int k = 0; k < i; ++k) {
+                Tc[(trow(i) + k) * GS] = re_kappa(xi, xs[qk], pi, ph[qk], kp);
+                if (++qk == N) qk = 0;
+            }
+            Tc[(trow(i) + i) * GS] = kp.diag + mu;
+        } else {
+            for (int k = 0; k < i; ++k) Tc[(trow(i) + k) * GS] = 0.0;
+            Tc[(trow(i) + i) * GS] = 1.0;
+        }
+    }
+    for (int k = g; k < Dw; k += G) {
+        double r = 0.0;
+        if (k < n) {
+            int q = s + k;
+            if (q >= N) q -= N;
+            r = re_kappa(tl, xs[q], pl, ph[q], kp);
+        }
+        Tc[(trow(NMAX) + k) * GS] = r;
+    }
+}
+
+template <int NMAX, int G>
+__global__ void __launch_bounds__(G * 32, 1)
+k_lsq_group(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
+            const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
+            KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
+            double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ tiles,
+            int tiles_counter, int32_t* __restrict__ counters) {
+    constexpr int C = 32 / G;          // columns per warp
+    constexpr int R = (NMAX + G) / G;  // row slots per lane: rows 0 .. NMAX, from the bottom
+    constexpr int NT = 32 * G;         // threads per CTA
+    static_assert(32 % G == 0, "G divides the warp");
+    static_assert(group_tri_doubles<NMAX>() % 2 == 0 && TILE_UMAX % 2 == 0, "double2 phases 16-byte aligned");
+    extern __shared__ double lsq_smem[];
+    double* T = lsq_smem;                                       // element e of column c at T[e * GS + c]
+    double* ux = T + group_tri_doubles<NMAX>();                 // union x      [TILE_UMAX]
+    double2* up = (double2*)(ux + TILE_UMAX);                   // union phases [TILE_UMAX]
+    int* crs = (int*)(up + TILE_UMAX);                          // tile-relative start per column [32]
+    int* cnn = crs + 32;                                        // size per column [32]
+    int* cfst = cnn + 32;                                       // per union node: first candidate column
+    int* clst = cfst + TILE_UMAX;                               // per union node: last candidate column
+    int* tinfo = clst + TILE_UMAX;                              // S, U, D, tile_ok, near
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int g = lane % G, gbase = lane - g;
+    const int c = wid * C + lane / G;
+    double* Tc = T + c;
+    int rowo[R], colo[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        const int i = max(NMAX - g - G * t, 0);
+        rowo[t] = trow(i) * GS;
+        colo[t] = i * GS;
+    }
+
+    const int ntiles = counters[tiles_counter];
+    for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+        __syncthreads();                  // the previous tile is done with shared memory
+        const int tile = tiles[it];
+        if (wid == 0) {
+            const int p = tile * 32 + lane;
+            const bool live = p < Ms;
+            const int n = live ? col_count[p] : 0;
+            const int s = live ? col_start[p] : 0;
+            const int S = __shfl_sync(0xffffffffu, s, 0);
+            int rs = s - S;
+            if (rs < 0) rs += N;
+            const bool mine = n > 0;
+            int U = mine ? rs + n : 0, D = n;
+            const bool fits = !mine || (rs + n <= TILE_UMAX);
+            for (int o = 16; o; o >>= 1) {
+                U = max(U, __shfl_xor_sync(0xffffffffu, U, o));
+                D = max(D, __shfl_xor_sync(0xffffffffu, D, o));
+            }
+            const bool tile_ok = __all_sync(0xffffffffu, fits) && U <= N && U > 0;
+            crs[lane] = mine ? rs : 0;
+            cnn[lane] = n;
+            if (lane == 0) {
+                tinfo[0] = S;
+                tinfo[1] = U;
+                tinfo[2] = D;
+                tinfo[3] = tile_ok;
+            }
+        }
+        __syncthreads();
+        const int S = tinfo[0], U = tinfo[1], D = tinfo[2];
+        const bool tile_ok = tinfo[3] != 0;
+        if (D > NMAX) {                   // not routed here; kept as a guard
+            if (threadIdx.x == 0) atomicAdd(&counters[CNT_UNSUPPORTED], 1);
+            continue;
+        }
+        const int p = tile * 32 + c;
+        const bool live = p < Ms;
+        const int n = cnn[c], rs = crs[c];
+        const double tl = col_t(p, Ms);
+        const double2 pl = phase_of(kp.M, tl);
+        bool near = false;
+        if (tile_ok) {
+            for (int q = threadIdx.x; q < U; q += NT) {
+                int gq = S + q;
+                if (gq >= N) gq -= N;
+                ux[q] = xs[gq];
+                up[q] = ph[gq];
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < U; q += NT) {
+                int cf = 32, cl = -1;
+                for (int cc = 0; cc < 32; ++cc) {
+                    if (cnn[cc] > 0 && crs[cc] + cnn[cc] > q && cf == 32) cf = cc;
+                    if (cnn[cc] > 0 && crs[cc] <= q) cl = cc;
+                }
+                cfst[q] = cf;
+                clst[q] = cl;
+            }
+            if (wid == 0) {
+                // the near path needs the union and the columns' grid points to lie
+                // within 1/64 of each other without crossing the seam
+                const double x0 = ux[0], x1 = ux[U - 1];
+                const double tq = col_t(tile * 32 + lane, Ms);
+                const bool mine = cnn[lane] > 0;
+                const bool nr = !kp.sym && x1 >= x0 && x1 - x0 <= 1.0 / 64.0 &&
+                                __all_sync(0xffffffffu, !mine || (tq >= x0 - 1.0 / 64.0 && tq <= x1 + 1.0 / 64.0));
+                if (lane == 0) tinfo[4] = nr;
+            }
+            __syncthreads();
+            near = tinfo[4] != 0;
+            // every pair (a, b), a < b < a + D, of the union, evaluated once
+            const int per = D - 1;
+            if (per > 0) {
+                const int pairs = U * per;
+                const int qa = NT / per, ra = NT % per;
+                int a = threadIdx.x / per, off = threadIdx.x % per;
+                for (int e = threadIdx.x; e < pairs; e += NT) {
+                    const int b = a + 1 + off;
+                    if (b < U) {
+                        const int c0 = cfst[b], c1 = clst[a];
+                        if (c0 <= c1) {
+                            const double val = near ? kappa_near(ux[b] - ux[a], up[b], up[a], kp)
+                                                    : re_kappa(ux[b], ux[a], up[b], up[a], kp);
+                            for (int cc = c0; cc <= c1; ++cc) {
+                                const int r0 = crs[cc];
+                                if (r0 <= a && b < r0 + cnn[cc]) T[(trow(b - r0) + (a - r0)) * GS + cc] = val;
+                            }
+                        }
+                    }
+                    a += qa;
+                    off += ra;
+                    if (off >= per) { off -= per; ++a; }
+                }
+            }
+            __syncthreads();
+        }
+        // this warp's largest column: the extent of the (padded) systems
+        int Dw = n;
+        for (int o = 16; o; o >>= 1) Dw = max(Dw, __shfl_xor_sync(0xffffffffu, Dw, o));
+        if (live && n == 0 && g == 0) {
+            Jout[p] = 1.0;
+            wide[p] = 0;
+        }
+        const int s = live ? col_start[p] : 0;
+        double mu = mu0;
+
+        if (tile_ok) {
+            for (int i = g; i < Dw; i += G) {
+                if (i < n) {
+                    Tc[(trow(i) + i) * GS] = kp.diag + mu;
+                } else {
+                    for (int k = 0; k < i; ++k) Tc[(trow(i) + k) * GS] = 0.0;
+                    Tc[(trow(i) + i) * GS] = 1.0;
+                }
+            }
+            for (int k = g; k < Dw; k += G) {
+                double r = 0.0;
+                if (k < n)
+                    r = near ? kappa_near(tl - ux[rs + k], pl, up[rs + k], kp)
+                             : re_kappa(tl, ux[rs + k], pl, up[rs + k], kp);
+                Tc[(trow(NMAX) + k) * GS] = r;
+            }
+        } else {
+            group_fill_direct<NMAX, G>(Tc, g, n, Dw, s, xs, ph, N, tl, pl, mu, kp);
+        }
+        bool need = n > 0;
+        const int off = live ? col_off[p] : 0;
+        for (int attempt = 0; attempt < 3; ++attempt) {
+            if (attempt > 0) {
+                if (!__any_sync(0xffffffffu, need)) break;
+                if (need) {
+                    mu *= 1e3;
+                    group_fill_direct<NMAX, G>(Tc, g, n, Dw, s, xs, ph, N, tl, pl, mu, kp);
+                }
+            }
+            __syncwarp();
+            const bool ok = group_factor<NMAX, G, R>(Tc, g, gbase, Dw, rowo);
+            double bacc[R], ysq = 0.0;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                bacc[t] = Tc[trow(NMAX) * GS + colo[t]];
+                const int k = NMAX - g - G * t;
+                if (k >= 0 && k < n) ysq = fma(bacc[t], bacc[t], ysq);
+            }
+            group_backsolve<NMAX, G, R>(Tc, g, gbase, Dw, colo, bacc);
+            const bool write = need && ok;
+            double bsq = 0.0, babs = 0.0;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int k = NMAX - g - G * t;
+                if (write && k >= 0 && k < n) {
+                    w64[off + k] = bacc[t];
+                    w32[off + k] = (float)bacc[t];
+                    bsq = fma(bacc[t], bacc[t], bsq);
+                    babs += fabs(bacc[t]);
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o; o >>= 1) {
+                ysq += __shfl_xor_sync(0xffffffffu, ysq, o);
+                bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+                babs += __shfl_xor_sync(0xffffffffu, babs, o);
+            }
+            if (write && g == 0) {
+                // J_l = ||L b - e_l||^2 = 1 - r.b - mu ||b||^2 at the regularised optimum
+                Jout[p] = 1.0 - ysq - mu * bsq;
+                wide[p] = babs > WIDE_COLUMN_L1;
+                if (mu != mu0) atomicAdd(&counters[CNT_FALLBACK], 1);
+            }
+            if (write) need = false;
+        }
+        if (need) {
+            for (int k = g; k < n; k += G) { w64[off + k] = 0.0; w32[off + k] = 0.0f; }
+            if (g == 0) {
+                Jout[p] = 1.0;
+                wide[p] = 0;
+                atomicAdd(&counters[CNT_FALLBACK], 1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tier 4: warp per column
 
 // One warp per column; lane t owns rows t, t + 32, ... (NMAX / 32 rows).  Columns
 // come from `list` (count at counters[list_counter]).
@@ -757,15 +1120,16 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 148;
 
-    // thread tiers: a tile of 32 consecutive columns goes to the first tier whose
-    // NMAX covers its largest column; tiles above the last go to the warp tier
+    // thread tier: a tile of 32 consecutive columns goes to the first tier whose NMAX
+    // covers its largest column (this kernel routes the others); group tiers: G lanes
+    // per column; tiles above the last go to the warp tier
     constexpr int A1 = LSQ_THREAD_NMAX1, A2 = LSQ_THREAD_NMAX2, A3 = LSQ_THREAD_NMAX3;
-    constexpr int W1 = 5, W2 = 2, W3 = 1, W4 = 4;
+    constexpr int W1 = 5, G2 = LSQ_GROUP_G2, G3 = LSQ_GROUP_G3, W4 = 4;
     auto t1 = k_lsq_thread<A1, W1>;
-    auto t2 = k_lsq_thread<A2, W2>;
-    auto t3 = k_lsq_thread<A3, W3>;
+    auto t2 = k_lsq_group<A2, G2>;
+    auto t3 = k_lsq_group<A3, G3>;
     auto k4 = k_lsq_warp<LSQ_WARP2_NMAX, W4>;
-    const size_t s1 = W1 * tile_warp_bytes<A1>(), s2 = W2 * tile_warp_bytes<A2>(), s3 = W3 * tile_warp_bytes<A3>();
+    const size_t s1 = W1 * tile_warp_bytes<A1>(), s2 = group_smem_bytes<A2>(), s3 = group_smem_bytes<A3>();
     const size_t s4 = warp_smem_bytes<LSQ_WARP2_NMAX, W4>();
     const size_t s5 = (size_t)(CN * (CN + 1) / 2 + 4 * CN) * sizeof(double);
     if ((e = set_smem(t1, s1)) != cudaSuccess) return e;
@@ -774,21 +1138,24 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     if ((e = set_smem(k4, s4)) != cudaSuccess) return e;
     if ((e = set_smem(k_lsq_cta, s5)) != cudaSuccess) return e;
     const int tiles = (Ms + 31) / 32;
+    int occ2 = 1, occ3 = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, t2, G2 * 32, s2)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, t3, G3 * 32, s3)) != cudaSuccess) return e;
+    occ2 = std::max(occ2, 1);
+    occ3 = std::max(occ3, 1);
 
     launch_begin(p, "lsq_thread17", s);
     t1<<<(tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
                                                   kp, mu, p->w64, p->w32, p->J, p->wide, nullptr, 0, p->tiles_mid,
                                                   p->tiles_big, p->list_a, p->counters);
     launch_end(p, s);
-    launch_begin(p, "lsq_thread25", s);
-    t2<<<sms, W2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
-                                p->w32, p->J, p->wide, p->tiles_mid, CNT_TILES_MID, nullptr, nullptr, nullptr,
-                                p->counters);
+    launch_begin(p, "lsq_group25", s);
+    t2<<<occ2 * sms, G2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+                                       p->w64, p->w32, p->J, p->wide, p->tiles_mid, CNT_TILES_MID, p->counters);
     launch_end(p, s);
-    launch_begin(p, "lsq_thread33", s);
-    t3<<<sms, W3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu, p->w64,
-                                p->w32, p->J, p->wide, p->tiles_big, CNT_TILES_BIG, nullptr, nullptr, nullptr,
-                                p->counters);
+    launch_begin(p, "lsq_group33", s);
+    t3<<<occ3 * sms, G3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
+                                       p->w64, p->w32, p->J, p->wide, p->tiles_big, CNT_TILES_BIG, p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // warp tier: columns of tiles whose largest column exceeds the thread tiers, |I(l)| <= 64

@@ -29,6 +29,8 @@ constexpr int LSQ_THREAD_NMAX1 = 17;
 constexpr int LSQ_THREAD_NMAX2 = 25;
 constexpr int LSQ_THREAD_NMAX3 = 33;
 constexpr int LSQ_WARP2_NMAX = 64;
+constexpr int LSQ_GROUP_G2 = 4;      // lanes per column in the <= 25 tier
+constexpr int LSQ_GROUP_G3 = 8;      // lanes per column in the <= 33 tier
 constexpr int LSQ_CTA_NMAX = 224;
 
 // Columns whose ||b_l||_1 exceeds this are spread and interpolated with fp64

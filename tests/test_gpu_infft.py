@@ -36,12 +36,15 @@ def problem(name):
     if name == "jit_small":          # M_sigma = 2048: single-CTA FFT
         p = make_problem(2, M=1024, N=4096, m=4)
         return p.x, p.f, p.M, 2.0, 4, "full"
-    if name == "jit_fourstep":       # M_sigma = 8192: four-step FFT
+    if name == "jit_fourstep":       # M_sigma = 8192: four-step FFT; |I(l)| = 25: group tier
         p = make_problem(2, M=4096, N=16384, m=6)
         return p.x, p.f, p.M, 2.0, 6, "full"
-    if name == "jit_m8":             # |I(l)| = 31..33: warp tiers 1 and 2
+    if name == "jit_m8":             # |I(l)| = 33: group tier, 4 lanes per column
         p = make_problem(2, M=2048, N=8192, m=8)
         return p.x, p.f, p.M, 2.0, 8, "full"
+    if name == "unif_m4":            # i.i.d. uniform nodes: column sizes mixed within tiles, every tier
+        p = make_problem(5, M=2048, N=8192, m=4)
+        return p.x, p.f, p.M, 2.0, 4, "full"
     if name == "cheb":               # |I(l)| up to ~86: CTA tier
         x = chebyshev_jittered(11, 768)
         fh = complex_normal(12, 256)
@@ -64,7 +67,7 @@ def problem(name):
     raise KeyError(name)
 
 
-CASES = ["cfg1", "jit_small", "jit_fourstep", "jit_m8", "cheb", "cheb_big", "ragged", "sigma1", "sym"]
+CASES = ["cfg1", "jit_small", "jit_fourstep", "jit_m8", "unif_m4", "cheb", "cheb_big", "ragged", "sigma1", "sym"]
 _cache = {}
 
 
