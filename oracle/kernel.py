@@ -79,6 +79,24 @@ def re_kappa_closed(t, M, Ms, kernel):
     return v / Ms
 
 
+def kappa_closed(t, M, Ms, kernel):
+    """kappa(t) (complex) in closed form, the geometric sum over the kept k:
+
+    full: (1/M_sigma) exp(-i pi t) sin(pi M t) / sin(pi t), value M/M_sigma at t = 0;
+    sym : the real Dirichlet kernel (1/M_sigma) sin(pi (M-1) t) / sin(pi t)
+          (eq:kernel_Dirichlet; Remark remark:Dirichlet_ansatz1 uses it for K_j)."""
+    t = _wrap(t)
+    if kernel == "sym":
+        return re_kappa_closed(t, M, Ms, kernel).astype(np.complex128)
+    if kernel != "full":
+        raise ValueError(kernel)
+    s = np.sin(np.pi * t)
+    zero = (t == 0.0)
+    v = np.sin(np.pi * M * t) / np.where(zero, 1.0, s)
+    v = np.where(zero, float(M), v)
+    return np.exp(-1j * np.pi * t) * v / Ms
+
+
 def gram_diag(M, Ms, kernel):
     """Diagonal entry of Re G_l = Re(L_l^* L_l): (#kept frequencies)/M_sigma."""
     return kept(M, kernel).sum() / Ms
