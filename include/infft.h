@@ -66,6 +66,13 @@ typedef enum {
  *   INFFT_KERNEL_SYM : the remark's literal choice, D's k = -M/2 entry set to 0. */
 enum { INFFT_KERNEL_FULL = 0, INFFT_KERNEL_SYM = 1 };
 
+/* Which optimisation fills B (Sec. 3.2): the overdetermined case (Sec. 3.2.2, one
+ * least-squares problem per grid point l, fhat = D^* F^* B_opt^* f, the default) or the
+ * underdetermined case (Sec. 3.2.1, one problem per node x_j,
+ * min ||K_j b - M e_j|| with K_j = A D^* T_j (eq:matrix_Kj), fhat = (1/M) D^* F^* B_opt^* f,
+ * eq:approx_ansatz1). */
+enum { INFFT_ANSATZ_UNDERDETERMINED = 1, INFFT_ANSATZ_OVERDETERMINED = 2 };
+
 /* Diagnostic counters of a plan (infft_get_info synchronises the plan's last stream). */
 typedef struct {
     int64_t M, N, M_sigma;
@@ -79,8 +86,11 @@ typedef struct {
     int32_t unsupported_columns; /* columns larger than the largest solver tier */
     int32_t nodes_set;       /* 1 once infft_set_nodes ran */
     int32_t precomputed;     /* 1 once infft_precompute ran after the last set_nodes */
-    double objective;        /* sum_l J_l = ||F D A^* B_opt - I||_F^2 (eq:matrixnorm_opt_ansatz2 squared) */
+    double objective;        /* overdetermined: sum_l J_l = ||F D A^* B_opt - I||_F^2 (eq:matrixnorm_opt_ansatz2
+                              * squared); underdetermined: sum_j J_j = ||A D^* F^* B_opt^* - M I_N||_F^2
+                              * (eq:matrixnorm_opt_ansatz1 squared) */
     int32_t grad_failed_columns; /* columns the last infft_grad_nodes could not factor (terms set to 0) */
+    int32_t ansatz;          /* INFFT_ANSATZ_OVERDETERMINED or INFFT_ANSATZ_UNDERDETERMINED */
 } infft_info;
 
 /* ---- the five calls of the method ------------------------------------- */
@@ -131,6 +141,22 @@ infft_status plan_destroy(infft_plan_t plan);
 infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int kernel,
                                double tau, infft_plan_t* out);
 
+/* As infft_plan_create, with the choice of optimisation (INFFT_ANSATZ_OVERDETERMINED,
+ * which infft_plan_create makes, or INFFT_ANSATZ_UNDERDETERMINED).  For the
+ * underdetermined case (Sec. 3.2.1), infft_precompute solves, per node x_j, the
+ * Tikhonov-regularised normal equations
+ *   (Re K_j^* K_j + mu_j I) b_j = M Re(K_j^* e_j),   mu_j = tau * mean diagonal entry,
+ * of min ||K_j b - M e_j||_2^2 over real b (eq:opt_ansatz1, eq:solution_ansatz1), b_j on
+ * the 2m or 2m+1 grid points of I(x_j) (eq:set_xj).  Re K_j^* K_j sums over all N nodes;
+ * it is formed from the node moments sum_h exp(2 pi i n x_h), |n| < M (fp64, O(N M)), and
+ * one fp64 FFT of length M_sigma per offset of two grid points (2m+1 of them).  The plan
+ * stores B_opt / M, so infft_apply returns (1/M) D^* F^* B_opt^* f (eq:approx_ansatz1) and
+ * nfft_apply returns (1/M) B_opt F D fhat, the inverse adjoint estimate of Remark
+ * remark:ansatz1_adj when fhat = A^* f.  The underdetermined case requires 2m+1 <= 17
+ * (INFFT_EUNSUPPORTED otherwise) and has no infft_grad_nodes (INFFT_EUNSUPPORTED). */
+infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m, int kernel,
+                                      int ansatz, double tau, infft_plan_t* out);
+
 /* The pattern step (eq:set_l): copies x (N fp64, host or device), sorts the
  * nodes by grid cell and derives, for every grid point l, I(l) as a contiguous
  * (wrapping) range of sorted nodes.  A node belongs to I(l) iff
@@ -169,7 +195,9 @@ infft_status infft_get_info(infft_plan_t plan, infft_info* info);
  * col_start[p] = first sorted position of I(l), col_count[p] = |I(l)| (M_sigma
  * each, p = l + M_sigma/2; the range wraps modulo N); col_offset[p] = offset of
  * column p's weights (M_sigma + 1); weights[col_offset[p] + i] = b_{l, perm[(col_start[p] + i) mod N]}
- * in fp64 (nnz); objective[p] = J_l = ||L_l b_l - e_l||^2 (M_sigma). */
+ * in fp64 (nnz); objective[p] = J_l = ||L_l b_l - e_l||^2 (M_sigma).  Underdetermined
+ * plans: the weights are B_opt / M and objective[j] = J_j = ||K_j b_j - M e_j||^2 in the
+ * caller's node order (N). */
 infft_status infft_copy_plan_data(infft_plan_t plan, int32_t* perm, int32_t* col_start,
                                   int32_t* col_count, int32_t* col_offset, double* weights,
                                   double* objective);

@@ -1,4 +1,4 @@
-"""GB300-native direct inverse NFFT (Kircheis & Potts, Sec. 3.2.2).
+"""GB300-native direct inverse NFFT (Kircheis & Potts, Sec. 3.2.1 and 3.2.2).
 
 Thin Python binding of the C ABI in include/infft.h: argument marshalling only.
 Every numerical step runs in the CUDA kernels of libinfft_gb300.so; importing a
@@ -8,7 +8,7 @@ from .binding import (  # noqa: F401
     InfftError, Plan, library, infft_plan, infft_plan_create, infft_set_nodes, infft_precompute,
     infft_apply, nfft_apply, infft_apply_z, nfft_apply_z, plan_destroy, infft_get_info,
     infft_copy_plan_data, infft_profile, infft_profile_read, infft_launch_count, infft_version,
-    infft_fft_deconv_noalloc, infft_grad_nodes,
-    EXPORTED_SYMBOLS, KERNEL_FULL, KERNEL_SYM,
+    infft_fft_deconv_noalloc, infft_grad_nodes, infft_plan_create_ansatz,
+    EXPORTED_SYMBOLS, KERNEL_FULL, KERNEL_SYM, ANSATZ_UNDERDETERMINED, ANSATZ_OVERDETERMINED,
 )
 from .autograd import InverseNFFT, inverse_nfft  # noqa: F401

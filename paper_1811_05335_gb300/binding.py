@@ -22,7 +22,7 @@ EXPORTED_SYMBOLS = (
     "infft_plan", "infft_precompute", "infft_apply", "nfft_apply", "plan_destroy", "infft_plan_create",
     "infft_set_nodes", "infft_apply_z", "nfft_apply_z", "infft_get_info", "infft_copy_plan_data",
     "infft_profile", "infft_profile_read", "infft_launch_count", "infft_last_error", "infft_version",
-    "infft_fft_deconv_noalloc", "infft_grad_nodes",
+    "infft_fft_deconv_noalloc", "infft_grad_nodes", "infft_plan_create_ansatz",
 )
 
 
@@ -39,7 +39,7 @@ class _Info(ctypes.Structure):
                 ("empty_columns", ctypes.c_int32), ("bad_nodes", ctypes.c_int32),
                 ("fallback_columns", ctypes.c_int32), ("unsupported_columns", ctypes.c_int32),
                 ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32), ("objective", ctypes.c_double),
-                ("grad_failed_columns", ctypes.c_int32)]
+                ("grad_failed_columns", ctypes.c_int32), ("ansatz", ctypes.c_int32)]
 
 
 _lib = None
@@ -58,6 +58,7 @@ def library():
     sig = {
         "infft_plan": [I64, I64, VP, D, I32, ctypes.POINTER(P)],
         "infft_plan_create": [I64, I64, D, I32, I32, D, ctypes.POINTER(P)],
+        "infft_plan_create_ansatz": [I64, I64, D, I32, I32, I32, D, ctypes.POINTER(P)],
         "infft_set_nodes": [P, VP, VP],
         "infft_precompute": [P, VP],
         "infft_apply": [P, VP, VP, VP],
@@ -172,6 +173,23 @@ def infft_plan_create(M, N, sigma, m, kernel="full", tau=1e-12):
     return Plan(h.value, M, N, _ms(M, sigma), m)
 
 
+ANSATZ_UNDERDETERMINED, ANSATZ_OVERDETERMINED = 1, 2
+_ANSATZ = {"under": ANSATZ_UNDERDETERMINED, "underdetermined": ANSATZ_UNDERDETERMINED,
+           "over": ANSATZ_OVERDETERMINED, "overdetermined": ANSATZ_OVERDETERMINED}
+
+
+def infft_plan_create_ansatz(M, N, sigma, m, kernel="full", ansatz="over", tau=1e-12):
+    """As infft_plan_create with the optimisation of Sec. 3.2.1 ("under") or 3.2.2 ("over")."""
+    h = ctypes.c_void_p()
+    k = _KERNELS.get(kernel, kernel) if isinstance(kernel, (str, int)) else kernel
+    a = _ANSATZ.get(ansatz, ansatz)
+    _check(library().infft_plan_create_ansatz(M, N, float(sigma), int(m), int(k), int(a), float(tau),
+                                              ctypes.byref(h)))
+    plan = Plan(h.value, M, N, _ms(M, sigma), m)
+    plan.ansatz = int(a)
+    return plan
+
+
 def infft_set_nodes(plan, x, stream=None):
     keep = []
     _check(library().infft_set_nodes(plan.handle, _as_ptr(x, "f64", keep), _stream(stream, x)))
@@ -226,7 +244,8 @@ def infft_copy_plan_data(plan, weights=True):
     count = np.empty(Ms, np.int32)
     off = np.empty(Ms + 1, np.int32)
     w = np.empty(max(nnz, 1), np.float64) if weights else None
-    J = np.empty(Ms, np.float64) if weights else None
+    nJ = N if info.get("ansatz") == ANSATZ_UNDERDETERMINED else Ms
+    J = np.empty(nJ, np.float64) if weights else None
     ptr = lambda a: a.ctypes.data if a is not None else None
     _check(library().infft_copy_plan_data(plan.handle, ptr(perm), ptr(start), ptr(count), ptr(off), ptr(w),
                                           ptr(J)))

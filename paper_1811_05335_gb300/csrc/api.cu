@@ -57,10 +57,14 @@ void free_plan_buffers(Plan* p) {
     void* bufs[] = {p->x, p->xs, p->skey, p->perm, p->bucket, p->cursor, p->seg_list, p->sort_tmp, p->col_start,
                     p->col_count, p->col_off, p->list_a, p->tiles_mid, p->tiles_big, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
                     p->w32, p->J, p->wide, p->gterm, p->grid,
-                    p->work, p->stage_in, p->stage_out};
+                    p->work, p->stage_in, p->stage_out, p->under_step, p->under_part, p->under_mom,
+                    p->under_S};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
+
+// entries of the objective: one per grid point (overdetermined) or per node (underdetermined)
+int64_t objective_count(const Plan* p) { return p->ansatz == INFFT_ANSATZ_UNDERDETERMINED ? p->N : p->Ms; }
 
 template <typename X> cudaError_t dalloc(X** ptr, size_t count) {
     return cudaMalloc((void**)ptr, count * sizeof(X) + 16);
@@ -180,15 +184,26 @@ extern "C" {
 
 infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int kernel, double tau,
                                infft_plan_t* out) {
+    return infft_plan_create_ansatz(M, N, sigma, m, kernel, INFFT_ANSATZ_OVERDETERMINED, tau, out);
+}
+
+infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m, int kernel, int ansatz,
+                                      double tau, infft_plan_t* out) {
     if (!out) return fail(INFFT_EINVAL, "out is NULL");
     *out = nullptr;
     int64_t Ms = 0;
     int logMs = 0;
     infft_status st = validate_sizes(M, N, sigma, m, kernel, tau, &Ms, &logMs);
     if (st != INFFT_OK) return st;
+    if (ansatz != INFFT_ANSATZ_OVERDETERMINED && ansatz != INFFT_ANSATZ_UNDERDETERMINED)
+        return fail(INFFT_EINVAL, "ansatz must be INFFT_ANSATZ_OVERDETERMINED or INFFT_ANSATZ_UNDERDETERMINED (got %d)",
+                    ansatz);
+    if (ansatz == INFFT_ANSATZ_UNDERDETERMINED && 2 * m + 1 > UNDER_NMAX)
+        return fail(INFFT_EUNSUPPORTED, "underdetermined case: 2m+1 = %d exceeds %d", 2 * m + 1, UNDER_NMAX);
     Plan* p = new Plan();
     cudaGetDevice(&p->device);
     p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
+    p->ansatz = ansatz;
     p->logMs = logMs;
     p->nnz_cap = N * (2 * (int64_t)m + 1);
     const int64_t stage = (N > M ? N : M);
@@ -201,7 +216,13 @@ infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int ke
     ALLOC(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
     ALLOC(p->phase, N);
     ALLOC(p->counters, CNT_N);
-    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms); ALLOC(p->wide, Ms); ALLOC(p->gterm, p->nnz_cap);
+    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms > N ? Ms : N); ALLOC(p->wide, Ms); ALLOC(p->gterm, p->nnz_cap);
+    if (ansatz == INFFT_ANSATZ_UNDERDETERMINED) {
+        double2 *ustep = nullptr, *upart = nullptr, *umom = nullptr, *uS = nullptr;
+        ALLOC(ustep, N); ALLOC(upart, (int64_t)under_moment_chunks(N) * M); ALLOC(umom, M);
+        ALLOC(uS, (2 * (int64_t)m + 1) * Ms);
+        p->under_step = ustep; p->under_part = upart; p->under_mom = umom; p->under_S = uS;
+    }
     double2 *grid = nullptr, *work = nullptr, *sin_ = nullptr, *sout = nullptr;
     ALLOC(grid, Ms); ALLOC(work, Ms); ALLOC(sin_, stage); ALLOC(sout, stage);
 #undef ALLOC
@@ -263,7 +284,7 @@ infft_status infft_precompute(infft_plan_t p, infft_stream_t stream) {
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
-    cudaError_t e = run_precompute(p, s);
+    cudaError_t e = p->ansatz == INFFT_ANSATZ_UNDERDETERMINED ? run_precompute_under(p, s) : run_precompute(p, s);
     if (e != cudaSuccess) return cuda_fail(e, "precompute");
     p->precomputed = 1;
     return INFFT_OK;
@@ -287,6 +308,8 @@ infft_status infft_grad_nodes(infft_plan_t p, const float* f, const float* w, do
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
     if (!f || !w || !grad_x) return fail(INFFT_EINVAL, "f, w and grad_x must not be NULL");
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_grad_nodes before infft_precompute");
+    if (p->ansatz != INFFT_ANSATZ_OVERDETERMINED)
+        return fail(INFFT_EUNSUPPORTED, "infft_grad_nodes: underdetermined plans have no node gradient");
     DeviceGuard g(p->device);
     if (!is_device_pointer(f) || !is_device_pointer(w) || !is_device_pointer(grad_x))
         return fail(INFFT_EINVAL, "infft_grad_nodes takes device pointers only");
@@ -320,6 +343,7 @@ infft_status infft_get_info(infft_plan_t p, infft_info* info) {
     std::memset(info, 0, sizeof *info);
     info->M = p->M; info->N = p->N; info->M_sigma = p->Ms; info->m = p->m; info->kernel = p->kernel;
     info->sigma = p->sigma; info->tau = p->tau;
+    info->ansatz = p->ansatz;
     info->nodes_set = p->nodes_set;
     info->precomputed = p->precomputed;
     if (p->nodes_set) {
@@ -335,12 +359,13 @@ infft_status infft_get_info(infft_plan_t p, infft_info* info) {
         info->fallback_columns = cnt[CNT_FALLBACK];
         info->unsupported_columns = cnt[CNT_UNSUPPORTED];
         info->grad_failed_columns = cnt[CNT_GRAD_FAIL];
-        std::string buf(p->Ms * sizeof(double), '\0');
-        if ((e = cudaMemcpy(&buf[0], p->J, p->Ms * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        const int64_t nJ = objective_count(p);
+        std::string buf(nJ * sizeof(double), '\0');
+        if ((e = cudaMemcpy(&buf[0], p->J, nJ * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "read objective");
         const double* J = (const double*)buf.data();
         double sum = 0.0;
-        for (int64_t i = 0; i < p->Ms; ++i) sum += J[i];
+        for (int64_t i = 0; i < nJ; ++i) sum += J[i];
         info->objective = sum;
     }
     return INFFT_OK;
@@ -361,7 +386,7 @@ infft_status infft_copy_plan_data(infft_plan_t p, int32_t* perm, int32_t* col_st
     if (e == cudaSuccess && col_count) e = cudaMemcpy(col_count, p->col_count, p->Ms * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && col_offset) e = cudaMemcpy(col_offset, p->col_off, (p->Ms + 1) * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && weights) e = cudaMemcpy(weights, p->w64, (size_t)nnz * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && objective) e = cudaMemcpy(objective, p->J, p->Ms * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && objective) e = cudaMemcpy(objective, p->J, objective_count(p) * 8, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "copy plan data");
     return INFFT_OK;
 }

@@ -228,18 +228,19 @@ cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// out_p = scale * sum_{k=-Mb/2}^{Mb/2-1} c_k in[k + Mb/2] exp(2 pi i k (p - M_sigma/2) / M_sigma),
+// p = 0 .. M_sigma-1, for a band of Mb <= M_sigma frequencies (c_k = 0 only at k = -Mb/2 when
+// sym); p->work is the four-step intermediate.
 template <typename T>
-cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s) {
+cudaError_t fft_forward_on(Plan* p, const void* in, void* out, int Mb, T scale, int sym, cudaStream_t s) {
     using C = cplx_t<T>;
-    const int Ms = (int)p->Ms, M = (int)p->M, logMs = p->logMs;
-    const T inv_Ms = (T)1 / (T)Ms;
-    const int sym = p->kernel == INFFT_KERNEL_SYM;
+    const int Ms = (int)p->Ms, logMs = p->logMs;
     cudaError_t e;
     if (Ms <= FFT_SMALL) {
         const size_t smem = 2 * (size_t)Ms * sizeof(C);
         if ((e = allow_smem(k_fft_small_forward<T>, smem)) != cudaSuccess) return e;
         launch_begin(p, sizeof(T) == 4 ? "fft_small_fwd" : "fft_small_fwd_z", s);
-        k_fft_small_forward<T><<<1, FFT_THREADS, smem, s>>>((const C*)fhat, (C*)p->grid, logMs, M, inv_Ms, sym);
+        k_fft_small_forward<T><<<1, FFT_THREADS, smem, s>>>((const C*)in, (C*)out, logMs, Mb, scale, sym);
         launch_end(p, s);
         return cudaGetLastError();
     }
@@ -250,13 +251,22 @@ cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s) {
     if ((e = allow_smem(k_fft_passB<T, 1, false>, smemB)) != cudaSuccess) return e;
     launch_begin(p, sizeof(T) == 4 ? "fft_fwd_passA_deconv" : "fft_fwd_passA_deconv_z", s);
     k_fft_passA<T, 1, true><<<(1 << sp.log2) / sp.CA, FFT_THREADS, smemA, s>>>(
-        (const C*)fhat, (C*)p->work, sp.log1, sp.log2, sp.CA, M, inv_Ms, sym);
+        (const C*)in, (C*)p->work, sp.log1, sp.log2, sp.CA, Mb, scale, sym);
     launch_end(p, s);
     launch_begin(p, sizeof(T) == 4 ? "fft_fwd_passB" : "fft_fwd_passB_z", s);
     k_fft_passB<T, 1, false><<<(1 << sp.log1) / sp.CB, FFT_THREADS, smemB, s>>>(
-        (const C*)p->work, (C*)p->grid, sp.log1, sp.log2, sp.CB, M, inv_Ms, sym);
+        (const C*)p->work, (C*)out, sp.log1, sp.log2, sp.CB, Mb, scale, sym);
     launch_end(p, s);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s) {
+    return fft_forward_on<T>(p, fhat, p->grid, (int)p->M, (T)1 / (T)p->Ms, p->kernel == INFFT_KERNEL_SYM, s);
+}
+
+cudaError_t run_fft_full_forward_z(Plan* p, const void* in, void* out, double scale, cudaStream_t s) {
+    return fft_forward_on<double>(p, in, out, (int)p->Ms, scale, 0, s);
 }
 
 template cudaError_t run_fft_adjoint<float>(Plan*, void*, cudaStream_t);

@@ -32,6 +32,8 @@ constexpr int LSQ_WARP2_NMAX = 64;
 constexpr int LSQ_GROUP_G2 = 4;      // lanes per column in the <= 25 tier
 constexpr int LSQ_GROUP_G3 = 8;      // lanes per column in the <= 33 tier
 constexpr int LSQ_CTA_NMAX = 224;
+// largest |I(x_j)| = 2m + 1 of the underdetermined case
+constexpr int UNDER_NMAX = 17;
 
 // Columns whose ||b_l||_1 exceeds this are spread and interpolated with fp64
 // weights and fp64 accumulation: their terms cancel, and fp32 rounding of
@@ -46,7 +48,7 @@ struct ProfileRec {
 struct infft_plan_s {
     int device = 0;
     int64_t M = 0, N = 0, Ms = 0;
-    int m = 0, kernel = INFFT_KERNEL_FULL;
+    int m = 0, kernel = INFFT_KERNEL_FULL, ansatz = INFFT_ANSATZ_OVERDETERMINED;
     double sigma = 2.0, tau = 1e-12;
     int logMs = 0;
     int64_t nnz_cap = 0;
@@ -74,9 +76,15 @@ struct infft_plan_s {
     // B_opt (a2)
     double* w64 = nullptr;      // nnz_cap
     float* w32 = nullptr;       // nnz_cap
-    double* J = nullptr;        // Ms
+    double* J = nullptr;        // Ms (overdetermined), N (underdetermined, caller order)
     uint8_t* wide = nullptr;    // Ms: 1 if column l uses fp64 weights in the fp32 applies
     double* gterm = nullptr;    // nnz_cap: per (column, node) terms of the node gradient
+
+    // underdetermined case (Sec. 3.2.1)
+    void* under_step = nullptr; // N double2: exp(2 pi i x_h) of the sorted nodes
+    void* under_part = nullptr; // chunks * M double2: partial node moments
+    void* under_mom = nullptr;  // M double2: node moments mu_n, n = 0 .. M-1
+    void* under_S = nullptr;    // (2m+1) * Ms double2: S(l' + d, l'), d = 0 .. 2m
 
     // apply buffers (a3-a5)
     void* grid = nullptr;       // Ms double2 (also used as float2)
@@ -108,6 +116,9 @@ cudaError_t run_pattern(Plan* p, cudaStream_t s);
 cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s);
 // lsq.cu
 cudaError_t run_precompute(Plan* p, cudaStream_t s);
+// under.cu: the underdetermined case; under_moment_chunks = partial-sum blocks of the node moments
+cudaError_t run_precompute_under(Plan* p, cudaStream_t s);
+int under_moment_chunks(int64_t N);
 // spread.cu: g = B_opt^* f onto p->grid (T = float or double, complex layout)
 template <typename T> cudaError_t run_spread(Plan* p, const void* f, cudaStream_t s);
 // spread.cu: f = B_opt g from p->grid, f in caller node order
@@ -116,5 +127,7 @@ template <typename T> cudaError_t run_interp(Plan* p, void* f, cudaStream_t s);
 template <typename T> cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s);
 // fft.cu: grid = F D fhat
 template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s);
+// fft.cu: out_p = scale * sum_{k=-Ms/2}^{Ms/2-1} in[k + Ms/2] exp(2 pi i k (p - Ms/2)/Ms), fp64, all bins
+cudaError_t run_fft_full_forward_z(Plan* p, const void* in, void* out, double scale, cudaStream_t s);
 // grad.cu: gx = dL/dx (caller order) for f (complex64, device) and w = dL/dfhat (complex64, device)
 cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cudaStream_t s);

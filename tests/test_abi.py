@@ -73,6 +73,18 @@ def test_invalid_kernel_and_tau():
             g.infft_plan_create(64, 128, 2.0, 4, tau=tau)
 
 
+def test_invalid_ansatz():
+    with pytest.raises(g.InfftError) as ei:
+        g.infft_plan_create_ansatz(64, 32, 2.0, 4, ansatz=3)
+    assert ei.value.code == 1                      # EINVAL: no such optimisation
+    with pytest.raises(g.InfftError) as ei:
+        g.infft_plan_create_ansatz(256, 32, 2.0, 9, ansatz="under")
+    assert ei.value.code == 5                      # EUNSUPPORTED: 2m+1 = 19 > 17 in the underdetermined case
+    with pytest.raises(g.InfftError) as ei:
+        g.infft_plan_create_ansatz(48, 32, 2.0, 4, ansatz="under")
+    assert ei.value.code == 5                      # M_sigma = 96 not a power of two
+
+
 def test_null_plan_calls():
     lib = g.library()
     assert lib.plan_destroy(None) == 0
