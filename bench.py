@@ -34,7 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import make_problem  # noqa: E402
+from workloads import make_problem, jittered  # noqa: E402
 
 METRIC = "iNFFT nodes/s at M=2^16,N=2^18 (rel.err≤1e-5 vs FP64), % HBM roofline"
 L2_FLUSH_BYTES = 256 << 20
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-under", action="store_true")
     return ap.parse_args()
 
 
@@ -138,19 +139,25 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 1.25 TFLOP/s nominal at 2070 MHz over 15
 KAPPA_FLOPS = 40                       # fp64 flops of one closed-form kernel value
 
 
+def sources_sha1(paths):
+    """sha1 over the concatenated contents of the kernel's source files."""
+    import hashlib
+    h = hashlib.sha1()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel`
-    from the last ncu capture recorded in profiles/traffic.json, or None when the
-    kernel's source file changed since that capture."""
-    import hashlib
+    from the last ncu capture recorded in profiles/traffic.json, or None when one of
+    the kernel's source files changed since that capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh).get(kernel)
-        if not rec:
+        if not rec or sources_sha1(rec["sources"]) != rec["sha1"]:
             return None
-        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
-            if hashlib.sha1(fh.read()).hexdigest() != rec["sha1"]:
-                return None
         return rec["bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         return None
@@ -343,6 +350,44 @@ def run_gpu(a):
                 "forward_ms": t_f, "backward_ms": t_b, "backward_over_forward": t_b / t_f,
                 "unit_note": "forward: pattern + fp64 B_opt + apply; backward: nfft_apply + node gradient"}
 
+    # ---- underdetermined case (Sec. 3.2.1): jittered nodes, M = 4N (the ratio of the paper's
+    # Example ex:trig_poly_ansatz1), N = 2^14, M = 2^16, sigma = 2, m = 4
+    under = None
+    if not a.no_under:
+        Nu, Mu = 2 ** 14, 2 ** 16
+        xu = torch.tensor(jittered(1811053360 + 1000 * rank, Nu), dtype=torch.float64, device=dev)
+        fu = torch.tensor(np.random.default_rng(13).standard_normal((Nu, 2)).astype(np.float32)
+                          .view(np.complex64).ravel(), device=dev)
+        planu = g.infft_plan_create_ansatz(Mu, Nu, 2.0, 4, ansatz="under")
+        fhu = torch.empty(Mu, dtype=torch.complex64, device=dev)
+
+        def pre_u():
+            g.infft_set_nodes(planu, xu, stream)
+            g.infft_precompute(planu, stream)
+
+        pre_u()
+        t_pre = timed(pre_u, reps=5)
+        t_app = timed(lambda: g.infft_apply(planu, fu, fhu, stream), reps=50)
+        g.infft_profile(planu, True)
+        pre_u()
+        torch.cuda.synchronize()
+        g.infft_profile(planu, False)
+        ukern = {name: ms for name, n, ms in g.infft_profile_read(planu)}
+        infou = g.infft_get_info(planu)
+        planu.close()
+        mom_ms = ukern.get("under_moments", float("nan"))
+        # one term of a node moment: complex rotate (4 mul, 2 add) + complex accumulate (2 add)
+        mom_flops = 8.0 * Nu * Mu
+        peak64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
+        ach = mom_flops / (mom_ms / 1e3) / 1e12
+        under = {"workload": f"1D jittered nodes N={Nu} M={Mu} sigma=2 m=4 (underdetermined, M = 4N)",
+                 "precompute_ms": t_pre, "apply_ms": t_app, "apply_nodes_per_s": Nu / (t_app / 1e3),
+                 "kernels_ms": ukern, "fallback_nodes": infou["fallback_columns"],
+                 "roofline_moments": {"kernel": "k_moments (node moments, O(N M) fp64)", "bound": "alu",
+                                      "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
+                                      "algorithmic_flops": mom_flops,
+                                      "peak_source": "derived: 152 SMs x 4 fp64 flop/clk x max SM clock"}}
+
     # ---- roofline of the dominant kernel and of the apply
     hbm, sm_max, src = peaks()
     ktab = {name: (n, ms) for name, n, ms in kernels}
@@ -387,6 +432,7 @@ def run_gpu(a):
         "fft_vs_cufft": {"own_fft_deconv_ms": own_fft_ms, "cufft_ms": cufft_ms, "length": plan.M_sigma,
                          "note": "own: pruned length-M_sigma FFT with D fused (M outputs); cuFFT: full FFT"},
         "differentiable": diff,
+        "underdetermined": under,
         "kernels": {name: {"launches": n, "ms_total": ms} for name, n, ms in kernels},
         "plan": {"nnz": info["nnz"], "max_column": info["max_column"], "fallback_columns": info["fallback_columns"]},
         "cpu_baseline": cpu,
