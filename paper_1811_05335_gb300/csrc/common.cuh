@@ -25,3 +25,43 @@ INFFT_D float2 expipi(float t) { float s, c; sincospif(t, &s, &c); return make_f
 INFFT_D double2 expipi(double t) { double s, c; sincospi(t, &s, &c); return make_double2(c, s); }
 
 INFFT_D unsigned lanemask_lt() { unsigned r; asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(r)); return r; }
+
+// Programmatic dependent launch (sm_90+): a kernel launched with
+// launch_pdl() may be scheduled while its predecessor in the stream is still
+// running.  It must call griddep_wait() before it touches global memory that
+// earlier stream work reads or writes; griddep_launch() lets the next kernel
+// of the stream be scheduled early.
+INFFT_D void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+INFFT_D void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Asynchronous global -> shared copies (cp.async): every copy of a thread is in
+// flight at once; cp_async_wait_all() waits for this thread's copies, and a
+// __syncthreads() after it publishes them to the CTA.
+INFFT_D void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+INFFT_D void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+INFFT_D void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}

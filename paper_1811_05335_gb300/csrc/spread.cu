@@ -116,6 +116,82 @@ k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32, const d
     g[p] = cmake((T)re, (T)im);
 }
 
+// The fp32 spreading of the apply.  Same layout as k_spread, with every load of
+// a CTA's block in flight at once: the weights [w0, w1) move to shared memory by
+// 16-byte asynchronous copies of the 16-byte aligned span around them, the node
+// indices of the window come to registers and the node values follow by 8-byte
+// asynchronous copies.  Launched as a programmatically dependent kernel.
+constexpr int SPREAD_UPT = SPREAD_UMAX / SPREAD_COLS;   // staged node values per thread
+
+__global__ void __launch_bounds__(SPREAD_COLS)
+k_spread_f32(const float2* __restrict__ f, const float* __restrict__ w32, const double* __restrict__ w64,
+             const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
+             const int32_t* __restrict__ col_start, const int32_t* __restrict__ col_count,
+             const int32_t* __restrict__ col_off, int N, int Ms, float2* __restrict__ g) {
+    __shared__ __align__(16) float ws[SPREAD_WMAX];
+    __shared__ __align__(16) float2 fu[SPREAD_UMAX];
+    griddep_wait();
+    griddep_launch();
+    const int p0 = blockIdx.x * SPREAD_COLS;
+    const int p = p0 + threadIdx.x;
+    const int plast = min(p0 + SPREAD_COLS, Ms) - 1;
+    const bool live = p < Ms;
+    const int n = live ? col_count[p] : 0;
+    const int s = live ? col_start[p] : 0;
+    const int off = live ? col_off[p] : 0;
+    const bool wide_col = live && wide[p];
+    const int w0 = col_off[p0], w1 = col_off[plast + 1];
+    const int S = col_start[p0];
+    int U = col_start[plast] + col_count[plast] - S;
+    if (U < 0) U += N;
+    int r0 = s - S;
+    if (r0 < 0) r0 += N;
+    const int wb = w0 & ~3, we = (w1 + 3) & ~3;
+    const int inside = !live || n == 0 || (r0 + n <= U);
+    const bool staged = __syncthreads_and(inside) && (we - wb) <= SPREAD_WMAX && U <= SPREAD_UMAX && U <= N;
+    if (!staged) {
+        if (live) g[p] = spread_direct<float>(f, w32, w64, wide_col, perm, n, s, off, N);
+        return;
+    }
+    for (int v = threadIdx.x; v < (we - wb) / 4; v += SPREAD_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
+    int pq[SPREAD_UPT];
+#pragma unroll
+    for (int u = 0; u < SPREAD_UPT; ++u) {
+        const int q = threadIdx.x + u * SPREAD_COLS;
+        int gq = S + q;
+        if (gq >= N) gq -= N;
+        pq[u] = q < U ? perm[gq] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < SPREAD_UPT; ++u) {
+        const int q = threadIdx.x + u * SPREAD_COLS;
+        if (q < U) cp_async8(fu + q, f + pq[u]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!live) return;
+    if (wide_col) {
+        g[p] = spread_direct<float>(f, w32, w64, true, perm, n, s, off, N);
+        return;
+    }
+    // Neighbouring threads' columns start about |I(l)| weights (and N/M_sigma nodes)
+    // apart in shared memory, so walking every column from its start would put a
+    // warp's accesses on a few banks; each thread starts its walk at its own lane
+    // (mod n) instead, which spreads the accesses over the banks.
+    const float* wc = ws + (off - wb);
+    const float2* fc = fu + r0;
+    float re = 0, im = 0;
+    int k = n ? (int)(threadIdx.x & 31) % n : 0;
+    for (int i = 0; i < n; ++i) {
+        const float wi = wc[k];
+        const float2 v = fc[k];
+        re = fmaf(wi, v.x, re);
+        im = fmaf(wi, v.y, im);
+        k = (k + 1 == n) ? 0 : k + 1;
+    }
+    g[p] = make_float2(re, im);
+}
+
 // One thread per sorted node: gathers from the 2m (or 2m+1) grid points of I(x_j).
 template <typename T>
 __global__ void k_interp(const cplx_t<T>* __restrict__ g, const float* __restrict__ w32,
@@ -155,10 +231,18 @@ template <typename T>
 cudaError_t run_spread(Plan* p, const void* f, cudaStream_t s) {
     const int Ms = (int)p->Ms;
     launch_begin(p, sizeof(T) == 4 ? "spread" : "spread_z", s);
-    k_spread<T><<<(Ms + SPREAD_COLS - 1) / SPREAD_COLS, SPREAD_COLS, 0, s>>>((const cplx_t<T>*)f, p->w32, p->w64, p->wide, p->perm, p->col_start,
-                                                  p->col_count, p->col_off, (int)p->N, Ms,
-                                                  (cplx_t<T>*)p->grid);
+    const int blocks = (Ms + SPREAD_COLS - 1) / SPREAD_COLS;
+    cudaError_t e = cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        e = launch_pdl(k_spread_f32, dim3(blocks), dim3(SPREAD_COLS), 0, s, (const float2*)f, p->w32, p->w64,
+                       p->wide, p->perm, p->col_start, p->col_count, p->col_off, (int)p->N, Ms, (float2*)p->grid);
+    } else {
+        k_spread<T><<<blocks, SPREAD_COLS, 0, s>>>((const cplx_t<T>*)f, p->w32, p->w64, p->wide, p->perm,
+                                                   p->col_start, p->col_count, p->col_off, (int)p->N, Ms,
+                                                   (cplx_t<T>*)p->grid);
+    }
     launch_end(p, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
