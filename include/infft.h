@@ -211,6 +211,64 @@ infft_status infft_profile(infft_plan_t plan, int enable);
 infft_status infft_profile_read(infft_plan_t plan, int cap, const char** names,
                                 int64_t* launches, double* milliseconds, int* n);
 
+/* ---- batched problems -------------------------------------------------------
+ * Many independent inversions of uneven size in one plan (the paper's "fixed
+ * nodes, several problems" use of the precomputed B_opt, Sec. 1 and Sec. 3.2.2):
+ * problem p has M_p coefficients and N_p nodes and is solved exactly as a plan
+ * of its own would solve it (eq:approx_ansatz2, same pattern, same B_opt, same
+ * D^* F^*), with sigma = 2 (M_sigma,p = 2 M_p, any even M_p in [4, 8192]; the
+ * length-M_sigma DFT is evaluated by a chirp convolution, so M_p need not be a
+ * power of two).  Columns with more than 224 nodes (clustered nodes) are solved
+ * by a large-column solver up to 1024 nodes; larger columns are counted as
+ * unsupported (b_l = 0).
+ * Layout: problems back to back in the order given.  x: sum N_p fp64 nodes;
+ * f: sum N_p complex64 values; fhat: sum M_p complex64 coefficients, problem p's
+ * block at offset sum_{q<p} M_q in the k + M_p/2 layout.
+ * The batch owns all device buffers (one arena for the members' patterns and
+ * weights, staging for host f/fhat) and a pool of streams ordered after the
+ * caller's stream. */
+typedef struct infft_batch_s* infft_batch_t;
+
+typedef struct {
+    int64_t P, sum_N, sum_M;
+    int32_t m, nodes_set, precomputed, max_column;
+    int64_t nnz;                 /* sum over problems of sum_l |I(l)| */
+    int64_t empty_columns, bad_nodes;
+    int64_t fallback_columns;    /* columns solved with a raised regulariser */
+    int64_t unsupported_columns; /* columns above 1024 nodes (b_l = 0) */
+    int64_t large_columns;       /* columns solved by the large-column solver */
+    double objective;            /* sum over problems of sum_l J_l (eq:matrixnorm_opt_ansatz2) */
+} infft_batch_info;
+
+/* Creates a batch of P >= 1 problems with sizes M[p], N[p] (host arrays, P each),
+ * sigma = 2 (others: INFFT_EUNSUPPORTED), cut-off m, kernel FULL or SYM and
+ * regulariser tau (as infft_plan_create).  Blocks while it fills the chirp
+ * transforms of the problems' DFT lengths. */
+infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, double sigma, int m,
+                                int kernel, double tau, infft_batch_t* out);
+
+/* The pattern step (eq:set_l) of every problem: x holds sum N_p nodes (host or
+ * device, each in [-1/2, 1/2)); the batch copies them. */
+infft_status infft_batch_set_nodes(infft_batch_t batch, const double* x, infft_stream_t stream);
+
+/* B_opt of every problem (as infft_precompute, eq:opt_ansatz2 .. eq:solution_ansatz2). */
+infft_status infft_batch_precompute(infft_batch_t batch, infft_stream_t stream);
+
+/* fhat_p = D^* F^* B_opt,p^* f_p for every problem p (eq:approx_ansatz2), fp32:
+ * f (sum N_p complex64) -> fhat (sum M_p complex64), host or device. */
+infft_status infft_batch_apply(infft_batch_t batch, const float* f, float* fhat, infft_stream_t stream);
+
+/* Synchronises the batch's last stream and fills *info (sums over problems). */
+infft_status infft_batch_get_info(infft_batch_t batch, infft_batch_info* info);
+
+/* infft_copy_plan_data for problem p of the batch (HOST arrays, synchronous). */
+infft_status infft_batch_copy_problem(infft_batch_t batch, int64_t p, int32_t* perm, int32_t* col_start,
+                                      int32_t* col_count, int32_t* col_offset, double* weights,
+                                      double* objective);
+
+/* Frees the batch (synchronises its device first). */
+infft_status infft_batch_destroy(infft_batch_t batch);
+
 /* ---- allocation-free entry point ------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that cannot
  * allocate device memory when they call: processes whose device memory belongs

@@ -23,6 +23,8 @@ EXPORTED_SYMBOLS = (
     "infft_set_nodes", "infft_apply_z", "nfft_apply_z", "infft_get_info", "infft_copy_plan_data",
     "infft_profile", "infft_profile_read", "infft_launch_count", "infft_last_error", "infft_version",
     "infft_fft_deconv_noalloc", "infft_grad_nodes", "infft_plan_create_ansatz",
+    "infft_batch_create", "infft_batch_set_nodes", "infft_batch_precompute", "infft_batch_apply",
+    "infft_batch_get_info", "infft_batch_copy_problem", "infft_batch_destroy",
 )
 
 
@@ -40,6 +42,15 @@ class _Info(ctypes.Structure):
                 ("fallback_columns", ctypes.c_int32), ("unsupported_columns", ctypes.c_int32),
                 ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32), ("objective", ctypes.c_double),
                 ("grad_failed_columns", ctypes.c_int32), ("ansatz", ctypes.c_int32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int64), ("sum_N", ctypes.c_int64), ("sum_M", ctypes.c_int64),
+                ("m", ctypes.c_int32), ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32),
+                ("max_column", ctypes.c_int32), ("nnz", ctypes.c_int64), ("empty_columns", ctypes.c_int64),
+                ("bad_nodes", ctypes.c_int64), ("fallback_columns", ctypes.c_int64),
+                ("unsupported_columns", ctypes.c_int64), ("large_columns", ctypes.c_int64),
+                ("objective", ctypes.c_double)]
 
 
 _lib = None
@@ -73,6 +84,13 @@ def library():
         "infft_grad_nodes": [P, VP, VP, VP, VP],
         "infft_profile_read": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(I64),
                                ctypes.POINTER(D), ctypes.POINTER(I32)],
+        "infft_batch_create": [I64, VP, VP, D, I32, I32, D, ctypes.POINTER(P)],
+        "infft_batch_set_nodes": [P, VP, VP],
+        "infft_batch_precompute": [P, VP],
+        "infft_batch_apply": [P, VP, VP, VP],
+        "infft_batch_get_info": [P, ctypes.POINTER(_BatchInfo)],
+        "infft_batch_copy_problem": [P, I64, VP, VP, VP, VP, VP, VP],
+        "infft_batch_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -298,3 +316,89 @@ def infft_launch_count():
 
 def infft_version():
     return library().infft_version().decode()
+
+
+class Batch:
+    """Owner of an infft_batch_t handle: P independent problems of sizes M[p], N[p]."""
+
+    def __init__(self, handle, M, N, m):
+        self.handle, self.M, self.N, self.m = handle, np.asarray(M, np.int64), np.asarray(N, np.int64), m
+        self.P = len(self.M)
+        self.n_off = np.concatenate([[0], np.cumsum(self.N)])
+        self.m_off = np.concatenate([[0], np.cumsum(self.M)])
+
+    def close(self):
+        if self.handle:
+            _check(library().infft_batch_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def infft_batch_create(M, N, sigma=2.0, m=6, kernel="full", tau=1e-12):
+    """Batch of len(M) problems (M[p] coefficients, N[p] nodes), sigma = 2."""
+    Ma = np.ascontiguousarray(M, np.int64)
+    Na = np.ascontiguousarray(N, np.int64)
+    if Ma.shape != Na.shape or Ma.ndim != 1:
+        raise ValueError("M and N must be 1-D arrays of the same length")
+    h = ctypes.c_void_p()
+    k = _KERNELS.get(kernel, kernel)
+    _check(library().infft_batch_create(len(Ma), Ma.ctypes.data, Na.ctypes.data, float(sigma), int(m), int(k),
+                                        float(tau), ctypes.byref(h)))
+    return Batch(h.value, Ma, Na, m)
+
+
+def infft_batch_set_nodes(batch, x, stream=None):
+    keep = []
+    _check(library().infft_batch_set_nodes(batch.handle, _as_ptr(x, "f64", keep), _stream(stream, x)))
+
+
+def infft_batch_precompute(batch, stream=None):
+    _check(library().infft_batch_precompute(batch.handle, _stream(stream)))
+
+
+def infft_batch_apply(batch, f, out=None, stream=None):
+    """fhat of every problem (complex64, problems back to back)."""
+    keep = []
+    if out is None:
+        out = _empty_like(f, int(batch.m_off[-1]), "c64")
+    _check(library().infft_batch_apply(batch.handle, _as_ptr(f, "c64", keep), _as_ptr(out, "c64", keep),
+                                       _stream(stream, f, out)))
+    return out
+
+
+def infft_batch_get_info(batch):
+    info = _BatchInfo()
+    _check(library().infft_batch_get_info(batch.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in _BatchInfo._fields_}
+
+
+def infft_batch_copy_problem(batch, p, weights=True):
+    """Pattern and B_opt of problem p as host numpy arrays (as infft_copy_plan_data)."""
+    N, Ms = int(batch.N[p]), 2 * int(batch.M[p])
+    perm = np.empty(N, np.int32)
+    start = np.empty(Ms, np.int32)
+    count = np.empty(Ms, np.int32)
+    off = np.empty(Ms + 1, np.int32)
+    ptr = lambda a: a.ctypes.data if a is not None else None
+    _check(library().infft_batch_copy_problem(batch.handle, int(p), ptr(perm), ptr(start), ptr(count), ptr(off),
+                                              None, None))
+    out = dict(perm=perm, col_start=start, col_count=count, col_offset=off)
+    if weights:
+        nnz = int(off[-1])
+        w = np.empty(max(nnz, 1), np.float64)
+        J = np.empty(Ms, np.float64)
+        _check(library().infft_batch_copy_problem(batch.handle, int(p), None, None, None, None, w.ctypes.data,
+                                                  J.ctypes.data))
+        out.update(weights=w[:nnz], objective=J)
+    return out

@@ -54,21 +54,12 @@ bool is_device_pointer(const void* ptr) {
 }
 
 void free_plan_buffers(Plan* p) {
-    void* bufs[] = {p->x, p->xs, p->skey, p->perm, p->bucket, p->cursor, p->seg_list, p->sort_tmp, p->col_start,
-                    p->col_count, p->col_off, p->list_a, p->tiles_mid, p->tiles_big, p->big_list, p->scan_sums, p->counters, p->phase, p->w64,
-                    p->w32, p->J, p->wide, p->gterm, p->grid,
-                    p->work, p->stage_in, p->stage_out, p->under_step, p->under_part, p->under_mom,
-                    p->under_S};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
+    if (p->arena) cudaFree(p->arena);
+    p->arena = nullptr;
 }
 
 // entries of the objective: one per grid point (overdetermined) or per node (underdetermined)
 int64_t objective_count(const Plan* p) { return p->ansatz == INFFT_ANSATZ_UNDERDETERMINED ? p->N : p->Ms; }
-
-template <typename X> cudaError_t dalloc(X** ptr, size_t count) {
-    return cudaMalloc((void**)ptr, count * sizeof(X) + 16);
-}
 
 infft_status validate_sizes(int64_t M, int64_t N, double sigma, int m, int kernel, double tau, int64_t* Ms_out,
                             int* logMs_out) {
@@ -162,6 +153,34 @@ infft_status set_error(infft_status st, const char* fmt, ...) {
     return st;
 }
 
+void plan_layout(Plan* p, Carver& c, bool member) {
+    const int64_t N = p->N, M = p->M, Ms = p->Ms, m = p->m;
+    if (!member) c.take(p->x, N);
+    c.take(p->xs, N);
+    c.take(p->skey, N); c.take(p->perm, N); c.take(p->sort_tmp, N);
+    c.take(p->bucket, 2 * Ms + 1); c.take(p->cursor, 2 * Ms); c.take(p->seg_list, N / 32 + 2);
+    c.take(p->col_start, Ms); c.take(p->col_count, Ms); c.take(p->col_off, Ms + 1);
+    c.take(p->big_list, Ms); c.take(p->list_a, Ms); c.take(p->tiles_mid, Ms / 32 + 2);
+    c.take(p->tiles_big, Ms / 32 + 2);
+    if (member) c.take(p->huge_list, Ms);
+    c.take(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
+    c.take(p->phase, N);
+    c.take(p->counters, CNT_N);
+    c.take(p->w64, p->nnz_cap); c.take(p->w32, p->nnz_cap); c.take(p->J, Ms > N ? Ms : N); c.take(p->wide, Ms);
+    if (member) return;
+    c.take(p->gterm, p->nnz_cap);
+    if (p->ansatz == INFFT_ANSATZ_UNDERDETERMINED) {
+        double2 *ustep, *upart, *umom, *uS;
+        c.take(ustep, N); c.take(upart, (int64_t)under_moment_chunks(N) * M); c.take(umom, M);
+        c.take(uS, (2 * m + 1) * Ms);
+        p->under_step = ustep; p->under_part = upart; p->under_mom = umom; p->under_S = uS;
+    }
+    const int64_t stage = (N > M ? N : M);
+    double2 *grid, *work, *sin_, *sout;
+    c.take(grid, Ms); c.take(work, Ms); c.take(sin_, stage); c.take(sout, stage);
+    p->grid = grid; p->work = work; p->stage_in = sin_; p->stage_out = sout;
+}
+
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void launch_begin(Plan* p, const char* name, cudaStream_t s) {
@@ -206,27 +225,14 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
     p->ansatz = ansatz;
     p->logMs = logMs;
     p->nnz_cap = N * (2 * (int64_t)m + 1);
-    const int64_t stage = (N > M ? N : M);
-    cudaError_t e = cudaSuccess;
-#define ALLOC(ptr, cnt) if (e == cudaSuccess) e = dalloc(&(ptr), (size_t)(cnt))
-    ALLOC(p->x, N); ALLOC(p->xs, N);
-    ALLOC(p->skey, N); ALLOC(p->perm, N); ALLOC(p->sort_tmp, N);
-    ALLOC(p->bucket, 2 * Ms + 1); ALLOC(p->cursor, 2 * Ms); ALLOC(p->seg_list, N / 32 + 2);
-    ALLOC(p->col_start, Ms); ALLOC(p->col_count, Ms); ALLOC(p->col_off, Ms + 1); ALLOC(p->big_list, Ms); ALLOC(p->list_a, Ms); ALLOC(p->tiles_mid, Ms / 32 + 2); ALLOC(p->tiles_big, Ms / 32 + 2);
-    ALLOC(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
-    ALLOC(p->phase, N);
-    ALLOC(p->counters, CNT_N);
-    ALLOC(p->w64, p->nnz_cap); ALLOC(p->w32, p->nnz_cap); ALLOC(p->J, Ms > N ? Ms : N); ALLOC(p->wide, Ms); ALLOC(p->gterm, p->nnz_cap);
-    if (ansatz == INFFT_ANSATZ_UNDERDETERMINED) {
-        double2 *ustep = nullptr, *upart = nullptr, *umom = nullptr, *uS = nullptr;
-        ALLOC(ustep, N); ALLOC(upart, (int64_t)under_moment_chunks(N) * M); ALLOC(umom, M);
-        ALLOC(uS, (2 * (int64_t)m + 1) * Ms);
-        p->under_step = ustep; p->under_part = upart; p->under_mom = umom; p->under_S = uS;
+    Carver c;
+    plan_layout(p, c, false);
+    cudaError_t e = cudaMalloc(&p->arena, c.off);
+    if (e == cudaSuccess) {
+        c.base = (char*)p->arena;
+        c.off = 0;
+        plan_layout(p, c, false);
     }
-    double2 *grid = nullptr, *work = nullptr, *sin_ = nullptr, *sout = nullptr;
-    ALLOC(grid, Ms); ALLOC(work, Ms); ALLOC(sin_, stage); ALLOC(sout, stage);
-#undef ALLOC
-    p->grid = grid; p->work = work; p->stage_in = sin_; p->stage_out = sout;
     if (e == cudaSuccess) e = cudaMemset(p->counters, 0, CNT_N * sizeof(int32_t));
     if (e != cudaSuccess) {
         free_plan_buffers(p);

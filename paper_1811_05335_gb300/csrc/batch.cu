@@ -1,0 +1,671 @@
+// Batched inverse NFFT: many independent problems of uneven size (M_p, N_p) in
+// one plan, the paper's overdetermined direct inversion (Sec. 3.2.2) for each.
+//
+// Pattern and precompute: every problem is a plan of its own whose buffers are
+// carved from one allocation; their launches are spread over a pool of streams
+// (stream-ordered after the caller's stream, so the whole precompute can be
+// captured in a CUDA graph), and the columns above the CTA solver's limit of
+// all problems go to one large-column launch.
+//
+// Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of
+// 256 grid points of one problem (the staged tile of the single-problem apply).
+// (2) One persistent CTA per SM takes problems by size: D^* F^* on the problem's
+// grid of M_sigma = 2M points.  M is any even number, so the pruned DFT
+//   h_k = sum_{l=-M}^{M-1} g_l w^{kl},  w = e^{-2 pi i/(2M)},  k = -M/2 .. M/2-1,
+// is split into even and odd grid points, h_k = E_k + w^k O_k with length-M DFTs
+//   E_k = sum_{n=-M/2}^{M/2-1} g_{2n} W^{kn},  O_k = sum_n g_{2n+1} W^{kn},  W = w^2,
+// and each is evaluated as a chirp convolution (Bluestein, "A linear filtering
+// approach to the computation of the discrete Fourier transform", 1970):
+//   kn = (k^2 + n^2 - (k-n)^2)/2  =>  E_k = W^{k^2/2} sum_n (g_{2n} W^{n^2/2}) W^{-(k-n)^2/2},
+// a cyclic convolution of length L = 2^ceil(log2(2M-1)) done with in-place
+// radix-8 transforms in shared memory: a decimation-in-frequency forward
+// transform (natural order in, digit-reversed out), a pointwise product with
+// the transform of the chirp (precomputed per problem in the same digit-reversed
+// order) and a decimation-in-time inverse (digit-reversed in, natural out).
+// W^{n^2/2} = e^{-i pi (n^2 mod 2M)/M} is evaluated on the exactly reduced integer.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "fft_device.cuh"
+#include "plan.h"
+#include "spread_device.cuh"
+
+namespace {
+
+constexpr int BATCH_FFT_THREADS = 1024;
+constexpr int TW_LOG = 14;
+constexpr int TW_N = 1 << TW_LOG;                 // twiddle table e^{-2 pi i t / TW_N}
+constexpr int BATCH_MMAX = TW_N / 2;              // 2M - 1 <= TW_N
+constexpr int BATCH_STASH = BATCH_MMAX / BATCH_FFT_THREADS;
+constexpr int BATCH_STREAMS = 16;
+
+struct BatchProblem {
+    const float* w32;
+    const double* w64;
+    const uint8_t* wide;
+    const int32_t* perm;
+    const int32_t* col_start;
+    const int32_t* col_count;
+    const int32_t* col_off;
+    const float2* bhat;    // L values: the chirp's transform, digit-reversed
+    int64_t f_off, fhat_off, g_off;
+    int N, M, logL, sym;
+};
+
+INFFT_HD int pad16(int i) { return i + (i >> 4); }   // one padding slot per 16 entries
+
+// W^{n^2/2} = e^{-i pi (n^2 mod 2M)/M} for n = idx - M/2
+INFFT_D float2 chirp(int idx, int M) {
+    const int n = idx - M / 2;
+    const int q = (n * n) % (2 * M);
+    float s, c;
+    sincospif(-(float)q / (float)M, &s, &c);
+    return make_float2(c, s);
+}
+
+// One in-place decimation-in-frequency radix-R stage on blocks of S entries:
+// butterfly (block, o) reads x_r = a[base + o + r S/R], transforms, multiplies
+// X_r by e^{-2 pi i o r / S} and writes back to the same entries.
+template <int R>
+INFFT_D void dif_stage(float2* buf, int L, int S, const float2* __restrict__ tw) {
+    const int h = S / R, lh = __ffs(h) - 1, nbf = L / R, ts = TW_N / S;
+    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+        const int base = ((bf >> lh) * S) + (bf & (h - 1));
+        const int o = bf & (h - 1);
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = buf[pad16(base + r * h)];
+        dft_r<-1>(x, int_constant_tag<R>());
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(tw + o * r * ts));
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16(base + r * h)] = x[r];
+    }
+}
+
+// The transpose of dif_stage with conjugate twiddles (decimation in time, +i).
+template <int R>
+INFFT_D void dit_stage_inv(float2* buf, int L, int S, const float2* __restrict__ tw) {
+    const int h = S / R, lh = __ffs(h) - 1, nbf = L / R, ts = TW_N / S;
+    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+        const int base = ((bf >> lh) * S) + (bf & (h - 1));
+        const int o = bf & (h - 1);
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = buf[pad16(base + r * h)];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            const float2 t = __ldg(tw + o * r * ts);
+            x[r] = cmul(x[r], make_float2(t.x, -t.y));
+        }
+        dft_r<1>(x, int_constant_tag<R>());
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16(base + r * h)] = x[r];
+    }
+}
+
+// Forward transform of L = 2^logL entries (natural order in, digit-reversed out).
+INFFT_D void cta_dif_forward(float2* buf, int logL, const float2* __restrict__ tw) {
+    const int L = 1 << logL;
+    int S = L;
+    for (int i = 0; i < logL / 3; ++i) {
+        dif_stage<8>(buf, L, S, tw);
+        __syncthreads();
+        S >>= 3;
+    }
+    if (logL % 3 == 1) { dif_stage<2>(buf, L, S, tw); __syncthreads(); }
+    if (logL % 3 == 2) { dif_stage<4>(buf, L, S, tw); __syncthreads(); }
+}
+
+// Inverse transform without the 1/L (digit-reversed in, natural order out).
+INFFT_D void cta_dit_inverse(float2* buf, int logL, const float2* __restrict__ tw) {
+    const int L = 1 << logL;
+    int S = 1;
+    if (logL % 3 == 1) { S = 2; dit_stage_inv<2>(buf, L, S, tw); __syncthreads(); }
+    if (logL % 3 == 2) { S = 4; dit_stage_inv<4>(buf, L, S, tw); __syncthreads(); }
+    for (int i = 0; i < logL / 3; ++i) {
+        S <<= 3;
+        dit_stage_inv<8>(buf, L, S, tw);
+        __syncthreads();
+    }
+}
+
+// buf <- L * (a (*) b) for a in buf (natural order) and bhat = DIF(b).
+INFFT_D void chirp_convolve(float2* buf, int logL, const float2* __restrict__ bhat, const float2* __restrict__ tw) {
+    const int L = 1 << logL;
+    cta_dif_forward(buf, logL, tw);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = cmul(buf[pad16(i)], __ldg(bhat + i));
+    __syncthreads();
+    cta_dit_inverse(buf, logL, tw);
+}
+
+// Per problem: bhat = DIF(b), b_d = W^{-d^2/2} = e^{+i pi (d^2 mod 2M)/M} for |d| < M
+// placed cyclically (d mod L), zero elsewhere.
+__global__ void __launch_bounds__(BATCH_FFT_THREADS)
+k_batch_chirp(const BatchProblem* __restrict__ probs, float2* __restrict__ bhat_all,
+              const int64_t* __restrict__ bhat_off, const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    const BatchProblem pr = probs[blockIdx.x];
+    const int M = pr.M, L = 1 << pr.logL;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const bool inside = i < M || i > L - M;   // |d| < M
+        const int d = i < M ? i : i - L;
+        float2 v = make_float2(0.f, 0.f);
+        if (inside) {
+            const int q = (d * d) % (2 * M);
+            float s, c;
+            sincospif((float)q / (float)M, &s, &c);
+            v = make_float2(c, s);
+        }
+        sm[pad16(i)] = v;
+    }
+    __syncthreads();
+    cta_dif_forward(sm, pr.logL, tw);
+    float2* out = bhat_all + bhat_off[blockIdx.x];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) out[i] = sm[pad16(i)];
+}
+
+// Spreading of all problems: CTA t spreads the tile of 256 grid points starting
+// at tile_p0[t] of problem tile_prob[t] into its slice of g_all.
+__global__ void __launch_bounds__(SPREAD_COLS)
+k_batch_spread(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ tile_prob,
+               const int32_t* __restrict__ tile_p0, const float2* __restrict__ f, float2* __restrict__ g_all) {
+    __shared__ __align__(16) float ws[SPREAD_WMAX];
+    __shared__ __align__(16) float2 fu[SPREAD_UMAX];
+    const BatchProblem pr = probs[tile_prob[blockIdx.x]];
+    spread_tile_f32(f + pr.f_off, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_count, pr.col_off, pr.N,
+                    2 * pr.M, tile_p0[blockIdx.x], g_all + pr.g_off, ws, fu);
+}
+
+// D^* F^* of every problem's grid (pruned to its M central frequencies): one CTA
+// per SM takes the problems in the order given (largest first) by a ticket.
+__global__ void __launch_bounds__(BATCH_FFT_THREADS, 1)
+k_batch_fft(const BatchProblem* __restrict__ probs, int P, const int32_t* __restrict__ order,
+            const float2* __restrict__ g_all, float2* __restrict__ fhat, const float2* __restrict__ tw,
+            int32_t* __restrict__ ticket) {
+    extern __shared__ __align__(16) float2 sm[];
+    float2* buf = sm;                    // pad16(L) <= pad16(TW_N)
+    float2* gO = sm + pad16(TW_N);       // odd grid values, M <= BATCH_MMAX
+    __shared__ int s_job;
+    for (;;) {
+        if (threadIdx.x == 0) s_job = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int job = s_job;
+        __syncthreads();
+        if (job >= P) break;
+        const BatchProblem pr = probs[order[job]];
+        const int M = pr.M, L = 1 << pr.logL;
+        const float4* g4 = (const float4*)(g_all + pr.g_off);   // (g_{2n'}, g_{2n'+1})
+        for (int n = threadIdx.x; n < M; n += blockDim.x) {
+            const float4 v = g4[n];
+            buf[pad16(n)] = cmul(make_float2(v.x, v.y), chirp(n, M));
+            gO[n] = make_float2(v.z, v.w);
+        }
+        for (int i = M + threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = make_float2(0.f, 0.f);
+        __syncthreads();
+        chirp_convolve(buf, pr.logL, pr.bhat, tw);
+        const float invL = 1.0f / (float)L;
+        float2 X0[BATCH_STASH];
+#pragma unroll
+        for (int j = 0; j < BATCH_STASH; ++j) {
+            const int k = threadIdx.x + j * BATCH_FFT_THREADS;
+            X0[j] = k < M ? cscale(cmul(buf[pad16(k)], chirp(k, M)), invL) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int n = threadIdx.x; n < M; n += blockDim.x) buf[pad16(n)] = cmul(gO[n], chirp(n, M));
+        for (int i = M + threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = make_float2(0.f, 0.f);
+        __syncthreads();
+        chirp_convolve(buf, pr.logL, pr.bhat, tw);
+        const float dk = 1.0f / (float)(2 * M);
+        float2* out = fhat + pr.fhat_off;
+#pragma unroll
+        for (int j = 0; j < BATCH_STASH; ++j) {
+            const int k = threadIdx.x + j * BATCH_FFT_THREADS;
+            if (k < M) {
+                const float2 X1 = cscale(cmul(buf[pad16(k)], chirp(k, M)), invL);
+                float s, c;
+                sincospif(-(float)(k - M / 2) / (float)M, &s, &c);   // w^k
+                const float2 h = cadd(X0[j], cmul(make_float2(c, s), X1));
+                out[k] = cscale(h, (pr.sym && k == 0) ? 0.0f : dk);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Per problem: nnz, the pattern and precompute counters and sum_l J_l.
+__global__ void k_batch_info(const int32_t* const* __restrict__ counters, const int32_t* const* __restrict__ col_off,
+                             const double* const* __restrict__ J, const int32_t* __restrict__ Ms,
+                             double* __restrict__ out) {
+    const int p = blockIdx.x;
+    const int n = Ms[p];
+    double sum = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sum += J[p][i];
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        double* o = out + 8 * (size_t)p;
+        o[0] = (double)col_off[p][n];
+        o[1] = (double)counters[p][CNT_MAX_COLUMN];
+        o[2] = (double)counters[p][CNT_EMPTY];
+        o[3] = (double)counters[p][CNT_BAD_NODES];
+        o[4] = (double)counters[p][CNT_FALLBACK];
+        o[5] = (double)counters[p][CNT_UNSUPPORTED];
+        o[6] = t;
+        o[7] = (double)counters[p][CNT_HUGE_LIST];
+    }
+}
+
+bool on_device(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int log2_ceil(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+struct infft_batch_s {
+    int device = 0;
+    int64_t P = 0, sumN = 0, sumM = 0, sumG = 0, sumL = 0;
+    int m = 0, kernel = INFFT_KERNEL_FULL, sms = 0, huge_slots = 0;
+    double sigma = 2.0, tau = 1e-12;
+    std::vector<int64_t> M, N, noff, moff;
+    std::vector<Plan*> plans;
+    void* arena = nullptr;          // all members' buffers
+    double* x_all = nullptr;        // sum N nodes
+    float2* g_all = nullptr;        // sum 2M grid values
+    float2* bhat = nullptr;         // sum L chirp transforms
+    float2* tw = nullptr;           // TW_N twiddles
+    float2* stage_f = nullptr;      // host staging: sum N
+    float2* stage_fhat = nullptr;   // host staging: sum M
+    BatchProblem* probs = nullptr;  // P apply descriptors
+    void* huge_probs = nullptr;     // P large-column descriptors
+    int32_t* job_off = nullptr;     // P + 1
+    double* huge_scratch = nullptr;
+    int32_t* order = nullptr;       // problems by decreasing size
+    int32_t* ticket = nullptr;
+    int32_t* tile_prob = nullptr;
+    int32_t* tile_p0 = nullptr;
+    int64_t tiles = 0;
+    const int32_t** d_counters = nullptr;
+    const int32_t** d_col_off = nullptr;
+    const double** d_J = nullptr;
+    int32_t* d_Ms = nullptr;
+    double* d_info = nullptr;       // 8 P
+    cudaStream_t streams[BATCH_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
+    int nodes_set = 0, precomputed = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+void batch_free(infft_batch_t b) {
+    for (Plan* p : b->plans) delete p;
+    void* bufs[] = {b->arena, b->x_all, b->g_all, b->bhat, b->tw, b->stage_f, b->stage_fhat, b->probs,
+                    b->huge_probs, b->job_off, b->huge_scratch, b->order, b->ticket, b->tile_prob, b->tile_p0,
+                    (void*)b->d_counters, (void*)b->d_col_off, (void*)b->d_J, b->d_Ms, b->d_info};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < BATCH_STREAMS; ++i) {
+        if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+infft_status cuda_err(cudaError_t e, const char* what) {
+    return set_error(e == cudaErrorMemoryAllocation ? INFFT_ENOMEM : INFFT_ECUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+// Makes every pool stream wait for the caller's stream s.
+cudaError_t fork_streams(infft_batch_t b, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    return e;
+}
+
+// Makes the caller's stream s wait for every pool stream.
+cudaError_t join_streams(infft_batch_t b, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(b->join[i], b->streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, double sigma, int m, int kernel,
+                                double tau, infft_batch_t* out) {
+    if (!out) return set_error(INFFT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (P < 1 || P > (1 << 24)) return set_error(INFFT_EINVAL, "P must be in [1, 2^24] (got %lld)", (long long)P);
+    if (!M || !N) return set_error(INFFT_EINVAL, "M and N must not be NULL");
+    if (sigma != 2.0) return set_error(INFFT_EUNSUPPORTED, "batched plans use sigma = 2 (got %g)", sigma);
+    if (kernel != INFFT_KERNEL_FULL && kernel != INFFT_KERNEL_SYM)
+        return set_error(INFFT_EINVAL, "kernel must be INFFT_KERNEL_FULL or INFFT_KERNEL_SYM (got %d)", kernel);
+    if (!(tau >= 0.0 && tau < 1.0)) return set_error(INFFT_EINVAL, "tau must be in [0, 1) (got %g)", tau);
+    for (int64_t i = 0; i < P; ++i) {
+        if (M[i] < 4 || (M[i] & 1) || M[i] > BATCH_MMAX)
+            return set_error(INFFT_EINVAL, "problem %lld: M must be even in [4, %d] (got %lld)", (long long)i,
+                             BATCH_MMAX, (long long)M[i]);
+        if (N[i] < 1 || (double)N[i] * (2.0 * m + 1.0) >= 2147483647.0)
+            return set_error(INFFT_EINVAL, "problem %lld: N = %lld out of range", (long long)i, (long long)N[i]);
+        if (m < 1 || 2 * (int64_t)m >= 2 * M[i])
+            return set_error(INFFT_EINVAL, "problem %lld: need m >= 1 and 2m < M_sigma", (long long)i);
+    }
+    infft_batch_t b = new infft_batch_s();
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (b->sms <= 0) b->sms = 148;
+    b->P = P; b->sigma = sigma; b->m = m; b->kernel = kernel; b->tau = tau;
+    b->M.assign(M, M + P);
+    b->N.assign(N, N + P);
+    b->noff.resize(P + 1);
+    b->moff.resize(P + 1);
+    b->noff[0] = b->moff[0] = 0;
+    std::vector<int64_t> goff(P + 1, 0), loff(P + 1, 0);
+    std::vector<int> logL(P);
+    int64_t maxN = 0;
+    for (int64_t i = 0; i < P; ++i) {
+        b->noff[i + 1] = b->noff[i] + N[i];
+        b->moff[i + 1] = b->moff[i] + M[i];
+        goff[i + 1] = goff[i] + 2 * M[i];
+        logL[i] = log2_ceil(2 * M[i] - 1);
+        loff[i + 1] = loff[i] + (int64_t(1) << logL[i]);
+        maxN = std::max(maxN, N[i]);
+    }
+    b->sumN = b->noff[P]; b->sumM = b->moff[P]; b->sumG = goff[P]; b->sumL = loff[P];
+    // member plans and their arena
+    std::vector<size_t> pos(P + 1, 0);
+    b->plans.resize(P);
+    for (int64_t i = 0; i < P; ++i) {
+        Plan* p = new Plan();
+        p->device = b->device;
+        p->M = M[i]; p->N = N[i]; p->Ms = 2 * M[i]; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
+        p->ansatz = INFFT_ANSATZ_OVERDETERMINED;
+        p->logMs = log2_ceil(p->Ms);
+        p->nnz_cap = N[i] * (2 * (int64_t)m + 1);
+        b->plans[i] = p;
+        Carver c;
+        plan_layout(p, c, true);
+        pos[i + 1] = pos[i] + ((c.off + 255) & ~(size_t)255);
+    }
+    cudaError_t e = cudaMalloc(&b->arena, pos[P]);
+    for (int64_t i = 0; i < P && e == cudaSuccess; ++i) {
+        Carver c;
+        c.base = (char*)b->arena + pos[i];
+        plan_layout(b->plans[i], c, true);
+    }
+    auto alloc = [&](auto** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)ptr, bytes + 16);
+    };
+    alloc(&b->x_all, b->sumN * sizeof(double));
+    alloc(&b->g_all, b->sumG * sizeof(float2));
+    alloc(&b->bhat, b->sumL * sizeof(float2));
+    alloc(&b->tw, TW_N * sizeof(float2));
+    alloc(&b->stage_f, b->sumN * sizeof(float2));
+    alloc(&b->stage_fhat, b->sumM * sizeof(float2));
+    alloc(&b->probs, P * sizeof(BatchProblem));
+    alloc(&b->huge_probs, P * huge_problem_bytes());
+    alloc(&b->job_off, (P + 1) * sizeof(int32_t));
+    alloc(&b->order, P * sizeof(int32_t));
+    alloc(&b->ticket, sizeof(int32_t));
+    alloc(&b->d_counters, P * sizeof(void*));
+    alloc(&b->d_col_off, P * sizeof(void*));
+    alloc(&b->d_J, P * sizeof(void*));
+    alloc(&b->d_Ms, P * sizeof(int32_t));
+    alloc(&b->d_info, 8 * P * sizeof(double));
+    b->huge_slots = maxN > LSQ_CTA_NMAX ? b->sms : 0;
+    if (b->huge_slots) alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots) * sizeof(double));
+    // tiles of the batched spreading
+    std::vector<int32_t> tprob, tp0;
+    for (int64_t i = 0; i < P; ++i)
+        for (int64_t p0 = 0; p0 < 2 * M[i]; p0 += SPREAD_COLS) {
+            tprob.push_back((int32_t)i);
+            tp0.push_back((int32_t)p0);
+        }
+    b->tiles = (int64_t)tprob.size();
+    alloc(&b->tile_prob, b->tiles * sizeof(int32_t));
+    alloc(&b->tile_p0, b->tiles * sizeof(int32_t));
+    for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_err(e, "allocate batch");
+    }
+    // descriptors and tables (host-built, copied once)
+    std::vector<BatchProblem> hp(P);
+    std::vector<const int32_t*> hc(P), ho(P);
+    std::vector<const double*> hj(P);
+    std::vector<int32_t> hms(P);
+    for (int64_t i = 0; i < P; ++i) {
+        Plan* p = b->plans[i];
+        p->x = b->x_all + b->noff[i];
+        BatchProblem& d = hp[i];
+        d.w32 = p->w32; d.w64 = p->w64; d.wide = p->wide; d.perm = p->perm;
+        d.col_start = p->col_start; d.col_count = p->col_count; d.col_off = p->col_off;
+        d.bhat = b->bhat + loff[i];
+        d.f_off = b->noff[i]; d.fhat_off = b->moff[i]; d.g_off = goff[i];
+        d.N = (int)N[i]; d.M = (int)M[i]; d.logL = logL[i]; d.sym = kernel == INFFT_KERNEL_SYM;
+        hc[i] = p->counters; ho[i] = p->col_off; hj[i] = p->J; hms[i] = (int32_t)p->Ms;
+    }
+    std::vector<char> hh(P * huge_problem_bytes());
+    huge_problems_fill(b->plans.data(), (int)P, hh.data());
+    std::vector<int32_t> ord(P);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) {
+        return (N[a] + M[a] * (int64_t)logL[a]) > (N[c] + M[c] * (int64_t)logL[c]);
+    });
+    std::vector<float2> htw(TW_N);
+    for (int t = 0; t < TW_N; ++t) {
+        // e^{-2 pi i t/TW_N} from the exactly reduced fraction t/TW_N
+        const double a = -2.0 * M_PI * (double)t / (double)TW_N;
+        htw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    std::vector<int64_t> hloff(loff.begin(), loff.end() - 1);
+    int64_t* d_loff = nullptr;
+    e = cudaMemcpy(b->probs, hp.data(), P * sizeof(BatchProblem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->huge_probs, hh.data(), hh.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->order, ord.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tw, htw.data(), TW_N * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tile_prob, tprob.data(), b->tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tile_p0, tp0.data(), b->tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_counters, hc.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_col_off, ho.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_J, hj.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_Ms, hms.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&d_loff, P * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_loff, hloff.data(), P * sizeof(int64_t), cudaMemcpyHostToDevice);
+    // every member's counters start at zero
+    for (int64_t i = 0; i < P && e == cudaSuccess; ++i)
+        e = cudaMemsetAsync(b->plans[i]->counters, 0, CNT_N * sizeof(int32_t), 0);
+    const size_t chirp_smem = (size_t)pad16(TW_N) * sizeof(float2);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_chirp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chirp_smem);
+    if (e == cudaSuccess) {
+        k_batch_chirp<<<(unsigned)P, BATCH_FFT_THREADS, chirp_smem>>>(b->probs, b->bhat, d_loff, b->tw);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (d_loff) cudaFree(d_loff);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_err(e, "initialise batch");
+    }
+    *out = b;
+    return INFFT_OK;
+}
+
+infft_status infft_batch_set_nodes(infft_batch_t b, const double* x, infft_stream_t stream) {
+    if (!b) return set_error(INFFT_EINVAL, "batch is NULL");
+    if (!x) return set_error(INFFT_EINVAL, "x is NULL");
+    DevGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last_stream = s;
+    cudaError_t e;
+    if (on_device(x)) {
+        e = cudaMemcpyAsync(b->x_all, x, b->sumN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    } else {
+        for (int64_t j = 0; j < b->sumN; ++j)
+            if (!(std::isfinite(x[j]) && x[j] >= -0.5 && x[j] < 0.5))
+                return set_error(INFFT_EINVAL, "node x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
+        e = cudaMemcpyAsync(b->x_all, x, b->sumN * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) return cuda_err(e, "copy nodes");
+    b->precomputed = 0;
+    if ((e = fork_streams(b, s)) != cudaSuccess) return cuda_err(e, "fork");
+    for (int64_t i = 0; i < b->P; ++i) {
+        if ((e = run_pattern(b->plans[i], b->streams[i % BATCH_STREAMS])) != cudaSuccess)
+            return cuda_err(e, "pattern");
+        b->plans[i]->nodes_set = 1;
+    }
+    if ((e = join_streams(b, s)) != cudaSuccess) return cuda_err(e, "join");
+    b->nodes_set = 1;
+    return INFFT_OK;
+}
+
+infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
+    if (!b) return set_error(INFFT_EINVAL, "batch is NULL");
+    if (!b->nodes_set) return set_error(INFFT_ENOTREADY, "infft_batch_precompute before infft_batch_set_nodes");
+    DevGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last_stream = s;
+    cudaError_t e;
+    if ((e = fork_streams(b, s)) != cudaSuccess) return cuda_err(e, "fork");
+    for (int64_t i = 0; i < b->P; ++i) {
+        if ((e = run_precompute(b->plans[i], b->streams[i % BATCH_STREAMS])) != cudaSuccess)
+            return cuda_err(e, "precompute");
+        b->plans[i]->precomputed = 1;
+    }
+    if ((e = join_streams(b, s)) != cudaSuccess) return cuda_err(e, "join");
+    if (b->huge_slots &&
+        (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->huge_scratch, b->huge_slots, s)) !=
+            cudaSuccess)
+        return cuda_err(e, "large-column precompute");
+    b->precomputed = 1;
+    return INFFT_OK;
+}
+
+infft_status infft_batch_apply(infft_batch_t b, const float* f, float* fhat, infft_stream_t stream) {
+    if (!b) return set_error(INFFT_EINVAL, "batch is NULL");
+    if (!f || !fhat) return set_error(INFFT_EINVAL, "f and fhat must not be NULL");
+    if (!b->precomputed) return set_error(INFFT_ENOTREADY, "infft_batch_apply before infft_batch_precompute");
+    DevGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last_stream = s;
+    cudaError_t e;
+    const float2* fin = (const float2*)f;
+    if (!on_device(f)) {
+        if ((e = cudaMemcpyAsync(b->stage_f, f, b->sumN * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_err(e, "copy f to device");
+        fin = b->stage_f;
+    }
+    const bool host_out = !on_device(fhat);
+    float2* fout = host_out ? b->stage_fhat : (float2*)fhat;
+    k_batch_spread<<<(unsigned)b->tiles, SPREAD_COLS, 0, s>>>(b->probs, b->tile_prob, b->tile_p0, fin, b->g_all);
+    const size_t smem = (size_t)(pad16(TW_N) + BATCH_MMAX) * sizeof(float2);
+    if ((e = cudaFuncSetAttribute(k_batch_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return cuda_err(e, "shared memory");
+    if ((e = cudaMemsetAsync(b->ticket, 0, sizeof(int32_t), s)) != cudaSuccess) return cuda_err(e, "ticket");
+    k_batch_fft<<<b->sms, BATCH_FFT_THREADS, smem, s>>>(b->probs, (int)b->P, b->order, b->g_all, fout, b->tw,
+                                                        b->ticket);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "launch");
+    if (host_out) {
+        if ((e = cudaMemcpyAsync(fhat, b->stage_fhat, b->sumM * sizeof(float2), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+            return cuda_err(e, "copy fhat to host");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "synchronize");
+    }
+    return INFFT_OK;
+}
+
+infft_status infft_batch_get_info(infft_batch_t b, infft_batch_info* info) {
+    if (!b || !info) return set_error(INFFT_EINVAL, "batch and info must not be NULL");
+    DevGuard g(b->device);
+    cudaError_t e = cudaStreamSynchronize(b->last_stream);
+    if (e != cudaSuccess) return cuda_err(e, "synchronize");
+    std::memset(info, 0, sizeof *info);
+    info->P = b->P; info->sum_N = b->sumN; info->sum_M = b->sumM; info->m = b->m;
+    info->nodes_set = b->nodes_set; info->precomputed = b->precomputed;
+    if (!b->nodes_set) return INFFT_OK;
+    k_batch_info<<<(unsigned)b->P, 256>>>(b->d_counters, b->d_col_off, b->d_J, b->d_Ms, b->d_info);
+    count_launches(1);
+    std::vector<double> h(8 * b->P);
+    if ((e = cudaMemcpy(h.data(), b->d_info, h.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_err(e, "read batch info");
+    for (int64_t i = 0; i < b->P; ++i) {
+        const double* o = &h[8 * i];
+        info->nnz += (int64_t)o[0];
+        info->max_column = std::max(info->max_column, (int32_t)o[1]);
+        info->empty_columns += (int64_t)o[2];
+        info->bad_nodes += (int64_t)o[3];
+        if (b->precomputed) {
+            info->fallback_columns += (int64_t)o[4];
+            info->unsupported_columns += (int64_t)o[5];
+            info->objective += o[6];
+            info->large_columns += (int64_t)o[7];
+        }
+    }
+    return INFFT_OK;
+}
+
+infft_status infft_batch_copy_problem(infft_batch_t b, int64_t i, int32_t* perm, int32_t* col_start,
+                                      int32_t* col_count, int32_t* col_offset, double* weights, double* objective) {
+    if (!b) return set_error(INFFT_EINVAL, "batch is NULL");
+    if (i < 0 || i >= b->P) return set_error(INFFT_EINVAL, "problem %lld out of range", (long long)i);
+    Plan* p = b->plans[i];
+    p->last_stream = b->last_stream;
+    return infft_copy_plan_data(p, perm, col_start, col_count, col_offset, weights, objective);
+}
+
+infft_status infft_batch_destroy(infft_batch_t b) {
+    if (!b) return INFFT_OK;
+    {
+        DevGuard g(b->device);
+        cudaDeviceSynchronize();
+        batch_free(b);
+    }
+    return INFFT_OK;
+}
+
+}  // extern "C"

@@ -745,7 +745,7 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
           const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
           KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
           double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ big_list,
-          int32_t* __restrict__ counters) {
+          int32_t* __restrict__ huge_list, int32_t* __restrict__ counters) {
     extern __shared__ double smem[];
     double* A = smem;                  // CN (CN + 1) / 2, packed rows
     double* r = A + CN * (CN + 1) / 2; // CN
@@ -758,6 +758,10 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
         const int p = big_list[it];
         const int n = col_count[p], s = col_start[p], off = col_off[p];
         if (n > CN) {
+            if (huge_list) {   // solved later by the large-column tier
+                if (threadIdx.x == 0) huge_list[atomicAdd(&counters[CNT_HUGE_LIST], 1)] = p;
+                continue;
+            }
             for (int i = threadIdx.x; i < n; i += CTA_THREADS) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
             if (threadIdx.x == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_UNSUPPORTED], 1); }
             continue;
@@ -859,6 +863,217 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
     }
 }
 
+// ---------------------------------------------------------------- tier 5: large columns
+//
+// Columns above the CTA tier (clustered nodes put hundreds of nodes into the
+// columns next to the cluster) are solved one CTA per column with the packed
+// triangle in a global scratch slot of the CTA.  Blocked right-looking Cholesky:
+// a panel of HUGE_PB columns is staged in shared memory, factored there, written
+// back, and the trailing triangle is updated in 4x4 register blocks (fp64-pipe
+// bound: 256 multiply-adds per 32 global accesses).  The kernel serves every
+// problem of a batch: jobs are numbered across the problems' huge lists through
+// an exclusive prefix of their lengths.
+
+constexpr int HUGE_PB = 16;
+constexpr int HUGE_THREADS = 256;
+
+__global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int32_t* __restrict__ job_off) {
+    __shared__ int32_t part[1024];
+    // one CTA of 1024 threads: per-thread serial sums, then a shared scan
+    const int per = (P + 1023) / 1024;
+    const int a = threadIdx.x * per, b = min(a + per, P);
+    int32_t sum = 0;
+    for (int i = a; i < b; ++i) sum += probs[i].counters[CNT_HUGE_LIST];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = a; i < b; ++i) {
+        job_off[i] = run;
+        run += probs[i].counters[CNT_HUGE_LIST];
+    }
+    if (threadIdx.x == 1023) job_off[P] = part[1023];
+}
+
+__global__ void __launch_bounds__(HUGE_THREADS, 1)
+k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
+           double* __restrict__ scratch) {
+    extern __shared__ double smem[];
+    double* pan = smem;                          // HUGE_NMAX x HUGE_PB panel (row-major)
+    double* r = pan + HUGE_NMAX * HUGE_PB;       // HUGE_NMAX
+    double* xl = r + HUGE_NMAX;                  // HUGE_NMAX
+    double2* pv = (double2*)(xl + HUGE_NMAX);    // HUGE_NMAX
+    __shared__ double s_red[2 * (HUGE_THREADS / 32)];
+    double* A = scratch + (size_t)blockIdx.x * (HUGE_NMAX * (HUGE_NMAX + 1) / 2);
+    const int total = job_off[P];
+    const int tid = threadIdx.x;
+    for (int job = blockIdx.x; job < total; job += gridDim.x) {
+        int lo = 0, hi = P - 1;   // problem: the last i with job_off[i] <= job
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (job_off[mid] <= job) lo = mid; else hi = mid - 1;
+        }
+        const HugeProblem& pr = probs[lo];
+        const int p = pr.huge_list[job - job_off[lo]];
+        const int n = pr.col_count[p], s = pr.col_start[p], off = pr.col_off[p], N = pr.N;
+        if (n > HUGE_NMAX) {
+            for (int i = tid; i < n; i += HUGE_THREADS) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
+            if (tid == 0) { pr.J[p] = 1.0; pr.wide[p] = 0; atomicAdd(&pr.counters[CNT_UNSUPPORTED], 1); }
+            continue;
+        }
+        const KernelParams& kp = pr.kp;
+        const double tl = col_t(p, pr.Ms);
+        const double2 pl = phase_of(kp.M, tl);
+        for (int i = tid; i < n; i += HUGE_THREADS) {
+            int q = s + i;
+            if (q >= N) q -= N;
+            xl[i] = pr.xs[q];
+            pv[i] = pr.ph[q];
+        }
+        __syncthreads();
+        double mu = pr.mu;
+        bool ok = false;
+        for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+            for (int i = tid; i < n; i += HUGE_THREADS) r[i] = re_kappa(tl, xl[i], pl, pv[i], kp);
+            const int ntri = n * (n + 1) / 2;
+            for (int i = 0; i < n; ++i)   // row by row: row i has i + 1 entries
+                for (int j = tid; j <= i; j += HUGE_THREADS)
+                    A[trow(i) + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kp);
+            (void)ntri;
+            __syncthreads();
+            bool failed = false;   // block-uniform: decided on shared values
+            for (int kb = 0; kb < n && !failed; kb += HUGE_PB) {
+                const int w = min(HUGE_PB, n - kb), R = n - kb;
+                for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
+                    const int i = e / HUGE_PB, c = e % HUGE_PB;
+                    pan[e] = (c < w && c <= i) ? A[trow(kb + i) + kb + c] : 0.0;
+                }
+                __syncthreads();
+                for (int c = 0; c < w; ++c) {
+                    const double akk = pan[c * HUGE_PB + c];
+                    if (!(akk > 0.0) || !isfinite(akk)) {
+                        failed = true;
+                        break;
+                    }
+                    const double rp = rsqrt(akk);
+                    __syncthreads();
+                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) pan[i * HUGE_PB + c] *= rp;
+                    if (tid == 0) pan[c * HUGE_PB + c] = rp;
+                    __syncthreads();
+                    // rank-1 update of the panel's remaining columns c' in (c, w), rows i >= c'
+                    const int nc = w - c - 1;
+                    for (int e = tid; e < (R - c - 1) * nc; e += HUGE_THREADS) {
+                        const int i = c + 1 + e / nc, cc = c + 1 + e % nc;
+                        if (cc <= i) pan[i * HUGE_PB + cc] = fma(-pan[i * HUGE_PB + c], pan[cc * HUGE_PB + c],
+                                                                 pan[i * HUGE_PB + cc]);
+                    }
+                    __syncthreads();
+                }
+                if (failed) break;
+                for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
+                    const int i = e / HUGE_PB, c = e % HUGE_PB;
+                    if (c < w && c <= i) A[trow(kb + i) + kb + c] = pan[e];
+                }
+                // trailing update of rows/columns [kb + w, n) in 4x4 blocks
+                const int T = n - kb - w;
+                const int nb = (T + 3) >> 2;
+                const int nblk = nb * (nb + 1) / 2;
+                for (int bk = tid; bk < nblk; bk += HUGE_THREADS) {
+                    int bi, bj;
+                    tri_index(bk, bi, bj);
+                    const int i0 = w + 4 * bi, j0 = w + 4 * bj;   // panel row indices
+                    double acc[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll 4
+                    for (int c = 0; c < HUGE_PB; ++c) {
+                        double li[4], lj[4];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            li[a] = (i0 + a < R) ? pan[(i0 + a) * HUGE_PB + c] : 0.0;
+                            lj[a] = (j0 + a < R) ? pan[(j0 + a) * HUGE_PB + c] : 0.0;
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fma(li[a], lj[b], acc[a][b]);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = kb + i0 + a;
+                        if (i >= n) break;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int j = kb + j0 + b;
+                            if (j <= i) A[trow(i) + j] -= acc[a][b];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            __syncthreads();
+            ok = !failed;
+            if (!ok) mu *= 1e3;
+        }
+        if (!ok) {
+            for (int i = tid; i < n; i += HUGE_THREADS) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
+            if (tid == 0) { pr.J[p] = 1.0; pr.wide[p] = 0; atomicAdd(&pr.counters[CNT_FALLBACK], 1); }
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0 && mu != pr.mu) atomicAdd(&pr.counters[CNT_FALLBACK], 1);
+        // forward solve L y = r (diagonal entries hold reciprocal pivots), column by column
+        double ysq = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double yk = r[k] * A[trow(k) + k];
+            ysq = fma(yk, yk, ysq);
+            __syncthreads();
+            if (tid == 0) r[k] = yk;
+            for (int i = k + 1 + tid; i < n; i += HUGE_THREADS) r[i] = fma(-A[trow(i) + k], yk, r[i]);
+            __syncthreads();
+        }
+        // back solve L^T b = y, row by row
+        for (int k = n - 1; k >= 0; --k) {
+            const double bk = r[k] * A[trow(k) + k];
+            __syncthreads();
+            if (tid == 0) r[k] = bk;
+            for (int i = tid; i < k; i += HUGE_THREADS) r[i] = fma(-A[trow(k) + i], bk, r[i]);
+            __syncthreads();
+        }
+        double bsq = 0.0, babs = 0.0;
+        for (int i = tid; i < n; i += HUGE_THREADS) {
+            const double b = r[i];
+            pr.w64[off + i] = b;
+            pr.w32[off + i] = (float)b;
+            bsq = fma(b, b, bsq);
+            babs += fabs(b);
+        }
+        for (int o = 16; o; o >>= 1) {
+            bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+            babs += __shfl_xor_sync(0xffffffffu, babs, o);
+        }
+        if ((tid & 31) == 0) {
+            s_red[tid >> 5] = bsq;
+            s_red[HUGE_THREADS / 32 + (tid >> 5)] = babs;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0, a = 0.0;
+            for (int w = 0; w < HUGE_THREADS / 32; ++w) { t += s_red[w]; a += s_red[HUGE_THREADS / 32 + w]; }
+            pr.J[p] = 1.0 - ysq - mu * t;
+            pr.wide[p] = a > WIDE_COLUMN_L1;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
@@ -874,6 +1089,7 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p->counters + CNT_FALLBACK, 0, 2 * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_LIST_A, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_BIG_LIST, 0, 3 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_HUGE_LIST, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -927,7 +1143,43 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     // CTA tier: the big list, one CTA per column, |I(l)| <= 224
     launch_begin(p, "lsq_cta", s);
     k_lsq_cta<<<sms, CTA_THREADS, s5, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                           p->w64, p->w32, p->J, p->wide, p->big_list, p->counters);
+                                           p->w64, p->w32, p->J, p->wide, p->big_list, p->huge_list,
+                                           p->counters);
     launch_end(p, s);
+    return cudaGetLastError();
+}
+
+namespace {
+HugeProblem huge_problem(const Plan* p) {
+    HugeProblem h;
+    h.xs = p->xs; h.ph = p->phase; h.col_start = p->col_start; h.col_count = p->col_count; h.col_off = p->col_off;
+    h.w64 = p->w64; h.w32 = p->w32; h.J = p->J; h.wide = p->wide; h.counters = p->counters;
+    h.huge_list = p->huge_list;
+    h.N = (int)p->N; h.Ms = (int)p->Ms;
+    h.kp = make_kernel_params(p);
+    h.mu = p->tau * h.kp.diag;
+    return h;
+}
+}  // namespace
+
+size_t huge_problem_bytes() { return sizeof(HugeProblem); }
+
+void huge_problems_fill(Plan* const* plans, int P, void* host) {
+    HugeProblem* h = (HugeProblem*)host;
+    for (int i = 0; i < P; ++i) h[i] = huge_problem(plans[i]);
+}
+
+size_t huge_scratch_doubles(int slots) { return (size_t)slots * (HUGE_NMAX * (HUGE_NMAX + 1) / 2); }
+
+cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots,
+                                cudaStream_t s) {
+    const size_t smem = (size_t)(HUGE_NMAX * HUGE_PB + 2 * HUGE_NMAX) * sizeof(double) +
+                        (size_t)HUGE_NMAX * sizeof(double2);
+    cudaError_t e = set_smem(k_lsq_huge, smem);
+    if (e != cudaSuccess) return e;
+    const HugeProblem* hp = (const HugeProblem*)probs;
+    k_huge_prefix<<<1, 1024, 0, s>>>(hp, P, job_off);
+    k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, scratch);
+    count_launches(2);
     return cudaGetLastError();
 }

@@ -226,6 +226,24 @@ INFFT_D bool chol_solve(double* T, int n, double (&v)[NMAX], double& ysq) {
 }
 
 // Kernel constants of a plan (host side).
+// Device view of one plan for the large-column tier (lsq.cu).
+struct HugeProblem {
+    const double* xs;
+    const double2* ph;
+    const int32_t* col_start;
+    const int32_t* col_count;
+    const int32_t* col_off;
+    double* w64;
+    float* w32;
+    double* J;
+    uint8_t* wide;
+    int32_t* counters;
+    const int32_t* huge_list;
+    int N, Ms;
+    double mu;
+    KernelParams kp;
+};
+
 inline KernelParams make_kernel_params(const Plan* p) {
     const int64_t Ms = p->Ms;
     KernelParams kp;

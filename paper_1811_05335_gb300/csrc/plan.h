@@ -21,7 +21,8 @@ enum {
     CNT_TILES_MID = 8,     // tiles routed to the 25-node thread tier
     CNT_TILES_BIG = 9,     // tiles routed to the 33-node thread tier
     CNT_GRAD_FAIL = 10,    // columns the node gradient could not factor (or too large)
-    CNT_N = 11
+    CNT_HUGE_LIST = 11,    // columns queued for the large-column solver (batch members)
+    CNT_N = 12
 };
 
 // largest column handled by the thread, warp and CTA solver tiers
@@ -70,6 +71,7 @@ struct infft_plan_s {
     int32_t* tiles_mid = nullptr;   // Ms/32 + 1 (tiles for the 25-node thread tier)
     int32_t* tiles_big = nullptr;   // Ms/32 + 1 (tiles for the 33-node thread tier)
     int32_t* big_list = nullptr;    // Ms (columns for the CTA solver)
+    int32_t* huge_list = nullptr;   // Ms (columns above the CTA solver; batch members only)
     int32_t* scan_sums = nullptr;   // per-block partial sums of the scans
     int32_t* counters = nullptr;    // CNT_N
 
@@ -92,6 +94,7 @@ struct infft_plan_s {
     void* stage_in = nullptr;   // max(N, M) double2: host-input staging
     void* stage_out = nullptr;  // max(N, M) double2: host-output staging
 
+    void* arena = nullptr;      // the one device allocation holding the buffers above (owned)
     int nodes_set = 0, precomputed = 0;
     cudaStream_t last_stream = nullptr;
 
@@ -100,6 +103,24 @@ struct infft_plan_s {
 };
 
 typedef infft_plan_s Plan;
+
+// Lays a plan's device buffers out in one arena.  With base == nullptr it only
+// measures (off grows by the bytes needed); every buffer starts on a 256-byte
+// boundary and has 16 bytes of slack behind it (vector loads may overrun).
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename X> void take(X*& ptr, size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        ptr = base ? (X*)(base + off) : nullptr;
+        off += count * sizeof(X) + 16;
+    }
+};
+
+// Buffers of plan p (sizes from p->M, N, Ms, m, ansatz).  A batch member gets
+// neither x (it points into the batch's node array) nor the buffers of the
+// single-problem applies, staging and node gradient.
+void plan_layout(Plan* p, Carver& c, bool batch_member);
 
 // Records a failure for infft_last_error() and returns st.
 infft_status set_error(infft_status st, const char* fmt, ...);
@@ -116,6 +137,14 @@ cudaError_t run_pattern(Plan* p, cudaStream_t s);
 cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s);
 // lsq.cu
 cudaError_t run_precompute(Plan* p, cudaStream_t s);
+// lsq.cu: the large-column tier over the huge lists of P problems (batch members);
+// job_off: P + 1 ints of device scratch; scratch: huge_scratch_doubles(slots) doubles
+constexpr int HUGE_NMAX = 1024;
+size_t huge_problem_bytes();                                   // size of one device descriptor
+void huge_problems_fill(Plan* const* plans, int P, void* host); // P descriptors into host memory
+size_t huge_scratch_doubles(int slots);
+cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots,
+                                cudaStream_t s);
 // under.cu: the underdetermined case; under_moment_chunks = partial-sum blocks of the node moments
 cudaError_t run_precompute_under(Plan* p, cudaStream_t s);
 int under_moment_chunks(int64_t N);

@@ -14,5 +14,5 @@ Uniforms take the top 53 bits; normals use the Box-Muller transform.
 from .rng import uniform01, uniform, normal, complex_normal  # noqa: F401
 from .nodes import jittered, iid_uniform, chebyshev_jittered, equispaced, wrap_half  # noqa: F401
 from .configs import (  # noqa: F401
-    Problem, make_problem, trig_poly_eval, CONFIG_SEED_BASE,
+    Problem, make_problem, trig_poly_eval, CONFIG_SEED_BASE, BatchWorkload, make_batch,
 )

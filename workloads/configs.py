@@ -6,7 +6,7 @@ derived by adding fixed offsets (nodes, coefficients, noise).
 from dataclasses import dataclass
 import numpy as np
 
-from .rng import complex_normal
+from .rng import complex_normal, uniform
 from .nodes import iid_uniform, jittered, chebyshev_jittered
 
 CONFIG_SEED_BASE = 1811053350
@@ -92,3 +92,44 @@ def make_problem(config, m=None, M=None, N=None, with_data=True, noise_rel=None,
             eta *= noise_rel * np.linalg.norm(f) / np.linalg.norm(eta)
             f = f + eta
     return Problem(f"config{config}", M, N, 2.0, m, x, fhat, f)
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    M: np.ndarray        # (P,) even coefficient counts
+    N: np.ndarray        # (P,) node counts
+    m: int
+    x: list              # P node arrays
+    seed: int
+
+    @property
+    def x_all(self):
+        return np.concatenate(self.x)
+
+
+_SIZES, _RATIOS = 4, 5
+
+
+def make_batch(P=4096, seed=None, M_range=(256, 8192), r_range=(2.0, 4.0), m=6, nodes="chebyshev"):
+    """Workload 3: P independent problems.
+
+    M_p = 2 round(exp(U(ln(M_lo/2), ln(M_hi/2)))) (even, log-uniform in M_range),
+    N_p = round(r_p M_p) with r_p ~ U(r_range), and per problem the Chebyshev-
+    clustered nodes x_j = cos(pi (j - 1/2)/N_p)/2 + U(-1e-3/N_p, 1e-3/N_p), wrapped
+    ("jittered" and "uniform" give the other node families).  sigma = 2, m = 6."""
+    seed = CONFIG_SEED_BASE + 3 if seed is None else seed
+    lo, hi = np.log(M_range[0] / 2.0), np.log(M_range[1] / 2.0)
+    M = 2 * np.round(np.exp(uniform(seed * 16 + _SIZES, P, lo, hi))).astype(np.int64)
+    r = uniform(seed * 16 + _RATIOS, P, r_range[0], r_range[1])
+    N = np.maximum(np.round(r * M).astype(np.int64), 1)
+    xs = []
+    for p in range(P):
+        s = seed * 16 * 65536 + 16 * p + _NODES
+        if nodes == "chebyshev":
+            xs.append(chebyshev_jittered(s, int(N[p])))
+        elif nodes == "jittered":
+            xs.append(jittered(s, int(N[p])))
+        else:
+            xs.append(iid_uniform(s, int(N[p])))
+    return BatchWorkload("config3", M, N, m, xs, seed)
