@@ -7,8 +7,10 @@
 // captured in a CUDA graph), and the columns above the CTA solver's limit of
 // all problems go to one large-column launch.
 //
-// Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of
-// 256 grid points of one problem (the staged tile of the single-problem apply).
+// Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of at
+// most 256 grid points of one problem (the staged tile of the single-problem
+// apply); tiles are cut after the precompute so that each holds fewer than
+// 4096 + |I(l)|max weights (clustered nodes make some columns hundreds of nodes long).
 // (2) One persistent CTA per SM takes problems by size: D^* F^* on the problem's
 // grid of M_sigma = 2M points.  M is any even number, so the pruned DFT
 //   h_k = sum_{l=-M}^{M-1} g_l w^{kl},  w = e^{-2 pi i/(2M)},  k = -M/2 .. M/2-1,
@@ -23,6 +25,10 @@
 // the transform of the chirp (precomputed per problem in the same digit-reversed
 // order) and a decimation-in-time inverse (digit-reversed in, natural out).
 // W^{n^2/2} = e^{-i pi (n^2 mod 2M)/M} is evaluated on the exactly reduced integer.
+// When 3M - 1 <= 16384 the even/odd split is not needed: with kl = (k^2 + l^2 -
+// (k-l)^2)/2 directly, h_k = w^{k^2/2} sum_l (g_l w^{l^2/2}) w^{-(k-l)^2/2} is one
+// cyclic convolution of length L >= 3M - 1 (the 2M inputs and M outputs do not
+// alias), two transforms instead of four.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -53,6 +59,7 @@ struct BatchProblem {
     const float2* bhat;    // L values: the chirp's transform, digit-reversed
     int64_t f_off, fhat_off, g_off;
     int N, M, logL, sym;
+    int full;              // 1: one convolution over all 2M grid points (3M - 1 <= TW_N)
 };
 
 INFFT_HD int pad16(int i) { return i + (i >> 4); }   // one padding slot per 16 entries
@@ -66,21 +73,60 @@ INFFT_D float2 chirp(int idx, int M) {
     return make_float2(c, s);
 }
 
+// w^{t^2/2} = e^{-i pi (t^2 mod 4M)/(2M)} for an integer t, w = e^{-2 pi i/(2M)}
+INFFT_D float2 chirp4(int t, int M) {
+    const int q = (t * t) % (4 * M);
+    float s, c;
+    sincospif(-(float)q / (float)(2 * M), &s, &c);
+    return make_float2(c, s);
+}
+
+// Twiddles of the in-CTA transforms: e^{-2 pi i t/TW_N} = C[t >> 7] F[t & 127]
+// from two 128-entry tables in shared memory (filled once per CTA from the global
+// table), and the powers w^r, r < 8, of a butterfly's w by products of depth <= 3.
+struct TwTables {
+    float2 c[128], f[128];
+};
+
+INFFT_D void tw_tables_load(TwTables* t, const float2* __restrict__ tw) {
+    for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+        t->c[j] = tw[j << 7];
+        t->f[j] = tw[j];
+    }
+}
+
+INFFT_D float2 tw_of(const TwTables* t, int e) { return cmul(t->c[e >> 7], t->f[e & 127]); }
+
+template <int R> INFFT_D void tw_powers(float2 w1, float2* w) {   // w[r] = w1^r, r = 1 .. R-1
+    w[1] = w1;
+    if (R > 2) {
+        w[2] = cmul(w1, w1);
+        w[3] = cmul(w[2], w1);
+    }
+    if (R > 4) {
+        w[4] = cmul(w[2], w[2]);
+        w[5] = cmul(w[4], w1);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+    }
+}
+
 // One in-place decimation-in-frequency radix-R stage on blocks of S entries:
 // butterfly (block, o) reads x_r = a[base + o + r S/R], transforms, multiplies
 // X_r by e^{-2 pi i o r / S} and writes back to the same entries.
 template <int R>
-INFFT_D void dif_stage(float2* buf, int L, int S, const float2* __restrict__ tw) {
+INFFT_D void dif_stage(float2* buf, int L, int S, const TwTables* tw) {
     const int h = S / R, lh = __ffs(h) - 1, nbf = L / R, ts = TW_N / S;
     for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
         const int base = ((bf >> lh) * S) + (bf & (h - 1));
         const int o = bf & (h - 1);
-        float2 x[R];
+        float2 x[R], w[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = buf[pad16(base + r * h)];
         dft_r<-1>(x, int_constant_tag<R>());
+        tw_powers<R>(tw_of(tw, o * ts), w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(tw + o * r * ts));
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[pad16(base + r * h)] = x[r];
     }
@@ -88,19 +134,17 @@ INFFT_D void dif_stage(float2* buf, int L, int S, const float2* __restrict__ tw)
 
 // The transpose of dif_stage with conjugate twiddles (decimation in time, +i).
 template <int R>
-INFFT_D void dit_stage_inv(float2* buf, int L, int S, const float2* __restrict__ tw) {
+INFFT_D void dit_stage_inv(float2* buf, int L, int S, const TwTables* tw) {
     const int h = S / R, lh = __ffs(h) - 1, nbf = L / R, ts = TW_N / S;
     for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
         const int base = ((bf >> lh) * S) + (bf & (h - 1));
         const int o = bf & (h - 1);
-        float2 x[R];
+        float2 x[R], w[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = buf[pad16(base + r * h)];
+        tw_powers<R>(tw_of(tw, o * ts), w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-            const float2 t = __ldg(tw + o * r * ts);
-            x[r] = cmul(x[r], make_float2(t.x, -t.y));
-        }
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], make_float2(w[r].x, -w[r].y));
         dft_r<1>(x, int_constant_tag<R>());
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[pad16(base + r * h)] = x[r];
@@ -108,7 +152,7 @@ INFFT_D void dit_stage_inv(float2* buf, int L, int S, const float2* __restrict__
 }
 
 // Forward transform of L = 2^logL entries (natural order in, digit-reversed out).
-INFFT_D void cta_dif_forward(float2* buf, int logL, const float2* __restrict__ tw) {
+INFFT_D void cta_dif_forward(float2* buf, int logL, const TwTables* tw) {
     const int L = 1 << logL;
     int S = L;
     for (int i = 0; i < logL / 3; ++i) {
@@ -121,7 +165,7 @@ INFFT_D void cta_dif_forward(float2* buf, int logL, const float2* __restrict__ t
 }
 
 // Inverse transform without the 1/L (digit-reversed in, natural order out).
-INFFT_D void cta_dit_inverse(float2* buf, int logL, const float2* __restrict__ tw) {
+INFFT_D void cta_dit_inverse(float2* buf, int logL, const TwTables* tw) {
     const int L = 1 << logL;
     int S = 1;
     if (logL % 3 == 1) { S = 2; dit_stage_inv<2>(buf, L, S, tw); __syncthreads(); }
@@ -134,7 +178,7 @@ INFFT_D void cta_dit_inverse(float2* buf, int logL, const float2* __restrict__ t
 }
 
 // buf <- L * (a (*) b) for a in buf (natural order) and bhat = DIF(b).
-INFFT_D void chirp_convolve(float2* buf, int logL, const float2* __restrict__ bhat, const float2* __restrict__ tw) {
+INFFT_D void chirp_convolve(float2* buf, int logL, const float2* __restrict__ bhat, const TwTables* tw) {
     const int L = 1 << logL;
     cta_dif_forward(buf, logL, tw);
     for (int i = threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = cmul(buf[pad16(i)], __ldg(bhat + i));
@@ -148,36 +192,128 @@ __global__ void __launch_bounds__(BATCH_FFT_THREADS)
 k_batch_chirp(const BatchProblem* __restrict__ probs, float2* __restrict__ bhat_all,
               const int64_t* __restrict__ bhat_off, const float2* __restrict__ tw) {
     extern __shared__ __align__(16) float2 sm[];
+    __shared__ TwTables twt;
+    tw_tables_load(&twt, tw);
     const BatchProblem pr = probs[blockIdx.x];
     const int M = pr.M, L = 1 << pr.logL;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        const bool inside = i < M || i > L - M;   // |d| < M
-        const int d = i < M ? i : i - L;
         float2 v = make_float2(0.f, 0.f);
-        if (inside) {
+        if (pr.full) {
+            // beta_s = w^{-(s + M/2)^2/2} for s = k' - j in (-2M, M), placed cyclically
+            if (i < M || i > L - 2 * M) {
+                const int t = (i < M ? i : i - L) + M / 2;
+                const int q = (t * t) % (4 * M);
+                float sn, cs;
+                sincospif((float)q / (float)(2 * M), &sn, &cs);
+                v = make_float2(cs, sn);
+            }
+        } else if (i < M || i > L - M) {   // |d| < M
+            const int d = i < M ? i : i - L;
             const int q = (d * d) % (2 * M);
-            float s, c;
-            sincospif((float)q / (float)M, &s, &c);
-            v = make_float2(c, s);
+            float sn, cs;
+            sincospif((float)q / (float)M, &sn, &cs);
+            v = make_float2(cs, sn);
         }
         sm[pad16(i)] = v;
     }
     __syncthreads();
-    cta_dif_forward(sm, pr.logL, tw);
+    cta_dif_forward(sm, pr.logL, &twt);
     float2* out = bhat_all + bhat_off[blockIdx.x];
     for (int i = threadIdx.x; i < L; i += blockDim.x) out[i] = sm[pad16(i)];
 }
 
-// Spreading of all problems: CTA t spreads the tile of 256 grid points starting
-// at tile_p0[t] of problem tile_prob[t] into its slice of g_all.
+// Tiles of the batched spreading.  Grid point p of a problem starts a tile when
+// p is a multiple of SPREAD_COLS or when its weight offset enters a new block of
+// TILE_WEIGHTS entries: a tile then has at most SPREAD_COLS grid points and fewer
+// than TILE_WEIGHTS + |I(l)|max weights, which the staged spreading holds.
+constexpr int TILE_WEIGHTS = 4096;
+constexpr int TILE_SCAN_THREADS = 1024;
+
+INFFT_D bool tile_start(const int32_t* __restrict__ col_off, int p) {
+    return p % SPREAD_COLS == 0 || (col_off[p] / TILE_WEIGHTS) != (col_off[p - 1] / TILE_WEIGHTS);
+}
+
+// Per problem (one CTA): its number of tiles.
+__global__ void __launch_bounds__(TILE_SCAN_THREADS)
+k_tile_count(const BatchProblem* __restrict__ probs, int32_t* __restrict__ count) {
+    const BatchProblem pr = probs[blockIdx.x];
+    const int Ms = 2 * pr.M;
+    int c = 0;
+    for (int p = threadIdx.x; p < Ms; p += blockDim.x) c += tile_start(pr.col_off, p);
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __shared__ int red[TILE_SCAN_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < TILE_SCAN_THREADS / 32; ++w) t += red[w];
+        count[blockIdx.x] = t;
+    }
+}
+
+// Exclusive prefix of the P tile counts (one CTA); off[P] = total.
+__global__ void __launch_bounds__(1024) k_tile_prefix(const int32_t* __restrict__ count, int P, int32_t* __restrict__ off) {
+    __shared__ int32_t part[1024];
+    const int per = (P + 1023) / 1024;
+    const int a = threadIdx.x * per, b = min(a + per, P);
+    int32_t sum = 0;
+    for (int i = a; i < b; ++i) sum += count[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = a; i < b; ++i) {
+        off[i] = run;
+        run += count[i];
+    }
+    if (threadIdx.x == 1023) off[P] = part[1023];
+}
+
+// Per problem (one CTA): writes its tiles (problem, first, end grid point) at its
+// offset; thread t scans a contiguous run of grid points.
+__global__ void __launch_bounds__(TILE_SCAN_THREADS)
+k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ off, int4* __restrict__ tiles) {
+    const BatchProblem pr = probs[blockIdx.x];
+    const int Ms = 2 * pr.M;
+    const int per = (Ms + TILE_SCAN_THREADS - 1) / TILE_SCAN_THREADS;
+    const int a = min((int)threadIdx.x * per, Ms), b = min(a + per, Ms);
+    int c = 0;
+    for (int p = a; p < b; ++p) c += tile_start(pr.col_off, p);
+    __shared__ int part[TILE_SCAN_THREADS];
+    part[threadIdx.x] = c;
+    __syncthreads();
+    for (int d = 1; d < TILE_SCAN_THREADS; d <<= 1) {
+        const int v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int pos = off[blockIdx.x] + part[threadIdx.x] - c;
+    for (int p = a; p < b; ++p) {
+        if (!tile_start(pr.col_off, p)) continue;
+        int q = p + 1;   // the tile ends at the next start
+        while (q < Ms && !tile_start(pr.col_off, q)) ++q;
+        tiles[pos++] = make_int4((int)blockIdx.x, p, q, 0);
+    }
+}
+
+// Spreading of all problems: CTA t spreads tile t (problem, [p0, p1)) into the
+// problem's slice of g_all; CTAs beyond the number of tiles return.
 __global__ void __launch_bounds__(SPREAD_COLS)
-k_batch_spread(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ tile_prob,
-               const int32_t* __restrict__ tile_p0, const float2* __restrict__ f, float2* __restrict__ g_all) {
+k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ tiles,
+               const int32_t* __restrict__ ntiles, const float2* __restrict__ f, float2* __restrict__ g_all) {
     __shared__ __align__(16) float ws[SPREAD_WMAX];
     __shared__ __align__(16) float2 fu[SPREAD_UMAX];
-    const BatchProblem pr = probs[tile_prob[blockIdx.x]];
+    if ((int)blockIdx.x >= *ntiles) return;
+    const int4 t = tiles[blockIdx.x];
+    const BatchProblem pr = probs[t.x];
     spread_tile_f32(f + pr.f_off, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_count, pr.col_off, pr.N,
-                    2 * pr.M, tile_p0[blockIdx.x], g_all + pr.g_off, ws, fu);
+                    t.y, t.z, g_all + pr.g_off, ws, fu);
 }
 
 // D^* F^* of every problem's grid (pruned to its M central frequencies): one CTA
@@ -190,6 +326,8 @@ k_batch_fft(const BatchProblem* __restrict__ probs, int P, const int32_t* __rest
     float2* buf = sm;                    // pad16(L) <= pad16(TW_N)
     float2* gO = sm + pad16(TW_N);       // odd grid values, M <= BATCH_MMAX
     __shared__ int s_job;
+    __shared__ TwTables twt;
+    tw_tables_load(&twt, tw);
     for (;;) {
         if (threadIdx.x == 0) s_job = atomicAdd(ticket, 1);
         __syncthreads();
@@ -198,6 +336,22 @@ k_batch_fft(const BatchProblem* __restrict__ probs, int P, const int32_t* __rest
         if (job >= P) break;
         const BatchProblem pr = probs[order[job]];
         const int M = pr.M, L = 1 << pr.logL;
+        const float dk = 1.0f / (float)(2 * M);
+        float2* out = fhat + pr.fhat_off;
+        if (pr.full) {
+            const float2* gp = g_all + pr.g_off;
+            for (int j = threadIdx.x; j < 2 * M; j += blockDim.x) buf[pad16(j)] = cmul(gp[j], chirp4(j - M, M));
+            for (int i = 2 * M + threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = make_float2(0.f, 0.f);
+            __syncthreads();
+            chirp_convolve(buf, pr.logL, pr.bhat, &twt);
+            const float invL = 1.0f / (float)L;
+            for (int k = threadIdx.x; k < M; k += blockDim.x) {
+                const float2 h = cscale(cmul(buf[pad16(k)], chirp4(k - M / 2, M)), invL);
+                out[k] = cscale(h, (pr.sym && k == 0) ? 0.0f : dk);
+            }
+            __syncthreads();
+            continue;
+        }
         const float4* g4 = (const float4*)(g_all + pr.g_off);   // (g_{2n'}, g_{2n'+1})
         for (int n = threadIdx.x; n < M; n += blockDim.x) {
             const float4 v = g4[n];
@@ -206,7 +360,7 @@ k_batch_fft(const BatchProblem* __restrict__ probs, int P, const int32_t* __rest
         }
         for (int i = M + threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = make_float2(0.f, 0.f);
         __syncthreads();
-        chirp_convolve(buf, pr.logL, pr.bhat, tw);
+        chirp_convolve(buf, pr.logL, pr.bhat, &twt);
         const float invL = 1.0f / (float)L;
         float2 X0[BATCH_STASH];
 #pragma unroll
@@ -218,9 +372,7 @@ k_batch_fft(const BatchProblem* __restrict__ probs, int P, const int32_t* __rest
         for (int n = threadIdx.x; n < M; n += blockDim.x) buf[pad16(n)] = cmul(gO[n], chirp(n, M));
         for (int i = M + threadIdx.x; i < L; i += blockDim.x) buf[pad16(i)] = make_float2(0.f, 0.f);
         __syncthreads();
-        chirp_convolve(buf, pr.logL, pr.bhat, tw);
-        const float dk = 1.0f / (float)(2 * M);
-        float2* out = fhat + pr.fhat_off;
+        chirp_convolve(buf, pr.logL, pr.bhat, &twt);
 #pragma unroll
         for (int j = 0; j < BATCH_STASH; ++j) {
             const int k = threadIdx.x + j * BATCH_FFT_THREADS;
@@ -300,9 +452,10 @@ struct infft_batch_s {
     double* huge_scratch = nullptr;
     int32_t* order = nullptr;       // problems by decreasing size
     int32_t* ticket = nullptr;
-    int32_t* tile_prob = nullptr;
-    int32_t* tile_p0 = nullptr;
-    int64_t tiles = 0;
+    int4* tiles = nullptr;          // (problem, first, end, -) per spreading tile
+    int32_t* tile_count = nullptr;  // P counts, then P + 1 offsets
+    int32_t* tile_off = nullptr;
+    int64_t max_tiles = 0;
     const int32_t** d_counters = nullptr;
     const int32_t** d_col_off = nullptr;
     const double** d_J = nullptr;
@@ -319,7 +472,7 @@ namespace {
 void batch_free(infft_batch_t b) {
     for (Plan* p : b->plans) delete p;
     void* bufs[] = {b->arena, b->x_all, b->g_all, b->bhat, b->tw, b->stage_f, b->stage_fhat, b->probs,
-                    b->huge_probs, b->job_off, b->huge_scratch, b->order, b->ticket, b->tile_prob, b->tile_p0,
+                    b->huge_probs, b->job_off, b->huge_scratch, b->order, b->ticket, b->tiles, b->tile_count, b->tile_off,
                     (void*)b->d_counters, (void*)b->d_col_off, (void*)b->d_J, b->d_Ms, b->d_info};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -399,13 +552,14 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     b->moff.resize(P + 1);
     b->noff[0] = b->moff[0] = 0;
     std::vector<int64_t> goff(P + 1, 0), loff(P + 1, 0);
-    std::vector<int> logL(P);
+    std::vector<int> logL(P), full(P);
     int64_t maxN = 0;
     for (int64_t i = 0; i < P; ++i) {
         b->noff[i + 1] = b->noff[i] + N[i];
         b->moff[i + 1] = b->moff[i] + M[i];
         goff[i + 1] = goff[i] + 2 * M[i];
-        logL[i] = log2_ceil(2 * M[i] - 1);
+        full[i] = 3 * M[i] - 1 <= TW_N;
+        logL[i] = log2_ceil(full[i] ? 3 * M[i] - 1 : 2 * M[i] - 1);
         loff[i + 1] = loff[i] + (int64_t(1) << logL[i]);
         maxN = std::max(maxN, N[i]);
     }
@@ -452,16 +606,13 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     alloc(&b->d_info, 8 * P * sizeof(double));
     b->huge_slots = maxN > LSQ_CTA_NMAX ? b->sms : 0;
     if (b->huge_slots) alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots) * sizeof(double));
-    // tiles of the batched spreading
-    std::vector<int32_t> tprob, tp0;
+    // tiles of the batched spreading: at most one per SPREAD_COLS grid points plus
+    // one per TILE_WEIGHTS weights of the largest possible nnz
     for (int64_t i = 0; i < P; ++i)
-        for (int64_t p0 = 0; p0 < 2 * M[i]; p0 += SPREAD_COLS) {
-            tprob.push_back((int32_t)i);
-            tp0.push_back((int32_t)p0);
-        }
-    b->tiles = (int64_t)tprob.size();
-    alloc(&b->tile_prob, b->tiles * sizeof(int32_t));
-    alloc(&b->tile_p0, b->tiles * sizeof(int32_t));
+        b->max_tiles += (2 * M[i] + SPREAD_COLS - 1) / SPREAD_COLS + b->plans[i]->nnz_cap / TILE_WEIGHTS + 1;
+    alloc(&b->tiles, b->max_tiles * sizeof(int4));
+    alloc(&b->tile_count, P * sizeof(int32_t));
+    alloc(&b->tile_off, (P + 1) * sizeof(int32_t));
     for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
@@ -485,15 +636,16 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
         d.bhat = b->bhat + loff[i];
         d.f_off = b->noff[i]; d.fhat_off = b->moff[i]; d.g_off = goff[i];
         d.N = (int)N[i]; d.M = (int)M[i]; d.logL = logL[i]; d.sym = kernel == INFFT_KERNEL_SYM;
+        d.full = full[i];
         hc[i] = p->counters; ho[i] = p->col_off; hj[i] = p->J; hms[i] = (int32_t)p->Ms;
     }
     std::vector<char> hh(P * huge_problem_bytes());
     huge_problems_fill(b->plans.data(), (int)P, hh.data());
     std::vector<int32_t> ord(P);
     std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) {
-        return (N[a] + M[a] * (int64_t)logL[a]) > (N[c] + M[c] * (int64_t)logL[c]);
-    });
+    // largest first: grid reads plus transform work (2 or 4 transforms of length L)
+    auto cost = [&](int32_t i) { return (double)N[i] + (full[i] ? 2.0 : 4.0) * (double)(int64_t(1) << logL[i]) * logL[i] / 8.0; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) { return cost(a) > cost(c); });
     std::vector<float2> htw(TW_N);
     for (int t = 0; t < TW_N; ++t) {
         // e^{-2 pi i t/TW_N} from the exactly reduced fraction t/TW_N
@@ -506,8 +658,6 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     if (e == cudaSuccess) e = cudaMemcpy(b->huge_probs, hh.data(), hh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->order, ord.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->tw, htw.data(), TW_N * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->tile_prob, tprob.data(), b->tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->tile_p0, tp0.data(), b->tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_counters, hc.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_col_off, ho.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_J, hj.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
@@ -581,6 +731,12 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
         (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->huge_scratch, b->huge_slots, s)) !=
             cudaSuccess)
         return cuda_err(e, "large-column precompute");
+    // spreading tiles from the weight offsets
+    k_tile_count<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, b->tile_count);
+    k_tile_prefix<<<1, 1024, 0, s>>>(b->tile_count, (int)b->P, b->tile_off);
+    k_tile_fill<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, b->tile_off, b->tiles);
+    count_launches(3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "spreading tiles");
     b->precomputed = 1;
     return INFFT_OK;
 }
@@ -601,7 +757,8 @@ infft_status infft_batch_apply(infft_batch_t b, const float* f, float* fhat, inf
     }
     const bool host_out = !on_device(fhat);
     float2* fout = host_out ? b->stage_fhat : (float2*)fhat;
-    k_batch_spread<<<(unsigned)b->tiles, SPREAD_COLS, 0, s>>>(b->probs, b->tile_prob, b->tile_p0, fin, b->g_all);
+    k_batch_spread<<<(unsigned)b->max_tiles, SPREAD_COLS, 0, s>>>(b->probs, b->tiles, b->tile_off + b->P, fin,
+                                                                 b->g_all);
     const size_t smem = (size_t)(pad16(TW_N) + BATCH_MMAX) * sizeof(float2);
     if ((e = cudaFuncSetAttribute(k_batch_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return cuda_err(e, "shared memory");

@@ -98,7 +98,8 @@ k_spread_f32(const float2* __restrict__ f, const float* __restrict__ w32, const 
     __shared__ __align__(16) float2 fu[SPREAD_UMAX];
     griddep_wait();
     griddep_launch();
-    spread_tile_f32(f, w32, w64, wide, perm, col_start, col_count, col_off, N, Ms, blockIdx.x * SPREAD_COLS, g,
+    const int p0 = blockIdx.x * SPREAD_COLS;
+    spread_tile_f32(f, w32, w64, wide, perm, col_start, col_count, col_off, N, p0, min(p0 + SPREAD_COLS, Ms), g,
                     ws, fu);
 }
 
