@@ -162,7 +162,6 @@ void plan_layout(Plan* p, Carver& c, bool member) {
     c.take(p->col_start, Ms); c.take(p->col_count, Ms); c.take(p->col_off, Ms + 1);
     c.take(p->big_list, Ms); c.take(p->list_a, Ms); c.take(p->tiles_mid, Ms / 32 + 2);
     c.take(p->tiles_big, Ms / 32 + 2);
-    if (member) c.take(p->huge_list, Ms);
     c.take(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
     c.take(p->phase, N);
     c.take(p->counters, CNT_N);

@@ -4,8 +4,8 @@
 // Pattern and precompute: every problem is a plan of its own whose buffers are
 // carved from one allocation; their launches are spread over a pool of streams
 // (stream-ordered after the caller's stream, so the whole precompute can be
-// captured in a CUDA graph), and the columns above the CTA solver's limit of
-// all problems go to one large-column launch.
+// captured in a CUDA graph), and the columns of more than 64 nodes of all
+// problems go to one launch of the blocked solver.
 //
 // Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of at
 // most 256 grid points of one problem (the staged tile of the single-problem
@@ -46,7 +46,7 @@ constexpr int TW_LOG = 14;
 constexpr int TW_N = 1 << TW_LOG;                 // twiddle table e^{-2 pi i t / TW_N}
 constexpr int BATCH_MMAX = TW_N / 2;              // 2M - 1 <= TW_N
 constexpr int BATCH_STASH = BATCH_MMAX / BATCH_FFT_THREADS;
-constexpr int BATCH_STREAMS = 16;
+constexpr int BATCH_STREAMS = 48;
 
 struct BatchProblem {
     const float* w32;
@@ -435,7 +435,7 @@ int log2_ceil(int64_t v) {
 struct infft_batch_s {
     int device = 0;
     int64_t P = 0, sumN = 0, sumM = 0, sumG = 0, sumL = 0;
-    int m = 0, kernel = INFFT_KERNEL_FULL, sms = 0, huge_slots = 0;
+    int m = 0, kernel = INFFT_KERNEL_FULL, sms = 0, huge_slots = 0, huge_nmax = 0;
     double sigma = 2.0, tau = 1e-12;
     std::vector<int64_t> M, N, noff, moff;
     std::vector<Plan*> plans;
@@ -574,6 +574,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
         p->ansatz = INFFT_ANSATZ_OVERDETERMINED;
         p->logMs = log2_ceil(p->Ms);
         p->nnz_cap = N[i] * (2 * (int64_t)m + 1);
+        p->batch_member = true;
         b->plans[i] = p;
         Carver c;
         plan_layout(p, c, true);
@@ -604,8 +605,11 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     alloc(&b->d_J, P * sizeof(void*));
     alloc(&b->d_Ms, P * sizeof(int32_t));
     alloc(&b->d_info, 8 * P * sizeof(double));
-    b->huge_slots = maxN > LSQ_CTA_NMAX ? b->sms : 0;
-    if (b->huge_slots) alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots) * sizeof(double));
+    // blocked solver for columns above the warp tier: one scratch triangle per CTA,
+    // sized for the largest column a problem can have (at most N nodes)
+    b->huge_nmax = (int)std::min<int64_t>(maxN, HUGE_NMAX);
+    b->huge_slots = maxN > LSQ_WARP2_NMAX ? b->sms : 0;
+    if (b->huge_slots) alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots, b->huge_nmax) * sizeof(double));
     // tiles of the batched spreading: at most one per SPREAD_COLS grid points plus
     // one per TILE_WEIGHTS weights of the largest possible nnz
     for (int64_t i = 0; i < P; ++i)
@@ -728,7 +732,8 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
     }
     if ((e = join_streams(b, s)) != cudaSuccess) return cuda_err(e, "join");
     if (b->huge_slots &&
-        (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->huge_scratch, b->huge_slots, s)) !=
+        (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->huge_scratch, b->huge_slots, b->huge_nmax,
+                                 s)) !=
             cudaSuccess)
         return cuda_err(e, "large-column precompute");
     // spreading tiles from the weight offsets

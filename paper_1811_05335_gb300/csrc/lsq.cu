@@ -745,7 +745,7 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
           const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
           KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
           double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ big_list,
-          int32_t* __restrict__ huge_list, int32_t* __restrict__ counters) {
+          int32_t* __restrict__ counters) {
     extern __shared__ double smem[];
     double* A = smem;                  // CN (CN + 1) / 2, packed rows
     double* r = A + CN * (CN + 1) / 2; // CN
@@ -758,10 +758,6 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
         const int p = big_list[it];
         const int n = col_count[p], s = col_start[p], off = col_off[p];
         if (n > CN) {
-            if (huge_list) {   // solved later by the large-column tier
-                if (threadIdx.x == 0) huge_list[atomicAdd(&counters[CNT_HUGE_LIST], 1)] = p;
-                continue;
-            }
             for (int i = threadIdx.x; i < n; i += CTA_THREADS) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
             if (threadIdx.x == 0) { Jout[p] = 1.0; wide[p] = 0; atomicAdd(&counters[CNT_UNSUPPORTED], 1); }
             continue;
@@ -865,13 +861,14 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
 
 // ---------------------------------------------------------------- tier 5: large columns
 //
-// Columns above the CTA tier (clustered nodes put hundreds of nodes into the
-// columns next to the cluster) are solved one CTA per column with the packed
-// triangle in a global scratch slot of the CTA.  Blocked right-looking Cholesky:
+// Columns above the warp tier of the problems of a batch (clustered nodes put
+// tens to hundreds of nodes into the columns next to the cluster) are solved in
+// one launch, one CTA per column with the packed triangle in a global scratch
+// slot of the CTA.  Blocked right-looking Cholesky:
 // a panel of HUGE_PB columns is staged in shared memory, factored there, written
 // back, and the trailing triangle is updated in 4x4 register blocks (fp64-pipe
 // bound: 256 multiply-adds per 32 global accesses).  The kernel serves every
-// problem of a batch: jobs are numbered across the problems' huge lists through
+// problem of a batch: jobs are numbered across the problems' big lists through
 // an exclusive prefix of their lengths.
 
 constexpr int HUGE_PB = 16;
@@ -883,7 +880,7 @@ __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int3
     const int per = (P + 1023) / 1024;
     const int a = threadIdx.x * per, b = min(a + per, P);
     int32_t sum = 0;
-    for (int i = a; i < b; ++i) sum += probs[i].counters[CNT_HUGE_LIST];
+    for (int i = a; i < b; ++i) sum += probs[i].counters[CNT_BIG_LIST];
     part[threadIdx.x] = sum;
     __syncthreads();
     for (int d = 1; d < 1024; d <<= 1) {
@@ -895,21 +892,21 @@ __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int3
     int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
     for (int i = a; i < b; ++i) {
         job_off[i] = run;
-        run += probs[i].counters[CNT_HUGE_LIST];
+        run += probs[i].counters[CNT_BIG_LIST];
     }
     if (threadIdx.x == 1023) job_off[P] = part[1023];
 }
 
 __global__ void __launch_bounds__(HUGE_THREADS, 1)
 k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
-           double* __restrict__ scratch) {
+           double* __restrict__ scratch, int nmax) {
     extern __shared__ double smem[];
     double* pan = smem;                          // HUGE_NMAX x HUGE_PB panel (row-major)
     double* r = pan + HUGE_NMAX * HUGE_PB;       // HUGE_NMAX
     double* xl = r + HUGE_NMAX;                  // HUGE_NMAX
     double2* pv = (double2*)(xl + HUGE_NMAX);    // HUGE_NMAX
     __shared__ double s_red[2 * (HUGE_THREADS / 32)];
-    double* A = scratch + (size_t)blockIdx.x * (HUGE_NMAX * (HUGE_NMAX + 1) / 2);
+    double* A = scratch + (size_t)blockIdx.x * ((size_t)nmax * (nmax + 1) / 2);
     const int total = job_off[P];
     const int tid = threadIdx.x;
     for (int job = blockIdx.x; job < total; job += gridDim.x) {
@@ -919,9 +916,10 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
             if (job_off[mid] <= job) lo = mid; else hi = mid - 1;
         }
         const HugeProblem& pr = probs[lo];
-        const int p = pr.huge_list[job - job_off[lo]];
+        const int p = pr.big_list[job - job_off[lo]];
         const int n = pr.col_count[p], s = pr.col_start[p], off = pr.col_off[p], N = pr.N;
-        if (n > HUGE_NMAX) {
+        if (tid == 0 && n > LSQ_CTA_NMAX) atomicAdd(&pr.counters[CNT_HUGE_LIST], 1);
+        if (n > nmax) {
             for (int i = tid; i < n; i += HUGE_THREADS) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
             if (tid == 0) { pr.J[p] = 1.0; pr.wide[p] = 0; atomicAdd(&pr.counters[CNT_UNSUPPORTED], 1); }
             continue;
@@ -937,14 +935,17 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
         }
         __syncthreads();
         double mu = pr.mu;
+        double ysq = 0.0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
             for (int i = tid; i < n; i += HUGE_THREADS) r[i] = re_kappa(tl, xl[i], pl, pv[i], kp);
             const int ntri = n * (n + 1) / 2;
-            for (int i = 0; i < n; ++i)   // row by row: row i has i + 1 entries
-                for (int j = tid; j <= i; j += HUGE_THREADS)
-                    A[trow(i) + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kp);
-            (void)ntri;
+            for (int e = tid; e < ntri; e += HUGE_THREADS) {   // packed row-major: entry e is (i, j)
+                int i, j;
+                tri_index(e, i, j);
+                A[e] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kp);
+            }
+            ysq = 0.0;
             __syncthreads();
             bool failed = false;   // block-uniform: decided on shared values
             for (int kb = 0; kb < n && !failed; kb += HUGE_PB) {
@@ -975,6 +976,16 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                     __syncthreads();
                 }
                 if (failed) break;
+                // forward solve L y = r for this panel's columns (the column-oriented
+                // elimination needs only the panel, which is in shared memory)
+                for (int c = 0; c < w; ++c) {
+                    const double yc = r[kb + c] * pan[c * HUGE_PB + c];
+                    ysq = fma(yc, yc, ysq);
+                    __syncthreads();
+                    if (tid == 0) r[kb + c] = yc;
+                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) r[kb + i] = fma(-pan[i * HUGE_PB + c], yc, r[kb + i]);
+                    __syncthreads();
+                }
                 for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
                     const int i = e / HUGE_PB, c = e % HUGE_PB;
                     if (c < w && c <= i) A[trow(kb + i) + kb + c] = pan[e];
@@ -1029,23 +1040,22 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
             continue;
         }
         if (tid == 0 && mu != pr.mu) atomicAdd(&pr.counters[CNT_FALLBACK], 1);
-        // forward solve L y = r (diagonal entries hold reciprocal pivots), column by column
-        double ysq = 0.0;
-        for (int k = 0; k < n; ++k) {
-            const double yk = r[k] * A[trow(k) + k];
-            ysq = fma(yk, yk, ysq);
+        // back solve L^T b = y in blocks of HUGE_PB rows of L staged in shared memory
+        // (row k of L is contiguous in the packed storage; diagonal = reciprocal pivot)
+        for (int kb = ((n - 1) / HUGE_PB) * HUGE_PB; kb >= 0; kb -= HUGE_PB) {
+            const int hb = min(HUGE_PB, n - kb);
             __syncthreads();
-            if (tid == 0) r[k] = yk;
-            for (int i = k + 1 + tid; i < n; i += HUGE_THREADS) r[i] = fma(-A[trow(i) + k], yk, r[i]);
+            for (int c = 0; c < hb; ++c)
+                for (int i = tid; i <= kb + c; i += HUGE_THREADS) pan[c * HUGE_NMAX + i] = A[trow(kb + c) + i];
             __syncthreads();
-        }
-        // back solve L^T b = y, row by row
-        for (int k = n - 1; k >= 0; --k) {
-            const double bk = r[k] * A[trow(k) + k];
-            __syncthreads();
-            if (tid == 0) r[k] = bk;
-            for (int i = tid; i < k; i += HUGE_THREADS) r[i] = fma(-A[trow(k) + i], bk, r[i]);
-            __syncthreads();
+            for (int c = hb - 1; c >= 0; --c) {
+                const int k = kb + c;
+                const double bk = r[k] * pan[c * HUGE_NMAX + k];
+                __syncthreads();
+                if (tid == 0) r[k] = bk;
+                for (int i = tid; i < k; i += HUGE_THREADS) r[i] = fma(-pan[c * HUGE_NMAX + i], bk, r[i]);
+                __syncthreads();
+            }
         }
         double bsq = 0.0, babs = 0.0;
         for (int i = tid; i < n; i += HUGE_THREADS) {
@@ -1140,11 +1150,13 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
                                     CNT_BIG_LIST, p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // CTA tier: the big list, one CTA per column, |I(l)| <= 224
+    // CTA tier: the big list, one CTA per column, |I(l)| <= 224.  Batch members leave
+    // their big list to the batch's blocked solver, which takes every problem's list
+    // in one launch.
+    if (p->batch_member) return cudaGetLastError();
     launch_begin(p, "lsq_cta", s);
     k_lsq_cta<<<sms, CTA_THREADS, s5, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                           p->w64, p->w32, p->J, p->wide, p->big_list, p->huge_list,
-                                           p->counters);
+                                           p->w64, p->w32, p->J, p->wide, p->big_list, p->counters);
     launch_end(p, s);
     return cudaGetLastError();
 }
@@ -1154,7 +1166,7 @@ HugeProblem huge_problem(const Plan* p) {
     HugeProblem h;
     h.xs = p->xs; h.ph = p->phase; h.col_start = p->col_start; h.col_count = p->col_count; h.col_off = p->col_off;
     h.w64 = p->w64; h.w32 = p->w32; h.J = p->J; h.wide = p->wide; h.counters = p->counters;
-    h.huge_list = p->huge_list;
+    h.big_list = p->big_list;
     h.N = (int)p->N; h.Ms = (int)p->Ms;
     h.kp = make_kernel_params(p);
     h.mu = p->tau * h.kp.diag;
@@ -1169,9 +1181,9 @@ void huge_problems_fill(Plan* const* plans, int P, void* host) {
     for (int i = 0; i < P; ++i) h[i] = huge_problem(plans[i]);
 }
 
-size_t huge_scratch_doubles(int slots) { return (size_t)slots * (HUGE_NMAX * (HUGE_NMAX + 1) / 2); }
+size_t huge_scratch_doubles(int slots, int nmax) { return (size_t)slots * ((size_t)nmax * (nmax + 1) / 2); }
 
-cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots,
+cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots, int nmax,
                                 cudaStream_t s) {
     const size_t smem = (size_t)(HUGE_NMAX * HUGE_PB + 2 * HUGE_NMAX) * sizeof(double) +
                         (size_t)HUGE_NMAX * sizeof(double2);
@@ -1179,7 +1191,7 @@ cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, doub
     if (e != cudaSuccess) return e;
     const HugeProblem* hp = (const HugeProblem*)probs;
     k_huge_prefix<<<1, 1024, 0, s>>>(hp, P, job_off);
-    k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, scratch);
+    k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, scratch, nmax);
     count_launches(2);
     return cudaGetLastError();
 }

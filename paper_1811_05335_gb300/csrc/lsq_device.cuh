@@ -238,7 +238,7 @@ struct HugeProblem {
     double* J;
     uint8_t* wide;
     int32_t* counters;
-    const int32_t* huge_list;
+    const int32_t* big_list;
     int N, Ms;
     double mu;
     KernelParams kp;

@@ -21,7 +21,7 @@ enum {
     CNT_TILES_MID = 8,     // tiles routed to the 25-node thread tier
     CNT_TILES_BIG = 9,     // tiles routed to the 33-node thread tier
     CNT_GRAD_FAIL = 10,    // columns the node gradient could not factor (or too large)
-    CNT_HUGE_LIST = 11,    // columns queued for the large-column solver (batch members)
+    CNT_HUGE_LIST = 11,    // batch members: columns above 224 nodes solved by the batch's blocked solver
     CNT_N = 12
 };
 
@@ -71,7 +71,6 @@ struct infft_plan_s {
     int32_t* tiles_mid = nullptr;   // Ms/32 + 1 (tiles for the 25-node thread tier)
     int32_t* tiles_big = nullptr;   // Ms/32 + 1 (tiles for the 33-node thread tier)
     int32_t* big_list = nullptr;    // Ms (columns for the CTA solver)
-    int32_t* huge_list = nullptr;   // Ms (columns above the CTA solver; batch members only)
     int32_t* scan_sums = nullptr;   // per-block partial sums of the scans
     int32_t* counters = nullptr;    // CNT_N
 
@@ -95,6 +94,7 @@ struct infft_plan_s {
     void* stage_out = nullptr;  // max(N, M) double2: host-output staging
 
     void* arena = nullptr;      // the one device allocation holding the buffers above (owned)
+    bool batch_member = false;  // buffers carved from a batch; big columns go to the batch's solver
     int nodes_set = 0, precomputed = 0;
     cudaStream_t last_stream = nullptr;
 
@@ -137,13 +137,14 @@ cudaError_t run_pattern(Plan* p, cudaStream_t s);
 cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s);
 // lsq.cu
 cudaError_t run_precompute(Plan* p, cudaStream_t s);
-// lsq.cu: the large-column tier over the huge lists of P problems (batch members);
-// job_off: P + 1 ints of device scratch; scratch: huge_scratch_doubles(slots) doubles
+// lsq.cu: the blocked solver over the big lists (columns above 64 nodes) of P batch members;
+// job_off: P + 1 ints of device scratch; scratch: huge_scratch_doubles(slots, nmax) doubles,
+// nmax <= HUGE_NMAX the largest column it solves (larger ones: b_l = 0, counted unsupported)
 constexpr int HUGE_NMAX = 1024;
 size_t huge_problem_bytes();                                   // size of one device descriptor
 void huge_problems_fill(Plan* const* plans, int P, void* host); // P descriptors into host memory
-size_t huge_scratch_doubles(int slots);
-cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots,
+size_t huge_scratch_doubles(int slots, int nmax);
+cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots, int nmax,
                                 cudaStream_t s);
 // under.cu: the underdetermined case; under_moment_chunks = partial-sum blocks of the node moments
 cudaError_t run_precompute_under(Plan* p, cudaStream_t s);
