@@ -449,6 +449,8 @@ struct infft_batch_s {
     BatchProblem* probs = nullptr;  // P apply descriptors
     void* huge_probs = nullptr;     // P large-column descriptors
     int32_t* job_off = nullptr;     // P + 1
+    int32_t* job_order = nullptr;   // sum M_sigma: blocked-solver jobs, largest first
+    int32_t* job_work = nullptr;    // HUGE_NMAX + 2: size buckets and the ticket
     double* huge_scratch = nullptr;
     int32_t* order = nullptr;       // problems by decreasing size
     int32_t* ticket = nullptr;
@@ -472,7 +474,7 @@ namespace {
 void batch_free(infft_batch_t b) {
     for (Plan* p : b->plans) delete p;
     void* bufs[] = {b->arena, b->x_all, b->g_all, b->bhat, b->tw, b->stage_f, b->stage_fhat, b->probs,
-                    b->huge_probs, b->job_off, b->huge_scratch, b->order, b->ticket, b->tiles, b->tile_count, b->tile_off,
+                    b->huge_probs, b->job_off, b->job_order, b->job_work, b->huge_scratch, b->order, b->ticket, b->tiles, b->tile_count, b->tile_off,
                     (void*)b->d_counters, (void*)b->d_col_off, (void*)b->d_J, b->d_Ms, b->d_info};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -609,7 +611,11 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     // sized for the largest column a problem can have (at most N nodes)
     b->huge_nmax = (int)std::min<int64_t>(maxN, HUGE_NMAX);
     b->huge_slots = maxN > LSQ_WARP2_NMAX ? b->sms : 0;
-    if (b->huge_slots) alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots, b->huge_nmax) * sizeof(double));
+    if (b->huge_slots) {
+        alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots, b->huge_nmax) * sizeof(double));
+        alloc(&b->job_order, b->sumG * sizeof(int32_t));
+        alloc(&b->job_work, (HUGE_NMAX + 2) * sizeof(int32_t));
+    }
     // tiles of the batched spreading: at most one per SPREAD_COLS grid points plus
     // one per TILE_WEIGHTS weights of the largest possible nnz
     for (int64_t i = 0; i < P; ++i)
@@ -732,8 +738,8 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
     }
     if ((e = join_streams(b, s)) != cudaSuccess) return cuda_err(e, "join");
     if (b->huge_slots &&
-        (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->huge_scratch, b->huge_slots, b->huge_nmax,
-                                 s)) !=
+        (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->job_order, b->job_work, b->huge_scratch,
+                                 b->huge_slots, b->huge_nmax, s)) !=
             cudaSuccess)
         return cuda_err(e, "large-column precompute");
     // spreading tiles from the weight offsets

@@ -872,6 +872,7 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
 // an exclusive prefix of their lengths.
 
 constexpr int HUGE_PB = 16;
+constexpr int HUGE_PS = HUGE_PB + 1;   // panel row stride: rows 4 apart hit different banks
 constexpr int HUGE_THREADS = 256;
 
 __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int32_t* __restrict__ job_off) {
@@ -897,19 +898,77 @@ __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int3
     if (threadIdx.x == 1023) job_off[P] = part[1023];
 }
 
+// Largest-first order of the jobs (a counting sort by column size, descending):
+// the cost of a column grows as n^3, so taking the largest first keeps the CTAs
+// of the persistent solver evenly loaded.
+INFFT_D int job_size(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off, int job,
+                     int nmax) {
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (job_off[mid] <= job) lo = mid; else hi = mid - 1;
+    }
+    const HugeProblem& pr = probs[lo];
+    return min(pr.col_count[pr.big_list[job - job_off[lo]]], nmax);
+}
+
+__global__ void k_job_hist(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
+                           int nmax, int32_t* __restrict__ hist) {
+    const int total = job_off[P];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x)
+        atomicAdd(&hist[nmax - job_size(probs, P, job_off, j, nmax)], 1);
+}
+
+// exclusive prefix of the nmax + 1 bucket counts (one CTA of 1024 threads), in place
+__global__ void __launch_bounds__(1024) k_job_scan(int32_t* __restrict__ hist, int nb) {
+    __shared__ int32_t part[1024];
+    const int per = (nb + 1023) / 1024;
+    const int a = threadIdx.x * per, b = min(a + per, nb);
+    int32_t sum = 0;
+    for (int i = a; i < b; ++i) sum += hist[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = a; i < b; ++i) {
+        const int32_t c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
+}
+
+__global__ void k_job_scatter(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
+                              int nmax, int32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+    const int total = job_off[P];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x)
+        order[atomicAdd(&cursor[nmax - job_size(probs, P, job_off, j, nmax)], 1)] = j;
+}
+
 __global__ void __launch_bounds__(HUGE_THREADS, 1)
 k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
-           double* __restrict__ scratch, int nmax) {
+           const int32_t* __restrict__ order, int32_t* __restrict__ ticket, double* __restrict__ scratch, int nmax) {
     extern __shared__ double smem[];
-    double* pan = smem;                          // HUGE_NMAX x HUGE_PB panel (row-major)
-    double* r = pan + HUGE_NMAX * HUGE_PB;       // HUGE_NMAX
+    double* pan = smem;                          // HUGE_NMAX x HUGE_PB panel (row stride HUGE_PS)
+    double* r = pan + HUGE_NMAX * HUGE_PS;       // HUGE_NMAX
     double* xl = r + HUGE_NMAX;                  // HUGE_NMAX
     double2* pv = (double2*)(xl + HUGE_NMAX);    // HUGE_NMAX
     __shared__ double s_red[2 * (HUGE_THREADS / 32)];
+    __shared__ int s_t;
     double* A = scratch + (size_t)blockIdx.x * ((size_t)nmax * (nmax + 1) / 2);
     const int total = job_off[P];
     const int tid = threadIdx.x;
-    for (int job = blockIdx.x; job < total; job += gridDim.x) {
+    for (;;) {
+        if (tid == 0) s_t = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= total) break;
+        const int job = order[t];   // largest columns first
         int lo = 0, hi = P - 1;   // problem: the last i with job_off[i] <= job
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -952,26 +1011,26 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                 const int w = min(HUGE_PB, n - kb), R = n - kb;
                 for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
                     const int i = e / HUGE_PB, c = e % HUGE_PB;
-                    pan[e] = (c < w && c <= i) ? A[trow(kb + i) + kb + c] : 0.0;
+                    pan[i * HUGE_PS + c] = (c < w && c <= i) ? A[trow(kb + i) + kb + c] : 0.0;
                 }
                 __syncthreads();
                 for (int c = 0; c < w; ++c) {
-                    const double akk = pan[c * HUGE_PB + c];
+                    const double akk = pan[c * HUGE_PS + c];
                     if (!(akk > 0.0) || !isfinite(akk)) {
                         failed = true;
                         break;
                     }
                     const double rp = rsqrt(akk);
                     __syncthreads();
-                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) pan[i * HUGE_PB + c] *= rp;
-                    if (tid == 0) pan[c * HUGE_PB + c] = rp;
+                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) pan[i * HUGE_PS + c] *= rp;
+                    if (tid == 0) pan[c * HUGE_PS + c] = rp;
                     __syncthreads();
                     // rank-1 update of the panel's remaining columns c' in (c, w), rows i >= c'
                     const int nc = w - c - 1;
                     for (int e = tid; e < (R - c - 1) * nc; e += HUGE_THREADS) {
                         const int i = c + 1 + e / nc, cc = c + 1 + e % nc;
-                        if (cc <= i) pan[i * HUGE_PB + cc] = fma(-pan[i * HUGE_PB + c], pan[cc * HUGE_PB + c],
-                                                                 pan[i * HUGE_PB + cc]);
+                        if (cc <= i) pan[i * HUGE_PS + cc] = fma(-pan[i * HUGE_PS + c], pan[cc * HUGE_PS + c],
+                                                                 pan[i * HUGE_PS + cc]);
                     }
                     __syncthreads();
                 }
@@ -979,16 +1038,16 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                 // forward solve L y = r for this panel's columns (the column-oriented
                 // elimination needs only the panel, which is in shared memory)
                 for (int c = 0; c < w; ++c) {
-                    const double yc = r[kb + c] * pan[c * HUGE_PB + c];
+                    const double yc = r[kb + c] * pan[c * HUGE_PS + c];
                     ysq = fma(yc, yc, ysq);
                     __syncthreads();
                     if (tid == 0) r[kb + c] = yc;
-                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) r[kb + i] = fma(-pan[i * HUGE_PB + c], yc, r[kb + i]);
+                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) r[kb + i] = fma(-pan[i * HUGE_PS + c], yc, r[kb + i]);
                     __syncthreads();
                 }
                 for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
                     const int i = e / HUGE_PB, c = e % HUGE_PB;
-                    if (c < w && c <= i) A[trow(kb + i) + kb + c] = pan[e];
+                    if (c < w && c <= i) A[trow(kb + i) + kb + c] = pan[i * HUGE_PS + c];
                 }
                 // trailing update of rows/columns [kb + w, n) in 4x4 blocks
                 const int T = n - kb - w;
@@ -1008,8 +1067,8 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                         double li[4], lj[4];
 #pragma unroll
                         for (int a = 0; a < 4; ++a) {
-                            li[a] = (i0 + a < R) ? pan[(i0 + a) * HUGE_PB + c] : 0.0;
-                            lj[a] = (j0 + a < R) ? pan[(j0 + a) * HUGE_PB + c] : 0.0;
+                            li[a] = (i0 + a < R) ? pan[(i0 + a) * HUGE_PS + c] : 0.0;
+                            lj[a] = (j0 + a < R) ? pan[(j0 + a) * HUGE_PS + c] : 0.0;
                         }
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
@@ -1183,15 +1242,21 @@ void huge_problems_fill(Plan* const* plans, int P, void* host) {
 
 size_t huge_scratch_doubles(int slots, int nmax) { return (size_t)slots * ((size_t)nmax * (nmax + 1) / 2); }
 
-cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots, int nmax,
-                                cudaStream_t s) {
-    const size_t smem = (size_t)(HUGE_NMAX * HUGE_PB + 2 * HUGE_NMAX) * sizeof(double) +
+cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int32_t* order, int32_t* work,
+                                double* scratch, int slots, int nmax, cudaStream_t s) {
+    const size_t smem = (size_t)(HUGE_NMAX * HUGE_PS + 2 * HUGE_NMAX) * sizeof(double) +
                         (size_t)HUGE_NMAX * sizeof(double2);
     cudaError_t e = set_smem(k_lsq_huge, smem);
     if (e != cudaSuccess) return e;
     const HugeProblem* hp = (const HugeProblem*)probs;
+    int32_t* hist = work;                  // nmax + 1 buckets (then their offsets, then cursors)
+    int32_t* ticket = work + nmax + 1;
+    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 2) * sizeof(int32_t), s)) != cudaSuccess) return e;
     k_huge_prefix<<<1, 1024, 0, s>>>(hp, P, job_off);
-    k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, scratch, nmax);
-    count_launches(2);
+    k_job_hist<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist);
+    k_job_scan<<<1, 1024, 0, s>>>(hist, nmax + 1);
+    k_job_scatter<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist, order);
+    k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, order, ticket, scratch, nmax);
+    count_launches(5);
     return cudaGetLastError();
 }

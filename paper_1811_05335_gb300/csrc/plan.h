@@ -144,8 +144,9 @@ constexpr int HUGE_NMAX = 1024;
 size_t huge_problem_bytes();                                   // size of one device descriptor
 void huge_problems_fill(Plan* const* plans, int P, void* host); // P descriptors into host memory
 size_t huge_scratch_doubles(int slots, int nmax);
-cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, double* scratch, int slots, int nmax,
-                                cudaStream_t s);
+// order: one int per possible job (sum of the problems' M_sigma); work: nmax + 2 ints
+cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int32_t* order, int32_t* work,
+                                double* scratch, int slots, int nmax, cudaStream_t s);
 // under.cu: the underdetermined case; under_moment_chunks = partial-sum blocks of the node moments
 cudaError_t run_precompute_under(Plan* p, cudaStream_t s);
 int under_moment_chunks(int64_t N);
