@@ -11,6 +11,7 @@
 // use the Taylor series of sin(z)/z and cos(z) instead of the phases, so the
 // cancellation in the angle addition never meets a tiny denominator.
 #pragma once
+#include <cmath>
 #include <cstring>
 
 #include "plan.h"
@@ -28,6 +29,7 @@ struct KernelParams {
     // cs(t^2) = pi M sin(z)/z, z = pi M t.
     double cx[7];
     double cs[9];
+    int short_cot;   // 1: |pi t| of every near pair is so small that terms beyond cx[2] drop below 2^-56
     unsigned long long near_bits;   // bit pattern of 0.25 / M (|t| below it: sin(z)/z series)
 };
 
@@ -146,12 +148,18 @@ INFFT_D double kappa_near(double t, double2 pa, double2 pb, const KernelParams& 
     const unsigned long long tb = (unsigned long long)__double_as_longlong(t) & 0x7fffffffffffffffULL;
     if (tb == 0ULL) return kp.diag;
     const double t2 = t * t;
-    double xc = fma(t2, kp.cx[6], kp.cx[5]);
-    xc = fma(t2, xc, kp.cx[4]);
-    xc = fma(t2, xc, kp.cx[3]);
-    xc = fma(t2, xc, kp.cx[2]);
-    xc = fma(t2, xc, kp.cx[1]);
-    xc = fma(t2, xc, kp.cx[0]);
+    double xc;
+    if (kp.short_cot) {   // uniform across the launch
+        xc = fma(t2, kp.cx[2], kp.cx[1]);
+        xc = fma(t2, xc, kp.cx[0]);
+    } else {
+        xc = fma(t2, kp.cx[6], kp.cx[5]);
+        xc = fma(t2, xc, kp.cx[4]);
+        xc = fma(t2, xc, kp.cx[3]);
+        xc = fma(t2, xc, kp.cx[2]);
+        xc = fma(t2, xc, kp.cx[1]);
+        xc = fma(t2, xc, kp.cx[0]);
+    }
     if (tb <= kp.near_bits) {
         double sz = fma(t2, kp.cs[8], kp.cs[7]);
         sz = fma(t2, sz, kp.cs[6]);
@@ -271,6 +279,13 @@ inline KernelParams make_kernel_params(const Plan* p) {
         }
         const double nb = 0.25 / (double)p->M;
         memcpy(&kp.near_bits, &nb, sizeof nb);
+        // The thread and group tiers call kappa_near only for pairs inside a tile's
+        // node union (32 consecutive columns: cells l0 - m .. l0 + 31 + m), so
+        // |t| < (2m + 34)/M_sigma.  The first dropped term of u cot u is then
+        // |c_3| u^6 with u = pi |t|; three terms suffice when it is below 2^-56.
+        const double u = pi * (double)(2 * p->m + 34) / (double)Ms;
+        const double w3 = u * u * u * u * u * u;
+        kp.short_cot = (2.0 / 945.0) * w3 < std::ldexp(1.0, -56);
     }
     return kp;
 }
