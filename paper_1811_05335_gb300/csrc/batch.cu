@@ -274,8 +274,9 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(const int32_t* __restrict_
     if (threadIdx.x == 1023) off[P] = part[1023];
 }
 
-// Per problem (one CTA): writes its tiles (problem, first, end grid point) at its
-// offset; thread t scans a contiguous run of grid points.
+// Per problem (one CTA): writes its tiles at its offset, two int4 each: (problem,
+// first grid point, end grid point, first node S) and (first weight, end weight,
+// node window U, 0); thread t scans a contiguous run of grid points.
 __global__ void __launch_bounds__(TILE_SCAN_THREADS)
 k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ off, int4* __restrict__ tiles) {
     const BatchProblem pr = probs[blockIdx.x];
@@ -298,19 +299,27 @@ k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ 
         if (!tile_start(pr.col_off, p)) continue;
         int q = p + 1;   // the tile ends at the next start
         while (q < Ms && !tile_start(pr.col_off, q)) ++q;
-        tiles[pos++] = make_int4((int)blockIdx.x, p, q, 0);
+        // the tile's weights [w0, w1) and its window of U sorted nodes from S (mod N)
+        const int S = pr.col_start[p];
+        int U = pr.col_start[q - 1] + pr.col_count[q - 1] - S;
+        if (U < 0) U += pr.N;
+        tiles[2 * pos] = make_int4((int)blockIdx.x, p, q, S);
+        tiles[2 * pos + 1] = make_int4(pr.col_off[p], pr.col_off[q], U, 0);
+        ++pos;
     }
 }
 
 // Spreading of all problems: CTA t spreads tile t (problem, [p0, p1)) into the
-// problem's slice of g_all; CTAs beyond the number of tiles return.
+// problem's slice of g_all; CTAs beyond the number of tiles return.  (A persistent,
+// two-stage software-pipelined variant was slower: 1.48 ms against 1.10 ms on the
+// batched workload, at half the resident threads per SM.)
 __global__ void __launch_bounds__(SPREAD_COLS)
 k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ tiles,
                const int32_t* __restrict__ ntiles, const float2* __restrict__ f, float2* __restrict__ g_all) {
     __shared__ __align__(16) float ws[SPREAD_WMAX];
     __shared__ __align__(16) float2 fu[SPREAD_UMAX];
     if ((int)blockIdx.x >= *ntiles) return;
-    const int4 t = tiles[blockIdx.x];
+    const int4 t = tiles[2 * blockIdx.x];
     const BatchProblem pr = probs[t.x];
     spread_tile_f32(f + pr.f_off, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_count, pr.col_off, pr.N,
                     t.y, t.z, g_all + pr.g_off, ws, fu);
@@ -454,7 +463,7 @@ struct infft_batch_s {
     double* huge_scratch = nullptr;
     int32_t* order = nullptr;       // problems by decreasing size
     int32_t* ticket = nullptr;
-    int4* tiles = nullptr;          // (problem, first, end, -) per spreading tile
+    int4* tiles = nullptr;          // two int4 per spreading tile (see k_tile_fill)
     int32_t* tile_count = nullptr;  // P counts, then P + 1 offsets
     int32_t* tile_off = nullptr;
     int64_t max_tiles = 0;
@@ -620,7 +629,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     // one per TILE_WEIGHTS weights of the largest possible nnz
     for (int64_t i = 0; i < P; ++i)
         b->max_tiles += (2 * M[i] + SPREAD_COLS - 1) / SPREAD_COLS + b->plans[i]->nnz_cap / TILE_WEIGHTS + 1;
-    alloc(&b->tiles, b->max_tiles * sizeof(int4));
+    alloc(&b->tiles, 2 * b->max_tiles * sizeof(int4));
     alloc(&b->tile_count, P * sizeof(int32_t));
     alloc(&b->tile_off, (P + 1) * sizeof(int32_t));
     for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) {

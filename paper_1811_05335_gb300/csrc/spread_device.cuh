@@ -38,6 +38,69 @@ INFFT_D cplx_t<T> spread_direct(const cplx_t<T>* __restrict__ f, const float* __
     return cmake((T)re, (T)im);
 }
 
+// Spreads grid points [p0, p1) whose weights [w0, w1) do not fit a staging buffer
+// (clustered nodes): the CTA walks the entries in storage order, SPREAD_COLS at a
+// time (coalesced weight and index loads); each thread follows its entry's column
+// with a running pointer over the tile's offsets, a warp-level segmented sum
+// combines neighbouring entries of one column and the segment's last lane adds it
+// to the column's sum in shared memory.  fp64 ("wide") columns are summed per
+// thread afterwards.  iw: 2 SPREAD_COLS + 1 ints, gs: SPREAD_COLS float2 of shared
+// memory.  Every thread of the CTA calls it.
+INFFT_D void spread_tile_segmented(const float2* __restrict__ f, const float* __restrict__ w32,
+                                   const double* __restrict__ w64, const uint8_t* __restrict__ wide,
+                                   const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
+                                   const int32_t* __restrict__ col_off, int N, int p0, int p1, int w0, int w1,
+                                   float2* __restrict__ g, int* iw, float2* gs) {
+    int* offs = iw;                         // ncols + 1 weight offsets
+    int* cst = offs + SPREAD_COLS + 1;      // ncols node starts
+    const int ncols = p1 - p0;
+    for (int c = threadIdx.x; c <= ncols; c += SPREAD_COLS) {
+        offs[c] = col_off[p0 + c];
+        if (c < ncols) {
+            cst[c] = col_start[p0 + c];
+            gs[c] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int c = 0;
+    for (int base = w0; base < w1; base += SPREAD_COLS) {
+        const int e = base + threadIdx.x;
+        const bool act = e < w1;
+        float2 v = make_float2(0.f, 0.f);
+        if (act) {
+            while (offs[c + 1] <= e) ++c;
+            if (!wide[p0 + c]) {
+                int r = cst[c] + (e - offs[c]);
+                if (r >= N) r -= N;
+                const float2 fv = f[perm[r]];
+                const float wi = w32[e];
+                v = make_float2(wi * fv.x, wi * fv.y);
+            }
+        }
+        const int key = act ? c : -1 - lane;     // inactive lanes form their own segments
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float tx = __shfl_up_sync(0xffffffffu, v.x, o);
+            const float ty = __shfl_up_sync(0xffffffffu, v.y, o);
+            const int tk = __shfl_up_sync(0xffffffffu, key, o);
+            if (lane >= o && tk == key) { v.x += tx; v.y += ty; }
+        }
+        const int nk = __shfl_down_sync(0xffffffffu, key, 1);
+        if (act && (lane == 31 || nk != key)) {
+            atomicAdd(&gs[c].x, v.x);
+            atomicAdd(&gs[c].y, v.y);
+        }
+    }
+    __syncthreads();
+    const int p = p0 + threadIdx.x;
+    if (p < p1) {
+        if (wide[p]) g[p] = spread_direct<float>(f, w32, w64, true, perm, col_off[p + 1] - col_off[p], col_start[p],
+                                                  col_off[p], N);
+        else g[p] = gs[threadIdx.x];
+    }
+}
+
 // Spreads grid points [p0, p1) (p1 - p0 <= SPREAD_COLS) of a problem with Ms grid points
 // into g (indexed by grid point): the tile's weights [w0, w1) move to shared
 // memory by 16-byte asynchronous copies of the 16-byte aligned span around them,
@@ -70,56 +133,7 @@ INFFT_D void spread_tile_f32(const float2* __restrict__ f, const float* __restri
     const int inside = !live || n == 0 || (r0 + n <= U);
     const bool staged = __syncthreads_and(inside) && (we - wb) <= SPREAD_WMAX && U <= SPREAD_UMAX && U <= N;
     if (!staged) {
-        // Oversized tile (clustered nodes): the CTA walks the tile's entries [w0, w1)
-        // in storage order, SPREAD_COLS at a time (coalesced weight and index loads);
-        // each thread follows its entry's column with a running pointer over the
-        // tile's offsets, a warp-level segmented sum combines neighbouring entries of
-        // one column and the segment's last lane adds it to the column's sum in
-        // shared memory.  fp64 ("wide") columns are summed per thread afterwards.
-        int* offs = (int*)ws;                   // ncols + 1 weight offsets
-        int* cst = offs + SPREAD_COLS + 1;      // ncols node starts
-        float2* gs = fu;                        // ncols partial sums
-        const int ncols = plast - p0 + 1;
-        for (int c = threadIdx.x; c <= ncols; c += SPREAD_COLS) {
-            offs[c] = col_off[p0 + c];
-            if (c < ncols) {
-                cst[c] = col_start[p0 + c];
-                gs[c] = make_float2(0.f, 0.f);
-            }
-        }
-        __syncthreads();
-        const int lane = threadIdx.x & 31;
-        int c = 0;
-        for (int base = w0; base < w1; base += SPREAD_COLS) {
-            const int e = base + threadIdx.x;
-            const bool act = e < w1;
-            float2 v = make_float2(0.f, 0.f);
-            if (act) {
-                while (offs[c + 1] <= e) ++c;
-                if (!wide[p0 + c]) {
-                    int r = cst[c] + (e - offs[c]);
-                    if (r >= N) r -= N;
-                    const float2 fv = f[perm[r]];
-                    const float wi = w32[e];
-                    v = make_float2(wi * fv.x, wi * fv.y);
-                }
-            }
-            const int key = act ? c : -1 - lane;     // inactive lanes form their own segments
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float tx = __shfl_up_sync(0xffffffffu, v.x, o);
-                const float ty = __shfl_up_sync(0xffffffffu, v.y, o);
-                const int tk = __shfl_up_sync(0xffffffffu, key, o);
-                if (lane >= o && tk == key) { v.x += tx; v.y += ty; }
-            }
-            const int nk = __shfl_down_sync(0xffffffffu, key, 1);
-            if (act && (lane == 31 || nk != key)) {
-                atomicAdd(&gs[c].x, v.x);
-                atomicAdd(&gs[c].y, v.y);
-            }
-        }
-        __syncthreads();
-        if (live) g[p] = wide_col ? spread_direct<float>(f, w32, w64, true, perm, n, s, off, N) : gs[threadIdx.x];
+        spread_tile_segmented(f, w32, w64, wide, perm, col_start, col_off, N, p0, p1, w0, w1, g, (int*)ws, fu);
         return;
     }
     for (int v = threadIdx.x; v < (we - wb) / 4; v += SPREAD_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
