@@ -310,19 +310,76 @@ k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ 
 }
 
 // Spreading of all problems: CTA t spreads tile t (problem, [p0, p1)) into the
-// problem's slice of g_all; CTAs beyond the number of tiles return.  (A persistent,
-// two-stage software-pipelined variant was slower: 1.48 ms against 1.10 ms on the
-// batched workload, at half the resident threads per SM.)
+// problem's slice of g_all; CTAs beyond the number of tiles return.  The tile
+// record carries the tile's weight range and node window, so the weights and
+// node indices are requested together with the threads' column data (two
+// dependent load phases per tile: weights and indices, then node values).  A tile
+// whose block does not fit the staging buffers takes the segmented walk.  (A
+// persistent, two-stage software-pipelined variant was slower: 1.48 ms against
+// 1.10 ms on the batched workload, at half the resident threads per SM.)
 __global__ void __launch_bounds__(SPREAD_COLS)
 k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ tiles,
                const int32_t* __restrict__ ntiles, const float2* __restrict__ f, float2* __restrict__ g_all) {
     __shared__ __align__(16) float ws[SPREAD_WMAX];
     __shared__ __align__(16) float2 fu[SPREAD_UMAX];
     if ((int)blockIdx.x >= *ntiles) return;
-    const int4 t = tiles[2 * blockIdx.x];
-    const BatchProblem pr = probs[t.x];
-    spread_tile_f32(f + pr.f_off, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_count, pr.col_off, pr.N,
-                    t.y, t.z, g_all + pr.g_off, ws, fu);
+    const int4 ra = tiles[2 * blockIdx.x], rb = tiles[2 * blockIdx.x + 1];
+    const int p0 = ra.y, p1 = ra.z, S = ra.w, w0 = rb.x, w1 = rb.y, U = rb.z;
+    const BatchProblem& pr = probs[ra.x];
+    const int N = pr.N;
+    const float2* fp = f + pr.f_off;
+    float2* g = g_all + pr.g_off;
+    const int wb = w0 & ~3, we = (w1 + 3) & ~3;
+    if ((we - wb) > SPREAD_WMAX || U > SPREAD_UMAX || U > N) {   // block-uniform
+        spread_tile_segmented(fp, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_off, N, p0, p1, w0, w1, g,
+                              (int*)ws, fu);
+        return;
+    }
+    const float* w32 = pr.w32;
+    const int32_t* perm = pr.perm;
+    for (int v = threadIdx.x; v < (we - wb) / 4; v += SPREAD_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
+    int pq[SPREAD_UPT];
+#pragma unroll
+    for (int u = 0; u < SPREAD_UPT; ++u) {
+        const int q = threadIdx.x + u * SPREAD_COLS;
+        int gq = S + q;
+        if (gq >= N) gq -= N;
+        pq[u] = q < U ? perm[gq] : 0;
+    }
+    const int p = p0 + threadIdx.x;
+    const bool live = p < p1;
+    const int n = live ? pr.col_count[p] : 0;
+    const int s = live ? pr.col_start[p] : 0;
+    const int off = live ? pr.col_off[p] : 0;
+    const bool wide_col = live && pr.wide[p];
+#pragma unroll
+    for (int u = 0; u < SPREAD_UPT; ++u) {
+        const int q = threadIdx.x + u * SPREAD_COLS;
+        if (q < U) cp_async8(fu + q, fp + pq[u]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!live) return;
+    int r0 = s - S;
+    if (r0 < 0) r0 += N;
+    if (wide_col || (n > 0 && r0 + n > U)) {
+        g[p] = spread_direct<float>(fp, w32, pr.w64, wide_col, perm, n, s, off, N);
+        return;
+    }
+    // walk the column from a lane-dependent start (neighbouring columns sit |I(l)|
+    // weights apart in shared memory, so a common start would hit few banks)
+    const float* wc = ws + (off - wb);
+    const float2* fc = fu + r0;
+    float re = 0, im = 0;
+    int k = n ? (int)(threadIdx.x & 31) % n : 0;
+    for (int i = 0; i < n; ++i) {
+        const float wi = wc[k];
+        const float2 v = fc[k];
+        re = fmaf(wi, v.x, re);
+        im = fmaf(wi, v.y, im);
+        k = (k + 1 == n) ? 0 : k + 1;
+    }
+    g[p] = make_float2(re, im);
 }
 
 // D^* F^* of every problem's grid (pruned to its M central frequencies): one CTA
