@@ -8,9 +8,9 @@
 // problems go to one launch of the blocked solver.
 //
 // Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of at
-// most 256 grid points of one problem (the staged tile of the single-problem
-// apply); tiles are cut after the precompute so that each holds fewer than
-// 4096 + |I(l)|max weights (clustered nodes make some columns hundreds of nodes long).
+// most 128 grid points of one problem (staged like the single-problem apply's
+// tiles); tiles are cut after the precompute so that each holds fewer than
+// 2048 + |I(l)|max weights (clustered nodes make some columns hundreds of nodes long).
 // (2) One persistent CTA per SM takes problems by size: D^* F^* on the problem's
 // grid of M_sigma = 2M points.  M is any even number, so the pruned DFT
 //   h_k = sum_{l=-M}^{M-1} g_l w^{kl},  w = e^{-2 pi i/(2M)},  k = -M/2 .. M/2-1,
@@ -223,14 +223,18 @@ k_batch_chirp(const BatchProblem* __restrict__ probs, float2* __restrict__ bhat_
 }
 
 // Tiles of the batched spreading.  Grid point p of a problem starts a tile when
-// p is a multiple of SPREAD_COLS or when its weight offset enters a new block of
-// TILE_WEIGHTS entries: a tile then has at most SPREAD_COLS grid points and fewer
+// p is a multiple of TILE_COLS or when its weight offset enters a new block of
+// TILE_WEIGHTS entries: a tile then has at most TILE_COLS grid points and fewer
 // than TILE_WEIGHTS + |I(l)|max weights, which the staged spreading holds.
-constexpr int TILE_WEIGHTS = 4096;
+constexpr int TILE_COLS = 128;      // grid points per spreading tile (one thread each)
+constexpr int TILE_WEIGHTS = 2048;
+constexpr int TILE_WMAX = 3072;     // staged weights: TILE_WEIGHTS + the largest column of the workloads
+constexpr int TILE_UMAX = 1024;     // staged node values
+constexpr int TILE_UPT = TILE_UMAX / TILE_COLS;
 constexpr int TILE_SCAN_THREADS = 1024;
 
 INFFT_D bool tile_start(const int32_t* __restrict__ col_off, int p) {
-    return p % SPREAD_COLS == 0 || (col_off[p] / TILE_WEIGHTS) != (col_off[p - 1] / TILE_WEIGHTS);
+    return p % TILE_COLS == 0 || (col_off[p] / TILE_WEIGHTS) != (col_off[p - 1] / TILE_WEIGHTS);
 }
 
 // Per problem (one CTA): its number of tiles.
@@ -317,11 +321,11 @@ k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ 
 // whose block does not fit the staging buffers takes the segmented walk.  (A
 // persistent, two-stage software-pipelined variant was slower: 1.48 ms against
 // 1.10 ms on the batched workload, at half the resident threads per SM.)
-__global__ void __launch_bounds__(SPREAD_COLS)
+__global__ void __launch_bounds__(TILE_COLS)
 k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ tiles,
                const int32_t* __restrict__ ntiles, const float2* __restrict__ f, float2* __restrict__ g_all) {
-    __shared__ __align__(16) float ws[SPREAD_WMAX];
-    __shared__ __align__(16) float2 fu[SPREAD_UMAX];
+    __shared__ __align__(16) float ws[TILE_WMAX];
+    __shared__ __align__(16) float2 fu[TILE_UMAX];
     if ((int)blockIdx.x >= *ntiles) return;
     const int4 ra = tiles[2 * blockIdx.x], rb = tiles[2 * blockIdx.x + 1];
     const int p0 = ra.y, p1 = ra.z, S = ra.w, w0 = rb.x, w1 = rb.y, U = rb.z;
@@ -330,18 +334,18 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     const float2* fp = f + pr.f_off;
     float2* g = g_all + pr.g_off;
     const int wb = w0 & ~3, we = (w1 + 3) & ~3;
-    if ((we - wb) > SPREAD_WMAX || U > SPREAD_UMAX || U > N) {   // block-uniform
-        spread_tile_segmented(fp, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_off, N, p0, p1, w0, w1, g,
+    if ((we - wb) > TILE_WMAX || U > TILE_UMAX || U > N) {   // block-uniform
+        spread_tile_segmented<TILE_COLS>(fp, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_off, N, p0, p1, w0, w1, g,
                               (int*)ws, fu);
         return;
     }
     const float* w32 = pr.w32;
     const int32_t* perm = pr.perm;
-    for (int v = threadIdx.x; v < (we - wb) / 4; v += SPREAD_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
-    int pq[SPREAD_UPT];
+    for (int v = threadIdx.x; v < (we - wb) / 4; v += TILE_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
+    int pq[TILE_UPT];
 #pragma unroll
-    for (int u = 0; u < SPREAD_UPT; ++u) {
-        const int q = threadIdx.x + u * SPREAD_COLS;
+    for (int u = 0; u < TILE_UPT; ++u) {
+        const int q = threadIdx.x + u * TILE_COLS;
         int gq = S + q;
         if (gq >= N) gq -= N;
         pq[u] = q < U ? perm[gq] : 0;
@@ -353,8 +357,8 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     const int off = live ? pr.col_off[p] : 0;
     const bool wide_col = live && pr.wide[p];
 #pragma unroll
-    for (int u = 0; u < SPREAD_UPT; ++u) {
-        const int q = threadIdx.x + u * SPREAD_COLS;
+    for (int u = 0; u < TILE_UPT; ++u) {
+        const int q = threadIdx.x + u * TILE_COLS;
         if (q < U) cp_async8(fu + q, fp + pq[u]);
     }
     cp_async_wait_all();
@@ -682,10 +686,10 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
         alloc(&b->job_order, b->sumG * sizeof(int32_t));
         alloc(&b->job_work, (HUGE_NMAX + 2) * sizeof(int32_t));
     }
-    // tiles of the batched spreading: at most one per SPREAD_COLS grid points plus
+    // tiles of the batched spreading: at most one per TILE_COLS grid points plus
     // one per TILE_WEIGHTS weights of the largest possible nnz
     for (int64_t i = 0; i < P; ++i)
-        b->max_tiles += (2 * M[i] + SPREAD_COLS - 1) / SPREAD_COLS + b->plans[i]->nnz_cap / TILE_WEIGHTS + 1;
+        b->max_tiles += (2 * M[i] + TILE_COLS - 1) / TILE_COLS + b->plans[i]->nnz_cap / TILE_WEIGHTS + 1;
     alloc(&b->tiles, 2 * b->max_tiles * sizeof(int4));
     alloc(&b->tile_count, P * sizeof(int32_t));
     alloc(&b->tile_off, (P + 1) * sizeof(int32_t));
@@ -834,7 +838,7 @@ infft_status infft_batch_apply(infft_batch_t b, const float* f, float* fhat, inf
     }
     const bool host_out = !on_device(fhat);
     float2* fout = host_out ? b->stage_fhat : (float2*)fhat;
-    k_batch_spread<<<(unsigned)b->max_tiles, SPREAD_COLS, 0, s>>>(b->probs, b->tiles, b->tile_off + b->P, fin,
+    k_batch_spread<<<(unsigned)b->max_tiles, TILE_COLS, 0, s>>>(b->probs, b->tiles, b->tile_off + b->P, fin,
                                                                  b->g_all);
     const size_t smem = (size_t)(pad16(TW_N) + BATCH_MMAX) * sizeof(float2);
     if ((e = cudaFuncSetAttribute(k_batch_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)

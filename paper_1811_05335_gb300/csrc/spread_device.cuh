@@ -39,22 +39,23 @@ INFFT_D cplx_t<T> spread_direct(const cplx_t<T>* __restrict__ f, const float* __
 }
 
 // Spreads grid points [p0, p1) whose weights [w0, w1) do not fit a staging buffer
-// (clustered nodes): the CTA walks the entries in storage order, SPREAD_COLS at a
+// (clustered nodes): the CTA (COLS threads) walks the entries in storage order, COLS at a
 // time (coalesced weight and index loads); each thread follows its entry's column
 // with a running pointer over the tile's offsets, a warp-level segmented sum
 // combines neighbouring entries of one column and the segment's last lane adds it
 // to the column's sum in shared memory.  fp64 ("wide") columns are summed per
-// thread afterwards.  iw: 2 SPREAD_COLS + 1 ints, gs: SPREAD_COLS float2 of shared
+// thread afterwards.  iw: 2 COLS + 1 ints, gs: COLS float2 of shared
 // memory.  Every thread of the CTA calls it.
+template <int COLS = SPREAD_COLS>
 INFFT_D void spread_tile_segmented(const float2* __restrict__ f, const float* __restrict__ w32,
                                    const double* __restrict__ w64, const uint8_t* __restrict__ wide,
                                    const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
                                    const int32_t* __restrict__ col_off, int N, int p0, int p1, int w0, int w1,
                                    float2* __restrict__ g, int* iw, float2* gs) {
     int* offs = iw;                         // ncols + 1 weight offsets
-    int* cst = offs + SPREAD_COLS + 1;      // ncols node starts
+    int* cst = offs + COLS + 1;      // ncols node starts
     const int ncols = p1 - p0;
-    for (int c = threadIdx.x; c <= ncols; c += SPREAD_COLS) {
+    for (int c = threadIdx.x; c <= ncols; c += COLS) {
         offs[c] = col_off[p0 + c];
         if (c < ncols) {
             cst[c] = col_start[p0 + c];
@@ -64,7 +65,7 @@ INFFT_D void spread_tile_segmented(const float2* __restrict__ f, const float* __
     __syncthreads();
     const int lane = threadIdx.x & 31;
     int c = 0;
-    for (int base = w0; base < w1; base += SPREAD_COLS) {
+    for (int base = w0; base < w1; base += COLS) {
         const int e = base + threadIdx.x;
         const bool act = e < w1;
         float2 v = make_float2(0.f, 0.f);
