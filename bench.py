@@ -67,6 +67,22 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value, device, world):
+    """The largest of every rank's value (the job's time is its slowest rank's).
+    Replicas exchange only this scalar; there is no data-path collective."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, steps, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
+
+
 # ---------------------------------------------------------------------------- clocks
 
 
@@ -244,12 +260,9 @@ def run_gpu(a):
     torch.cuda.synchronize()
     g.infft_profile(plan, False)
     kernels = g.infft_profile_read(plan)
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev, world)
     ms_step = ms_total / a.steps
-    value = world * a.N * a.steps / (ms_total / 1e3)
+    value = job_rate(a.N, a.steps, world, ms_total / 1e3)
 
     # ---- apply only (fixed plan): the paper's "fixed nodes, several problems" regime
     k_app = a.apply_steps
@@ -313,10 +326,8 @@ def run_gpu(a):
             t0 = time.perf_counter()
             step_host()
             wall += time.perf_counter() - t0
-        tw = torch.tensor([wall], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tw, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * a.N * a.steps / float(tw.item()), "unit": "nodes/s",
+        wall = max_over_ranks(wall, dev, world)
+        e2e = {"value": job_rate(a.N, a.steps, world, wall), "unit": "nodes/s",
                "h2d_bytes_per_step": int(xh.nbytes + fh_.nbytes), "d2h_bytes_per_step": int(outh.nbytes)}
         plan_h.close()
 
