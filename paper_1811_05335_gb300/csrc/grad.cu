@@ -8,20 +8,20 @@
 //   dL/dx_j = sum_{l : j in I(l)} [ -lambda_{l,j} kappa'(l/M_sigma - x_j)
 //                                   - lambda_{l,j} sum_k kappa'(x_j - x_k) b_{l,k}
 //                                   - b_{l,j} sum_i kappa'(x_j - x_i) lambda_{l,i} ].
-// One warp per column (lanes own rows) re-factors A_l in fp64, solves for lambda_l and
+// One warp per column (lanes own rows) re-factors A_l in fp64 (Gram entries as in the
+// precompute), solves for lambda_l, evaluates each pair's kappa' once (it is odd) and
 // writes each node's term next to the column's weights; a per-node pass sums them.
+#include <cmath>
 #include <cstring>
 
-#include "plan.h"
+#include "lsq_device.cuh"
 
 namespace {
-
-constexpr double PI = 3.141592653589793238462643383279502884;
-constexpr double SMALL_T = 1.0 / 32.0;
 
 struct GradParams {
     double M, inv_Ms, diag;
     int sym;
+    int short_series;   // 1: every near pair has |pi t| so small that three terms of each series suffice
     double cs[10];    // kappa'(t) = t * sum_p cs[p] t^{2p} for |M t| <= 1/4 (host-folded series)
 };
 
@@ -38,16 +38,6 @@ INFFT_D double g_recip(double u) {
     r = fma(r, e, r);
     e = fma(-u, r, 1.0);
     return fma(r, e, r);
-}
-
-// Re kappa(a - b) (value), library transcendentals; used for the Gram entries here.
-INFFT_D double g_kappa(double a, double b, const GradParams& kp) {
-    const double t = g_torus_diff(a, b);
-    if (t == 0.0) return kp.diag;
-    double s, c;
-    sincospi(t, &s, &c);
-    if (kp.sym) return sinpi((kp.M - 1.0) * t) / s * kp.inv_Ms;
-    return c * sinpi(kp.M * t) / s * kp.inv_Ms;
 }
 
 // d/dt Re kappa(t) at t = a - b; pa, pb = (sin, cos)(pi M a), (sin, cos)(pi M b).
@@ -83,20 +73,28 @@ INFFT_D double g_kappa_prime(double a, double b, double2 pa, double2 pb, const G
     double sinM, cosM, full;
     if (fabs(t) <= SMALL_T) {
         const double u = PI * t, w = u * u;
-        double xc = fma(w, -4.0 / 18243225.0, -1382.0 / 638512875.0);   // u cot u
-        xc = fma(w, xc, -2.0 / 93555.0);
-        xc = fma(w, xc, -1.0 / 4725.0);
-        xc = fma(w, xc, -2.0 / 945.0);
-        xc = fma(w, xc, -1.0 / 45.0);
-        xc = fma(w, xc, -1.0 / 3.0);
-        xc = fma(w, xc, 1.0);
-        double q = fma(w, 4.0 / 1403325.0, 1382.0 / 58046625.0);         // u^2 / sin^2 u
-        q = fma(w, q, 2.0 / 10395.0);
-        q = fma(w, q, 1.0 / 675.0);
-        q = fma(w, q, 2.0 / 189.0);
-        q = fma(w, q, 1.0 / 15.0);
-        q = fma(w, q, 1.0 / 3.0);
-        q = fma(w, q, 1.0);
+        double xc, q;
+        if (kp.short_series) {   // uniform across the launch
+            xc = fma(w, -1.0 / 45.0, -1.0 / 3.0);
+            xc = fma(w, xc, 1.0);
+            q = fma(w, 1.0 / 15.0, 1.0 / 3.0);
+            q = fma(w, q, 1.0);
+        } else {
+            xc = fma(w, -4.0 / 18243225.0, -1382.0 / 638512875.0);   // u cot u
+            xc = fma(w, xc, -2.0 / 93555.0);
+            xc = fma(w, xc, -1.0 / 4725.0);
+            xc = fma(w, xc, -2.0 / 945.0);
+            xc = fma(w, xc, -1.0 / 45.0);
+            xc = fma(w, xc, -1.0 / 3.0);
+            xc = fma(w, xc, 1.0);
+            q = fma(w, 4.0 / 1403325.0, 1382.0 / 58046625.0);         // u^2 / sin^2 u
+            q = fma(w, q, 2.0 / 10395.0);
+            q = fma(w, q, 1.0 / 675.0);
+            q = fma(w, q, 2.0 / 189.0);
+            q = fma(w, q, 1.0 / 15.0);
+            q = fma(w, q, 1.0 / 3.0);
+            q = fma(w, q, 1.0);
+        }
         sinM = fma(pa.x, pb.y, -pa.y * pb.x);
         cosM = fma(pa.y, pb.y, pa.x * pb.x);
         const double ru = g_recip(u);
@@ -120,7 +118,7 @@ __global__ void __launch_bounds__(GW * 32)
 k_grad_cols(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ perm,
             const int32_t* __restrict__ col_start, const int32_t* __restrict__ col_count,
             const int32_t* __restrict__ col_off, const double* __restrict__ w64, const float2* __restrict__ f,
-            const float2* __restrict__ gamma, int N, int Ms, GradParams kp, double mu,
+            const float2* __restrict__ gamma, int N, int Ms, GradParams kp, KernelParams kk, double mu,
             double* __restrict__ gterm, int32_t* __restrict__ counters) {
     extern __shared__ double gsm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -157,7 +155,7 @@ k_grad_cols(const double* __restrict__ xs, const double2* __restrict__ ph, const
         __syncwarp();
         for (int e = lane; e < n * n; e += 32) {
             const int i = e / n, j = e % n;
-            if (j <= i) A[i * GLD + j] = (i == j) ? kp.diag + mu : g_kappa(xl[i], xl[j], kp);
+            if (j <= i) A[i * GLD + j] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kk);
         }
         __syncwarp();
         bool ok = true;
@@ -216,12 +214,24 @@ k_grad_cols(const double* __restrict__ xs, const double2* __restrict__ ph, const
             }
             __syncwarp();
         }
+        // K'_{jk} = kappa'(x_j - x_k) is odd in its argument: each pair once, both halves
+        // stored (the factor in A is no longer needed)
+        __syncwarp();
+        for (int e = lane; e < n * (n - 1) / 2; e += 32) {
+            int i, j;
+            tri_index(e, i, j);          // (i, j), j <= i, of the (n-1)-triangle: pair (i + 1, j)
+            ++i;
+            const double v = g_kappa_prime(xl[i], xl[j], pv[i], pv[j], kp);
+            A[i * GLD + j] = v;
+            A[j * GLD + i] = -v;
+        }
+        for (int j = lane; j < n; j += 32) A[j * GLD + j] = 0.0;
+        __syncwarp();
         // per node j (lanes own rows): -lambda_j kappa'(t_lj) - lambda_j (K'b)_j - b_j (K'lambda)_j
         for (int j = lane; j < n; j += 32) {
             double kb = 0.0, kl = 0.0;
             for (int k = 0; k < n; ++k) {
-                if (k == j) continue;
-                const double kpjk = g_kappa_prime(xl[j], xl[k], pv[j], pv[k], kp);
+                const double kpjk = A[j * GLD + k];
                 kb = fma(kpjk, bb[k], kb);
                 kl = fma(kpjk, lam[k], kl);
             }
@@ -284,6 +294,13 @@ cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cu
             tp *= 4.0L * (long double)PI * (long double)PI;
         }
     }
+    {
+        // pairs of a column are within (2m + 2)/M_sigma; the fourth terms of u cot u and
+        // u^2/sin^2 u (2/945 u^6, 2/189 u^6) below 2^-56 let three terms stand
+        const double u = PI * (double)(2 * p->m + 2) / (double)Ms;
+        kp.short_series = (2.0 / 189.0) * u * u * u * u * u * u < std::ldexp(1.0, -56);
+    }
+    const KernelParams kk = make_kernel_params(p);
     const double mu = p->tau * kp.diag;
     if ((e = cudaMemsetAsync(p->counters + CNT_GRAD_FAIL, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     int sms = 0;
@@ -295,7 +312,7 @@ cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cu
         return e;
     launch_begin(p, "grad_cols", s);
     k_grad_cols<<<4 * sms, GW * 32, smem, s>>>(p->xs, p->phase, p->perm, p->col_start, p->col_count, p->col_off,
-                                               p->w64, (const float2*)f, (const float2*)p->grid, N, Ms, kp, mu,
+                                               p->w64, (const float2*)f, (const float2*)p->grid, N, Ms, kp, kk, mu,
                                                p->gterm, p->counters);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
