@@ -613,6 +613,18 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
         if (m < 1 || 2 * (int64_t)m >= 2 * M[i])
             return set_error(INFFT_EINVAL, "problem %lld: need m >= 1 and 2m < M_sigma", (long long)i);
     }
+    {
+        // every index of the batch's concatenated arrays (nodes, grid points, weights of
+        // one problem, spreading tiles) must fit the kernels' 32-bit arithmetic
+        int64_t sn = 0, sg = 0;
+        for (int64_t i = 0; i < P; ++i) {
+            sn += N[i];
+            sg += 2 * M[i];
+        }
+        if (sn >= (int64_t(1) << 31) || sg >= (int64_t(1) << 31))
+            return set_error(INFFT_EUNSUPPORTED, "batch too large: sum N = %lld, sum M_sigma = %lld (each < 2^31)",
+                             (long long)sn, (long long)sg);
+    }
     infft_batch_t b = new infft_batch_s();
     cudaGetDevice(&b->device);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
