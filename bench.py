@@ -308,6 +308,25 @@ def run_gpu(a):
     app_graph_ms = sum(s.elapsed_time(e) for s, e in zip(gs_ev, ge_ev)) / k_app
     del graph
 
+    # K data vectors on the same plan in one call (infft_apply_many): the weights are read
+    # once for all K; algorithmic bytes K (8N + 8M) + 4 nnz
+    K_many = 16
+    f_many = torch.randn((K_many, a.N), dtype=torch.complex64, device=dev)
+    out_many = torch.empty((K_many, a.M), dtype=torch.complex64, device=dev)
+    ws_many = torch.empty(g.infft_apply_many_workspace(plan, K_many), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        g.infft_apply_many(plan, f_many, out=out_many, workspace=ws_many, stream=stream)
+    ms_ev = [torch.cuda.Event(enable_timing=True) for _ in range(20)]
+    me_ev = [torch.cuda.Event(enable_timing=True) for _ in range(20)]
+    for i in range(20):
+        flush.fill_(float(i))
+        ms_ev[i].record(stream)
+        g.infft_apply_many(plan, f_many, out=out_many, workspace=ws_many, stream=stream)
+        me_ev[i].record(stream)
+    torch.cuda.synchronize()
+    many_ms = sum(x.elapsed_time(y) for x, y in zip(ms_ev, me_ev)) / 20
+    del f_many, out_many, ws_many
+
     # the own pruned FFT with fused deconvolution (D^* F^* on a grid, through the
     # allocation-free entry point) beside cuFFT's full FFT on the same grid
     grid = torch.randn(plan.M_sigma, dtype=torch.complex64, device=dev)
@@ -492,6 +511,14 @@ def run_gpu(a):
                       "graph_replay": {"ms_per_apply": app_graph_ms, "achieved": ach_app_graph,
                                        "frac": ach_app_graph / hbm}}
 
+    ab_many = K_many * (8 * a.N + 8 * a.M) + 4 * info["nnz"]
+    ach_many = ab_many / (many_ms / 1e3) / 1e9
+    apply_many = {"vectors": K_many, "ms_per_call": many_ms, "value": world * K_many * a.N / (many_ms / 1e3),
+                  "unit": "nodes/s",
+                  "roofline": {"kernel": "spread + fft passes of 16 data vectors (infft_apply_many)", "bound": "hbm",
+                               "achieved": ach_many, "peak": hbm, "unit": "GB/s", "frac": ach_many / hbm,
+                               "algorithmic_bytes": ab_many, "peak_source": src}}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a)
@@ -508,6 +535,7 @@ def run_gpu(a):
         "apply_only": {"value": world * a.N / (app_ms / 1e3), "unit": "nodes/s", "ms_per_apply": app_ms,
                        "kernel_ms_per_apply": app_kernel_ms, "steps": k_app,
                        "graph_replay": {"value": world * a.N / (app_graph_ms / 1e3), "ms_per_apply": app_graph_ms}},
+        "apply_many": apply_many,
         "fft_vs_cufft": {"own_fft_deconv_ms": own_fft_ms, "cufft_ms": cufft_ms, "length": plan.M_sigma,
                          "note": "own: pruned length-M_sigma FFT with D fused (M outputs); cuFFT: full FFT"},
         "differentiable": diff,

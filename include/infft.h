@@ -121,6 +121,19 @@ infft_status infft_precompute(infft_plan_t plan, infft_stream_t stream);
  * Requires infft_precompute. */
 infft_status infft_apply(infft_plan_t plan, const float* f, float* fhat, infft_stream_t stream);
 
+/* infft_apply for K data vectors sampled at the plan's nodes (the "fixed nodes, several
+ * problems" use of the precomputed B_opt, Sec. 1 and Sec. 3.2.2), in one launch per step:
+ *   f    : K x N complex64 on the device, vector k at k N (caller's node order), read only;
+ *   fhat : K x M complex64 on the device, vector k at k M (k + M/2 layout), written;
+ *   workspace : device memory of at least infft_apply_many_workspace(plan, K) bytes,
+ *               owned by the caller (the call allocates nothing), overwritten.
+ * Each vector's result equals infft_apply's for it.  1 <= K <= 65535; M_sigma > 2048
+ * (smaller plans: INFFT_EUNSUPPORTED); host pointers: INFFT_EINVAL.  Requires
+ * infft_precompute. */
+int64_t infft_apply_many_workspace(infft_plan_t plan, int64_t K);
+infft_status infft_apply_many(infft_plan_t plan, int64_t K, const float* f, float* fhat, void* workspace,
+                              int64_t workspace_bytes, infft_stream_t stream);
+
 /* The modified NFFT f = B_opt F D fhat (Remark remark:ansatz2_adj), the exact
  * adjoint of infft_apply: <infft_apply(f), g> = <f, nfft_apply(g)>.
  *   fhat : M complex64 (k + M/2 layout), read;  f : N complex64 in node order, written.

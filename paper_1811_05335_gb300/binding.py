@@ -25,6 +25,7 @@ EXPORTED_SYMBOLS = (
     "infft_fft_deconv_noalloc", "infft_grad_nodes", "infft_plan_create_ansatz",
     "infft_batch_create", "infft_batch_set_nodes", "infft_batch_precompute", "infft_batch_apply",
     "infft_batch_get_info", "infft_batch_copy_problem", "infft_batch_destroy",
+    "infft_apply_many", "infft_apply_many_workspace",
 )
 
 
@@ -91,11 +92,14 @@ def library():
         "infft_batch_get_info": [P, ctypes.POINTER(_BatchInfo)],
         "infft_batch_copy_problem": [P, I64, VP, VP, VP, VP, VP, VP],
         "infft_batch_destroy": [P],
+        "infft_apply_many": [P, I64, VP, VP, VP, I64, VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.infft_apply_many_workspace.restype = ctypes.c_int64
+    lib.infft_apply_many_workspace.argtypes = [P, I64]
     lib.infft_launch_count.restype = ctypes.c_int64
     lib.infft_launch_count.argtypes = []
     lib.infft_last_error.restype = ctypes.c_char_p
@@ -233,6 +237,27 @@ def infft_apply(plan, f, out=None, stream=None):
 def nfft_apply(plan, fhat, out=None, stream=None):
     """f = B_opt F D fhat (complex64), the adjoint of infft_apply."""
     return _apply(library().nfft_apply, plan, fhat, out, plan.N, "c64", stream)
+
+
+def infft_apply_many_workspace(plan, K):
+    """Bytes of device workspace infft_apply_many needs for K vectors."""
+    return int(library().infft_apply_many_workspace(plan.handle, int(K)))
+
+
+def infft_apply_many(plan, f, out=None, workspace=None, stream=None):
+    """fhat of K data vectors (f: K x N complex64 CUDA tensor) -> K x M complex64."""
+    import torch
+    keep = []
+    K = int(f.shape[0])
+    if out is None:
+        out = torch.empty((K, plan.M), dtype=torch.complex64, device=f.device)
+    need = infft_apply_many_workspace(plan, K)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=f.device)
+    _check(library().infft_apply_many(plan.handle, K, _as_ptr(f, "c64", keep), _as_ptr(out, "c64", keep),
+                                      workspace.data_ptr(), int(workspace.numel() * workspace.element_size()),
+                                      _stream(stream, f, out)))
+    return out
 
 
 def infft_apply_z(plan, f, out=None, stream=None):

@@ -301,6 +301,36 @@ infft_status infft_apply(infft_plan_t p, const float* f, float* fhat, infft_stre
 infft_status infft_apply_z(infft_plan_t p, const double* f, double* fhat, infft_stream_t stream) {
     return apply_impl<double>(p, f, fhat, stream);
 }
+int64_t infft_apply_many_workspace(infft_plan_t p, int64_t K) {
+    if (!p || K < 1) return 0;
+    return 2 * K * p->Ms * (int64_t)sizeof(float2) + 256;
+}
+
+infft_status infft_apply_many(infft_plan_t p, int64_t K, const float* f, float* fhat, void* workspace,
+                              int64_t workspace_bytes, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !fhat || !workspace) return fail(INFFT_EINVAL, "f, fhat and workspace must not be NULL");
+    if (K < 1 || K > 65535) return fail(INFFT_EINVAL, "K must be in [1, 65535] (got %lld)", (long long)K);
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_apply_many before infft_precompute");
+    if (p->Ms <= 2048) return fail(INFFT_EUNSUPPORTED, "infft_apply_many needs M_sigma > 2048 (got %lld)",
+                                   (long long)p->Ms);
+    if (workspace_bytes < infft_apply_many_workspace(p, K))
+        return fail(INFFT_EINVAL, "workspace of %lld bytes is smaller than infft_apply_many_workspace() = %lld",
+                    (long long)workspace_bytes, (long long)infft_apply_many_workspace(p, K));
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(f) || !is_device_pointer(fhat) || !is_device_pointer(workspace))
+        return fail(INFFT_EINVAL, "infft_apply_many takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    char* ws = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    void* grid = ws;
+    void* work = ws + K * p->Ms * sizeof(float2);
+    cudaError_t e;
+    if ((e = run_spread_many(p, f, grid, (int)K, s)) != cudaSuccess) return cuda_fail(e, "spread");
+    if ((e = run_fft_adjoint_many(p, grid, work, fhat, (int)K, s)) != cudaSuccess) return cuda_fail(e, "fft");
+    return INFFT_OK;
+}
+
 infft_status nfft_apply(infft_plan_t p, const float* fhat, float* f, infft_stream_t stream) {
     return nfft_impl<float>(p, fhat, f, stream);
 }

@@ -304,6 +304,8 @@ k_fftA_r8(const float2* __restrict__ g, float2* __restrict__ Y, int log2, int CA
     griddep_launch();
     const int p2 = blockIdx.x * CA + c;
     const int Ms = N1 << log2;
+    g += (size_t)blockIdx.y * Ms;   // data vector blockIdx.y
+    Y += (size_t)blockIdx.y * Ms;
     float2 v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = g[((j + r * T1) << log2) + p2];
@@ -344,6 +346,8 @@ k_fftB_r8(const float2* __restrict__ Y, float2* __restrict__ fhat, int log1, int
     griddep_launch();
     const int k1 = blockIdx.x * CB + c;
     const int Ms = N2 << log1;
+    Y += (size_t)blockIdx.y * Ms;   // data vector blockIdx.y
+    fhat += (size_t)blockIdx.y * M;
     float2 v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = Y[(k1 << LOG2) + j + r * T2];
@@ -359,7 +363,7 @@ k_fftB_r8(const float2* __restrict__ Y, float2* __restrict__ fhat, int log1, int
 // Launches both passes for a length-2^(log1+log2) grid; the pass B launch is
 // programmatically dependent on pass A (and pass A on the spread before it).
 cudaError_t fft_adjoint_r8(const float2* g, float2* work, float2* fhat, int logMs, int M, int sym, cudaStream_t s,
-                           Plan* p) {
+                           Plan* p, int K = 1) {
     const int log2 = logMs / 2, log1 = logMs - log2;
     const int Ms = 1 << logMs;
     const float inv_Ms = 1.0f / (float)Ms;
@@ -390,12 +394,12 @@ cudaError_t fft_adjoint_r8(const float2* g, float2* work, float2* fhat, int logM
     if ((e = allow_smem(ka, (size_t)a.smem)) != cudaSuccess) return e;
     if ((e = allow_smem(kb, (size_t)b.smem)) != cudaSuccess) return e;
     if (p) launch_begin(p, "fft_passA", s);
-    e = launch_pdl(ka, dim3((1 << log2) / a.per_cta), dim3(a.per_cta * a.threads_per), (size_t)a.smem, s, g, work,
+    e = launch_pdl(ka, dim3((1 << log2) / a.per_cta, K), dim3(a.per_cta * a.threads_per), (size_t)a.smem, s, g, work,
                    log2, a.per_cta);
     if (p) launch_end(p, s);
     if (e != cudaSuccess) return e;
     if (p) launch_begin(p, "fft_passB_deconv", s);
-    e = launch_pdl(kb, dim3((1 << log1) / b.per_cta), dim3(b.per_cta * b.threads_per), (size_t)b.smem, s, work, fhat,
+    e = launch_pdl(kb, dim3((1 << log1) / b.per_cta, K), dim3(b.per_cta * b.threads_per), (size_t)b.smem, s, work, fhat,
                    log1, b.per_cta, M, inv_Ms, sym);
     if (p) launch_end(p, s);
     return e;
@@ -497,6 +501,12 @@ cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s) {
 
 cudaError_t run_fft_full_forward_z(Plan* p, const void* in, void* out, double scale, cudaStream_t s) {
     return fft_forward_on<double>(p, in, out, (int)p->Ms, scale, 0, s);
+}
+
+// D^* F^* of K grids (grid: K x M_sigma, work: K x M_sigma, fhat: K x M), fp32, M_sigma > 2048.
+cudaError_t run_fft_adjoint_many(Plan* p, const void* grid, void* work, void* fhat, int K, cudaStream_t s) {
+    return fft_adjoint_r8((const float2*)grid, (float2*)work, (float2*)fhat, p->logMs, (int)p->M,
+                          p->kernel == INFFT_KERNEL_SYM, s, p, K);
 }
 
 template cudaError_t run_fft_adjoint<float>(Plan*, void*, cudaStream_t);

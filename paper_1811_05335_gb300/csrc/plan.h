@@ -156,6 +156,10 @@ template <typename T> cudaError_t run_spread(Plan* p, const void* f, cudaStream_
 template <typename T> cudaError_t run_interp(Plan* p, void* f, cudaStream_t s);
 // fft.cu: fhat = D^* F^* grid (pruned to the M central frequencies)
 template <typename T> cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s);
+// spread.cu / fft.cu: the fp32 apply of K data vectors (f: K x N, grid and work: K x M_sigma,
+// fhat: K x M); the FFT requires M_sigma > 2048
+cudaError_t run_spread_many(Plan* p, const void* f, void* grid, int K, cudaStream_t s);
+cudaError_t run_fft_adjoint_many(Plan* p, const void* grid, void* work, void* fhat, int K, cudaStream_t s);
 // fft.cu: grid = F D fhat
 template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s);
 // fft.cu: out_p = scale * sum_{k=-Ms/2}^{Ms/2-1} in[k + Ms/2] exp(2 pi i k (p - Ms/2)/Ms), fp64, all bins

@@ -98,9 +98,10 @@ k_spread_f32(const float2* __restrict__ f, const float* __restrict__ w32, const 
     __shared__ __align__(16) float2 fu[SPREAD_UMAX];
     griddep_wait();
     griddep_launch();
+    // data vector blockIdx.y: f and g of vector k at k N and k M_sigma
     const int p0 = blockIdx.x * SPREAD_COLS;
-    spread_tile_f32(f, w32, w64, wide, perm, col_start, col_count, col_off, N, p0, min(p0 + SPREAD_COLS, Ms), g,
-                    ws, fu);
+    spread_tile_f32(f + (size_t)blockIdx.y * N, w32, w64, wide, perm, col_start, col_count, col_off, N, p0,
+                    min(p0 + SPREAD_COLS, Ms), g + (size_t)blockIdx.y * Ms, ws, fu);
 }
 
 // One thread per sorted node: gathers from the 2m (or 2m+1) grid points of I(x_j).
@@ -172,3 +173,16 @@ template cudaError_t run_spread<float>(Plan*, const void*, cudaStream_t);
 template cudaError_t run_spread<double>(Plan*, const void*, cudaStream_t);
 template cudaError_t run_interp<float>(Plan*, void*, cudaStream_t);
 template cudaError_t run_interp<double>(Plan*, void*, cudaStream_t);
+
+// K data vectors at once (f: K x N, grid: K x M_sigma): one launch, the vector in
+// blockIdx.y; the tiles of all vectors read the same weights, which stay in L2.
+cudaError_t run_spread_many(Plan* p, const void* f, void* grid, int K, cudaStream_t s) {
+    const int Ms = (int)p->Ms;
+    launch_begin(p, "spread_many", s);
+    cudaError_t e = launch_pdl(k_spread_f32, dim3((Ms + SPREAD_COLS - 1) / SPREAD_COLS, K), dim3(SPREAD_COLS), 0, s,
+                               (const float2*)f, p->w32, p->w64, p->wide, p->perm, p->col_start, p->col_count,
+                               p->col_off, (int)p->N, Ms, (float2*)grid);
+    launch_end(p, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}

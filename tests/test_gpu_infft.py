@@ -308,3 +308,33 @@ def test_full_size_config2(m):
     err = oracle.infft.rel_l2(fhat, want)
     print(f"config2 m={m}: fp32 rel l2 vs oracle {err:.3e}; vs truth {oracle.infft.rel_l2(fhat, p.fhat):.3e}")
     assert err <= FP32_TOL
+
+
+def test_apply_many_equals_single_applies():
+    """K data vectors in one call give, vector by vector, what infft_apply gives (same
+    kernels, same summation order: identical values), and match the oracle."""
+    import torch
+    import paper_1811_05335_gb300 as g
+    p = make_problem(2, M=4096, N=16384, m=4, with_data=False)
+    dev = torch.device("cuda:0")
+    plan = g.infft_plan_create(p.M, p.N, 2.0, 4)
+    g.infft_set_nodes(plan, torch.tensor(p.x, dtype=torch.float64, device=dev))
+    g.infft_precompute(plan)
+    K = 5
+    fs = np.stack([trig_poly_eval(p.x, complex_normal(200 + k, p.M)) for k in range(K)]).astype(np.complex64)
+    ft = torch.tensor(fs, device=dev)
+    many = g.infft_apply_many(plan, ft).cpu().numpy()
+    B = oracle.bopt.bopt_closed(p.x, p.M, 2.0, 4)
+    for k in range(K):
+        one = g.infft_apply(plan, ft[k].contiguous()).cpu().numpy()
+        assert np.array_equal(many[k], one)
+        assert oracle.infft.rel_l2(many[k].astype(np.complex128), oracle.infft.infft_apply(B, c64(fs[k]))) <= FP32_TOL
+    with pytest.raises(g.InfftError):     # workspace too small
+        g.infft_apply_many(plan, ft, workspace=torch.empty(16, dtype=torch.uint8, device=dev))
+    small = g.infft_plan_create(64, 128, 2.0, 4)
+    g.infft_set_nodes(small, torch.tensor(make_problem(1).x, dtype=torch.float64, device=dev))
+    g.infft_precompute(small)
+    with pytest.raises(g.InfftError):     # M_sigma <= 2048
+        g.infft_apply_many(small, torch.zeros((2, 128), dtype=torch.complex64, device=dev))
+    plan.close()
+    small.close()
