@@ -233,6 +233,7 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
         plan_layout(p, c, false);
     }
     if (e == cudaSuccess) e = cudaMemset(p->counters, 0, CNT_N * sizeof(int32_t));
+    if (e == cudaSuccess) e = phase_table_init();
     if (e != cudaSuccess) {
         free_plan_buffers(p);
         delete p;

@@ -759,6 +759,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     // every member's counters start at zero
     for (int64_t i = 0; i < P && e == cudaSuccess; ++i)
         e = cudaMemsetAsync(b->plans[i]->counters, 0, CNT_N * sizeof(int32_t), 0);
+    if (e == cudaSuccess) e = phase_table_init();
     const size_t chirp_smem = (size_t)pad16(TW_N) * sizeof(float2);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_batch_chirp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chirp_smem);

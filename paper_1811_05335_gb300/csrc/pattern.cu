@@ -12,6 +12,10 @@
 // so the result -- and every later result -- is deterministic.  A last pass
 // gathers the sorted nodes and their phases (sin, cos)(pi M x) used by the
 // precompute.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
 #include "plan.h"
 
 namespace {
@@ -53,15 +57,30 @@ __global__ void k_bucket_scatter(const double* __restrict__ x, int N, int Ms, co
     skey[pos] = key;
 }
 
+// (sin, cos)(pi k / 1024) for k = -1024 .. 1024 at k + 1024, filled once per device
+// (phase_table_init) from long double evaluations rounded to double.
+constexpr int PHASE_TAB_HALF = 1024;
+__device__ double2 g_phase_tab[2 * PHASE_TAB_HALF + 1];
+
 // (sin, cos)(pi M z) with M z reduced modulo 2 exactly: M z = p + e with
-// p = fl(M z) and e = fma(M, z, -p); p - 2 rint(p/2) is exact.
+// p = fl(M z) and e = fma(M, z, -p); p - 2 rint(p/2) is exact.  The angle
+// a = r + e in [-1, 1] is split as k/1024 + d (d exact, |d| <= 1/2048): the table
+// gives (sin, cos)(pi k/1024), short Taylor series (sin z = z - z^3/6 + z^5/120,
+// cos z = 1 - z^2/2 + z^4/24 at |z| <= pi/2048, dropped terms below 1e-20
+// relative) give (sin, cos)(pi d), and the angle addition joins them.
 INFFT_D double2 node_phase(double M, double z) {
     const double p = M * z;
     const double e = fma(M, z, -p);
     const double r = p - 2.0 * rint(0.5 * p);
-    double s, c;
-    sincospi(r + e, &s, &c);
-    return make_double2(s, c);
+    const double a = r + e;
+    const double kf = fmin(fmax(rint(a * (double)PHASE_TAB_HALF), -(double)PHASE_TAB_HALF), (double)PHASE_TAB_HALF);
+    const double d = fma(kf, -1.0 / (double)PHASE_TAB_HALF, a);
+    const double zz = 3.141592653589793238462643383279502884 * d;
+    const double z2 = zz * zz;
+    const double sd = zz * fma(z2, fma(z2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+    const double cd = fma(z2, fma(z2, 1.0 / 24.0, -0.5), 1.0);
+    const double2 t = g_phase_tab[(int)kf + PHASE_TAB_HALF];   // (sin, cos)(pi k/1024)
+    return make_double2(fma(t.x, cd, t.y * sd), fma(t.y, cd, -(t.x * sd)));
 }
 
 // Per sorted node: its position and its phase (sin, cos)(pi M x).
@@ -211,6 +230,31 @@ cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, 
     k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, p->scan_sums);
     launch_end(p, s);
     return cudaGetLastError();
+}
+
+cudaError_t phase_table_init() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    std::vector<double2> t(2 * PHASE_TAB_HALF + 1);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = -PHASE_TAB_HALF; k <= PHASE_TAB_HALF; ++k) {
+        const long double a = pi * (long double)k / (long double)PHASE_TAB_HALF;
+        t[k + PHASE_TAB_HALF] = make_double2((double)sinl(a), (double)cosl(a));
+    }
+    // exact values where the angle is a multiple of pi/2
+    for (int k : {-PHASE_TAB_HALF, -PHASE_TAB_HALF / 2, 0, PHASE_TAB_HALF / 2, PHASE_TAB_HALF}) {
+        const int q = ((k / (PHASE_TAB_HALF / 2)) % 4 + 4) % 4;
+        t[k + PHASE_TAB_HALF] = make_double2(q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0), q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0));
+    }
+    e = cudaMemcpyToSymbol(g_phase_tab, t.data(), t.size() * sizeof(double2));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
 }
 
 cudaError_t run_pattern(Plan* p, cudaStream_t s) {

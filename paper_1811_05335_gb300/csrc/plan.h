@@ -134,6 +134,9 @@ void launch_end(Plan* p, cudaStream_t s);
 
 // pattern.cu
 cudaError_t run_pattern(Plan* p, cudaStream_t s);
+// pattern.cu: fills the node-phase table on the current device (once; synchronous, so it is
+// called when a plan or batch is created, not inside a stream capture)
+cudaError_t phase_table_init();
 cudaError_t run_exclusive_scan(Plan* p, const int32_t* in, int32_t* out, int n, cudaStream_t s);
 // lsq.cu
 cudaError_t run_precompute(Plan* p, cudaStream_t s);
