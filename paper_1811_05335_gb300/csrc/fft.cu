@@ -277,10 +277,13 @@ struct R8Shape {
     int threads_per, per_cta, smem;
 };
 
-INFFT_HD R8Shape r8_shape(int logn, int count) {
+INFFT_HD R8Shape r8_shape(int logn, int count, int K = 1) {
     R8Shape s;
     s.threads_per = (1 << logn) / 8;
     s.per_cta = s.threads_per >= R8_MIN_THREADS ? 1 : R8_MIN_THREADS / s.threads_per;
+    // several data vectors fill the GPU anyway: wider CTAs read whole 32-byte sectors
+    // of the strided columns (4 consecutive complex64) and write longer output runs
+    if (K >= 4 && s.threads_per < 256 && s.per_cta * s.threads_per < 256) s.per_cta = 256 / s.threads_per;
     if (s.per_cta > count) s.per_cta = count;
     const int n = 1 << logn;
     s.smem = (n + 2 * s.per_cta * (n + n / 8)) * (int)sizeof(float2);
@@ -367,7 +370,7 @@ cudaError_t fft_adjoint_r8(const float2* g, float2* work, float2* fhat, int logM
     const int log2 = logMs / 2, log1 = logMs - log2;
     const int Ms = 1 << logMs;
     const float inv_Ms = 1.0f / (float)Ms;
-    const R8Shape a = r8_shape(log1, 1 << log2), b = r8_shape(log2, 1 << log1);
+    const R8Shape a = r8_shape(log1, 1 << log2, K), b = r8_shape(log2, 1 << log1, K);
     void (*ka)(const float2*, float2*, int, int) = nullptr;
     void (*kb)(const float2*, float2*, int, int, int, float, int) = nullptr;
     switch (log1) {

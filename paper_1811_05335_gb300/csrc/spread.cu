@@ -174,14 +174,111 @@ template cudaError_t run_spread<double>(Plan*, const void*, cudaStream_t);
 template cudaError_t run_interp<float>(Plan*, void*, cudaStream_t);
 template cudaError_t run_interp<double>(Plan*, void*, cudaStream_t);
 
-// K data vectors at once (f: K x N, grid: K x M_sigma): one launch, the vector in
-// blockIdx.y; the tiles of all vectors read the same weights, which stay in L2.
+// K data vectors at once (f: K x N, grid: K x M_sigma).  A CTA stages its tile's
+// weights and node indices once and then streams the K vectors' node windows
+// through MANY_NB shared-memory buffers (the next MANY_NB - 1 vectors' values are in
+// flight while the current one is summed).  A tile whose block does not fit takes
+// the one-vector tile path per vector.
+static constexpr int MANY_UMAX = SPREAD_UMAX / 2;   // node values per buffer
+static constexpr int MANY_NB = 4;                   // buffers (prefetch depth MANY_NB - 1)
+static constexpr size_t MANY_SMEM = SPREAD_WMAX * sizeof(float) + MANY_NB * MANY_UMAX * sizeof(float2);
+
+static __global__ void __launch_bounds__(SPREAD_COLS, 3)
+k_spread_many(const float2* __restrict__ f, int K, const float* __restrict__ w32, const double* __restrict__ w64,
+              const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
+              const int32_t* __restrict__ col_start, const int32_t* __restrict__ col_count,
+              const int32_t* __restrict__ col_off, int N, int Ms, float2* __restrict__ g) {
+    extern __shared__ __align__(16) unsigned char many_raw[];   // MANY_SMEM bytes
+    float* ws = (float*)many_raw;                                  // SPREAD_WMAX
+    float2* fu = (float2*)(many_raw + SPREAD_WMAX * sizeof(float)); // MANY_NB * MANY_UMAX
+    griddep_wait();
+    griddep_launch();
+    const int p0 = blockIdx.x * SPREAD_COLS, p1 = min(p0 + SPREAD_COLS, Ms);
+    const int p = p0 + threadIdx.x;
+    const bool live = p < p1;
+    const int n = live ? col_count[p] : 0;
+    const int s = live ? col_start[p] : 0;
+    const int off = live ? col_off[p] : 0;
+    const bool wide_col = live && wide[p];
+    const int w0 = col_off[p0], w1 = col_off[p1];
+    const int S = col_start[p0];
+    int U = col_start[p1 - 1] + col_count[p1 - 1] - S;
+    if (U < 0) U += N;
+    int r0 = s - S;
+    if (r0 < 0) r0 += N;
+    const int wb = w0 & ~3, we = (w1 + 3) & ~3;
+    const int inside = !live || n == 0 || (r0 + n <= U);
+    const bool staged = __syncthreads_and(inside) && (we - wb) <= SPREAD_WMAX && U <= MANY_UMAX && U <= N;
+    if (!staged) {
+        for (int k = 0; k < K; ++k) {
+            spread_tile_f32(f + (size_t)k * N, w32, w64, wide, perm, col_start, col_count, col_off, N, p0, p1,
+                            g + (size_t)k * Ms, ws, fu);
+            __syncthreads();
+        }
+        return;
+    }
+    for (int v = threadIdx.x; v < (we - wb) / 4; v += SPREAD_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
+    constexpr int UPT = MANY_UMAX / SPREAD_COLS;
+    int pq[UPT];
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int q = threadIdx.x + u * SPREAD_COLS;
+        int gq = S + q;
+        if (gq >= N) gq -= N;
+        pq[u] = q < U ? perm[gq] : 0;
+    }
+    auto issue = [&](int k) {
+        const float2* fk = f + (size_t)k * N;
+        float2* dst = fu + (k % MANY_NB) * MANY_UMAX;
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+            const int q = threadIdx.x + u * SPREAD_COLS;
+            if (q < U) cp_async8(dst + q, fk + pq[u]);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int k = 0; k < MANY_NB - 1 && k < K; ++k) issue(k);   // the first with the weights
+    for (int k = 0; k < K; ++k) {
+        if (k + MANY_NB - 1 < K) issue(k + MANY_NB - 1);
+        // groups still allowed in flight: those of vectors k+1 .. min(K-1, k+MANY_NB-1)
+        const int ahead = min(K - 1 - k, MANY_NB - 1);
+        if (ahead >= 3) asm volatile("cp.async.wait_group 3;" ::: "memory");
+        else if (ahead == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else if (ahead == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (live) {
+            float2* gk = g + (size_t)k * Ms;
+            if (wide_col) {
+                gk[p] = spread_direct<float>(f + (size_t)k * N, w32, w64, true, perm, n, s, off, N);
+            } else {
+                // walk the column from a lane-dependent start (see spread_tile_f32)
+                const float* wc = ws + (off - wb);
+                const float2* fc = fu + (k % MANY_NB) * MANY_UMAX + r0;
+                float re = 0, im = 0;
+                int j = n ? (int)(threadIdx.x & 31) % n : 0;
+                for (int i = 0; i < n; ++i) {
+                    const float wi = wc[j];
+                    const float2 v = fc[j];
+                    re = fmaf(wi, v.x, re);
+                    im = fmaf(wi, v.y, im);
+                    j = (j + 1 == n) ? 0 : j + 1;
+                }
+                gk[p] = make_float2(re, im);
+            }
+        }
+        __syncthreads();   // buffer k % MANY_NB is refilled for vector k + MANY_NB
+    }
+}
+
 cudaError_t run_spread_many(Plan* p, const void* f, void* grid, int K, cudaStream_t s) {
     const int Ms = (int)p->Ms;
+    cudaError_t e = cudaFuncSetAttribute(k_spread_many, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MANY_SMEM);
+    if (e != cudaSuccess) return e;
     launch_begin(p, "spread_many", s);
-    cudaError_t e = launch_pdl(k_spread_f32, dim3((Ms + SPREAD_COLS - 1) / SPREAD_COLS, K), dim3(SPREAD_COLS), 0, s,
-                               (const float2*)f, p->w32, p->w64, p->wide, p->perm, p->col_start, p->col_count,
-                               p->col_off, (int)p->N, Ms, (float2*)grid);
+    e = launch_pdl(k_spread_many, dim3((Ms + SPREAD_COLS - 1) / SPREAD_COLS), dim3(SPREAD_COLS), MANY_SMEM, s,
+                   (const float2*)f, K, p->w32, p->w64, p->wide, p->perm, p->col_start, p->col_count, p->col_off,
+                   (int)p->N, Ms, (float2*)grid);
     launch_end(p, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
