@@ -24,6 +24,8 @@ Layout (each function cites the passage it follows):
                   (eq:approx_ansatz2), its adjoint B_opt F D (Remark
                   remark:ansatz2_adj), the Frobenius objective and the
                   per-node error measures (eq:errors_per_node_lagrange).
+* ``infft2d``  -- the 2-D tensor-product reading of Sec. 3.2.2 (box pattern,
+                  product kernel, 2-D F and D), naive and closed-form tiers.
 * ``under``    -- the underdetermined case of Sec. 3.2.1: one least-squares
                   problem per node with the explicit matrix K_j (eq:matrix_Kj),
                   f_check = (1/M) D^* F^* B_opt^* f (eq:approx_ansatz1) and the
@@ -47,4 +49,4 @@ Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against the true coefficients, whose values the paper prints only as figures
 ("parity unpinned" for that comparison; it is reported, not asserted).
 """
-from . import nfft, pattern, kernel, bopt, infft, under  # noqa: F401
+from . import nfft, pattern, kernel, bopt, infft, under, infft2d  # noqa: F401

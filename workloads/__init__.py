@@ -12,7 +12,8 @@ generator: draw ``i`` of stream ``seed`` is ``mix(seed + (i + 1) * GAMMA)``.
 Uniforms take the top 53 bits; normals use the Box-Muller transform.
 """
 from .rng import uniform01, uniform, normal, complex_normal  # noqa: F401
-from .nodes import jittered, iid_uniform, chebyshev_jittered, equispaced, wrap_half  # noqa: F401
+from .nodes import jittered, iid_uniform, chebyshev_jittered, equispaced, wrap_half, radial  # noqa: F401
 from .configs import (  # noqa: F401
-    Problem, make_problem, trig_poly_eval, CONFIG_SEED_BASE, BatchWorkload, make_batch,
+    Problem, make_problem, trig_poly_eval, CONFIG_SEED_BASE, BatchWorkload, make_batch, Workload2D, make_2d,
+    trig_poly_eval_2d,
 )

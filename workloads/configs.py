@@ -7,7 +7,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .rng import complex_normal, uniform
-from .nodes import iid_uniform, jittered, chebyshev_jittered
+from .nodes import iid_uniform, jittered, chebyshev_jittered, radial
 
 CONFIG_SEED_BASE = 1811053350
 _NODES, _COEF, _NOISE = 1, 2, 3
@@ -133,3 +133,48 @@ def make_batch(P=4096, seed=None, M_range=(256, 8192), r_range=(2.0, 4.0), m=6, 
         else:
             xs.append(iid_uniform(s, int(N[p])))
     return BatchWorkload("config3", M, N, m, xs, seed)
+
+
+def trig_poly_eval_2d(x, fhat):
+    """f_j = sum_{k1, k2} fhat[k1, k2] exp(2 pi i (k1 x_j1 + k2 x_j2)), k_t = -M_t/2 .. M_t/2-1
+    (eq:trig_polynomial on the 2-D torus), in fp64.  The sum over k2 is one complex
+    matrix product per block of nodes; every exponential is formed from its own
+    argument reduced modulo 1.  Input generation, not part of the inversion method."""
+    x = np.asarray(x, dtype=np.float64)
+    fhat = np.asarray(fhat, dtype=np.complex128)
+    M1, M2 = fhat.shape
+    k1 = np.arange(-(M1 // 2), M1 // 2, dtype=np.float64)
+    k2 = np.arange(-(M2 // 2), M2 // 2, dtype=np.float64)
+    out = np.empty(x.shape[0], dtype=np.complex128)
+    for s in range(0, x.shape[0], 8192):
+        xs = x[s:s + 8192]
+        a1 = np.outer(xs[:, 0], k1)
+        a1 -= np.round(a1)
+        a2 = np.outer(xs[:, 1], k2)
+        a2 -= np.round(a2)
+        T = np.exp(2j * np.pi * a2) @ fhat.T            # (n, M1): sum over k2
+        out[s:s + 8192] = np.sum(np.exp(2j * np.pi * a1) * T, axis=1)
+    return out
+
+
+@dataclass
+class Workload2D:
+    name: str
+    M1: int
+    M2: int
+    m: int
+    x: np.ndarray        # (N, 2) nodes in [-1/2, 1/2)^2
+    seed: int
+
+    @property
+    def N(self):
+        return self.x.shape[0]
+
+
+def make_2d(spokes=512, samples=512, M=(256, 256), m=4, jitter=1e-4, seed=None):
+    """Workload 4: the 2-D tensor-product form on a radial trajectory: spokes at
+    angles pi s / spokes, equispaced radii -1/2 + i / samples, U(-jitter, jitter)
+    per coordinate; M = M1 x M2 coefficients, sigma = 2 per dimension, m = 4."""
+    seed = CONFIG_SEED_BASE + 4 if seed is None else seed
+    x = radial(seed * 16 + _NODES, spokes, samples, jitter)
+    return Workload2D("config4", int(M[0]), int(M[1]), m, x, seed)

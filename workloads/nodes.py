@@ -38,3 +38,19 @@ def chebyshev_jittered(seed, n, rel_jitter=1e-3):
     j = np.arange(1, n + 1, dtype=np.float64)
     base = 0.5 * np.cos(np.pi * (j - 0.5) / n)
     return wrap_half(base + uniform(seed, n, -rel_jitter / n, rel_jitter / n))
+
+
+def radial(seed, spokes, samples, jitter=1e-4):
+    """Radial trajectory in [-1/2, 1/2)^2 (the 2-D workload): spoke s at angle
+    theta_s = pi s / spokes (s = 0 .. spokes-1), samples at radii
+    r_i = -1/2 + i / samples (i = 0 .. samples-1), each coordinate perturbed by
+    U(-jitter, jitter) and wrapped.  Node j = s * samples + i; returns (N, 2)."""
+    s = np.arange(spokes, dtype=np.float64)
+    r = -0.5 + np.arange(samples, dtype=np.float64) / samples
+    th = np.pi * s / spokes
+    n = spokes * samples
+    x = np.empty((n, 2))
+    x[:, 0] = (np.cos(th)[:, None] * r[None, :]).ravel()
+    x[:, 1] = (np.sin(th)[:, None] * r[None, :]).ravel()
+    jit = uniform(seed, 2 * n, -jitter, jitter).reshape(n, 2)
+    return wrap_half(x + jit).reshape(n, 2)
