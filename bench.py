@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-under", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--no-2d", action="store_true")
     return ap.parse_args()
 
 
@@ -482,6 +483,39 @@ def run_gpu(a):
                                       "bound": "hbm", "achieved": ach_b, "peak": peaks()[0], "unit": "GB/s",
                                       "frac": ach_b / peaks()[0], "algorithmic_bytes": ab_b}}
 
+    # ---- 2-D tensor-product form (workload 4: radial trajectory of 512 spokes x 512
+    # samples, M = 256 x 256, sigma = 2 per dimension, m = 4)
+    two_d = None
+    if not a.no_2d:
+        from workloads import make_2d
+        w2 = make_2d(seed=1811053354 + 1000 * rank)
+        x2 = torch.tensor(w2.x, dtype=torch.float64, device=dev)
+        f2 = torch.tensor(np.random.default_rng(22).standard_normal((w2.N, 2)).astype(np.float32)
+                          .view(np.complex64).ravel(), device=dev)
+        out2 = torch.empty(w2.M1 * w2.M2, dtype=torch.complex64, device=dev)
+        q2 = g.infft2d_plan_create(w2.M1, w2.M2, w2.N, 2.0, w2.m)
+        t_pat2 = timed(lambda: g.infft2d_set_nodes(q2, x2, stream), reps=2, warm=1)
+        t_pre2 = timed(lambda: g.infft2d_precompute(q2, stream), reps=2, warm=1)
+        t_app2 = timed(lambda: g.infft2d_apply(q2, f2, out=out2, stream=stream), reps=50)
+        info2 = g.infft2d_get_info(q2)
+        q2.close()
+        M2d = w2.M1 * w2.M2
+        ab2 = 8 * w2.N + 4 * info2["nnz"] + 8 * M2d          # f, weights, fhat
+        idx2 = 4 * info2["nnz"] + 4 * (4 * M2d + 1)          # node index per entry, column offsets
+        ach2 = ab2 / (t_app2 / 1e3) / 1e9
+        two_d = {"workload": f"2-D radial trajectory {w2.N} nodes (512 spokes x 512 samples, 1e-4 jitter), "
+                             f"M = {w2.M1} x {w2.M2}, sigma = 2 per dimension, m = {w2.m}",
+                 "pattern_ms": t_pat2, "precompute_ms": t_pre2, "apply_ms": t_app2,
+                 "apply_nodes_per_s": w2.N / (t_app2 / 1e3),
+                 "nnz": info2["nnz"], "max_column": info2["max_column"], "empty_columns": info2["empty_columns"],
+                 "large_columns": info2["large_columns"], "wide_columns": info2["wide_columns"],
+                 "fallback_columns": info2["fallback_columns"], "unsupported_columns": info2["unsupported_columns"],
+                 "objective": info2["objective"],
+                 "roofline_apply": {"kernel": "2-D spread + row and column FFT passes (one apply)", "bound": "hbm",
+                                    "achieved": ach2, "peak": peaks()[0], "unit": "GB/s",
+                                    "frac": ach2 / peaks()[0], "algorithmic_bytes": ab2,
+                                    "index_bytes": idx2}}
+
     # ---- roofline of the dominant kernel and of the apply
     hbm, sm_max, src = peaks()
     ktab = {name: (n, ms) for name, n, ms in kernels}
@@ -541,6 +575,7 @@ def run_gpu(a):
         "differentiable": diff,
         "underdetermined": under,
         "batched": batched,
+        "two_d": two_d,
         "kernels": {name: {"launches": n, "ms_total": ms} for name, n, ms in kernels},
         "plan": {"nnz": info["nnz"], "max_column": info["max_column"], "fallback_columns": info["fallback_columns"]},
         "cpu_baseline": cpu,

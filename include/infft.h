@@ -305,6 +305,79 @@ infft_status infft_batch_destroy(infft_batch_t batch);
 infft_status infft_fft_deconv_noalloc(const float* grid, int64_t M, int64_t M_sigma, int kernel,
                                       float* fhat, infft_stream_t stream);
 
+/* ---- two-dimensional tensor-product form ----------------------------------
+ * The paper treats one dimension and leaves higher dimensions open (Sec. 5).
+ * This form takes every object of Sec. 3.2.2 as the tensor product of its 1-D
+ * counterpart: frequencies k = (k1, k2), k_t = -M_t/2 .. M_t/2-1; nodes
+ * x_j = (x_j1, x_j2) in [-1/2, 1/2)^2; grid points l = (l1, l2) on the
+ * M_sigma,1 x M_sigma,2 grid (M_sigma,t = sigma M_t); D = diag(c_k1 c_k2/(M_sigma,1 M_sigma,2))
+ * with the 1-D Dirichlet choices (eq:matrix_D, Remark remark:Dirichlet_ansatz2);
+ * the pattern I(l) = { j : l_t in I_t(x_jt), t = 1, 2 } (eq:set_xj per dimension, a
+ * box); and per grid point the regularised real least-squares problem of
+ * eq:opt_ansatz2 .. eq:solution_ansatz2, whose Gram entries are the real part of the
+ * product of the two complex 1-D kernels.  fhat = D^* F^* B_opt^* f (eq:approx_ansatz2).
+ * Layout: x is N (x1, x2) fp64 pairs (2N doubles); f is N complex64 (or complex128
+ * for the _z call) in the caller's node order; fhat is M1 x M2 complex, k1-major:
+ * (k1, k2) at (k1 + M1/2) M2 + k2 + M2/2.  Grid column p = (l1 + M_sigma,1/2) M_sigma,2 +
+ * l2 + M_sigma,2/2.
+ * Sizes: M_t even, M_sigma,t = sigma M_t a power of two in [4, 2048]; 1 <= m and
+ * 2m < M_sigma,t; N (2m+1)^2 < 2^31.  Columns of more than 8192 nodes are
+ * counted as unsupported (b_l = 0). */
+typedef struct infft2d_plan_s* infft2d_plan_t;
+
+typedef struct {
+    int64_t M1, M2, M_sigma1, M_sigma2, N;
+    int32_t m, kernel;
+    double sigma, tau;
+    int64_t nnz;                  /* sum over l of |I(l)| */
+    int32_t max_column;           /* max |I(l)| */
+    int32_t empty_columns;        /* columns with I(l) empty (J_l = 1) */
+    int32_t bad_nodes;            /* nodes not finite or outside [-1/2, 1/2)^2 */
+    int32_t fallback_columns;     /* columns whose Cholesky needed a larger regulariser */
+    int32_t unsupported_columns;  /* columns above 8192 nodes (b_l = 0) */
+    int32_t large_columns;        /* columns solved by the blocked solver (above 128 nodes) */
+    int32_t wide_columns;         /* columns spread with fp64 weights (||b_l||_1 > 32) */
+    int32_t nodes_set, precomputed;
+    double objective;             /* sum_l J_l = ||F D A^* B_opt - I||_F^2 */
+} infft2d_info;
+
+/* Creates a 2-D plan (sizes as above; kernel FULL or SYM; tau >= 0 the regulariser
+ * factor).  Allocates the plan's device buffers; *out is NULL on failure. */
+infft_status infft2d_plan_create(int64_t M1, int64_t M2, int64_t N, double sigma, int m, int kernel,
+                                 double tau, infft2d_plan_t* out);
+
+/* The pattern step: copies the 2N doubles of x (host or device), sorts the nodes
+ * by grid cell and builds I(l) for every grid point.  Synchronises `stream` before
+ * it returns (the column sizes are read back); INFFT_EINVAL if a node is not finite
+ * or outside [-1/2, 1/2)^2. */
+infft_status infft2d_set_nodes(infft2d_plan_t plan, const double* x, infft_stream_t stream);
+
+/* Fills B_opt in fp64 (Cholesky of Re G_l + mu I, mu = tau Re kappa(0); a column whose
+ * factorisation fails is retried with mu raised 1000-fold, twice, then set to 0 and
+ * counted).  Allocates the large-column scratch on first use and synchronises
+ * `stream` once before its launches. */
+infft_status infft2d_precompute(infft2d_plan_t plan, infft_stream_t stream);
+
+/* fhat = D^* F^* B_opt^* f: spreading onto the grid, the 2-D FFT pruned to the
+ * M1 x M2 central frequencies with D^* fused into its last pass.  fp32 arithmetic
+ * and accumulation (columns with ||b_l||_1 > 32 spread in fp64).  f and fhat host
+ * or device; with a host fhat the call returns after the result is copied. */
+infft_status infft2d_apply(infft2d_plan_t plan, const float* f, float* fhat, infft_stream_t stream);
+/* The same in fp64 throughout (complex128 f and fhat). */
+infft_status infft2d_apply_z(infft2d_plan_t plan, const double* f, double* fhat, infft_stream_t stream);
+
+/* Synchronises the plan's last stream and fills *info. */
+infft_status infft2d_get_info(infft2d_plan_t plan, infft2d_info* info);
+
+/* Copies the pattern and B_opt to HOST arrays (any may be NULL): col_offset
+ * (P + 1 int32, P = M_sigma,1 M_sigma,2), col_node (nnz int32, caller node index of each
+ * entry, column by column), weights (nnz fp64), objective (P fp64, J_l).  Synchronous. */
+infft_status infft2d_copy_plan_data(infft2d_plan_t plan, int32_t* col_offset, int32_t* col_node,
+                                    double* weights, double* objective);
+
+/* Frees the plan (synchronises its device first). */
+infft_status infft2d_plan_destroy(infft2d_plan_t plan);
+
 /* Number of kernels this library has launched in the process so far. */
 int64_t infft_launch_count(void);
 

@@ -26,6 +26,8 @@ EXPORTED_SYMBOLS = (
     "infft_batch_create", "infft_batch_set_nodes", "infft_batch_precompute", "infft_batch_apply",
     "infft_batch_get_info", "infft_batch_copy_problem", "infft_batch_destroy",
     "infft_apply_many", "infft_apply_many_workspace",
+    "infft2d_plan_create", "infft2d_set_nodes", "infft2d_precompute", "infft2d_apply", "infft2d_apply_z",
+    "infft2d_get_info", "infft2d_copy_plan_data", "infft2d_plan_destroy",
 )
 
 
@@ -51,6 +53,17 @@ class _BatchInfo(ctypes.Structure):
                 ("max_column", ctypes.c_int32), ("nnz", ctypes.c_int64), ("empty_columns", ctypes.c_int64),
                 ("bad_nodes", ctypes.c_int64), ("fallback_columns", ctypes.c_int64),
                 ("unsupported_columns", ctypes.c_int64), ("large_columns", ctypes.c_int64),
+                ("objective", ctypes.c_double)]
+
+
+class _Info2D(ctypes.Structure):
+    _fields_ = [("M1", ctypes.c_int64), ("M2", ctypes.c_int64), ("M_sigma1", ctypes.c_int64),
+                ("M_sigma2", ctypes.c_int64), ("N", ctypes.c_int64), ("m", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("sigma", ctypes.c_double), ("tau", ctypes.c_double),
+                ("nnz", ctypes.c_int64), ("max_column", ctypes.c_int32), ("empty_columns", ctypes.c_int32),
+                ("bad_nodes", ctypes.c_int32), ("fallback_columns", ctypes.c_int32),
+                ("unsupported_columns", ctypes.c_int32), ("large_columns", ctypes.c_int32),
+                ("wide_columns", ctypes.c_int32), ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32),
                 ("objective", ctypes.c_double)]
 
 
@@ -93,6 +106,14 @@ def library():
         "infft_batch_copy_problem": [P, I64, VP, VP, VP, VP, VP, VP],
         "infft_batch_destroy": [P],
         "infft_apply_many": [P, I64, VP, VP, VP, I64, VP],
+        "infft2d_plan_create": [I64, I64, I64, D, I32, I32, D, ctypes.POINTER(P)],
+        "infft2d_set_nodes": [P, VP, VP],
+        "infft2d_precompute": [P, VP],
+        "infft2d_apply": [P, VP, VP, VP],
+        "infft2d_apply_z": [P, VP, VP, VP],
+        "infft2d_get_info": [P, ctypes.POINTER(_Info2D)],
+        "infft2d_copy_plan_data": [P, VP, VP, VP, VP],
+        "infft2d_plan_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -425,5 +446,88 @@ def infft_batch_copy_problem(batch, p, weights=True):
         J = np.empty(Ms, np.float64)
         _check(library().infft_batch_copy_problem(batch.handle, int(p), None, None, None, None, w.ctypes.data,
                                                   J.ctypes.data))
+        out.update(weights=w[:nnz], objective=J)
+    return out
+
+
+class Plan2D:
+    """Owner of an infft2d_plan_t handle (the 2-D tensor-product form)."""
+
+    def __init__(self, handle, M1, M2, N, Ms1, Ms2, m):
+        self.handle, self.M1, self.M2, self.N, self.m = handle, M1, M2, N, m
+        self.M_sigma1, self.M_sigma2 = Ms1, Ms2
+
+    def close(self):
+        if self.handle:
+            _check(library().infft2d_plan_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def infft2d_plan_create(M1, M2, N, sigma=2.0, m=4, kernel="full", tau=1e-12):
+    h = ctypes.c_void_p()
+    k = _KERNELS.get(kernel, kernel)
+    _check(library().infft2d_plan_create(int(M1), int(M2), int(N), float(sigma), int(m), int(k), float(tau),
+                                         ctypes.byref(h)))
+    return Plan2D(h.value, int(M1), int(M2), int(N), int(round(sigma * M1)), int(round(sigma * M2)), int(m))
+
+
+def infft2d_set_nodes(plan, x, stream=None):
+    """x: (N, 2) float64 nodes (host or device); synchronous."""
+    keep = []
+    _check(library().infft2d_set_nodes(plan.handle, _as_ptr(x, "f64", keep), _stream(stream, x)))
+
+
+def infft2d_precompute(plan, stream=None):
+    _check(library().infft2d_precompute(plan.handle, _stream(stream)))
+
+
+def _apply2(fn, plan, f, out, kind, stream):
+    keep = []
+    if out is None:
+        out = _empty_like(f, plan.M1 * plan.M2, kind)
+    _check(fn(plan.handle, _as_ptr(f, kind, keep), _as_ptr(out, kind, keep), _stream(stream, f, out)))
+    return out.reshape(plan.M1, plan.M2)
+
+
+def infft2d_apply(plan, f, out=None, stream=None):
+    """fhat (M1 x M2 complex64, k1-major) = D^* F^* B_opt^* f for N complex64 samples."""
+    return _apply2(library().infft2d_apply, plan, f, out, "c64", stream)
+
+
+def infft2d_apply_z(plan, f, out=None, stream=None):
+    return _apply2(library().infft2d_apply_z, plan, f, out, "c128", stream)
+
+
+def infft2d_get_info(plan):
+    info = _Info2D()
+    _check(library().infft2d_get_info(plan.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in _Info2D._fields_}
+
+
+def infft2d_copy_plan_data(plan, weights=True):
+    """Pattern (col_offset, col_node) and, once precomputed, B_opt (weights, objective) as numpy arrays."""
+    info = infft2d_get_info(plan)
+    P = plan.M_sigma1 * plan.M_sigma2
+    nnz = int(info["nnz"])
+    off = np.empty(P + 1, np.int32)
+    node = np.empty(max(nnz, 1), np.int32)
+    w = np.empty(max(nnz, 1), np.float64) if weights else None
+    J = np.empty(P, np.float64) if weights else None
+    ptr = lambda a: a.ctypes.data if a is not None else None
+    _check(library().infft2d_copy_plan_data(plan.handle, ptr(off), ptr(node), ptr(w), ptr(J)))
+    out = dict(col_offset=off, col_node=node[:nnz])
+    if weights:
         out.update(weights=w[:nnz], objective=J)
     return out

@@ -29,32 +29,6 @@ constexpr int FFT_SMALL = 2048;
 
 template <typename T> INFFT_D cplx_t<T> czero() { return cmake((T)0, (T)0); }
 
-// Batched radix-2 Stockham FFTs of length n = 2^logn in shared memory.  a holds
-// `batch` transforms back to back; b is scratch of the same size.  Returns the
-// buffer that holds the result.  DIR = -1: exp(-2 pi i ...), +1: exp(+2 pi i ...).
-template <typename T, int DIR>
-INFFT_D cplx_t<T>* smem_fft(cplx_t<T>* a, cplx_t<T>* b, int logn, int batch) {
-    using C = cplx_t<T>;
-    const int n = 1 << logn, half = n >> 1;
-    const int total = batch * half;
-    for (int Ns = 1; Ns < n; Ns <<= 1) {
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int bi = t >> (logn - 1), j = t & (half - 1);
-            const C* src = a + bi * n;
-            C* dst = b + bi * n;
-            const int jm = j & (Ns - 1);
-            C v0 = src[j], v1 = src[j + half];
-            v1 = cmul(v1, expipi((T)(DIR * jm) / (T)Ns));
-            const int d = ((j - jm) << 1) + jm;
-            dst[d] = cadd(v0, v1);
-            dst[d + Ns] = csub(v0, v1);
-        }
-        __syncthreads();
-        C* tmp = a; a = b; b = tmp;
-    }
-    return a;
-}
-
 // frequency k of DFT bin q (or INT_MIN when q is pruned)
 INFFT_D int bin_to_k(int q, int Ms, int M) {
     if (q < M / 2) return q;

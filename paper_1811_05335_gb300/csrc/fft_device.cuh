@@ -1,4 +1,6 @@
-// Register-level pieces of the FFT kernels: length-2, 4 and 8 DFTs of complex
+// Device pieces of the FFT kernels.
+//
+// Register-level pieces: length-2, 4 and 8 DFTs of complex
 // fp32 values held in registers, X_k = sum_r x_r e^{DIR 2 pi i r k / R}, output in
 // natural order.
 #pragma once
@@ -39,5 +41,32 @@ template <int DIR> __device__ __forceinline__ static void dft_r(float2* x, int_c
         x[k] = cadd(e[k], o[k]);
         x[k + 4] = csub(e[k], o[k]);
     }
+}
+
+
+// Batched radix-2 Stockham FFTs of length n = 2^logn in shared memory.  a holds
+// `batch` transforms back to back; b is scratch of the same size.  Returns the
+// buffer that holds the result.  DIR = -1: exp(-2 pi i ...), +1: exp(+2 pi i ...).
+template <typename T, int DIR>
+__device__ __forceinline__ static cplx_t<T>* smem_fft(cplx_t<T>* a, cplx_t<T>* b, int logn, int batch) {
+    using C = cplx_t<T>;
+    const int n = 1 << logn, half = n >> 1;
+    const int total = batch * half;
+    for (int Ns = 1; Ns < n; Ns <<= 1) {
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int bi = t >> (logn - 1), j = t & (half - 1);
+            const C* src = a + bi * n;
+            C* dst = b + bi * n;
+            const int jm = j & (Ns - 1);
+            C v0 = src[j], v1 = src[j + half];
+            v1 = cmul(v1, expipi((T)(DIR * jm) / (T)Ns));
+            const int d = ((j - jm) << 1) + jm;
+            dst[d] = cadd(v0, v1);
+            dst[d + Ns] = csub(v0, v1);
+        }
+        __syncthreads();
+        C* tmp = a; a = b; b = tmp;
+    }
+    return a;
 }
 

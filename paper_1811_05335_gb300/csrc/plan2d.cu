@@ -1,0 +1,1097 @@
+// Two-dimensional tensor-product form of the modified adjoint NFFT: the method of
+// Sec. 3.2.2 taken per dimension (the paper treats d = 1; Sec. 5 leaves d > 1 open).
+//
+//   pattern : nodes are counting-sorted by grid cell (c1, c2), c_t = floor(M_sigma,t x_t)
+//             + M_sigma,t/2, and ordered by node index inside a cell.  The candidates of
+//             column l are the nodes of the (2m+1)^2 cells around it; a candidate enters
+//             I(l) by the exact test of eq:set_xj in each dimension, decided on
+//             u_t = fl(M_sigma,t x_t).  One warp per column: a counting pass, a scan and a
+//             filling pass whose ballot ranks keep the candidate order (deterministic).
+//   B_opt   : per column the fp64 normal equations (Re G_l + mu I) b = Re r_l of
+//             eq:opt_ansatz2 .. eq:solution_ansatz2 (real b, Tikhonov mu = tau Re kappa(0)),
+//             Gram entries Re[kappa_1(d_1) kappa_2(d_2)] of the product kernel.
+//             Columns of up to 128 nodes: one CTA each, one thread per row, packed
+//             triangle in shared memory, right-looking Cholesky with the forward solve
+//             fused.  Larger columns: one CTA each, largest first, packed triangle in a
+//             global scratch slot, Cholesky blocked by PB columns: the PB x PB diagonal
+//             block in shared memory, the rows below by a row-wise triangular solve, the
+//             trailing update in TB x TB tiles whose panel slices are staged in shared
+//             memory (4 x 4 register blocks per thread).
+//   apply   : one warp per column gathers g_l = sum_j b_lj f_j (fp32; fp64 weights and
+//             accumulation for columns with ||b_l||_1 > 32), then the 2-D FFT: rows
+//             (length M_sigma,2, the kept k2 stored transposed) and the kept columns
+//             (length M_sigma,1), with (-1)^(k1+k2) d_k fused into the last store.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "plan.h"
+#include "fft_device.cuh"
+
+struct infft2d_plan_s {
+    int device = 0;
+    int64_t M1 = 0, M2 = 0, Ms1 = 0, Ms2 = 0, N = 0, P = 0;
+    int m = 0, kernel = INFFT_KERNEL_FULL, log1 = 0, log2 = 0;
+    double sigma = 2.0, tau = 1e-12;
+    int64_t nnz_cap = 0, nnz = 0;
+    int max_column = 0;
+
+    double2* x = nullptr;          // N nodes, caller order
+    double2* xs = nullptr;         // N nodes, sorted by cell
+    int32_t* node_cell = nullptr;  // N: cell of each node (-1: invalid node)
+    int32_t* perm = nullptr;       // N: sorted position -> caller index
+    int32_t* cell_start = nullptr; // P + 1: node counts per cell, then their exclusive prefix
+    int32_t* cursor = nullptr;     // P: scatter cursors
+    int32_t* big_cells = nullptr;  // P: cells with more than 32 nodes (ordered by one CTA each)
+    int32_t* col_count = nullptr;  // P
+    int32_t* col_off = nullptr;    // P + 1
+    int32_t* col_node = nullptr;   // nnz_cap: caller index of each entry, column by column
+    int32_t* lists = nullptr;      // 4 P: columns of the three shared-memory tiers and the large tier
+    int32_t* order = nullptr;      // P: large columns, largest first
+    int32_t* hist = nullptr;       // LARGE_NMAX + 2: size buckets, then offsets / cursors; ticket
+    int32_t* counters = nullptr;   // C2_N
+    float* w32 = nullptr;          // nnz_cap
+    double* w64 = nullptr;         // nnz_cap
+    double* J = nullptr;           // P
+    uint8_t* wide = nullptr;       // P
+    void* grid = nullptr;          // P complex128 (also used as complex64)
+    void* work = nullptr;          // M2 Ms1 complex128: the row transforms, transposed
+    void* stage_in = nullptr;      // max(N, M1 M2) complex128
+    void* stage_out = nullptr;
+    void* arena = nullptr;
+    double* scratch = nullptr;     // large-column triangles (owned, grown on demand)
+    size_t scratch_doubles = 0;
+    int nodes_set = 0, precomputed = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+enum {
+    C2_BAD = 0, C2_FALLBACK = 1, C2_UNSUPPORTED = 2, C2_MAX_COLUMN = 3, C2_EMPTY = 4,
+    C2_LIST0 = 5,   // C2_LIST0 + t: length of the list of tier t (0..2 shared memory, 3 large)
+    C2_BIG_CELLS = 9, C2_WIDE = 10, C2_N = 11
+};
+
+constexpr int TIER_NMAX[3] = {32, 64, 128};
+constexpr int SMALL_NMAX = 128;
+constexpr int LARGE_NMAX = 8192;
+constexpr int PB = 16;             // panel width of the blocked solver
+constexpr int TB = 64;             // trailing-update tile
+constexpr int TBP = TB + 2;        // shared-memory row stride of the staged panel slices
+constexpr int LARGE_THREADS = 256;
+constexpr int CELL_SORT_MAX = 4096;
+constexpr int FFT2_THREADS = 256;
+
+thread_local std::string g_err2;
+
+infft_status fail2(infft_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return set_error(st, "%s", buf);
+}
+
+infft_status cuda_fail2(cudaError_t e, const char* what) {
+    return fail2(e == cudaErrorMemoryAllocation ? INFFT_ENOMEM : INFFT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceGuard2 {
+    int prev = -1;
+    explicit DeviceGuard2(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard2() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool on_device2(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- kernel entries (Gram and right-hand side) -------------------------------
+
+struct K2 {
+    double M1, M2;   // kept frequencies per dimension enter as M (full) or M - 1 (sym)
+    double inv;      // 1 / (M_sigma,1 M_sigma,2)
+    double diag;     // Re kappa(0)
+    int sym;
+};
+
+// a - b as the representative in [-1/2, 1/2] on the torus; across the seam the
+// +-1/2 shifts go to the operands first, so close nodes keep their difference exactly
+INFFT_D double tdiff(double a, double b) {
+    double d = a - b;
+    if (d > 0.5) d = (a - 0.5) - (b + 0.5);
+    else if (d < -0.5) d = (a + 0.5) - (b - 0.5);
+    return d;
+}
+
+// sin(pi K d) / sin(pi d), value K at d = 0 (the 1-D Dirichlet sums of both kernels)
+INFFT_D double dirichlet_ratio(double d, double K) {
+    if (d == 0.0) return K;
+    return sinpi(K * d) / sinpi(d);
+}
+
+// Re kappa(d) = Re[kappa_1(d_1) kappa_2(d_2)]: full kernel kappa_t(d) = e^{-i pi d} sin(pi M d)/
+// (M_sigma sin(pi d)), so the real part carries cos(pi (d_1 + d_2)); sym kernel: real Dirichlet
+// kernels sin(pi (M - 1) d)/(M_sigma sin(pi d)) (Remark remark:Dirichlet_ansatz2 per dimension)
+INFFT_D double re_kappa2(double d1, double d2, const K2& k) {
+    if (k.sym) return dirichlet_ratio(d1, k.M1 - 1.0) * dirichlet_ratio(d2, k.M2 - 1.0) * k.inv;
+    return cospi(d1 + d2) * dirichlet_ratio(d1, k.M1) * dirichlet_ratio(d2, k.M2) * k.inv;
+}
+
+INFFT_D int trow(int i) { return i * (i + 1) / 2; }
+
+// ---- pattern ------------------------------------------------------------------
+
+__global__ void k2_cells(const double2* __restrict__ x, int N, int Ms1, int Ms2, int32_t* __restrict__ node_cell,
+                         int32_t* __restrict__ cell_count, int32_t* __restrict__ counters) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double2 v = x[j];
+    if (!(v.x >= -0.5 && v.x < 0.5 && v.y >= -0.5 && v.y < 0.5)) {   // NaN fails too
+        node_cell[j] = -1;
+        atomicAdd(&counters[C2_BAD], 1);
+        return;
+    }
+    const int c1 = (int)floor((double)Ms1 * v.x) + Ms1 / 2;
+    const int c2 = (int)floor((double)Ms2 * v.y) + Ms2 / 2;
+    const int c = c1 * Ms2 + c2;
+    node_cell[j] = c;
+    atomicAdd(&cell_count[c], 1);
+}
+
+// exclusive prefix of a[0 .. n) in place, total in a[n] (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) k2_scan(int32_t* __restrict__ a, int n) {
+    __shared__ int32_t part[1024];
+    const int per = (n + 1023) / 1024;
+    const int lo = min(threadIdx.x * per, n), hi = min(lo + per, n);
+    int32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = lo; i < hi; ++i) {
+        const int32_t c = a[i];
+        a[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) a[n] = part[1023];
+}
+
+__global__ void k2_scatter(const int32_t* __restrict__ node_cell, int N, const int32_t* __restrict__ cell_start,
+                           int32_t* __restrict__ cursor, int32_t* __restrict__ perm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int c = node_cell[j];
+    if (c < 0) return;
+    perm[cell_start[c] + atomicAdd(&cursor[c], 1)] = j;
+}
+
+// order the nodes of each cell by caller index: cells of up to 32 nodes by one thread,
+// larger ones are listed for k2_cell_sort_big
+__global__ void k2_cell_sort(const int32_t* __restrict__ cell_start, int P, int32_t* __restrict__ perm,
+                             int32_t* __restrict__ big_cells, int32_t* __restrict__ counters) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P) return;
+    const int s = cell_start[c], n = cell_start[c + 1] - s;
+    if (n <= 1) return;
+    if (n > 32) {
+        big_cells[atomicAdd(&counters[C2_BIG_CELLS], 1)] = c;
+        return;
+    }
+    for (int i = 1; i < n; ++i) {
+        const int v = perm[s + i];
+        int k = i - 1;
+        while (k >= 0 && perm[s + k] > v) {
+            perm[s + k + 1] = perm[s + k];
+            --k;
+        }
+        perm[s + k + 1] = v;
+    }
+}
+
+// one CTA per listed cell: rank sort of its (distinct) caller indices; cells above
+// CELL_SORT_MAX nodes keep the scatter order (valid, not reproducible run to run)
+__global__ void __launch_bounds__(256) k2_cell_sort_big(const int32_t* __restrict__ cell_start,
+                                                        int32_t* __restrict__ perm,
+                                                        const int32_t* __restrict__ big_cells,
+                                                        const int32_t* __restrict__ counters) {
+    __shared__ int32_t v[CELL_SORT_MAX];
+    const int cnt = counters[C2_BIG_CELLS];
+    for (int b = blockIdx.x; b < cnt; b += gridDim.x) {
+        const int c = big_cells[b];
+        const int s = cell_start[c], n = cell_start[c + 1] - s;
+        if (n > CELL_SORT_MAX) continue;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = perm[s + i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int vi = v[i];
+            int r = 0;
+            for (int k = 0; k < n; ++k) r += v[k] < vi;
+            perm[s + r] = vi;
+        }
+    }
+}
+
+__global__ void k2_gather_nodes(const double2* __restrict__ x, const int32_t* __restrict__ perm,
+                                const int32_t* __restrict__ cell_start, int P, double2* __restrict__ xs) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cell_start[P]) return;
+    xs[q] = x[perm[q]];
+}
+
+// does the node coordinate xt put grid index a (= l + M_sigma/2) into its set (eq:set_xj)?
+// l in [ceil(u) - m, floor(u) + m] mod M_sigma, u = fl(M_sigma xt); with c = floor(u) + M_sigma/2,
+// a - c lies in [1 - m, m] (mod M_sigma), or equals -m when u is an integer
+INFFT_D bool covers(int a, double xt, int Ms, int m) {
+    const double u = (double)Ms * xt;
+    const double fu = floor(u);
+    const int c = (int)fu + Ms / 2;
+    int d = (a - c + m) % Ms;
+    if (d < 0) d += Ms;
+    d -= m;
+    return d <= m && (d > -m || u == fu);
+}
+
+// One warp per column p = a1 Ms2 + a2: candidates in the cells (a1 + d1, a2 - m .. a2 + m)
+// for d1 = -m .. m (wrapped; the c2 range is at most two runs of consecutive cells)
+template <bool FILL>
+__global__ void __launch_bounds__(256) k2_columns(const double2* __restrict__ xs, const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ cell_start, int Ms1, int Ms2, int m,
+                                                  int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off,
+                                                  int32_t* __restrict__ col_node, int32_t* __restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (p >= Ms1 * Ms2) return;
+    const int a1 = p / Ms2, a2 = p - a1 * Ms2;
+    const int out = FILL ? col_off[p] : 0;
+    const unsigned below = lanemask_lt();
+    int cnt = 0;
+    int r0[2], r1[2], nr = 1;
+    const int lo = a2 - m, hi = a2 + m;
+    if (lo < 0) { r0[0] = lo + Ms2; r1[0] = Ms2 - 1; r0[1] = 0; r1[1] = hi; nr = 2; }
+    else if (hi >= Ms2) { r0[0] = lo; r1[0] = Ms2 - 1; r0[1] = 0; r1[1] = hi - Ms2; nr = 2; }
+    else { r0[0] = lo; r1[0] = hi; }
+    for (int d1 = -m; d1 <= m; ++d1) {
+        const int c1 = (a1 + d1 + Ms1) % Ms1;
+        for (int r = 0; r < nr; ++r) {
+            const int s = cell_start[c1 * Ms2 + r0[r]], e = cell_start[c1 * Ms2 + r1[r] + 1];
+            for (int base = s; base < e; base += 32) {
+                const int q = base + lane;
+                bool in = false;
+                if (q < e) {
+                    const double2 v = xs[q];
+                    in = covers(a1, v.x, Ms1, m) && covers(a2, v.y, Ms2, m);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (FILL && in) col_node[out + cnt + __popc(bal & below)] = perm[q];
+                cnt += __popc(bal);
+            }
+        }
+    }
+    if (!FILL && lane == 0) {
+        col_count[p] = cnt;
+        atomicMax(&counters[C2_MAX_COLUMN], cnt);
+        if (cnt == 0) atomicAdd(&counters[C2_EMPTY], 1);
+    }
+}
+
+// ---- precompute: routing ------------------------------------------------------
+
+__global__ void k2_route(const int32_t* __restrict__ col_off, int P, int32_t* __restrict__ lists,
+                         double* __restrict__ w64, float* __restrict__ w32, double* __restrict__ J,
+                         uint8_t* __restrict__ wide, int32_t* __restrict__ hist, int32_t* __restrict__ counters) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int off = col_off[p], n = col_off[p + 1] - off;
+    wide[p] = 0;
+    if (n == 0) { J[p] = 1.0; return; }
+    if (n > LARGE_NMAX) {   // not built: b_l = 0 (J_l = 1)
+        for (int i = 0; i < n; ++i) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
+        J[p] = 1.0;
+        atomicAdd(&counters[C2_UNSUPPORTED], 1);
+        return;
+    }
+    const int t = n <= TIER_NMAX[0] ? 0 : n <= TIER_NMAX[1] ? 1 : n <= TIER_NMAX[2] ? 2 : 3;
+    lists[t * P + atomicAdd(&counters[C2_LIST0 + t], 1)] = p;
+    if (t == 3) atomicAdd(&hist[LARGE_NMAX - n], 1);
+}
+
+// the large list in largest-first order (counting sort by size, descending)
+__global__ void k2_order_large(const int32_t* __restrict__ col_off, const int32_t* __restrict__ large, int P,
+                               int32_t* __restrict__ cursor, int32_t* __restrict__ order,
+                               const int32_t* __restrict__ counters) {
+    const int cnt = counters[C2_LIST0 + 3];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int p = large[i];
+        const int n = col_off[p + 1] - col_off[p];
+        order[atomicAdd(&cursor[LARGE_NMAX - n], 1)] = p;
+    }
+}
+
+// ---- precompute: columns of up to NMAX nodes (one CTA of NMAX threads each) ---
+
+template <int NMAX> constexpr size_t small_smem() {
+    return (size_t)(NMAX * (NMAX + 1) / 2 + 3 * NMAX) * sizeof(double) + NMAX * sizeof(double2);
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(NMAX) k2_solve_small(const double2* __restrict__ x, const int32_t* __restrict__ col_off,
+                                                       const int32_t* __restrict__ col_node,
+                                                       const int32_t* __restrict__ list, int list_id, int Ms1,
+                                                       int Ms2, K2 kp, double mu0, double* __restrict__ w64,
+                                                       float* __restrict__ w32, double* __restrict__ J,
+                                                       uint8_t* __restrict__ wide, int32_t* __restrict__ counters) {
+    extern __shared__ __align__(16) double sm2[];
+    double* A = sm2;                                   // packed lower triangle, row-major
+    double* r = A + NMAX * (NMAX + 1) / 2;             // right-hand side, then y
+    double* lk = r + NMAX;                             // two buffers of L's current column
+    double2* xl = (double2*)(lk + 2 * NMAX);
+    __shared__ double red[2 * (NMAX / 32 > 0 ? NMAX / 32 : 1)];
+    const int i = threadIdx.x;                         // this thread's row
+    const int count = counters[C2_LIST0 + list_id];
+    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+        const int p = list[it];
+        const int off = col_off[p], n = col_off[p + 1] - off;
+        const double t1 = (double)(p / Ms2 - Ms1 / 2) / (double)Ms1;
+        const double t2 = (double)(p % Ms2 - Ms2 / 2) / (double)Ms2;
+        __syncthreads();
+        if (i < n) xl[i] = x[col_node[off + i]];
+        __syncthreads();
+        double mu = mu0, ysq = 0.0;
+        bool ok = false;
+        for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+            if (i < n) {
+                const double2 xi = xl[i];
+                for (int j = 0; j < i; ++j)
+                    A[trow(i) + j] = re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
+                A[trow(i) + i] = kp.diag + mu;
+                r[i] = re_kappa2(tdiff(t1, xi.x), tdiff(t2, xi.y), kp);
+            }
+            __syncthreads();
+            ysq = 0.0;
+            bool failed = false;
+            for (int k = 0; k < n; ++k) {
+                const double akk = A[trow(k) + k];
+                if (!(akk > 0.0) || !isfinite(akk)) { failed = true; break; }   // CTA-uniform
+                const double rp = rsqrt(akk);
+                const double yk = r[k] * rp;
+                ysq = fma(yk, yk, ysq);
+                double* l = lk + (k & 1) * NMAX;
+                if (i > k && i < n) l[i] = A[trow(i) + k] * rp;
+                __syncthreads();
+                if (i > k && i < n) {
+                    const double li = l[i];
+                    A[trow(i) + k] = li;
+                    for (int j = k + 1; j <= i; ++j) A[trow(i) + j] = fma(-li, l[j], A[trow(i) + j]);
+                    r[i] = fma(-li, yk, r[i]);
+                }
+                if (i == k) { A[trow(k) + k] = rp; r[k] = yk; }
+                __syncthreads();
+            }
+            ok = !failed;
+            if (!ok) mu *= 1e3;
+            __syncthreads();
+        }
+        if (!ok) {
+            if (i < n) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
+            if (i == 0) { J[p] = 1.0; atomicAdd(&counters[C2_FALLBACK], 1); }
+            continue;
+        }
+        if (i == 0 && mu != mu0) atomicAdd(&counters[C2_FALLBACK], 1);
+        // back solve L^T b = y: b_k = y_k rp_k after rows k' > k were taken out;
+        // then row k of L removes b_k from the remaining entries
+        double bsq = 0.0, babs = 0.0;
+        for (int k = n - 1; k >= 0; --k) {
+            const double bk = r[k] * A[trow(k) + k];
+            if (i < k) r[i] = fma(-A[trow(k) + i], bk, r[i]);
+            if (i == k) {
+                w64[off + k] = bk;
+                w32[off + k] = (float)bk;
+                bsq = bk * bk;
+                babs = fabs(bk);
+            }
+            __syncthreads();
+        }
+        for (int o = 16; o; o >>= 1) {
+            bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+            babs += __shfl_xor_sync(0xffffffffu, babs, o);
+        }
+        constexpr int W = NMAX / 32 > 0 ? NMAX / 32 : 1;
+        if ((i & 31) == 0) { red[i >> 5] = bsq; red[W + (i >> 5)] = babs; }
+        __syncthreads();
+        if (i == 0) {
+            double t = 0.0, a = 0.0;
+            for (int w = 0; w < W; ++w) { t += red[w]; a += red[W + w]; }
+            J[p] = 1.0 - ysq - mu * t;
+            const bool wd = a > WIDE_COLUMN_L1;
+            wide[p] = wd;
+            if (wd) atomicAdd(&counters[C2_WIDE], 1);
+        }
+    }
+}
+
+// ---- precompute: large columns (blocked, global scratch) ----------------------
+
+size_t large_smem(int nmax) {
+    return (size_t)nmax * (sizeof(double2) + sizeof(double)) + (size_t)2 * TBP * PB * sizeof(double) +
+           (size_t)PB * (PB + 1) * sizeof(double) + 2 * PB * sizeof(double);
+}
+
+__global__ void __launch_bounds__(LARGE_THREADS, 1)
+k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_off, const int32_t* __restrict__ col_node,
+               const int32_t* __restrict__ order, int Ms1, int Ms2, K2 kp, double mu0, double* __restrict__ scratch,
+               size_t slot_doubles, int32_t* __restrict__ ticket, double* __restrict__ w64, float* __restrict__ w32,
+               double* __restrict__ J, uint8_t* __restrict__ wide, int32_t* __restrict__ counters, int nmax) {
+    extern __shared__ __align__(16) double sm2[];
+    double2* xl = (double2*)sm2;                 // nmax nodes of the column
+    double* r = (double*)(xl + nmax);            // nmax: right-hand side, then y, then the back solve
+    double* Li = r + nmax;                       // PB x TBP: panel slice of a tile's rows ([c][row])
+    double* Lj = Li + PB * TBP;                  // PB x TBP: panel slice of a tile's columns
+    double* D = Lj + PB * TBP;                   // PB x (PB + 1): diagonal block
+    double* ypan = D + PB * (PB + 1);            // PB: y of the panel
+    __shared__ int s_job, s_fail;
+    __shared__ double s_ysq;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = LARGE_THREADS / 32;
+    double* A = scratch + (size_t)blockIdx.x * slot_doubles;
+    const int count = counters[C2_LIST0 + 3];
+    for (;;) {
+        if (tid == 0) s_job = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int job = s_job;
+        if (job >= count) break;
+        const int p = order[job];
+        const int off = col_off[p], n = col_off[p + 1] - off;
+        const double t1 = (double)(p / Ms2 - Ms1 / 2) / (double)Ms1;
+        const double t2 = (double)(p % Ms2 - Ms2 / 2) / (double)Ms2;
+        for (int i = tid; i < n; i += LARGE_THREADS) xl[i] = x[col_node[off + i]];
+        __syncthreads();
+        double mu = mu0;
+        bool ok = false;
+        for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+            for (int i = warp; i < n; i += NW) {       // one warp per row: coalesced stores
+                const double2 xi = xl[i];
+                for (int j = lane; j <= i; j += 32)
+                    A[trow(i) + j] = (j == i) ? kp.diag + mu
+                                              : re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
+            }
+            for (int i = tid; i < n; i += LARGE_THREADS) r[i] = re_kappa2(tdiff(t1, xl[i].x), tdiff(t2, xl[i].y), kp);
+            if (tid == 0) { s_fail = 0; s_ysq = 0.0; }
+            __syncthreads();
+            for (int kb = 0; kb < n; kb += PB) {
+                const int w = min(PB, n - kb);
+                // (1) diagonal block: factor in shared memory (warp 0, one lane per row), then y
+                for (int e = tid; e < PB * PB; e += LARGE_THREADS) {
+                    const int a = e / PB, b = e % PB;
+                    D[a * (PB + 1) + b] = (a < w && b <= a) ? A[trow(kb + a) + kb + b] : 0.0;
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    bool bad = false;
+                    for (int c = 0; c < w; ++c) {
+                        const double akk = D[c * (PB + 1) + c];
+                        if (!(akk > 0.0) || !isfinite(akk)) { bad = true; break; }
+                        const double rp = rsqrt(akk);
+                        __syncwarp();
+                        if (lane > c && lane < w) D[lane * (PB + 1) + c] *= rp;
+                        __syncwarp();
+                        if (lane > c && lane < w) {
+                            const double li = D[lane * (PB + 1) + c];
+                            for (int b = c + 1; b <= lane; ++b)
+                                D[lane * (PB + 1) + b] = fma(-li, D[b * (PB + 1) + c], D[lane * (PB + 1) + b]);
+                        }
+                        __syncwarp();
+                        if (lane == 0) D[c * (PB + 1) + c] = rp;
+                        __syncwarp();
+                    }
+                    if (lane == 0) {
+                        if (bad) {
+                            s_fail = 1;
+                        } else {
+                            double ysq = s_ysq;
+                            for (int c = 0; c < w; ++c) {
+                                double v = r[kb + c];
+                                for (int b = 0; b < c; ++b) v = fma(-D[c * (PB + 1) + b], ypan[b], v);
+                                v *= D[c * (PB + 1) + c];
+                                ypan[c] = v;
+                                r[kb + c] = v;
+                                ysq = fma(v, v, ysq);
+                            }
+                            s_ysq = ysq;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (s_fail) break;                      // CTA-uniform
+                for (int e = tid; e < PB * PB; e += LARGE_THREADS) {
+                    const int a = e / PB, b = e % PB;
+                    if (a < w && b <= a) A[trow(kb + a) + kb + b] = D[a * (PB + 1) + b];
+                }
+                // (2) rows below the block: L_ib = (A_ib - sum_{b'<b} L_ib' L_bb') rp_b, and r_i -= L_i. y
+                for (int i = kb + w + tid; i < n; i += LARGE_THREADS) {
+                    double v[PB];
+                    const double* row = A + trow(i) + kb;
+#pragma unroll
+                    for (int b = 0; b < PB; ++b) v[b] = b < w ? row[b] : 0.0;
+                    double acc = r[i];
+#pragma unroll
+                    for (int b = 0; b < PB; ++b) {
+                        if (b < w) {
+                            double s = v[b];
+#pragma unroll
+                            for (int c = 0; c < b; ++c) s = fma(-v[c], D[b * (PB + 1) + c], s);
+                            v[b] = s * D[b * (PB + 1) + b];
+                            acc = fma(-v[b], ypan[b], acc);
+                        }
+                    }
+                    double* wrow = A + trow(i) + kb;
+#pragma unroll
+                    for (int b = 0; b < PB; ++b)
+                        if (b < w) wrow[b] = v[b];
+                    r[i] = acc;
+                }
+                __syncthreads();
+                // (3) trailing update of rows / columns [kb + w, n), lower-triangular tiles
+                const int base = kb + w, T = n - base;
+                const int nt = (T + TB - 1) / TB;
+                const int ntiles = nt * (nt + 1) / 2;
+                const int tx = tid & 15, ty = tid >> 4;
+                for (int tile = 0; tile < ntiles; ++tile) {
+                    int ti = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+                    while (trow(ti + 1) <= tile) ++ti;
+                    while (trow(ti) > tile) --ti;
+                    const int tj = tile - trow(ti);
+                    const int i0 = base + ti * TB, j0 = base + tj * TB;
+                    for (int e = tid; e < TB * PB; e += LARGE_THREADS) {
+                        const int rr = e / PB, c = e % PB;      // consecutive threads: one row's panel entries
+                        const int ii = i0 + rr, jj = j0 + rr;
+                        Li[c * TBP + rr] = (ii < n && c < w) ? A[trow(ii) + kb + c] : 0.0;
+                        Lj[c * TBP + rr] = (jj < n && c < w) ? A[trow(jj) + kb + c] : 0.0;
+                    }
+                    __syncthreads();
+                    double acc[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll 4
+                    for (int c = 0; c < PB; ++c) {
+                        const double2 la = *(const double2*)&Li[c * TBP + ty * 4];
+                        const double2 lb = *(const double2*)&Li[c * TBP + ty * 4 + 2];
+                        const double2 ra = *(const double2*)&Lj[c * TBP + tx * 4];
+                        const double2 rb = *(const double2*)&Lj[c * TBP + tx * 4 + 2];
+                        const double li[4] = {la.x, la.y, lb.x, lb.y}, lj[4] = {ra.x, ra.y, rb.x, rb.y};
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fma(li[a], lj[b], acc[a][b]);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = i0 + ty * 4 + a;
+                        if (i >= n) break;
+                        double* row = A + trow(i);
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int j = j0 + tx * 4 + b;
+                            if (j <= i) row[j] -= acc[a][b];
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+            ok = !s_fail;
+            if (!ok) mu *= 1e3;
+            __syncthreads();
+        }
+        if (!ok) {
+            for (int i = tid; i < n; i += LARGE_THREADS) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
+            if (tid == 0) { J[p] = 1.0; atomicAdd(&counters[C2_FALLBACK], 1); }
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0 && mu != mu0) atomicAdd(&counters[C2_FALLBACK], 1);
+        // back solve L^T b = y, one row of L per step (row k removes b_k from r_0 .. r_{k-1})
+        double bsq = 0.0, babs = 0.0;
+        for (int k = n - 1; k >= 0; --k) {
+            const double* row = A + trow(k);
+            const double bk = r[k] * row[k];
+            for (int i = tid; i < k; i += LARGE_THREADS) r[i] = fma(-row[i], bk, r[i]);
+            if (tid == 0) {
+                w64[off + k] = bk;
+                w32[off + k] = (float)bk;
+                bsq = fma(bk, bk, bsq);
+                babs += fabs(bk);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            J[p] = 1.0 - s_ysq - mu * bsq;
+            const bool wd = babs > WIDE_COLUMN_L1;
+            wide[p] = wd;
+            if (wd) atomicAdd(&counters[C2_WIDE], 1);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- apply ---------------------------------------------------------------------
+
+// g_p = sum_{e in column p} b_e f_{node(e)}, one warp per column
+template <typename T>
+__global__ void __launch_bounds__(256) k2_spread(const cplx_t<T>* __restrict__ f, const int32_t* __restrict__ col_off,
+                                                 const int32_t* __restrict__ col_node, const float* __restrict__ w32,
+                                                 const double* __restrict__ w64, const uint8_t* __restrict__ wide,
+                                                 int P, cplx_t<T>* __restrict__ g) {
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (p >= P) return;
+    const int s = col_off[p], e = col_off[p + 1];
+    if constexpr (sizeof(T) == 4) {
+        if (!wide[p]) {
+            float ar = 0.f, ai = 0.f;
+            for (int q = s + lane; q < e; q += 32) {
+                const float w = w32[q];
+                const float2 v = f[col_node[q]];
+                ar = fmaf(w, v.x, ar);
+                ai = fmaf(w, v.y, ai);
+            }
+            for (int o = 16; o; o >>= 1) {
+                ar += __shfl_xor_sync(0xffffffffu, ar, o);
+                ai += __shfl_xor_sync(0xffffffffu, ai, o);
+            }
+            if (lane == 0) g[p] = make_float2(ar, ai);
+            return;
+        }
+    }
+    double ar = 0.0, ai = 0.0;
+    for (int q = s + lane; q < e; q += 32) {
+        const double w = w64[q];
+        const cplx_t<T> v = f[col_node[q]];
+        ar = fma(w, (double)v.x, ar);
+        ai = fma(w, (double)v.y, ai);
+    }
+    for (int o = 16; o; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) g[p] = cmake((T)ar, (T)ai);
+}
+
+// pass R: rows a1 in [a1_0, a1_0 + C) of the grid, transform over a2 (length Ms2), keep
+// k2 = -M2/2 .. M2/2-1 with the factor (-1)^k2 and store Y[k2 + M2/2][a1]
+template <typename T>
+__global__ void __launch_bounds__(FFT2_THREADS) k2_fft_rows(const cplx_t<T>* __restrict__ g, cplx_t<T>* __restrict__ Y,
+                                                            int log2, int Ms1, int M2, int C) {
+    using Cx = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int Ms2 = 1 << log2;
+    Cx* a = (Cx*)fsm;
+    Cx* b = a + C * Ms2;
+    const int a1_0 = blockIdx.x * C;
+    for (int t = threadIdx.x; t < C * Ms2; t += blockDim.x) a[t] = g[(size_t)a1_0 * Ms2 + t];
+    __syncthreads();
+    const Cx* res = smem_fft<T, -1>(a, b, log2, C);
+    for (int t = threadIdx.x; t < C * M2; t += blockDim.x) {
+        const int rr = t % C, kk = t / C;
+        const int k2 = kk - M2 / 2;
+        const Cx v = res[rr * Ms2 + (k2 & (Ms2 - 1))];
+        Y[(size_t)kk * Ms1 + a1_0 + rr] = (k2 & 1) ? cmake(-v.x, -v.y) : v;
+    }
+}
+
+// pass C: rows kk in [kk_0, kk_0 + C) of Y, transform over a1 (length Ms1), keep k1 and
+// store fhat[k1 + M1/2][kk] = (-1)^k1 d_k * value (d_k = 1/(Ms1 Ms2), 0 for kernel sym
+// when k1 = -M1/2 or k2 = -M2/2)
+template <typename T>
+__global__ void __launch_bounds__(FFT2_THREADS) k2_fft_cols(const cplx_t<T>* __restrict__ Y, cplx_t<T>* __restrict__ fhat,
+                                                            int log1, int M1, int M2, int C, T inv, int sym) {
+    using Cx = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int Ms1 = 1 << log1;
+    Cx* a = (Cx*)fsm;
+    Cx* b = a + C * Ms1;
+    const int kk_0 = blockIdx.x * C;
+    for (int t = threadIdx.x; t < C * Ms1; t += blockDim.x) a[t] = Y[(size_t)kk_0 * Ms1 + t];
+    __syncthreads();
+    const Cx* res = smem_fft<T, -1>(a, b, log1, C);
+    for (int t = threadIdx.x; t < C * M1; t += blockDim.x) {
+        const int rr = t % C, k1i = t / C;
+        const int k1 = k1i - M1 / 2;
+        const int kk = kk_0 + rr;
+        T d = (k1 & 1) ? -inv : inv;
+        if (sym && (k1 == -M1 / 2 || kk == 0)) d = (T)0;
+        const Cx v = res[rr * Ms1 + (k1 & (Ms1 - 1))];
+        fhat[(size_t)k1i * M2 + kk] = cmake(v.x * d, v.y * d);
+    }
+}
+
+int fft_batch(int logn) { return std::max(1, 2048 >> logn); }
+
+template <typename K> cudaError_t smem_attr(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+K2 kernel_params(const infft2d_plan_s* p) {
+    K2 k;
+    k.M1 = (double)p->M1;
+    k.M2 = (double)p->M2;
+    k.sym = p->kernel == INFFT_KERNEL_SYM;
+    k.inv = 1.0 / ((double)p->Ms1 * (double)p->Ms2);
+    k.diag = k.sym ? (k.M1 - 1.0) * (k.M2 - 1.0) * k.inv : k.M1 * k.M2 * k.inv;
+    return k;
+}
+
+struct Carver2 {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename X> void take(X*& ptr, size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        ptr = base ? (X*)(base + off) : nullptr;
+        off += count * sizeof(X) + 16;
+    }
+};
+
+void layout2(infft2d_plan_s* p, Carver2& c) {
+    const size_t N = p->N, P = p->P, M = p->M1 * p->M2;
+    c.take(p->x, N); c.take(p->xs, N); c.take(p->node_cell, N); c.take(p->perm, N);
+    c.take(p->cell_start, P + 1); c.take(p->cursor, P); c.take(p->big_cells, P);
+    c.take(p->col_count, P); c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
+    c.take(p->lists, 4 * P); c.take(p->order, P); c.take(p->hist, LARGE_NMAX + 2);
+    c.take(p->counters, C2_N);
+    c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
+    double2 *grid, *work, *si, *so;
+    c.take(grid, P); c.take(work, (size_t)p->M2 * p->Ms1);
+    const size_t stage = std::max(N, M);
+    c.take(si, stage); c.take(so, stage);
+    p->grid = grid; p->work = work; p->stage_in = si; p->stage_out = so;
+}
+
+cudaError_t run_pattern2(infft2d_plan_s* p, cudaStream_t s) {
+    const int N = (int)p->N, P = (int)p->P, Ms1 = (int)p->Ms1, Ms2 = (int)p->Ms2;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->counters, 0, C2_N * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->cell_start, 0, (P + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->cursor, 0, P * sizeof(int32_t), s)) != cudaSuccess) return e;
+    const int nb = (N + 255) / 256, pb = (P + 255) / 256;
+    k2_cells<<<nb, 256, 0, s>>>(p->x, N, Ms1, Ms2, p->node_cell, p->cell_start, p->counters);
+    k2_scan<<<1, 1024, 0, s>>>(p->cell_start, P);
+    k2_scatter<<<nb, 256, 0, s>>>(p->node_cell, N, p->cell_start, p->cursor, p->perm);
+    k2_cell_sort<<<pb, 256, 0, s>>>(p->cell_start, P, p->perm, p->big_cells, p->counters);
+    k2_cell_sort_big<<<256, 256, 0, s>>>(p->cell_start, p->perm, p->big_cells, p->counters);
+    k2_gather_nodes<<<nb, 256, 0, s>>>(p->x, p->perm, p->cell_start, P, p->xs);
+    const int cb = (P + 7) / 8;
+    k2_columns<false><<<cb, 256, 0, s>>>(p->xs, p->perm, p->cell_start, Ms1, Ms2, p->m, p->col_off, nullptr,
+                                         nullptr, p->counters);
+    k2_scan<<<1, 1024, 0, s>>>(p->col_off, P);
+    k2_columns<true><<<cb, 256, 0, s>>>(p->xs, p->perm, p->cell_start, Ms1, Ms2, p->m, nullptr, p->col_off,
+                                        p->col_node, p->counters);
+    count_launches(9);
+    return cudaGetLastError();
+}
+
+cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
+    const int P = (int)p->P, Ms1 = (int)p->Ms1, Ms2 = (int)p->Ms2;
+    const K2 kp = kernel_params(p);
+    const double mu = p->tau * kp.diag;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->counters + C2_FALLBACK, 0, 2 * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->counters + C2_LIST0, 0, 4 * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->counters + C2_WIDE, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->hist, 0, (LARGE_NMAX + 2) * sizeof(int32_t), s)) != cudaSuccess) return e;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (sms <= 0) sms = 148;
+    k2_route<<<(P + 255) / 256, 256, 0, s>>>(p->col_off, P, p->lists, p->w64, p->w32, p->J, p->wide, p->hist,
+                                             p->counters);
+    count_launches(1);
+    // shared-memory tiers
+    auto t0 = k2_solve_small<32>;
+    auto t1 = k2_solve_small<64>;
+    auto t2 = k2_solve_small<128>;
+    const size_t s0 = small_smem<32>(), s1 = small_smem<64>(), s2 = small_smem<128>();
+    if ((e = smem_attr(t0, s0)) != cudaSuccess) return e;
+    if ((e = smem_attr(t1, s1)) != cudaSuccess) return e;
+    if ((e = smem_attr(t2, s2)) != cudaSuccess) return e;
+    int o0 = 1, o1 = 1, o2 = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, t0, 32, s0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, t1, 64, s1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, t2, 128, s2);
+    t0<<<std::max(o0, 1) * sms, 32, s0, s>>>(p->x, p->col_off, p->col_node, p->lists, 0, Ms1, Ms2, kp, mu, p->w64,
+                                              p->w32, p->J, p->wide, p->counters);
+    t1<<<std::max(o1, 1) * sms, 64, s1, s>>>(p->x, p->col_off, p->col_node, p->lists + P, 1, Ms1, Ms2, kp, mu,
+                                              p->w64, p->w32, p->J, p->wide, p->counters);
+    t2<<<std::max(o2, 1) * sms, 128, s2, s>>>(p->x, p->col_off, p->col_node, p->lists + 2 * P, 2, Ms1, Ms2, kp, mu,
+                                               p->w64, p->w32, p->J, p->wide, p->counters);
+    count_launches(3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // large tier
+    // the shared-memory layout of the large solver keeps 16-byte alignment with an even nmax
+    const int nmax = (std::min(p->max_column, LARGE_NMAX) + 1) & ~1;
+    if (nmax <= SMALL_NMAX) return cudaSuccess;
+    const size_t slot = (size_t)nmax * (nmax + 1) / 2;
+    // as many CTAs as SMs, fewer when the triangles would exceed 16 GiB
+    const int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)sms, ((size_t)16 << 30) / (slot * 8)));
+    if (p->scratch_doubles < slot * slots) {
+        if (p->scratch) cudaFree(p->scratch);
+        p->scratch = nullptr;
+        p->scratch_doubles = 0;
+        if ((e = cudaMalloc(&p->scratch, slot * slots * sizeof(double))) != cudaSuccess) return e;
+        p->scratch_doubles = slot * slots;
+    }
+    k2_scan<<<1, 1024, 0, s>>>(p->hist, LARGE_NMAX + 1);
+    k2_order_large<<<4 * sms, 256, 0, s>>>(p->col_off, p->lists + 3 * P, P, p->hist, p->order, p->counters);
+    if ((e = cudaMemsetAsync(p->hist + LARGE_NMAX + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    const size_t sm = large_smem(nmax);
+    if ((e = smem_attr(k2_solve_large, sm)) != cudaSuccess) return e;
+    k2_solve_large<<<slots, LARGE_THREADS, sm, s>>>(p->x, p->col_off, p->col_node, p->order, Ms1, Ms2, kp, mu,
+                                                    p->scratch, slot, p->hist + LARGE_NMAX + 1, p->w64, p->w32, p->J,
+                                                    p->wide, p->counters, nmax);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
+    using Cx = cplx_t<T>;
+    const int P = (int)p->P;
+    Cx* g = (Cx*)p->grid;
+    Cx* Y = (Cx*)p->work;
+    k2_spread<T><<<(P + 7) / 8, 256, 0, s>>>((const Cx*)f, p->col_off, p->col_node, p->w32, p->w64, p->wide, P, g);
+    const int C2 = std::min<int>(fft_batch(p->log2), (int)p->Ms1);
+    const int C1 = std::min<int>(fft_batch(p->log1), (int)(p->M2 & -p->M2));   // a divisor of M2
+    const size_t sm2 = 2 * (size_t)C2 * p->Ms2 * sizeof(Cx), sm1 = 2 * (size_t)C1 * p->Ms1 * sizeof(Cx);
+    cudaError_t e;
+    if ((e = smem_attr(k2_fft_rows<T>, sm2)) != cudaSuccess) return e;
+    if ((e = smem_attr(k2_fft_cols<T>, sm1)) != cudaSuccess) return e;
+    k2_fft_rows<T><<<(int)p->Ms1 / C2, FFT2_THREADS, sm2, s>>>(g, Y, p->log2, (int)p->Ms1, (int)p->M2, C2);
+    k2_fft_cols<T><<<(int)p->M2 / C1, FFT2_THREADS, sm1, s>>>(Y, (Cx*)fhat, p->log1, (int)p->M1, (int)p->M2, C1,
+                                                              (T)(1.0 / ((double)p->Ms1 * (double)p->Ms2)),
+                                                              p->kernel == INFFT_KERNEL_SYM);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+int ilog2_exact(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return (int64_t(1) << l) == v ? l : -1;
+}
+
+template <typename T> infft_status apply2_impl(infft2d_plan_s* p, const T* f, T* fhat, infft_stream_t stream) {
+    if (!p) return fail2(INFFT_EINVAL, "plan is NULL");
+    if (!f || !fhat) return fail2(INFFT_EINVAL, "f and fhat must not be NULL");
+    if (!p->precomputed) return fail2(INFFT_ENOTREADY, "infft2d_apply before infft2d_precompute");
+    DeviceGuard2 g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    const size_t csz = 2 * sizeof(T);
+    const int64_t M = p->M1 * p->M2;
+    const void* fin = f;
+    cudaError_t e;
+    if (!on_device2(f)) {
+        if ((e = cudaMemcpyAsync(p->stage_in, f, p->N * csz, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail2(e, "copy f to device");
+        fin = p->stage_in;
+    }
+    const bool host_out = !on_device2(fhat);
+    void* out = host_out ? p->stage_out : (void*)fhat;
+    if ((e = run_apply2<T>(p, fin, out, s)) != cudaSuccess) return cuda_fail2(e, "apply");
+    if (host_out) {
+        if ((e = cudaMemcpyAsync(fhat, p->stage_out, M * csz, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail2(e, "copy fhat to host");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail2(e, "synchronize");
+    }
+    return INFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+infft_status infft2d_plan_create(int64_t M1, int64_t M2, int64_t N, double sigma, int m, int kernel, double tau,
+                                 infft2d_plan_t* out) {
+    if (!out) return fail2(INFFT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (M1 < 2 || (M1 & 1) || M2 < 2 || (M2 & 1))
+        return fail2(INFFT_EINVAL, "M1 and M2 must be even and >= 2 (got %lld, %lld)", (long long)M1, (long long)M2);
+    if (N < 1) return fail2(INFFT_EINVAL, "N must be >= 1 (got %lld)", (long long)N);
+    if (!std::isfinite(sigma) || sigma < 1.0) return fail2(INFFT_EINVAL, "sigma must be >= 1 (got %g)", sigma);
+    if (kernel != INFFT_KERNEL_FULL && kernel != INFFT_KERNEL_SYM)
+        return fail2(INFFT_EINVAL, "kernel must be INFFT_KERNEL_FULL or INFFT_KERNEL_SYM (got %d)", kernel);
+    if (!(tau >= 0.0 && tau < 1.0)) return fail2(INFFT_EINVAL, "tau must be in [0, 1) (got %g)", tau);
+    const double d1 = sigma * (double)M1, d2 = sigma * (double)M2;
+    if (d1 != std::floor(d1) || d2 != std::floor(d2) || d1 > 4096.0 || d2 > 4096.0)
+        return fail2(INFFT_EINVAL, "sigma*M_t must be integers (got %.17g, %.17g)", d1, d2);
+    const int64_t Ms1 = (int64_t)d1, Ms2 = (int64_t)d2;
+    const int l1 = ilog2_exact(Ms1), l2 = ilog2_exact(Ms2);
+    if (l1 < 2 || l2 < 2 || Ms1 > 2048 || Ms2 > 2048)
+        return fail2(INFFT_EUNSUPPORTED, "M_sigma,t = sigma M_t must be powers of two in [4, 2048] (got %lld, %lld)",
+                     (long long)Ms1, (long long)Ms2);
+    if (m < 1 || 2 * (int64_t)m >= Ms1 || 2 * (int64_t)m >= Ms2)
+        return fail2(INFFT_EINVAL, "need m >= 1 and 2m < M_sigma,t (m = %d)", m);
+    if ((double)N * (2.0 * m + 1.0) * (2.0 * m + 1.0) >= 2147483647.0)
+        return fail2(INFFT_EINVAL, "N (2m+1)^2 must be < 2^31 (N = %lld, m = %d)", (long long)N, m);
+    infft2d_plan_s* p = new infft2d_plan_s();
+    cudaGetDevice(&p->device);
+    p->M1 = M1; p->M2 = M2; p->Ms1 = Ms1; p->Ms2 = Ms2; p->N = N; p->P = Ms1 * Ms2;
+    p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau; p->log1 = l1; p->log2 = l2;
+    p->nnz_cap = N * (2 * (int64_t)m + 1) * (2 * (int64_t)m + 1);
+    Carver2 c;
+    layout2(p, c);
+    cudaError_t e = cudaMalloc(&p->arena, c.off);
+    if (e == cudaSuccess) {
+        c.base = (char*)p->arena;
+        c.off = 0;
+        layout2(p, c);
+        e = cudaMemset(p->counters, 0, C2_N * sizeof(int32_t));
+    }
+    if (e != cudaSuccess) {
+        if (p->arena) cudaFree(p->arena);
+        delete p;
+        return cuda_fail2(e, "allocate plan buffers");
+    }
+    *out = p;
+    return INFFT_OK;
+}
+
+infft_status infft2d_set_nodes(infft2d_plan_t p, const double* x, infft_stream_t stream) {
+    if (!p) return fail2(INFFT_EINVAL, "plan is NULL");
+    if (!x) return fail2(INFFT_EINVAL, "x is NULL");
+    DeviceGuard2 g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    p->nodes_set = 0;
+    p->precomputed = 0;
+    cudaError_t e;
+    if (on_device2(x)) {
+        e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+    } else {
+        for (int64_t j = 0; j < 2 * p->N; ++j)
+            if (!(std::isfinite(x[j]) && x[j] >= -0.5 && x[j] < 0.5))
+                return fail2(INFFT_EINVAL, "node coordinate x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
+        e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double2), cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) return cuda_fail2(e, "copy nodes");
+    if ((e = run_pattern2(p, s)) != cudaSuccess) return cuda_fail2(e, "pattern");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail2(e, "synchronize");
+    int32_t cnt[C2_N];
+    if ((e = cudaMemcpy(cnt, p->counters, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail2(e, "read counters");
+    if (cnt[C2_BAD] > 0) return fail2(INFFT_EINVAL, "%d nodes are not finite or not in [-1/2, 1/2)^2", cnt[C2_BAD]);
+    int32_t nnz = 0;
+    if ((e = cudaMemcpy(&nnz, p->col_off + p->P, sizeof nnz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail2(e, "read nnz");
+    p->nnz = nnz;
+    p->max_column = cnt[C2_MAX_COLUMN];
+    p->nodes_set = 1;
+    return INFFT_OK;
+}
+
+infft_status infft2d_precompute(infft2d_plan_t p, infft_stream_t stream) {
+    if (!p) return fail2(INFFT_EINVAL, "plan is NULL");
+    if (!p->nodes_set) return fail2(INFFT_ENOTREADY, "infft2d_precompute before infft2d_set_nodes");
+    DeviceGuard2 g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = run_precompute2(p, s);
+    if (e != cudaSuccess) return cuda_fail2(e, "precompute");
+    p->precomputed = 1;
+    return INFFT_OK;
+}
+
+infft_status infft2d_apply(infft2d_plan_t p, const float* f, float* fhat, infft_stream_t stream) {
+    return apply2_impl<float>(p, f, fhat, stream);
+}
+
+infft_status infft2d_apply_z(infft2d_plan_t p, const double* f, double* fhat, infft_stream_t stream) {
+    return apply2_impl<double>(p, f, fhat, stream);
+}
+
+infft_status infft2d_get_info(infft2d_plan_t p, infft2d_info* info) {
+    if (!p || !info) return fail2(INFFT_EINVAL, "plan and info must not be NULL");
+    DeviceGuard2 g(p->device);
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_fail2(e, "synchronize");
+    int32_t cnt[C2_N];
+    if ((e = cudaMemcpy(cnt, p->counters, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail2(e, "read counters");
+    std::memset(info, 0, sizeof *info);
+    info->M1 = p->M1; info->M2 = p->M2; info->M_sigma1 = p->Ms1; info->M_sigma2 = p->Ms2; info->N = p->N;
+    info->m = p->m; info->kernel = p->kernel; info->sigma = p->sigma; info->tau = p->tau;
+    info->nodes_set = p->nodes_set;
+    info->precomputed = p->precomputed;
+    info->bad_nodes = cnt[C2_BAD];
+    if (p->nodes_set) {
+        info->nnz = p->nnz;
+        info->max_column = cnt[C2_MAX_COLUMN];
+        info->empty_columns = cnt[C2_EMPTY];
+    }
+    if (p->precomputed) {
+        info->fallback_columns = cnt[C2_FALLBACK];
+        info->unsupported_columns = cnt[C2_UNSUPPORTED];
+        info->large_columns = cnt[C2_LIST0 + 3];
+        info->wide_columns = cnt[C2_WIDE];
+        std::string buf(p->P * sizeof(double), '\0');
+        if ((e = cudaMemcpy(&buf[0], p->J, p->P * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail2(e, "read objective");
+        const double* J = (const double*)buf.data();
+        double sum = 0.0;
+        for (int64_t i = 0; i < p->P; ++i) sum += J[i];
+        info->objective = sum;
+    }
+    return INFFT_OK;
+}
+
+infft_status infft2d_copy_plan_data(infft2d_plan_t p, int32_t* col_offset, int32_t* col_node, double* weights,
+                                    double* objective) {
+    if (!p) return fail2(INFFT_EINVAL, "plan is NULL");
+    if (!p->nodes_set) return fail2(INFFT_ENOTREADY, "no nodes set");
+    if ((weights || objective) && !p->precomputed) return fail2(INFFT_ENOTREADY, "not precomputed");
+    DeviceGuard2 g(p->device);
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e == cudaSuccess && col_offset) e = cudaMemcpy(col_offset, p->col_off, (p->P + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && col_node) e = cudaMemcpy(col_node, p->col_node, (size_t)p->nnz * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && weights) e = cudaMemcpy(weights, p->w64, (size_t)p->nnz * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && objective) e = cudaMemcpy(objective, p->J, p->P * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail2(e, "copy plan data");
+    return INFFT_OK;
+}
+
+infft_status infft2d_plan_destroy(infft2d_plan_t p) {
+    if (!p) return INFFT_OK;
+    {
+        DeviceGuard2 g(p->device);
+        cudaDeviceSynchronize();
+        if (p->scratch) cudaFree(p->scratch);
+        if (p->arena) cudaFree(p->arena);
+    }
+    delete p;
+    return INFFT_OK;
+}
+
+}  // extern "C"
