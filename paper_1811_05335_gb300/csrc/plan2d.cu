@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "plan.h"
 #include "fft_device.cuh"
@@ -49,7 +50,7 @@ struct infft2d_plan_s {
     int32_t* col_count = nullptr;  // P
     int32_t* col_off = nullptr;    // P + 1
     int32_t* col_node = nullptr;   // nnz_cap: caller index of each entry, column by column
-    int32_t* lists = nullptr;      // 4 P: columns of the three shared-memory tiers and the large tier
+    int32_t* lists = nullptr;      // 5 P: columns of the three shared-memory tiers and the two large tiers
     int32_t* order = nullptr;      // P: large columns, largest first
     int32_t* hist = nullptr;       // LARGE_NMAX + 2: size buckets, then offsets / cursors; ticket
     int32_t* counters = nullptr;   // C2_N
@@ -64,6 +65,12 @@ struct infft2d_plan_s {
     void* arena = nullptr;
     double* scratch = nullptr;     // large-column triangles (owned, grown on demand)
     size_t scratch_doubles = 0;
+    double* gscratch = nullptr;    // triangles of the columns factored by many CTAs (owned)
+    size_t gscratch_doubles = 0;
+    void* gdesc = nullptr;         // their descriptors (owned)
+    int gdesc_cap = 0;
+    int32_t* gprefix = nullptr;    // per panel step, the exclusive tile prefix over those columns (owned)
+    size_t gprefix_cap = 0;
     int nodes_set = 0, precomputed = 0;
     cudaStream_t last_stream = nullptr;
 };
@@ -72,13 +79,14 @@ namespace {
 
 enum {
     C2_BAD = 0, C2_FALLBACK = 1, C2_UNSUPPORTED = 2, C2_MAX_COLUMN = 3, C2_EMPTY = 4,
-    C2_LIST0 = 5,   // C2_LIST0 + t: length of the list of tier t (0..2 shared memory, 3 large)
-    C2_BIG_CELLS = 9, C2_WIDE = 10, C2_N = 11
+    C2_LIST0 = 5,   // C2_LIST0 + t: length of the list of tier t (0..2 shared memory, 3 one CTA, 4 many CTAs)
+    C2_BIG_CELLS = 10, C2_WIDE = 11, C2_N = 12
 };
 
 constexpr int TIER_NMAX[3] = {32, 64, 128};
-constexpr int SMALL_NMAX = 128;
 constexpr int LARGE_NMAX = 8192;
+constexpr int GIANT_N = 1024;     // columns above this are factored by many CTAs
+constexpr size_t GIANT_BUDGET = (size_t)16 << 30;   // bytes of giant triangles factored at once
 constexpr int PB = 16;             // panel width of the blocked solver
 constexpr int TB = 64;             // trailing-update tile
 constexpr int TBP = TB + 2;        // shared-memory row stride of the staged panel slices
@@ -334,7 +342,7 @@ __global__ void k2_route(const int32_t* __restrict__ col_off, int P, int32_t* __
         atomicAdd(&counters[C2_UNSUPPORTED], 1);
         return;
     }
-    const int t = n <= TIER_NMAX[0] ? 0 : n <= TIER_NMAX[1] ? 1 : n <= TIER_NMAX[2] ? 2 : 3;
+    const int t = n <= TIER_NMAX[0] ? 0 : n <= TIER_NMAX[1] ? 1 : n <= TIER_NMAX[2] ? 2 : n <= GIANT_N ? 3 : 4;
     lists[t * P + atomicAdd(&counters[C2_LIST0 + t], 1)] = p;
     if (t == 3) atomicAdd(&hist[LARGE_NMAX - n], 1);
 }
@@ -453,13 +461,184 @@ __global__ void __launch_bounds__(NMAX) k2_solve_small(const double2* __restrict
     }
 }
 
-// ---- precompute: large columns (blocked, global scratch) ----------------------
+// ---- precompute: large columns (blocked, triangle in global memory) -------------
+//
+// Building blocks shared by the one-CTA-per-column solver (columns of 129 .. GIANT_N
+// nodes) and the multi-CTA solver of the largest columns.  A is a packed lower
+// triangle (row i at i(i+1)/2, the diagonal holding the reciprocal pivot once
+// factored); r is the right-hand side, overwritten by y and then by the back solve.
 
-size_t large_smem(int nmax) {
-    return (size_t)nmax * (sizeof(double2) + sizeof(double)) + (size_t)2 * TBP * PB * sizeof(double) +
-           (size_t)PB * (PB + 1) * sizeof(double) + 2 * PB * sizeof(double);
+struct PanelShared {
+    double D[PB * (PB + 1)];   // diagonal block
+    double ypan[PB];           // y of the block's columns
+    double ysq;                // running |y|^2
+    int fail;
+};
+
+// One panel step at column kb (whole CTA, ends with __syncthreads): the PB x PB diagonal
+// block is factored by warp 0 in shared memory together with its part of y = L^{-1} r; the
+// rows below are solved row by row (L_ib = (A_ib - sum_{b'<b} L_ib' L_bb') / L_bb) and
+// take y out of r.  A failed pivot sets ps.fail (CTA-uniform after the return).
+INFFT_D void panel_step(double* __restrict__ A, double* __restrict__ r, int n, int kb, PanelShared& ps) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int w = min(PB, n - kb);
+    double* D = ps.D;
+    double* ypan = ps.ypan;
+    for (int e = tid; e < PB * PB; e += blockDim.x) {
+        const int a = e / PB, b = e % PB;
+        D[a * (PB + 1) + b] = (a < w && b <= a) ? A[trow(kb + a) + kb + b] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        bool bad = false;
+        for (int c = 0; c < w; ++c) {
+            const double akk = D[c * (PB + 1) + c];
+            if (!(akk > 0.0) || !isfinite(akk)) { bad = true; break; }   // warp-uniform
+            const double rp = rsqrt(akk);
+            __syncwarp();
+            if (lane > c && lane < w) D[lane * (PB + 1) + c] *= rp;
+            __syncwarp();
+            if (lane > c && lane < w) {
+                const double li = D[lane * (PB + 1) + c];
+                for (int b = c + 1; b <= lane; ++b)
+                    D[lane * (PB + 1) + b] = fma(-li, D[b * (PB + 1) + c], D[lane * (PB + 1) + b]);
+            }
+            __syncwarp();
+            if (lane == 0) D[c * (PB + 1) + c] = rp;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (bad) {
+                ps.fail = 1;
+            } else {
+                double ysq = ps.ysq;
+                for (int c = 0; c < w; ++c) {
+                    double v = r[kb + c];
+                    for (int b = 0; b < c; ++b) v = fma(-D[c * (PB + 1) + b], ypan[b], v);
+                    v *= D[c * (PB + 1) + c];
+                    ypan[c] = v;
+                    r[kb + c] = v;
+                    ysq = fma(v, v, ysq);
+                }
+                ps.ysq = ysq;
+            }
+        }
+    }
+    __syncthreads();
+    if (ps.fail) return;
+    for (int e = tid; e < PB * PB; e += blockDim.x) {
+        const int a = e / PB, b = e % PB;
+        if (a < w && b <= a) A[trow(kb + a) + kb + b] = D[a * (PB + 1) + b];
+    }
+    for (int i = kb + w + tid; i < n; i += blockDim.x) {
+        double v[PB];
+        double* row = A + trow(i) + kb;
+#pragma unroll
+        for (int b = 0; b < PB; ++b) v[b] = b < w ? row[b] : 0.0;
+        double acc = r[i];
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+            if (b < w) {
+                double s = v[b];
+#pragma unroll
+                for (int c = 0; c < b; ++c) s = fma(-v[c], D[b * (PB + 1) + c], s);
+                v[b] = s * D[b * (PB + 1) + b];
+                acc = fma(-v[b], ypan[b], acc);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < PB; ++b)
+            if (b < w) row[b] = v[b];
+        r[i] = acc;
+    }
+    __syncthreads();
 }
 
+// number of TB x TB lower-triangular tiles of the trailing matrix after the panel at kb
+INFFT_HD int trailing_tiles(int n, int kb) {
+    const int T = n - kb - PB;
+    if (T <= 0) return 0;
+    const int nt = (T + TB - 1) / TB;
+    return nt * (nt + 1) / 2;
+}
+
+// tile index -> (ti, tj), tj <= ti, row-major over the lower triangle of tiles
+INFFT_D void tile_coords(int tile, int& ti, int& tj) {
+    ti = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+    while (trow(ti + 1) <= tile) ++ti;
+    while (trow(ti) > tile) --ti;
+    tj = tile - trow(ti);
+}
+
+// A_ij -= sum_c L_ic L_jc over the panel columns kb .. kb + PB - 1, for the tile (ti, tj) of
+// the rows / columns from kb + PB (whole CTA of 256 threads, 4 x 4 entries each; the panel
+// slices of the tile's rows and columns are staged in Li, Lj with row stride TBP)
+INFFT_D void trailing_tile(double* __restrict__ A, int n, int kb, int ti, int tj, double* Li, double* Lj) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int base = kb + PB;
+    const int i0 = base + ti * TB, j0 = base + tj * TB;
+    for (int e = tid; e < TB * PB; e += LARGE_THREADS) {
+        const int rr = e / PB, c = e % PB;      // consecutive threads: one row's panel entries
+        const int ii = i0 + rr, jj = j0 + rr;
+        Li[c * TBP + rr] = ii < n ? A[trow(ii) + kb + c] : 0.0;
+        Lj[c * TBP + rr] = jj < n ? A[trow(jj) + kb + c] : 0.0;
+    }
+    __syncthreads();
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll 4
+    for (int c = 0; c < PB; ++c) {
+        const double2 la = *(const double2*)&Li[c * TBP + ty * 4];
+        const double2 lb = *(const double2*)&Li[c * TBP + ty * 4 + 2];
+        const double2 ra = *(const double2*)&Lj[c * TBP + tx * 4];
+        const double2 rb = *(const double2*)&Lj[c * TBP + tx * 4 + 2];
+        const double li[4] = {la.x, la.y, lb.x, lb.y}, lj[4] = {ra.x, ra.y, rb.x, rb.y};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(li[a], lj[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + ty * 4 + a;
+        if (i >= n) break;
+        double* row = A + trow(i);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = j0 + tx * 4 + b;
+            if (j <= i) row[j] -= acc[a][b];
+        }
+    }
+    __syncthreads();
+}
+
+// L^T b = y (whole CTA, one row of L per step: row k removes b_k from r_0 .. r_{k-1}); b is
+// written to w64 / w32; thread 0 returns sum b^2 and sum |b|
+INFFT_D void back_solve(const double* __restrict__ A, double* __restrict__ r, int n, double* __restrict__ w64,
+                        float* __restrict__ w32, double& bsq, double& babs) {
+    const int tid = threadIdx.x;
+    bsq = 0.0;
+    babs = 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+        const double* row = A + trow(k);
+        const double bk = r[k] * row[k];
+        for (int i = tid; i < k; i += blockDim.x) r[i] = fma(-row[i], bk, r[i]);
+        if (tid == 0) {
+            w64[k] = bk;
+            w32[k] = (float)bk;
+            bsq = fma(bk, bk, bsq);
+            babs += fabs(bk);
+        }
+        __syncthreads();
+    }
+}
+
+size_t large_smem(int nmax) { return (size_t)nmax * (sizeof(double2) + sizeof(double)); }
+
+// one CTA per column of 129 .. GIANT_N nodes, largest first (atomic ticket)
 __global__ void __launch_bounds__(LARGE_THREADS, 1)
 k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_off, const int32_t* __restrict__ col_node,
                const int32_t* __restrict__ order, int Ms1, int Ms2, K2 kp, double mu0, double* __restrict__ scratch,
@@ -467,13 +646,10 @@ k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_of
                double* __restrict__ J, uint8_t* __restrict__ wide, int32_t* __restrict__ counters, int nmax) {
     extern __shared__ __align__(16) double sm2[];
     double2* xl = (double2*)sm2;                 // nmax nodes of the column
-    double* r = (double*)(xl + nmax);            // nmax: right-hand side, then y, then the back solve
-    double* Li = r + nmax;                       // PB x TBP: panel slice of a tile's rows ([c][row])
-    double* Lj = Li + PB * TBP;                  // PB x TBP: panel slice of a tile's columns
-    double* D = Lj + PB * TBP;                   // PB x (PB + 1): diagonal block
-    double* ypan = D + PB * (PB + 1);            // PB: y of the panel
-    __shared__ int s_job, s_fail;
-    __shared__ double s_ysq;
+    double* r = (double*)(xl + nmax);            // nmax
+    __shared__ __align__(16) double Li[PB * TBP], Lj[PB * TBP];
+    __shared__ PanelShared ps;
+    __shared__ int s_job;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = LARGE_THREADS / 32;
     double* A = scratch + (size_t)blockIdx.x * slot_doubles;
@@ -499,132 +675,20 @@ k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_of
                                               : re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
             }
             for (int i = tid; i < n; i += LARGE_THREADS) r[i] = re_kappa2(tdiff(t1, xl[i].x), tdiff(t2, xl[i].y), kp);
-            if (tid == 0) { s_fail = 0; s_ysq = 0.0; }
+            if (tid == 0) { ps.fail = 0; ps.ysq = 0.0; }
             __syncthreads();
             for (int kb = 0; kb < n; kb += PB) {
-                const int w = min(PB, n - kb);
-                // (1) diagonal block: factor in shared memory (warp 0, one lane per row), then y
-                for (int e = tid; e < PB * PB; e += LARGE_THREADS) {
-                    const int a = e / PB, b = e % PB;
-                    D[a * (PB + 1) + b] = (a < w && b <= a) ? A[trow(kb + a) + kb + b] : 0.0;
-                }
-                __syncthreads();
-                if (warp == 0) {
-                    bool bad = false;
-                    for (int c = 0; c < w; ++c) {
-                        const double akk = D[c * (PB + 1) + c];
-                        if (!(akk > 0.0) || !isfinite(akk)) { bad = true; break; }
-                        const double rp = rsqrt(akk);
-                        __syncwarp();
-                        if (lane > c && lane < w) D[lane * (PB + 1) + c] *= rp;
-                        __syncwarp();
-                        if (lane > c && lane < w) {
-                            const double li = D[lane * (PB + 1) + c];
-                            for (int b = c + 1; b <= lane; ++b)
-                                D[lane * (PB + 1) + b] = fma(-li, D[b * (PB + 1) + c], D[lane * (PB + 1) + b]);
-                        }
-                        __syncwarp();
-                        if (lane == 0) D[c * (PB + 1) + c] = rp;
-                        __syncwarp();
-                    }
-                    if (lane == 0) {
-                        if (bad) {
-                            s_fail = 1;
-                        } else {
-                            double ysq = s_ysq;
-                            for (int c = 0; c < w; ++c) {
-                                double v = r[kb + c];
-                                for (int b = 0; b < c; ++b) v = fma(-D[c * (PB + 1) + b], ypan[b], v);
-                                v *= D[c * (PB + 1) + c];
-                                ypan[c] = v;
-                                r[kb + c] = v;
-                                ysq = fma(v, v, ysq);
-                            }
-                            s_ysq = ysq;
-                        }
-                    }
-                }
-                __syncthreads();
-                if (s_fail) break;                      // CTA-uniform
-                for (int e = tid; e < PB * PB; e += LARGE_THREADS) {
-                    const int a = e / PB, b = e % PB;
-                    if (a < w && b <= a) A[trow(kb + a) + kb + b] = D[a * (PB + 1) + b];
-                }
-                // (2) rows below the block: L_ib = (A_ib - sum_{b'<b} L_ib' L_bb') rp_b, and r_i -= L_i. y
-                for (int i = kb + w + tid; i < n; i += LARGE_THREADS) {
-                    double v[PB];
-                    const double* row = A + trow(i) + kb;
-#pragma unroll
-                    for (int b = 0; b < PB; ++b) v[b] = b < w ? row[b] : 0.0;
-                    double acc = r[i];
-#pragma unroll
-                    for (int b = 0; b < PB; ++b) {
-                        if (b < w) {
-                            double s = v[b];
-#pragma unroll
-                            for (int c = 0; c < b; ++c) s = fma(-v[c], D[b * (PB + 1) + c], s);
-                            v[b] = s * D[b * (PB + 1) + b];
-                            acc = fma(-v[b], ypan[b], acc);
-                        }
-                    }
-                    double* wrow = A + trow(i) + kb;
-#pragma unroll
-                    for (int b = 0; b < PB; ++b)
-                        if (b < w) wrow[b] = v[b];
-                    r[i] = acc;
-                }
-                __syncthreads();
-                // (3) trailing update of rows / columns [kb + w, n), lower-triangular tiles
-                const int base = kb + w, T = n - base;
-                const int nt = (T + TB - 1) / TB;
-                const int ntiles = nt * (nt + 1) / 2;
-                const int tx = tid & 15, ty = tid >> 4;
-                for (int tile = 0; tile < ntiles; ++tile) {
-                    int ti = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
-                    while (trow(ti + 1) <= tile) ++ti;
-                    while (trow(ti) > tile) --ti;
-                    const int tj = tile - trow(ti);
-                    const int i0 = base + ti * TB, j0 = base + tj * TB;
-                    for (int e = tid; e < TB * PB; e += LARGE_THREADS) {
-                        const int rr = e / PB, c = e % PB;      // consecutive threads: one row's panel entries
-                        const int ii = i0 + rr, jj = j0 + rr;
-                        Li[c * TBP + rr] = (ii < n && c < w) ? A[trow(ii) + kb + c] : 0.0;
-                        Lj[c * TBP + rr] = (jj < n && c < w) ? A[trow(jj) + kb + c] : 0.0;
-                    }
-                    __syncthreads();
-                    double acc[4][4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-#pragma unroll 4
-                    for (int c = 0; c < PB; ++c) {
-                        const double2 la = *(const double2*)&Li[c * TBP + ty * 4];
-                        const double2 lb = *(const double2*)&Li[c * TBP + ty * 4 + 2];
-                        const double2 ra = *(const double2*)&Lj[c * TBP + tx * 4];
-                        const double2 rb = *(const double2*)&Lj[c * TBP + tx * 4 + 2];
-                        const double li[4] = {la.x, la.y, lb.x, lb.y}, lj[4] = {ra.x, ra.y, rb.x, rb.y};
-#pragma unroll
-                        for (int a = 0; a < 4; ++a)
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) acc[a][b] = fma(li[a], lj[b], acc[a][b]);
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int i = i0 + ty * 4 + a;
-                        if (i >= n) break;
-                        double* row = A + trow(i);
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const int j = j0 + tx * 4 + b;
-                            if (j <= i) row[j] -= acc[a][b];
-                        }
-                    }
-                    __syncthreads();
+                panel_step(A, r, n, kb, ps);
+                if (ps.fail) break;
+                const int nt = trailing_tiles(n, kb);
+                for (int tile = 0; tile < nt; ++tile) {
+                    int ti, tj;
+                    tile_coords(tile, ti, tj);
+                    trailing_tile(A, n, kb, ti, tj, Li, Lj);
                 }
             }
             __syncthreads();
-            ok = !s_fail;
+            ok = !ps.fail;
             if (!ok) mu *= 1e3;
             __syncthreads();
         }
@@ -635,28 +699,128 @@ k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_of
             continue;
         }
         if (tid == 0 && mu != mu0) atomicAdd(&counters[C2_FALLBACK], 1);
-        // back solve L^T b = y, one row of L per step (row k removes b_k from r_0 .. r_{k-1})
-        double bsq = 0.0, babs = 0.0;
-        for (int k = n - 1; k >= 0; --k) {
-            const double* row = A + trow(k);
-            const double bk = r[k] * row[k];
-            for (int i = tid; i < k; i += LARGE_THREADS) r[i] = fma(-row[i], bk, r[i]);
-            if (tid == 0) {
-                w64[off + k] = bk;
-                w32[off + k] = (float)bk;
-                bsq = fma(bk, bk, bsq);
-                babs += fabs(bk);
-            }
-            __syncthreads();
-        }
+        double bsq, babs;
+        back_solve(A, r, n, w64 + off, w32 + off, bsq, babs);
         if (tid == 0) {
-            J[p] = 1.0 - s_ysq - mu * bsq;
+            J[p] = 1.0 - ps.ysq - mu * bsq;
             const bool wd = babs > WIDE_COLUMN_L1;
             wide[p] = wd;
             if (wd) atomicAdd(&counters[C2_WIDE], 1);
         }
         __syncthreads();
     }
+}
+
+// ---- precompute: the largest columns, each spread over many CTAs -----------------
+//
+// Columns above GIANT_N nodes carry most of the Cholesky work (n^3/3) and would leave
+// one SM busy long after the others.  They are factored together, one panel step per
+// pair of launches: k2g_panel (one CTA per column) and k2g_update, whose grid walks the
+// trailing tiles of all these columns as one flat index space (the per-step tile
+// prefix over the columns is computed on the host from the column sizes).
+
+struct GiantCol {
+    int p, n, fail, pad;
+    long long a_off;       // packed triangle in the giant scratch
+    long long v_off;       // r (n doubles), then the nodes (n double2)
+    double ysq;
+};
+
+__global__ void __launch_bounds__(LARGE_THREADS) k2g_stage(const double2* __restrict__ x,
+                                                           const int32_t* __restrict__ col_off,
+                                                           const int32_t* __restrict__ col_node,
+                                                           GiantCol* __restrict__ gs, double* __restrict__ gbase,
+                                                           int Ms1, int Ms2, K2 kp) {
+    GiantCol& g = gs[blockIdx.y];
+    const int n = g.n, off = col_off[g.p];
+    double* r = gbase + g.v_off;
+    double2* xl = (double2*)(r + n + (n & 1));
+    const double t1 = (double)(g.p / Ms2 - Ms1 / 2) / (double)Ms1;
+    const double t2 = (double)(g.p % Ms2 - Ms2 / 2) / (double)Ms2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 v = x[col_node[off + i]];
+        xl[i] = v;
+        r[i] = re_kappa2(tdiff(t1, v.x), tdiff(t2, v.y), kp);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { g.fail = 0; g.ysq = 0.0; }
+}
+
+__global__ void __launch_bounds__(LARGE_THREADS) k2g_fill(GiantCol* __restrict__ gs, double* __restrict__ gbase,
+                                                          K2 kp, double mu) {
+    const GiantCol& g = gs[blockIdx.y];
+    const int n = g.n;
+    double* A = gbase + g.a_off;
+    const double* r = gbase + g.v_off;
+    const double2* xl = (const double2*)(r + n + (n & 1));
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * (LARGE_THREADS / 32) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (LARGE_THREADS / 32);
+    for (int i = wid; i < n; i += nw) {
+        const double2 xi = xl[i];
+        for (int j = lane; j <= i; j += 32)
+            A[trow(i) + j] = (j == i) ? kp.diag + mu : re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
+    }
+}
+
+__global__ void __launch_bounds__(LARGE_THREADS) k2g_panel(GiantCol* __restrict__ gs, double* __restrict__ gbase,
+                                                           int kb) {
+    __shared__ PanelShared ps;
+    GiantCol& g = gs[blockIdx.x];
+    if (g.fail || kb >= g.n) return;                   // CTA-uniform
+    if (threadIdx.x == 0) { ps.fail = 0; ps.ysq = g.ysq; }
+    __syncthreads();
+    panel_step(gbase + g.a_off, gbase + g.v_off, g.n, kb, ps);
+    if (threadIdx.x == 0) { g.fail = ps.fail; g.ysq = ps.ysq; }
+}
+
+// prefix: G + 1 exclusive tile offsets of this step's trailing updates
+__global__ void __launch_bounds__(LARGE_THREADS) k2g_update(const GiantCol* __restrict__ gs,
+                                                            double* __restrict__ gbase, int kb,
+                                                            const int32_t* __restrict__ prefix, int G) {
+    __shared__ __align__(16) double Li[PB * TBP], Lj[PB * TBP];
+    const int total = prefix[G];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = G - 1;                            // last g with prefix[g] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const GiantCol& g = gs[lo];
+        if (g.fail) continue;                              // CTA-uniform
+        int ti, tj;
+        tile_coords(t - prefix[lo], ti, tj);
+        trailing_tile(gbase + g.a_off, g.n, kb, ti, tj, Li, Lj);
+    }
+}
+
+__global__ void __launch_bounds__(LARGE_THREADS) k2g_back(const GiantCol* __restrict__ gs, double* __restrict__ gbase,
+                                                          const int32_t* __restrict__ col_off, double mu, int retried,
+                                                          double* __restrict__ w64, float* __restrict__ w32,
+                                                          double* __restrict__ J, uint8_t* __restrict__ wide,
+                                                          int32_t* __restrict__ counters) {
+    const GiantCol& g = gs[blockIdx.x];
+    if (g.fail) return;                                    // retried by the host with a larger mu
+    const int off = col_off[g.p];
+    double bsq, babs;
+    back_solve(gbase + g.a_off, gbase + g.v_off, g.n, w64 + off, w32 + off, bsq, babs);
+    if (threadIdx.x == 0) {
+        J[g.p] = 1.0 - g.ysq - mu * bsq;
+        const bool wd = babs > WIDE_COLUMN_L1;
+        wide[g.p] = wd;
+        if (wd) atomicAdd(&counters[C2_WIDE], 1);
+        if (retried) atomicAdd(&counters[C2_FALLBACK], 1);
+    }
+}
+
+// columns that failed every attempt: b_l = 0, J_l = 1, counted
+__global__ void k2g_give_up(const GiantCol* __restrict__ gs, const int32_t* __restrict__ col_off,
+                            double* __restrict__ w64, float* __restrict__ w32, double* __restrict__ J,
+                            int32_t* __restrict__ counters) {
+    const GiantCol& g = gs[blockIdx.x];
+    if (!g.fail) return;
+    const int off = col_off[g.p];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
+    if (threadIdx.x == 0) { J[g.p] = 1.0; atomicAdd(&counters[C2_FALLBACK], 1); }
 }
 
 // ---- apply ---------------------------------------------------------------------
@@ -781,7 +945,7 @@ void layout2(infft2d_plan_s* p, Carver2& c) {
     c.take(p->x, N); c.take(p->xs, N); c.take(p->node_cell, N); c.take(p->perm, N);
     c.take(p->cell_start, P + 1); c.take(p->cursor, P); c.take(p->big_cells, P);
     c.take(p->col_count, P); c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
-    c.take(p->lists, 4 * P); c.take(p->order, P); c.take(p->hist, LARGE_NMAX + 2);
+    c.take(p->lists, 5 * P); c.take(p->order, P); c.take(p->hist, LARGE_NMAX + 2);
     c.take(p->counters, C2_N);
     c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
     double2 *grid, *work, *si, *so;
@@ -814,13 +978,125 @@ cudaError_t run_pattern2(infft2d_plan_s* p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The columns above GIANT_N nodes (list 4): groups whose triangles fit GIANT_BUDGET are
+// factored together, one panel step per (k2g_panel, k2g_update) pair of launches; a group's
+// columns whose Cholesky failed are retried with mu raised 1000-fold, twice.
+cudaError_t run_giants(infft2d_plan_s* p, int G, const K2& kp, double mu, int sms, cudaStream_t s) {
+    cudaError_t e;
+    std::vector<int32_t> list(G), off(p->P + 1);
+    if ((e = cudaMemcpy(list.data(), p->lists + 4 * p->P, G * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(off.data(), p->col_off, (p->P + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    std::sort(list.begin(), list.end());
+    std::vector<std::vector<GiantCol>> groups(1);
+    size_t used = 0, need = 0;
+    for (int q : list) {
+        GiantCol g = {};
+        g.p = q;
+        g.n = off[q + 1] - off[q];
+        const size_t tri = ((size_t)g.n * (g.n + 1) / 2 + 1) & ~(size_t)1;
+        const size_t vec = ((size_t)3 * g.n + 3) & ~(size_t)1;   // even: the next triangle and node pairs stay 16-byte aligned
+        if (!groups.back().empty() && (used + tri + vec) * sizeof(double) > GIANT_BUDGET) {
+            groups.emplace_back();
+            used = 0;
+        }
+        g.a_off = (long long)used;
+        g.v_off = (long long)(used + tri);
+        used += tri + vec;
+        need = std::max(need, used);
+        groups.back().push_back(g);
+    }
+    if (p->gscratch_doubles < need) {
+        if (p->gscratch) cudaFree(p->gscratch);
+        p->gscratch = nullptr;
+        p->gscratch_doubles = 0;
+        if ((e = cudaMalloc(&p->gscratch, need * sizeof(double))) != cudaSuccess) return e;
+        p->gscratch_doubles = need;
+    }
+    size_t gmax = 0;
+    for (auto& grp : groups) gmax = std::max(gmax, grp.size());
+    if (p->gdesc_cap < (int)gmax) {
+        if (p->gdesc) cudaFree(p->gdesc);
+        p->gdesc = nullptr;
+        p->gdesc_cap = 0;
+        if ((e = cudaMalloc(&p->gdesc, gmax * sizeof(GiantCol))) != cudaSuccess) return e;
+        p->gdesc_cap = (int)gmax;
+    }
+    GiantCol* gd = (GiantCol*)p->gdesc;
+    for (auto grp : groups) {
+        for (int attempt = 0; attempt < 3 && !grp.empty(); ++attempt) {
+            const int Gg = (int)grp.size();
+            const double mu_a = mu * std::pow(1e3, attempt);
+            int nmax = 0;
+            for (auto& g : grp) nmax = std::max(nmax, g.n);
+            const int steps = (nmax + PB - 1) / PB;
+            std::vector<int32_t> prefix((size_t)steps * (Gg + 1));
+            for (int st = 0; st < steps; ++st) {
+                int32_t run = 0;
+                for (int i = 0; i < Gg; ++i) {
+                    prefix[(size_t)st * (Gg + 1) + i] = run;
+                    run += trailing_tiles(grp[i].n, st * PB);
+                }
+                prefix[(size_t)st * (Gg + 1) + Gg] = run;
+            }
+            if (p->gprefix_cap < prefix.size()) {
+                if (p->gprefix) cudaFree(p->gprefix);
+                p->gprefix = nullptr;
+                p->gprefix_cap = 0;
+                if ((e = cudaMalloc(&p->gprefix, prefix.size() * sizeof(int32_t))) != cudaSuccess) return e;
+                p->gprefix_cap = prefix.size();
+            }
+            if ((e = cudaMemcpy(gd, grp.data(), Gg * sizeof(GiantCol), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return e;
+            if ((e = cudaMemcpy(p->gprefix, prefix.data(), prefix.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return e;
+            const int xs = std::max(1, std::min((nmax + 255) / 256, (4 * sms + Gg - 1) / Gg));
+            k2g_stage<<<dim3(xs, Gg), LARGE_THREADS, 0, s>>>(p->x, p->col_off, p->col_node, gd, p->gscratch,
+                                                            (int)p->Ms1, (int)p->Ms2, kp);
+            const int xf = std::max(1, std::min((nmax + 7) / 8, (8 * sms + Gg - 1) / Gg));
+            k2g_fill<<<dim3(xf, Gg), LARGE_THREADS, 0, s>>>(gd, p->gscratch, kp, mu_a);
+            int launches = 2;
+            for (int st = 0; st < steps; ++st) {
+                k2g_panel<<<Gg, LARGE_THREADS, 0, s>>>(gd, p->gscratch, st * PB);
+                const int tiles = prefix[(size_t)st * (Gg + 1) + Gg];
+                if (tiles > 0)
+                    k2g_update<<<std::min(tiles, 4 * sms), LARGE_THREADS, 0, s>>>(
+                        gd, p->gscratch, st * PB, p->gprefix + (size_t)st * (Gg + 1), Gg);
+                launches += 1 + (tiles > 0);
+            }
+            k2g_back<<<Gg, LARGE_THREADS, 0, s>>>(gd, p->gscratch, p->col_off, mu_a, attempt > 0, p->w64, p->w32,
+                                                  p->J, p->wide, p->counters);
+            count_launches(launches + 1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            std::vector<GiantCol> back(Gg);
+            if ((e = cudaMemcpyAsync(back.data(), gd, Gg * sizeof(GiantCol), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            std::vector<GiantCol> failed;
+            for (auto& g : back)
+                if (g.fail) failed.push_back(g);
+            if (!failed.empty() && attempt == 2) {
+                if ((e = cudaMemcpy(gd, failed.data(), failed.size() * sizeof(GiantCol), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                    return e;
+                k2g_give_up<<<(int)failed.size(), 256, 0, s>>>(gd, p->col_off, p->w64, p->w32, p->J, p->counters);
+                count_launches(1);
+            }
+            grp = failed;
+        }
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     const int P = (int)p->P, Ms1 = (int)p->Ms1, Ms2 = (int)p->Ms2;
     const K2 kp = kernel_params(p);
     const double mu = p->tau * kp.diag;
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->counters + C2_FALLBACK, 0, 2 * sizeof(int32_t), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(p->counters + C2_LIST0, 0, 4 * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->counters + C2_LIST0, 0, 5 * sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p->counters + C2_WIDE, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p->hist, 0, (LARGE_NMAX + 2) * sizeof(int32_t), s)) != cudaSuccess) return e;
     int sms = 0;
@@ -829,6 +1105,11 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     k2_route<<<(P + 255) / 256, 256, 0, s>>>(p->col_off, P, p->lists, p->w64, p->w32, p->J, p->wide, p->hist,
                                              p->counters);
     count_launches(1);
+    // the list lengths and the columns for the multi-CTA solver decide the launches below
+    int32_t cnt[C2_N];
+    if ((e = cudaMemcpyAsync(cnt, p->counters, sizeof cnt, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    const int G = cnt[C2_LIST0 + 4];
     // shared-memory tiers
     auto t0 = k2_solve_small<32>;
     auto t1 = k2_solve_small<64>;
@@ -841,38 +1122,43 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, t0, 32, s0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, t1, 64, s1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, t2, 128, s2);
-    t0<<<std::max(o0, 1) * sms, 32, s0, s>>>(p->x, p->col_off, p->col_node, p->lists, 0, Ms1, Ms2, kp, mu, p->w64,
-                                              p->w32, p->J, p->wide, p->counters);
-    t1<<<std::max(o1, 1) * sms, 64, s1, s>>>(p->x, p->col_off, p->col_node, p->lists + P, 1, Ms1, Ms2, kp, mu,
-                                              p->w64, p->w32, p->J, p->wide, p->counters);
-    t2<<<std::max(o2, 1) * sms, 128, s2, s>>>(p->x, p->col_off, p->col_node, p->lists + 2 * P, 2, Ms1, Ms2, kp, mu,
-                                               p->w64, p->w32, p->J, p->wide, p->counters);
+    if (cnt[C2_LIST0 + 0])
+        t0<<<std::max(o0, 1) * sms, 32, s0, s>>>(p->x, p->col_off, p->col_node, p->lists, 0, Ms1, Ms2, kp, mu,
+                                                  p->w64, p->w32, p->J, p->wide, p->counters);
+    if (cnt[C2_LIST0 + 1])
+        t1<<<std::max(o1, 1) * sms, 64, s1, s>>>(p->x, p->col_off, p->col_node, p->lists + P, 1, Ms1, Ms2, kp, mu,
+                                                  p->w64, p->w32, p->J, p->wide, p->counters);
+    if (cnt[C2_LIST0 + 2])
+        t2<<<std::max(o2, 1) * sms, 128, s2, s>>>(p->x, p->col_off, p->col_node, p->lists + 2 * P, 2, Ms1, Ms2, kp,
+                                                   mu, p->w64, p->w32, p->J, p->wide, p->counters);
     count_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // large tier
-    // the shared-memory layout of the large solver keeps 16-byte alignment with an even nmax
-    const int nmax = (std::min(p->max_column, LARGE_NMAX) + 1) & ~1;
-    if (nmax <= SMALL_NMAX) return cudaSuccess;
-    const size_t slot = (size_t)nmax * (nmax + 1) / 2;
-    // as many CTAs as SMs, fewer when the triangles would exceed 16 GiB
-    const int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)sms, ((size_t)16 << 30) / (slot * 8)));
-    if (p->scratch_doubles < slot * slots) {
-        if (p->scratch) cudaFree(p->scratch);
-        p->scratch = nullptr;
-        p->scratch_doubles = 0;
-        if ((e = cudaMalloc(&p->scratch, slot * slots * sizeof(double))) != cudaSuccess) return e;
-        p->scratch_doubles = slot * slots;
+    // one CTA per column of 129 .. GIANT_N nodes
+    if (cnt[C2_LIST0 + 3]) {
+        // the shared-memory layout keeps 16-byte alignment with an even nmax
+        const int nmax = (std::min(p->max_column, GIANT_N) + 1) & ~1;
+        const size_t slot = (size_t)nmax * (nmax + 1) / 2;
+        const int slots = std::max(1, std::min(sms, cnt[C2_LIST0 + 3]));
+        if (p->scratch_doubles < slot * slots) {
+            if (p->scratch) cudaFree(p->scratch);
+            p->scratch = nullptr;
+            p->scratch_doubles = 0;
+            if ((e = cudaMalloc(&p->scratch, slot * slots * sizeof(double))) != cudaSuccess) return e;
+            p->scratch_doubles = slot * slots;
+        }
+        k2_scan<<<1, 1024, 0, s>>>(p->hist, LARGE_NMAX + 1);
+        k2_order_large<<<4 * sms, 256, 0, s>>>(p->col_off, p->lists + 3 * P, P, p->hist, p->order, p->counters);
+        if ((e = cudaMemsetAsync(p->hist + LARGE_NMAX + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+        const size_t sm = large_smem(nmax);
+        if ((e = smem_attr(k2_solve_large, sm)) != cudaSuccess) return e;
+        k2_solve_large<<<slots, LARGE_THREADS, sm, s>>>(p->x, p->col_off, p->col_node, p->order, Ms1, Ms2, kp, mu,
+                                                        p->scratch, slot, p->hist + LARGE_NMAX + 1, p->w64, p->w32,
+                                                        p->J, p->wide, p->counters, nmax);
+        count_launches(3);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k2_scan<<<1, 1024, 0, s>>>(p->hist, LARGE_NMAX + 1);
-    k2_order_large<<<4 * sms, 256, 0, s>>>(p->col_off, p->lists + 3 * P, P, p->hist, p->order, p->counters);
-    if ((e = cudaMemsetAsync(p->hist + LARGE_NMAX + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-    const size_t sm = large_smem(nmax);
-    if ((e = smem_attr(k2_solve_large, sm)) != cudaSuccess) return e;
-    k2_solve_large<<<slots, LARGE_THREADS, sm, s>>>(p->x, p->col_off, p->col_node, p->order, Ms1, Ms2, kp, mu,
-                                                    p->scratch, slot, p->hist + LARGE_NMAX + 1, p->w64, p->w32, p->J,
-                                                    p->wide, p->counters, nmax);
-    count_launches(3);
-    return cudaGetLastError();
+    if (G == 0) return cudaSuccess;
+    return run_giants(p, G, kp, mu, sms, s);
 }
 
 template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
@@ -1054,7 +1340,7 @@ infft_status infft2d_get_info(infft2d_plan_t p, infft2d_info* info) {
     if (p->precomputed) {
         info->fallback_columns = cnt[C2_FALLBACK];
         info->unsupported_columns = cnt[C2_UNSUPPORTED];
-        info->large_columns = cnt[C2_LIST0 + 3];
+        info->large_columns = cnt[C2_LIST0 + 3] + cnt[C2_LIST0 + 4];
         info->wide_columns = cnt[C2_WIDE];
         std::string buf(p->P * sizeof(double), '\0');
         if ((e = cudaMemcpy(&buf[0], p->J, p->P * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
@@ -1088,6 +1374,9 @@ infft_status infft2d_plan_destroy(infft2d_plan_t p) {
         DeviceGuard2 g(p->device);
         cudaDeviceSynchronize();
         if (p->scratch) cudaFree(p->scratch);
+        if (p->gscratch) cudaFree(p->gscratch);
+        if (p->gdesc) cudaFree(p->gdesc);
+        if (p->gprefix) cudaFree(p->gprefix);
         if (p->arena) cudaFree(p->arena);
     }
     delete p;

@@ -11,7 +11,8 @@ Tolerances, as for the 1-D plan:
 The cases mix node families (radial spokes with a cluster at the origin, i.i.d.
 uniform, a jittered tensor grid, nodes on grid lines and across the seam, duplicates),
 both kernels, m = 1, 2 and 4, and column sizes across every solver tier (up to 32,
-64 and 128 nodes in shared memory, the blocked solver above).  The full radial
+64 and 128 nodes in shared memory, one CTA per column up to 1024, many CTAs per column
+above).  The full radial
 workload (512 x 512 nodes, M = 256 x 256, m = 4) is checked on sampled columns,
 including the 4726-node column at the origin, and on single-node data whose exact
 fhat the oracle evaluates from the columns that node enters.
@@ -50,6 +51,7 @@ def cases():
         "edge": (edge_nodes(), 8, 8, 2.0, 2, "full"),
         "radial_m4": (radial(406, 64, 64, 1e-4), 32, 32, 2.0, 4, "full"),
         "radial_sym_m4": (radial(407, 48, 48, 1e-4), 32, 16, 2.0, 3, "sym"),
+        "radial_giant": (radial(408, 96, 64, 1e-4), 16, 16, 2.0, 3, "full"),
     }
 
 
@@ -136,10 +138,11 @@ def test_bopt_attains_regularised_minimum(name):
 
 
 def test_large_tier_is_exercised():
-    """The radial cases put columns above 128 nodes (the blocked solver) and columns
-    spanning several panels and trailing tiles."""
-    sizes = [np.diff(solved(n)[6].ptr).max() for n in ("radial_small", "radial_m4", "radial_sym_m4")]
-    assert sizes[0] > 128 and sizes[1] > 2 * 64 + 16 and sizes[2] > 128
+    """The radial cases put columns above 128 nodes (one CTA each), columns spanning
+    several panels and trailing tiles, and columns above 1024 nodes (many CTAs each)."""
+    sizes = [np.diff(solved(n)[6].ptr).max() for n in ("radial_small", "radial_m4", "radial_sym_m4", "radial_giant")]
+    assert sizes[0] > 128 and sizes[1] > 2 * 64 + 16 and sizes[2] > 128 and sizes[3] > 1024
+    assert (np.diff(solved("radial_giant")[6].ptr) > 1024).sum() >= 20
 
 
 @pytest.mark.parametrize("name", list(cases()))
