@@ -354,8 +354,9 @@ infft_status infft2d_set_nodes(infft2d_plan_t plan, const double* x, infft_strea
 
 /* Fills B_opt in fp64 (Cholesky of Re G_l + mu I, mu = tau Re kappa(0); a column whose
  * factorisation fails is retried with mu raised 1000-fold, twice, then set to 0 and
- * counted).  Allocates the large-column scratch on first use and synchronises
- * `stream` once before its launches. */
+ * counted).  Synchronous: it reads the column-size lists back to plan its launches and
+ * returns when B_opt is complete; the scratch of the columns above 128 nodes (about
+ * 4 n^2 bytes per column being factored) is allocated for the call and released. */
 infft_status infft2d_precompute(infft2d_plan_t plan, infft_stream_t stream);
 
 /* fhat = D^* F^* B_opt^* f: spreading onto the grid, the 2-D FFT pruned to the

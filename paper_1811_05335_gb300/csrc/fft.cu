@@ -382,6 +382,94 @@ cudaError_t fft_adjoint_r8(const float2* g, float2* work, float2* fhat, int logM
     return e;
 }
 
+// ---- the fp32 2-D transform of the tensor-product plan ------------------------
+//
+// fhat[k1 + M1/2][k2 + M2/2] = (-1)^(k1+k2) d_k sum_{a1, a2} g[a1][a2] e^{-2 pi i (k1 a1/Ms1 + k2 a2/Ms2)}
+// (grid index a_t = l_t + Ms_t/2, so e^{-2 pi i k l/Ms} = (-1)^k e^{-2 pi i k a/Ms}): a row pass
+// over a2 that keeps the M2 central k2, then a column pass over a1 for each kept k2.
+
+// Rows: CTA owns grid rows a1 in [blockIdx.x CB, +CB) (thread t: row c = t / T2, j = t mod T2),
+// transforms over a2 (length N2 = 2^LOG2) and stores Y[a1 M2 + k2 + M2/2] = (-1)^k2 value.
+template <int LOG2>
+__global__ void __launch_bounds__(512) k_fft2_rows_r8(const float2* __restrict__ g, float2* __restrict__ Y, int CB,
+                                                      int M2) {
+    constexpr int N2 = 1 << LOG2, T2 = N2 / 8, RS = N2 + N2 / 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tw = (float2*)smem_raw;
+    const int t = threadIdx.x, c = t / T2, j = t % T2;
+    float2* bufA = tw + N2 + 2 * c * RS;
+    r8_twiddles<N2>(tw, t, blockDim.x);
+    griddep_wait();
+    griddep_launch();
+    const int a1 = blockIdx.x * CB + c;
+    float2 v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = g[(a1 << LOG2) + j + r * T2];
+    fft_r8<LOG2, -1>(v, bufA, bufA + RS, tw, j);
+#pragma unroll
+    for (int sl = 0; sl < 8; ++sl) {
+        const int k2 = bin_to_k(r8_bin<LOG2>(j, sl), N2, M2);
+        if (k2 != INT_MIN) Y[a1 * M2 + k2 + M2 / 2] = (k2 & 1) ? make_float2(-v[sl].x, -v[sl].y) : v[sl];
+    }
+}
+
+// Columns: CTA owns kept columns kk in [blockIdx.x CA, +CA) (thread t: column c = t mod CA,
+// j = t / CA), transforms Y[a1 M2 + kk] over a1 (length N1 = 2^LOG1) and stores
+// fhat[(k1 + M1/2) M2 + kk] = (-1)^k1 d_k value (d_k = inv, 0 for kernel sym at k1 = -M1/2
+// or k2 = -M2/2, i.e. kk = 0).
+template <int LOG1>
+__global__ void __launch_bounds__(512) k_fft2_cols_r8(const float2* __restrict__ Y, float2* __restrict__ fhat, int CA,
+                                                      int M1, int M2, float inv, int sym) {
+    constexpr int N1 = 1 << LOG1, T1 = N1 / 8, RS = N1 + N1 / 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tw = (float2*)smem_raw;
+    const int t = threadIdx.x, c = t % CA, j = t / CA;
+    float2* bufA = tw + N1 + 2 * c * RS;
+    r8_twiddles<N1>(tw, t, blockDim.x);
+    griddep_wait();
+    griddep_launch();
+    const int kk = blockIdx.x * CA + c;
+    float2 v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = Y[(j + r * T1) * M2 + kk];
+    fft_r8<LOG1, -1>(v, bufA, bufA + RS, tw, j);
+#pragma unroll
+    for (int sl = 0; sl < 8; ++sl) {
+        const int k1 = bin_to_k(r8_bin<LOG1>(j, sl), N1, M1);
+        if (k1 == INT_MIN) continue;
+        float d = (k1 & 1) ? -inv : inv;
+        if (sym && (k1 == -M1 / 2 || kk == 0)) d = 0.0f;
+        fhat[(k1 + M1 / 2) * M2 + kk] = make_float2(v[sl].x * d, v[sl].y * d);
+    }
+}
+
+using RowsFn = void (*)(const float2*, float2*, int, int);
+using ColsFn = void (*)(const float2*, float2*, int, int, int, float, int);
+
+RowsFn pick_rows(int lg) {
+    switch (lg) {
+        case 6: return k_fft2_rows_r8<6>;
+        case 7: return k_fft2_rows_r8<7>;
+        case 8: return k_fft2_rows_r8<8>;
+        case 9: return k_fft2_rows_r8<9>;
+        case 10: return k_fft2_rows_r8<10>;
+        case 11: return k_fft2_rows_r8<11>;
+        default: return nullptr;
+    }
+}
+
+ColsFn pick_cols(int lg) {
+    switch (lg) {
+        case 6: return k_fft2_cols_r8<6>;
+        case 7: return k_fft2_cols_r8<7>;
+        case 8: return k_fft2_cols_r8<8>;
+        case 9: return k_fft2_cols_r8<9>;
+        case 10: return k_fft2_cols_r8<10>;
+        case 11: return k_fft2_cols_r8<11>;
+        default: return nullptr;
+    }
+}
+
 struct Split {
     int log1, log2, CA, CB;
 };
@@ -577,4 +665,30 @@ extern "C" infft_status infft_fft_deconv_noalloc(const float* grid, int64_t M, i
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return set_error(INFFT_ECUDA, "launch: %s", cudaGetErrorString(e));
     return INFFT_OK;
+}
+
+bool fft2d_r8_supported(int log1, int log2, int M2) {
+    if (!pick_rows(log2) || !pick_cols(log1)) return false;
+    const R8Shape b = r8_shape(log1, M2, 4);
+    return M2 % b.per_cta == 0;
+}
+
+cudaError_t fft2d_adjoint_r8(const float2* g, float2* Y, float2* fhat, int log1, int log2, int M1, int M2, int sym,
+                             cudaStream_t s) {
+    RowsFn kr = pick_rows(log2);
+    ColsFn kc = pick_cols(log1);
+    if (!kr || !kc) return cudaErrorInvalidValue;
+    const R8Shape a = r8_shape(log2, 1 << log1, 4), b = r8_shape(log1, M2, 4);
+    if (M2 % b.per_cta) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = allow_smem(kr, (size_t)a.smem)) != cudaSuccess) return e;
+    if ((e = allow_smem(kc, (size_t)b.smem)) != cudaSuccess) return e;
+    const float inv = 1.0f / ((float)(1 << log1) * (float)(1 << log2));
+    e = launch_pdl(kr, dim3((1 << log1) / a.per_cta), dim3(a.per_cta * a.threads_per), (size_t)a.smem, s, g, Y,
+                   a.per_cta, M2);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(kc, dim3(M2 / b.per_cta), dim3(b.per_cta * b.threads_per), (size_t)b.smem, s, (const float2*)Y, fhat,
+                   b.per_cta, M1, M2, inv, sym);
+    count_launches(2);
+    return e;
 }

@@ -169,3 +169,9 @@ template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cud
 cudaError_t run_fft_full_forward_z(Plan* p, const void* in, void* out, double scale, cudaStream_t s);
 // grad.cu: gx = dL/dx (caller order) for f (complex64, device) and w = dL/dfhat (complex64, device)
 cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cudaStream_t s);
+// fft.cu: the fp32 2-D transform of the tensor-product plan: grid g (2^log1 x 2^log2 complex64,
+// row-major) -> fhat (M1 x M2, k1-major, (-1)^(k1+k2) d_k applied); Y holds 2^log1 x M2 complex64.
+// Supported for 2^log_t in [64, 2048] with M2 a multiple of the column pass's CTA width.
+bool fft2d_r8_supported(int log1, int log2, int M2);
+cudaError_t fft2d_adjoint_r8(const float2* g, float2* Y, float2* fhat, int log1, int log2, int M1, int M2, int sym,
+                             cudaStream_t s);

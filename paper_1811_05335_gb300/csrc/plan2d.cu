@@ -55,6 +55,8 @@ struct infft2d_plan_s {
     int32_t* hist = nullptr;       // LARGE_NMAX + 2: size buckets, then offsets / cursors; ticket
     int32_t* counters = nullptr;   // C2_N
     float* w32 = nullptr;          // nnz_cap
+    int2* ent = nullptr;           // nnz_cap: (caller node index, fp32 weight bits) for the fp32 spread
+    float* wlo = nullptr;          // nnz_cap: fp32(b - fp32(b)), the low part of wide columns' weights
     double* w64 = nullptr;         // nnz_cap
     double* J = nullptr;           // P
     uint8_t* wide = nullptr;       // P
@@ -85,7 +87,7 @@ enum {
 
 constexpr int TIER_NMAX[3] = {32, 64, 128};
 constexpr int LARGE_NMAX = 8192;
-constexpr int GIANT_N = 1024;     // columns above this are factored by many CTAs
+constexpr int GIANT_N = 384;      // columns above this are factored by many CTAs
 constexpr size_t GIANT_BUDGET = (size_t)16 << 30;   // bytes of giant triangles factored at once
 constexpr int PB = 16;             // panel width of the blocked solver
 constexpr int TB = 64;             // trailing-update tile
@@ -133,10 +135,12 @@ bool on_device2(const void* ptr) {
 // ---- kernel entries (Gram and right-hand side) -------------------------------
 
 struct K2 {
-    double M1, M2;   // kept frequencies per dimension enter as M (full) or M - 1 (sym)
+    double M1, M2;   // band sizes
+    double K1, K2;   // Dirichlet frequencies per dimension: M (full) or M - 1 (sym)
     double inv;      // 1 / (M_sigma,1 M_sigma,2)
     double diag;     // Re kappa(0)
     int sym;
+    int shortd;      // every kernel argument pi d is at most 0.25: sin(pi d), cos(pi (d1 + d2)) by series
 };
 
 // a - b as the representative in [-1/2, 1/2] on the torus; across the seam the
@@ -148,18 +152,86 @@ INFFT_D double tdiff(double a, double b) {
     return d;
 }
 
-// sin(pi K d) / sin(pi d), value K at d = 0 (the 1-D Dirichlet sums of both kernels)
-INFFT_D double dirichlet_ratio(double d, double K) {
-    if (d == 0.0) return K;
-    return sinpi(K * d) / sinpi(d);
+constexpr double PI_D = 3.141592653589793;
+
+// Taylor series of sin x and cos x (|x| <= 0.5 where used; the first omitted terms,
+// x^17/17! and x^18/18!, stay below 1e-20 relative)
+INFFT_D double sin_series(double x) {
+    const double x2 = x * x;
+    double q = 1.0;
+#pragma unroll
+    for (int k = 14; k >= 2; k -= 2) q = fma(-x2 * (1.0 / (double)(k * (k + 1))), q, 1.0);   // folded constants
+    return x * q;
+}
+INFFT_D double cos_series(double x) {
+    const double x2 = x * x;
+    double q = 1.0;
+#pragma unroll
+    for (int k = 15; k >= 1; k -= 2) q = fma(-x2 * (1.0 / (double)(k * (k + 1))), q, 1.0);
+    return q;
 }
 
-// Re kappa(d) = Re[kappa_1(d_1) kappa_2(d_2)]: full kernel kappa_t(d) = e^{-i pi d} sin(pi M d)/
+// A point of the kernel's argument: its coordinates and, per dimension, (sin, cos)(pi K_t x_t)
+struct NodeK {
+    double x1, x2, s1, c1, s2, c2;
+};
+
+// (sin, cos)(pi K x) with K x split exactly (K x = h + lo by an FMA), h reduced modulo 2
+// exactly, and the tiny lo added to first order
+INFFT_D void phase_pi(double K, double x, double& s, double& c) {
+    const double h = K * x;
+    const double lo = fma(K, x, -h);
+    const double hr = h - 2.0 * rint(0.5 * h);
+    double sn, cs;
+    sincospi(hr, &sn, &cs);
+    const double e = PI_D * lo;
+    s = fma(e, cs, sn);
+    c = fma(-e, sn, cs);
+}
+
+INFFT_D NodeK node_k(double2 x, const K2& k) {
+    NodeK n;
+    n.x1 = x.x;
+    n.x2 = x.y;
+    phase_pi(k.K1, x.x, n.s1, n.c1);
+    phase_pi(k.K2, x.y, n.s2, n.c2);
+    return n;
+}
+
+// sin(pi K d) and sin(pi d) for the torus difference d = a - b (at d = 0: K and 1, the
+// ratio's limit).  sin(pi K d) comes from the two points' phases, sin(pi K (a - b)) =
+// s_a c_b - c_a s_b, which changes sign with d -> d -+ 1 when K is odd; where |K d| < 1/8
+// that difference would lose relative accuracy and sinpi(K d) is evaluated instead.
+INFFT_D void dirichlet_parts(double a, double sa, double ca, double b, double sb, double cb, double K, bool oddK,
+                             bool shortd, double& num, double& den, double& d) {
+    d = tdiff(a, b);
+    if (d == 0.0) { num = K; den = 1.0; return; }
+    const double kd = K * d;
+    if (fabs(kd) < 0.125) {
+        num = sinpi(kd);
+    } else {
+        num = sa * cb - ca * sb;
+        if (oddK && fabs(a - b) > 0.5) num = -num;
+    }
+    den = shortd ? sin_series(PI_D * d) : sinpi(d);
+}
+
+// Re kappa(a - b) = Re[kappa_1(d_1) kappa_2(d_2)]: full kernel kappa_t(d) = e^{-i pi d} sin(pi M d)/
 // (M_sigma sin(pi d)), so the real part carries cos(pi (d_1 + d_2)); sym kernel: real Dirichlet
 // kernels sin(pi (M - 1) d)/(M_sigma sin(pi d)) (Remark remark:Dirichlet_ansatz2 per dimension)
-INFFT_D double re_kappa2(double d1, double d2, const K2& k) {
-    if (k.sym) return dirichlet_ratio(d1, k.M1 - 1.0) * dirichlet_ratio(d2, k.M2 - 1.0) * k.inv;
-    return cospi(d1 + d2) * dirichlet_ratio(d1, k.M1) * dirichlet_ratio(d2, k.M2) * k.inv;
+INFFT_D double re_kappa2(const NodeK& a, const NodeK& b, const K2& k) {
+    double n1, e1, d1, n2, e2, d2;
+    dirichlet_parts(a.x1, a.s1, a.c1, b.x1, b.s1, b.c1, k.K1, k.sym, k.shortd, n1, e1, d1);
+    dirichlet_parts(a.x2, a.s2, a.c2, b.x2, b.s2, b.c2, k.K2, k.sym, k.shortd, n2, e2, d2);
+    double v = (n1 * n2) / (e1 * e2) * k.inv;
+    if (!k.sym) v *= k.shortd ? cos_series(PI_D * (d1 + d2)) : cospi(d1 + d2);
+    return v;
+}
+
+// the grid point of column p as a kernel argument (l_t / M_sigma,t is exact)
+INFFT_D NodeK column_point(int p, int Ms1, int Ms2, const K2& k) {
+    return node_k(make_double2((double)(p / Ms2 - Ms1 / 2) / (double)Ms1, (double)(p % Ms2 - Ms2 / 2) / (double)Ms2),
+                  k);
 }
 
 INFFT_D int trow(int i) { return i * (i + 1) / 2; }
@@ -362,7 +434,7 @@ __global__ void k2_order_large(const int32_t* __restrict__ col_off, const int32_
 // ---- precompute: columns of up to NMAX nodes (one CTA of NMAX threads each) ---
 
 template <int NMAX> constexpr size_t small_smem() {
-    return (size_t)(NMAX * (NMAX + 1) / 2 + 3 * NMAX) * sizeof(double) + NMAX * sizeof(double2);
+    return (size_t)(NMAX * (NMAX + 1) / 2 + 3 * NMAX) * sizeof(double) + NMAX * sizeof(NodeK);
 }
 
 template <int NMAX>
@@ -376,27 +448,25 @@ __global__ void __launch_bounds__(NMAX) k2_solve_small(const double2* __restrict
     double* A = sm2;                                   // packed lower triangle, row-major
     double* r = A + NMAX * (NMAX + 1) / 2;             // right-hand side, then y
     double* lk = r + NMAX;                             // two buffers of L's current column
-    double2* xl = (double2*)(lk + 2 * NMAX);
+    NodeK* xl = (NodeK*)(lk + 2 * NMAX);               // the column's nodes with their phases
     __shared__ double red[2 * (NMAX / 32 > 0 ? NMAX / 32 : 1)];
     const int i = threadIdx.x;                         // this thread's row
     const int count = counters[C2_LIST0 + list_id];
     for (int it = blockIdx.x; it < count; it += gridDim.x) {
         const int p = list[it];
         const int off = col_off[p], n = col_off[p + 1] - off;
-        const double t1 = (double)(p / Ms2 - Ms1 / 2) / (double)Ms1;
-        const double t2 = (double)(p % Ms2 - Ms2 / 2) / (double)Ms2;
+        const NodeK cp = column_point(p, Ms1, Ms2, kp);
         __syncthreads();
-        if (i < n) xl[i] = x[col_node[off + i]];
+        if (i < n) xl[i] = node_k(x[col_node[off + i]], kp);
         __syncthreads();
         double mu = mu0, ysq = 0.0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
             if (i < n) {
-                const double2 xi = xl[i];
-                for (int j = 0; j < i; ++j)
-                    A[trow(i) + j] = re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
+                const NodeK xi = xl[i];
+                for (int j = 0; j < i; ++j) A[trow(i) + j] = re_kappa2(xi, xl[j], kp);
                 A[trow(i) + i] = kp.diag + mu;
-                r[i] = re_kappa2(tdiff(t1, xi.x), tdiff(t2, xi.y), kp);
+                r[i] = re_kappa2(cp, xi, kp);
             }
             __syncthreads();
             ysq = 0.0;
@@ -636,7 +706,7 @@ INFFT_D void back_solve(const double* __restrict__ A, double* __restrict__ r, in
     }
 }
 
-size_t large_smem(int nmax) { return (size_t)nmax * (sizeof(double2) + sizeof(double)); }
+size_t large_smem(int nmax) { return (size_t)nmax * (sizeof(NodeK) + sizeof(double)); }
 
 // one CTA per column of 129 .. GIANT_N nodes, largest first (atomic ticket)
 __global__ void __launch_bounds__(LARGE_THREADS, 1)
@@ -645,7 +715,7 @@ k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_of
                size_t slot_doubles, int32_t* __restrict__ ticket, double* __restrict__ w64, float* __restrict__ w32,
                double* __restrict__ J, uint8_t* __restrict__ wide, int32_t* __restrict__ counters, int nmax) {
     extern __shared__ __align__(16) double sm2[];
-    double2* xl = (double2*)sm2;                 // nmax nodes of the column
+    NodeK* xl = (NodeK*)sm2;                     // nmax nodes of the column with their phases
     double* r = (double*)(xl + nmax);            // nmax
     __shared__ __align__(16) double Li[PB * TBP], Lj[PB * TBP];
     __shared__ PanelShared ps;
@@ -661,20 +731,17 @@ k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_of
         if (job >= count) break;
         const int p = order[job];
         const int off = col_off[p], n = col_off[p + 1] - off;
-        const double t1 = (double)(p / Ms2 - Ms1 / 2) / (double)Ms1;
-        const double t2 = (double)(p % Ms2 - Ms2 / 2) / (double)Ms2;
-        for (int i = tid; i < n; i += LARGE_THREADS) xl[i] = x[col_node[off + i]];
+        const NodeK cp = column_point(p, Ms1, Ms2, kp);
+        for (int i = tid; i < n; i += LARGE_THREADS) xl[i] = node_k(x[col_node[off + i]], kp);
         __syncthreads();
         double mu = mu0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
             for (int i = warp; i < n; i += NW) {       // one warp per row: coalesced stores
-                const double2 xi = xl[i];
-                for (int j = lane; j <= i; j += 32)
-                    A[trow(i) + j] = (j == i) ? kp.diag + mu
-                                              : re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
+                const NodeK xi = xl[i];
+                for (int j = lane; j <= i; j += 32) A[trow(i) + j] = (j == i) ? kp.diag + mu : re_kappa2(xi, xl[j], kp);
             }
-            for (int i = tid; i < n; i += LARGE_THREADS) r[i] = re_kappa2(tdiff(t1, xl[i].x), tdiff(t2, xl[i].y), kp);
+            for (int i = tid; i < n; i += LARGE_THREADS) r[i] = re_kappa2(cp, xl[i], kp);
             if (tid == 0) { ps.fail = 0; ps.ysq = 0.0; }
             __syncthreads();
             for (int kb = 0; kb < n; kb += PB) {
@@ -722,7 +789,7 @@ k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_of
 struct GiantCol {
     int p, n, fail, pad;
     long long a_off;       // packed triangle in the giant scratch
-    long long v_off;       // r (n doubles), then the nodes (n double2)
+    long long v_off;       // r (n doubles, padded to even), then the nodes (n NodeK)
     double ysq;
 };
 
@@ -734,31 +801,36 @@ __global__ void __launch_bounds__(LARGE_THREADS) k2g_stage(const double2* __rest
     GiantCol& g = gs[blockIdx.y];
     const int n = g.n, off = col_off[g.p];
     double* r = gbase + g.v_off;
-    double2* xl = (double2*)(r + n + (n & 1));
-    const double t1 = (double)(g.p / Ms2 - Ms1 / 2) / (double)Ms1;
-    const double t2 = (double)(g.p % Ms2 - Ms2 / 2) / (double)Ms2;
+    NodeK* xl = (NodeK*)(r + n + (n & 1));
+    const NodeK cp = column_point(g.p, Ms1, Ms2, kp);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double2 v = x[col_node[off + i]];
+        const NodeK v = node_k(x[col_node[off + i]], kp);
         xl[i] = v;
-        r[i] = re_kappa2(tdiff(t1, v.x), tdiff(t2, v.y), kp);
+        r[i] = re_kappa2(cp, v, kp);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) { g.fail = 0; g.ysq = 0.0; }
 }
 
-__global__ void __launch_bounds__(LARGE_THREADS) k2g_fill(GiantCol* __restrict__ gs, double* __restrict__ gbase,
-                                                          K2 kp, double mu) {
-    const GiantCol& g = gs[blockIdx.y];
-    const int n = g.n;
-    double* A = gbase + g.a_off;
-    const double* r = gbase + g.v_off;
-    const double2* xl = (const double2*)(r + n + (n & 1));
+// one warp per triangle row over all columns of the group (rows numbered through the
+// exclusive prefix rowpre over the columns' sizes)
+__global__ void __launch_bounds__(LARGE_THREADS) k2g_fill(const GiantCol* __restrict__ gs, double* __restrict__ gbase,
+                                                          K2 kp, double mu, const int32_t* __restrict__ rowpre, int G) {
     const int lane = threadIdx.x & 31;
-    const int wid = blockIdx.x * (LARGE_THREADS / 32) + (threadIdx.x >> 5);
     const int nw = gridDim.x * (LARGE_THREADS / 32);
-    for (int i = wid; i < n; i += nw) {
-        const double2 xi = xl[i];
-        for (int j = lane; j <= i; j += 32)
-            A[trow(i) + j] = (j == i) ? kp.diag + mu : re_kappa2(tdiff(xi.x, xl[j].x), tdiff(xi.y, xl[j].y), kp);
+    const int total = rowpre[G];
+    for (int t = blockIdx.x * (LARGE_THREADS / 32) + (threadIdx.x >> 5); t < total; t += nw) {
+        int lo = 0, hi = G - 1;                            // last g with rowpre[g] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rowpre[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const GiantCol& g = gs[lo];
+        const int n = g.n, i = t - rowpre[lo];
+        double* A = gbase + g.a_off;
+        const double* r = gbase + g.v_off;
+        const NodeK* xl = (const NodeK*)(r + n + (n & 1));
+        const NodeK xi = xl[i];
+        for (int j = lane; j <= i; j += 32) A[trow(i) + j] = (j == i) ? kp.diag + mu : re_kappa2(xi, xl[j], kp);
     }
 }
 
@@ -825,45 +897,114 @@ __global__ void k2g_give_up(const GiantCol* __restrict__ gs, const int32_t* __re
 
 // ---- apply ---------------------------------------------------------------------
 
-// g_p = sum_{e in column p} b_e f_{node(e)}, one warp per column
-template <typename T>
-__global__ void __launch_bounds__(256) k2_spread(const cplx_t<T>* __restrict__ f, const int32_t* __restrict__ col_off,
-                                                 const int32_t* __restrict__ col_node, const float* __restrict__ w32,
-                                                 const double* __restrict__ w64, const uint8_t* __restrict__ wide,
-                                                 int P, cplx_t<T>* __restrict__ g) {
+// the entries of the fp32 spread: node index and fp32 weight in one 8-byte load, and the
+// low part of each weight for the columns that spread in float-float
+__global__ void k2_pack(const int32_t* __restrict__ col_node, const float* __restrict__ w32,
+                        const double* __restrict__ w64, int nnz, int2* __restrict__ ent, float* __restrict__ wlo) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
+        const float hi = w32[e];
+        ent[e] = make_int2(col_node[e], __float_as_int(hi));
+        wlo[e] = (float)(w64[e] - (double)hi);
+    }
+}
+
+// s + e = a + b exactly (Knuth's two-sum; the _rn intrinsics keep the compiler from
+// reassociating or contracting)
+INFFT_D void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// fp32 apply: g_p = sum_{e in column p} b_e f_{node(e)}, one warp per column.  Ordinary
+// columns: fp32 weights, two fp32 accumulator chains per lane.  Wide columns (||b_l||_1 > 32,
+// whose terms cancel): float-float -- b = hi + lo, each product split exactly by an FMA,
+// sums carried as (s, c) pairs through two-sum -- about 44 significant bits on the fp32
+// pipe, which runs 64 times as many lanes per clock as the fp64 pipe
+__global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f, const int32_t* __restrict__ col_off,
+                                                   const int2* __restrict__ ent, const float* __restrict__ wlo,
+                                                   const uint8_t* __restrict__ wide, int P, float2* __restrict__ g) {
     const int lane = threadIdx.x & 31;
     const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (p >= P) return;
     const int s = col_off[p], e = col_off[p + 1];
-    if constexpr (sizeof(T) == 4) {
-        if (!wide[p]) {
-            float ar = 0.f, ai = 0.f;
-            for (int q = s + lane; q < e; q += 32) {
-                const float w = w32[q];
-                const float2 v = f[col_node[q]];
-                ar = fmaf(w, v.x, ar);
-                ai = fmaf(w, v.y, ai);
-            }
-            for (int o = 16; o; o >>= 1) {
-                ar += __shfl_xor_sync(0xffffffffu, ar, o);
-                ai += __shfl_xor_sync(0xffffffffu, ai, o);
-            }
-            if (lane == 0) g[p] = make_float2(ar, ai);
-            return;
+    if (!wide[p]) {
+        float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+        int q = s + lane;
+        for (; q + 32 < e; q += 64) {
+            const int2 e0 = ent[q], e1 = ent[q + 32];
+            const float2 v0 = f[e0.x], v1 = f[e1.x];
+            const float w0 = __int_as_float(e0.y), w1 = __int_as_float(e1.y);
+            ar = fmaf(w0, v0.x, ar);
+            ai = fmaf(w0, v0.y, ai);
+            br = fmaf(w1, v1.x, br);
+            bi = fmaf(w1, v1.y, bi);
         }
+        if (q < e) {
+            const int2 e0 = ent[q];
+            const float2 v0 = f[e0.x];
+            const float w0 = __int_as_float(e0.y);
+            ar = fmaf(w0, v0.x, ar);
+            ai = fmaf(w0, v0.y, ai);
+        }
+        ar += br;
+        ai += bi;
+        for (int o = 16; o; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == 0) g[p] = make_float2(ar, ai);
+        return;
     }
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    for (int q = s + lane; q < e; q += 32) {
+        const int2 en = ent[q];
+        const float wh = __int_as_float(en.y), wl = wlo[q];
+        const float2 v = f[en.x];
+        const float tr = __fmul_rn(wh, v.x), ti = __fmul_rn(wh, v.y);
+        const float lr = fmaf(wl, v.x, fmaf(wh, v.x, -tr)), li = fmaf(wl, v.y, fmaf(wh, v.y, -ti));
+        float t, err;
+        two_sum(sr, tr, t, err);
+        sr = t;
+        cr += err + lr;
+        two_sum(si, ti, t, err);
+        si = t;
+        ci += err + li;
+    }
+    for (int o = 16; o; o >>= 1) {
+        float t, err;
+        const float osr = __shfl_xor_sync(0xffffffffu, sr, o), ocr = __shfl_xor_sync(0xffffffffu, cr, o);
+        const float osi = __shfl_xor_sync(0xffffffffu, si, o), oci = __shfl_xor_sync(0xffffffffu, ci, o);
+        two_sum(sr, osr, t, err);
+        sr = t;
+        cr += ocr + err;
+        two_sum(si, osi, t, err);
+        si = t;
+        ci += oci + err;
+    }
+    if (lane == 0) g[p] = make_float2(sr + cr, si + ci);
+}
+
+// fp64 apply: fp64 weights, inputs and accumulation, one warp per column
+__global__ void __launch_bounds__(256) k2_spread64(const double2* __restrict__ f, const int32_t* __restrict__ col_off,
+                                                   const int32_t* __restrict__ col_node,
+                                                   const double* __restrict__ w64, int P, double2* __restrict__ g) {
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (p >= P) return;
+    const int s = col_off[p], e = col_off[p + 1];
     double ar = 0.0, ai = 0.0;
     for (int q = s + lane; q < e; q += 32) {
         const double w = w64[q];
-        const cplx_t<T> v = f[col_node[q]];
-        ar = fma(w, (double)v.x, ar);
-        ai = fma(w, (double)v.y, ai);
+        const double2 v = f[col_node[q]];
+        ar = fma(w, v.x, ar);
+        ai = fma(w, v.y, ai);
     }
     for (int o = 16; o; o >>= 1) {
         ar += __shfl_xor_sync(0xffffffffu, ar, o);
         ai += __shfl_xor_sync(0xffffffffu, ai, o);
     }
-    if (lane == 0) g[p] = cmake((T)ar, (T)ai);
+    if (lane == 0) g[p] = make_double2(ar, ai);
 }
 
 // pass R: rows a1 in [a1_0, a1_0 + C) of the grid, transform over a2 (length Ms2), keep
@@ -925,8 +1066,14 @@ K2 kernel_params(const infft2d_plan_s* p) {
     k.M1 = (double)p->M1;
     k.M2 = (double)p->M2;
     k.sym = p->kernel == INFFT_KERNEL_SYM;
+    k.K1 = k.sym ? k.M1 - 1.0 : k.M1;
+    k.K2 = k.sym ? k.M2 - 1.0 : k.M2;
     k.inv = 1.0 / ((double)p->Ms1 * (double)p->Ms2);
-    k.diag = k.sym ? (k.M1 - 1.0) * (k.M2 - 1.0) * k.inv : k.M1 * k.M2 * k.inv;
+    k.diag = k.K1 * k.K2 * k.inv;
+    // node differences within a column are at most (2m + 1)/M_sigma,t per dimension
+    const double a1 = 3.141592653589793 * (2.0 * p->m + 1.0) / (double)p->Ms1;
+    const double a2 = 3.141592653589793 * (2.0 * p->m + 1.0) / (double)p->Ms2;
+    k.shortd = a1 <= 0.25 && a2 <= 0.25;
     return k;
 }
 
@@ -947,7 +1094,7 @@ void layout2(infft2d_plan_s* p, Carver2& c) {
     c.take(p->col_count, P); c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
     c.take(p->lists, 5 * P); c.take(p->order, P); c.take(p->hist, LARGE_NMAX + 2);
     c.take(p->counters, C2_N);
-    c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
+    c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->ent, p->nnz_cap); c.take(p->wlo, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
     double2 *grid, *work, *si, *so;
     c.take(grid, P); c.take(work, (size_t)p->M2 * p->Ms1);
     const size_t stage = std::max(N, M);
@@ -996,7 +1143,7 @@ cudaError_t run_giants(infft2d_plan_s* p, int G, const K2& kp, double mu, int sm
         g.p = q;
         g.n = off[q + 1] - off[q];
         const size_t tri = ((size_t)g.n * (g.n + 1) / 2 + 1) & ~(size_t)1;
-        const size_t vec = ((size_t)3 * g.n + 3) & ~(size_t)1;   // even: the next triangle and node pairs stay 16-byte aligned
+        const size_t vec = ((size_t)7 * g.n + 3) & ~(size_t)1;   // r, the nodes (6 doubles each); even: 16-byte alignment
         if (!groups.back().empty() && (used + tri + vec) * sizeof(double) > GIANT_BUDGET) {
             groups.emplace_back();
             used = 0;
@@ -1031,7 +1178,7 @@ cudaError_t run_giants(infft2d_plan_s* p, int G, const K2& kp, double mu, int sm
             int nmax = 0;
             for (auto& g : grp) nmax = std::max(nmax, g.n);
             const int steps = (nmax + PB - 1) / PB;
-            std::vector<int32_t> prefix((size_t)steps * (Gg + 1));
+            std::vector<int32_t> prefix((size_t)(steps + 1) * (Gg + 1));
             for (int st = 0; st < steps; ++st) {
                 int32_t run = 0;
                 for (int i = 0; i < Gg; ++i) {
@@ -1040,6 +1187,13 @@ cudaError_t run_giants(infft2d_plan_s* p, int G, const K2& kp, double mu, int sm
                 }
                 prefix[(size_t)st * (Gg + 1) + Gg] = run;
             }
+            int32_t* rowpre = &prefix[(size_t)steps * (Gg + 1)];   // triangle rows of the group's columns
+            int32_t rows = 0;
+            for (int i = 0; i < Gg; ++i) {
+                rowpre[i] = rows;
+                rows += grp[i].n;
+            }
+            rowpre[Gg] = rows;
             if (p->gprefix_cap < prefix.size()) {
                 if (p->gprefix) cudaFree(p->gprefix);
                 p->gprefix = nullptr;
@@ -1055,8 +1209,8 @@ cudaError_t run_giants(infft2d_plan_s* p, int G, const K2& kp, double mu, int sm
             const int xs = std::max(1, std::min((nmax + 255) / 256, (4 * sms + Gg - 1) / Gg));
             k2g_stage<<<dim3(xs, Gg), LARGE_THREADS, 0, s>>>(p->x, p->col_off, p->col_node, gd, p->gscratch,
                                                             (int)p->Ms1, (int)p->Ms2, kp);
-            const int xf = std::max(1, std::min((nmax + 7) / 8, (8 * sms + Gg - 1) / Gg));
-            k2g_fill<<<dim3(xf, Gg), LARGE_THREADS, 0, s>>>(gd, p->gscratch, kp, mu_a);
+            k2g_fill<<<std::min((rows + 7) / 8, 16 * sms), LARGE_THREADS, 0, s>>>(
+                gd, p->gscratch, kp, mu_a, p->gprefix + (size_t)steps * (Gg + 1), Gg);
             int launches = 2;
             for (int st = 0; st < steps; ++st) {
                 k2g_panel<<<Gg, LARGE_THREADS, 0, s>>>(gd, p->gscratch, st * PB);
@@ -1157,8 +1311,13 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
         count_launches(3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (G == 0) return cudaSuccess;
-    return run_giants(p, G, kp, mu, sms, s);
+    if (G > 0 && (e = run_giants(p, G, kp, mu, sms, s)) != cudaSuccess) return e;
+    if (p->nnz > 0) {
+        k2_pack<<<(int)std::min<int64_t>((p->nnz + 255) / 256, 16 * sms), 256, 0, s>>>(
+            p->col_node, p->w32, p->w64, (int)p->nnz, p->ent, p->wlo);
+        count_launches(1);
+    }
+    return cudaGetLastError();
 }
 
 template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
@@ -1166,7 +1325,16 @@ template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, v
     const int P = (int)p->P;
     Cx* g = (Cx*)p->grid;
     Cx* Y = (Cx*)p->work;
-    k2_spread<T><<<(P + 7) / 8, 256, 0, s>>>((const Cx*)f, p->col_off, p->col_node, p->w32, p->w64, p->wide, P, g);
+    if constexpr (sizeof(T) == 4)
+        k2_spread32<<<(P + 7) / 8, 256, 0, s>>>((const float2*)f, p->col_off, p->ent, p->wlo, p->wide, P, g);
+    else
+        k2_spread64<<<(P + 7) / 8, 256, 0, s>>>((const double2*)f, p->col_off, p->col_node, p->w64, P, g);
+    count_launches(1);
+    if constexpr (sizeof(T) == 4) {
+        if (fft2d_r8_supported(p->log1, p->log2, (int)p->M2))
+            return fft2d_adjoint_r8((const float2*)g, (float2*)Y, (float2*)fhat, p->log1, p->log2, (int)p->M1,
+                                    (int)p->M2, p->kernel == INFFT_KERNEL_SYM, s);
+    }
     const int C2 = std::min<int>(fft_batch(p->log2), (int)p->Ms1);
     const int C1 = std::min<int>(fft_batch(p->log1), (int)(p->M2 & -p->M2));   // a divisor of M2
     const size_t sm2 = 2 * (size_t)C2 * p->Ms2 * sizeof(Cx), sm1 = 2 * (size_t)C1 * p->Ms1 * sizeof(Cx);
@@ -1177,7 +1345,7 @@ template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, v
     k2_fft_cols<T><<<(int)p->M2 / C1, FFT2_THREADS, sm1, s>>>(Y, (Cx*)fhat, p->log1, (int)p->M1, (int)p->M2, C1,
                                                               (T)(1.0 / ((double)p->Ms1 * (double)p->Ms2)),
                                                               p->kernel == INFFT_KERNEL_SYM);
-    count_launches(3);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -1305,6 +1473,14 @@ infft_status infft2d_precompute(infft2d_plan_t p, infft_stream_t stream) {
     p->last_stream = s;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = run_precompute2(p, s);
+    // the large-column scratch (gigabytes for clustered nodes) is not kept between precomputes
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        if (p->scratch) cudaFree(p->scratch);
+        if (p->gscratch) cudaFree(p->gscratch);
+        p->scratch = p->gscratch = nullptr;
+        p->scratch_doubles = p->gscratch_doubles = 0;
+    }
     if (e != cudaSuccess) return cuda_fail2(e, "precompute");
     p->precomputed = 1;
     return INFFT_OK;
