@@ -52,6 +52,8 @@ struct infft2d_plan_s {
     int32_t* col_node = nullptr;   // nnz_cap: caller index of each entry, column by column
     int32_t* lists = nullptr;      // 5 P: columns of the three shared-memory tiers and the two large tiers
     int32_t* order = nullptr;      // P: large columns, largest first
+    int32_t* spread_big = nullptr; // P: columns above SPREAD_BIG entries
+    int spread_big_count = 0;
     int32_t* hist = nullptr;       // LARGE_NMAX + 2: size buckets, then offsets / cursors; ticket
     int32_t* counters = nullptr;   // C2_N
     float* w32 = nullptr;          // nnz_cap
@@ -82,7 +84,9 @@ namespace {
 enum {
     C2_BAD = 0, C2_FALLBACK = 1, C2_UNSUPPORTED = 2, C2_MAX_COLUMN = 3, C2_EMPTY = 4,
     C2_LIST0 = 5,   // C2_LIST0 + t: length of the list of tier t (0..2 shared memory, 3 one CTA, 4 many CTAs)
-    C2_BIG_CELLS = 10, C2_WIDE = 11, C2_N = 12
+    C2_BIG_CELLS = 10, C2_WIDE = 11,
+    C2_SPREAD_BIG = 12,   // columns above SPREAD_BIG entries, spread by a whole CTA each
+    C2_N = 13
 };
 
 constexpr int TIER_NMAX[3] = {32, 64, 128};
@@ -95,6 +99,8 @@ constexpr int TBP = TB + 2;        // shared-memory row stride of the staged pan
 constexpr int LARGE_THREADS = 256;
 constexpr int CELL_SORT_MAX = 4096;
 constexpr int FFT2_THREADS = 256;
+constexpr int SPREAD_LPC = 16;    // lanes per column of the fp32 spread
+constexpr int SPREAD_BIG = 512;   // longer columns are spread by one CTA each
 
 thread_local std::string g_err2;
 
@@ -402,11 +408,13 @@ __global__ void __launch_bounds__(256) k2_columns(const double2* __restrict__ xs
 
 __global__ void k2_route(const int32_t* __restrict__ col_off, int P, int32_t* __restrict__ lists,
                          double* __restrict__ w64, float* __restrict__ w32, double* __restrict__ J,
-                         uint8_t* __restrict__ wide, int32_t* __restrict__ hist, int32_t* __restrict__ counters) {
+                         uint8_t* __restrict__ wide, int32_t* __restrict__ hist, int32_t* __restrict__ spread_big,
+                         int32_t* __restrict__ counters) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int off = col_off[p], n = col_off[p + 1] - off;
     wide[p] = 0;
+    if (n > SPREAD_BIG) spread_big[atomicAdd(&counters[C2_SPREAD_BIG], 1)] = p;
     if (n == 0) { J[p] = 1.0; return; }
     if (n > LARGE_NMAX) {   // not built: b_l = 0 (J_l = 1)
         for (int i = 0; i < n; ++i) { w64[off + i] = 0.0; w32[off + i] = 0.0f; }
@@ -916,48 +924,58 @@ INFFT_D void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// fp32 apply: g_p = sum_{e in column p} b_e f_{node(e)}, one warp per column.  Ordinary
-// columns: fp32 weights, two fp32 accumulator chains per lane.  Wide columns (||b_l||_1 > 32,
-// whose terms cancel): float-float -- b = hi + lo, each product split exactly by an FMA,
-// sums carried as (s, c) pairs through two-sum -- about 44 significant bits on the fp32
-// pipe, which runs 64 times as many lanes per clock as the fp64 pipe
-__global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f, const int32_t* __restrict__ col_off,
-                                                   const int2* __restrict__ ent, const float* __restrict__ wlo,
-                                                   const uint8_t* __restrict__ wide, int P, float2* __restrict__ g) {
-    const int lane = threadIdx.x & 31;
-    const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (p >= P) return;
+// fp32 apply: g_p = sum_{e in column p} b_e f_{node(e)}, LPC lanes per column (the lanes of
+// a column walk its entries LPC apart, four loads in flight each).  Ordinary columns: fp32
+// weights and accumulation.  Wide columns (||b_l||_1 > 32, whose terms cancel): float-float --
+// b = hi + lo, each product split exactly by an FMA, sums carried as (s, c) pairs through
+// two-sum -- about 44 significant bits on the fp32 pipe, which runs 64 times as many lanes
+// per clock as the fp64 pipe.
+// one column by the whole CTA (256 threads): per-thread sums, warp shuffles, then the
+// eight warp partials in shared memory
+INFFT_D void spread_column_cta(int p, const float2* __restrict__ f, const int32_t* __restrict__ col_off,
+                               const int2* __restrict__ ent, const float* __restrict__ wlo,
+                               const uint8_t* __restrict__ wide, float2* __restrict__ g) {
+    __shared__ float red[4][8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = col_off[p], e = col_off[p + 1];
     if (!wide[p]) {
-        float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-        int q = s + lane;
-        for (; q + 32 < e; q += 64) {
-            const int2 e0 = ent[q], e1 = ent[q + 32];
-            const float2 v0 = f[e0.x], v1 = f[e1.x];
-            const float w0 = __int_as_float(e0.y), w1 = __int_as_float(e1.y);
-            ar = fmaf(w0, v0.x, ar);
-            ai = fmaf(w0, v0.y, ai);
-            br = fmaf(w1, v1.x, br);
-            bi = fmaf(w1, v1.y, bi);
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+        int q = s + tid;
+        for (; q + 3 * 256 < e; q += 4 * 256) {
+            int2 en[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) en[u] = ent[q + u * 256];
+            float2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = f[en[u].x];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ar[u] = fmaf(__int_as_float(en[u].y), v[u].x, ar[u]);
+                ai[u] = fmaf(__int_as_float(en[u].y), v[u].y, ai[u]);
+            }
         }
-        if (q < e) {
-            const int2 e0 = ent[q];
-            const float2 v0 = f[e0.x];
-            const float w0 = __int_as_float(e0.y);
-            ar = fmaf(w0, v0.x, ar);
-            ai = fmaf(w0, v0.y, ai);
+        for (; q < e; q += 256) {
+            const int2 en = ent[q];
+            const float2 v = f[en.x];
+            ar[0] = fmaf(__int_as_float(en.y), v.x, ar[0]);
+            ai[0] = fmaf(__int_as_float(en.y), v.y, ai[0]);
         }
-        ar += br;
-        ai += bi;
+        float r = (ar[0] + ar[1]) + (ar[2] + ar[3]), i = (ai[0] + ai[1]) + (ai[2] + ai[3]);
         for (int o = 16; o; o >>= 1) {
-            ar += __shfl_xor_sync(0xffffffffu, ar, o);
-            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+            r += __shfl_xor_sync(0xffffffffu, r, o);
+            i += __shfl_xor_sync(0xffffffffu, i, o);
         }
-        if (lane == 0) g[p] = make_float2(ar, ai);
+        if (lane == 0) { red[0][warp] = r; red[1][warp] = i; }
+        __syncthreads();
+        if (tid == 0) {
+            float a = 0.f, b = 0.f;
+            for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; }
+            g[p] = make_float2(a, b);
+        }
         return;
     }
     float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    for (int q = s + lane; q < e; q += 32) {
+    for (int q = s + tid; q < e; q += 256) {
         const int2 en = ent[q];
         const float wh = __int_as_float(en.y), wl = wlo[q];
         const float2 v = f[en.x];
@@ -982,7 +1000,97 @@ __global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f,
         si = t;
         ci += oci + err;
     }
-    if (lane == 0) g[p] = make_float2(sr + cr, si + ci);
+    if (lane == 0) { red[0][warp] = sr; red[1][warp] = cr; red[2][warp] = si; red[3][warp] = ci; }
+    __syncthreads();
+    if (tid == 0) {
+        float a = red[0][0], ac = red[1][0], b = red[2][0], bc = red[3][0];
+        for (int w = 1; w < 8; ++w) {
+            float t, err;
+            two_sum(a, red[0][w], t, err);
+            a = t;
+            ac += red[1][w] + err;
+            two_sum(b, red[2][w], t, err);
+            b = t;
+            bc += red[3][w] + err;
+        }
+        g[p] = make_float2(a + ac, b + bc);
+    }
+}
+
+template <int LPC>
+__global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f, const int32_t* __restrict__ col_off,
+                                                   const int2* __restrict__ ent, const float* __restrict__ wlo,
+                                                   const uint8_t* __restrict__ wide, int P, float2* __restrict__ g,
+                                                   const int32_t* __restrict__ big, int nbig) {
+    if ((int)blockIdx.x < nbig) {                          // the columns above SPREAD_BIG entries
+        spread_column_cta(big[blockIdx.x], f, col_off, ent, wlo, wide, g);
+        return;
+    }
+    const int sub = threadIdx.x & (LPC - 1);
+    const int p = (blockIdx.x - nbig) * (256 / LPC) + threadIdx.x / LPC;
+    const unsigned mask = LPC == 32 ? 0xffffffffu : ((1u << LPC) - 1) << ((threadIdx.x & 31) & ~(LPC - 1));
+    if (p >= P) return;                                    // uniform over the column's lanes
+    const int s = col_off[p], e = col_off[p + 1];
+    if (e - s > SPREAD_BIG) return;                        // spread by its own CTA
+    if (!wide[p]) {
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+        int q = s + sub;
+        for (; q + 3 * LPC < e; q += 4 * LPC) {
+            int2 en[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) en[u] = ent[q + u * LPC];
+            float2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = f[en[u].x];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ar[u] = fmaf(__int_as_float(en[u].y), v[u].x, ar[u]);
+                ai[u] = fmaf(__int_as_float(en[u].y), v[u].y, ai[u]);
+            }
+        }
+        for (; q < e; q += LPC) {
+            const int2 en = ent[q];
+            const float2 v = f[en.x];
+            ar[0] = fmaf(__int_as_float(en.y), v.x, ar[0]);
+            ai[0] = fmaf(__int_as_float(en.y), v.y, ai[0]);
+        }
+        float r = (ar[0] + ar[1]) + (ar[2] + ar[3]), i = (ai[0] + ai[1]) + (ai[2] + ai[3]);
+#pragma unroll
+        for (int o = LPC / 2; o; o >>= 1) {
+            r += __shfl_xor_sync(mask, r, o);
+            i += __shfl_xor_sync(mask, i, o);
+        }
+        if (sub == 0) g[p] = make_float2(r, i);
+        return;
+    }
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    for (int q = s + sub; q < e; q += LPC) {
+        const int2 en = ent[q];
+        const float wh = __int_as_float(en.y), wl = wlo[q];
+        const float2 v = f[en.x];
+        const float tr = __fmul_rn(wh, v.x), ti = __fmul_rn(wh, v.y);
+        const float lr = fmaf(wl, v.x, fmaf(wh, v.x, -tr)), li = fmaf(wl, v.y, fmaf(wh, v.y, -ti));
+        float t, err;
+        two_sum(sr, tr, t, err);
+        sr = t;
+        cr += err + lr;
+        two_sum(si, ti, t, err);
+        si = t;
+        ci += err + li;
+    }
+#pragma unroll
+    for (int o = LPC / 2; o; o >>= 1) {
+        float t, err;
+        const float osr = __shfl_xor_sync(mask, sr, o), ocr = __shfl_xor_sync(mask, cr, o);
+        const float osi = __shfl_xor_sync(mask, si, o), oci = __shfl_xor_sync(mask, ci, o);
+        two_sum(sr, osr, t, err);
+        sr = t;
+        cr += ocr + err;
+        two_sum(si, osi, t, err);
+        si = t;
+        ci += oci + err;
+    }
+    if (sub == 0) g[p] = make_float2(sr + cr, si + ci);
 }
 
 // fp64 apply: fp64 weights, inputs and accumulation, one warp per column
@@ -1092,7 +1200,7 @@ void layout2(infft2d_plan_s* p, Carver2& c) {
     c.take(p->x, N); c.take(p->xs, N); c.take(p->node_cell, N); c.take(p->perm, N);
     c.take(p->cell_start, P + 1); c.take(p->cursor, P); c.take(p->big_cells, P);
     c.take(p->col_count, P); c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
-    c.take(p->lists, 5 * P); c.take(p->order, P); c.take(p->hist, LARGE_NMAX + 2);
+    c.take(p->lists, 5 * P); c.take(p->order, P); c.take(p->spread_big, P); c.take(p->hist, LARGE_NMAX + 2);
     c.take(p->counters, C2_N);
     c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->ent, p->nnz_cap); c.take(p->wlo, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
     double2 *grid, *work, *si, *so;
@@ -1256,14 +1364,16 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 148;
+    if ((e = cudaMemsetAsync(p->counters + C2_SPREAD_BIG, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     k2_route<<<(P + 255) / 256, 256, 0, s>>>(p->col_off, P, p->lists, p->w64, p->w32, p->J, p->wide, p->hist,
-                                             p->counters);
+                                             p->spread_big, p->counters);
     count_launches(1);
     // the list lengths and the columns for the multi-CTA solver decide the launches below
     int32_t cnt[C2_N];
     if ((e = cudaMemcpyAsync(cnt, p->counters, sizeof cnt, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     const int G = cnt[C2_LIST0 + 4];
+    p->spread_big_count = cnt[C2_SPREAD_BIG];
     // shared-memory tiers
     auto t0 = k2_solve_small<32>;
     auto t1 = k2_solve_small<64>;
@@ -1326,7 +1436,8 @@ template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, v
     Cx* g = (Cx*)p->grid;
     Cx* Y = (Cx*)p->work;
     if constexpr (sizeof(T) == 4)
-        k2_spread32<<<(P + 7) / 8, 256, 0, s>>>((const float2*)f, p->col_off, p->ent, p->wlo, p->wide, P, g);
+        k2_spread32<SPREAD_LPC><<<p->spread_big_count + (P + 256 / SPREAD_LPC - 1) / (256 / SPREAD_LPC), 256, 0, s>>>(
+            (const float2*)f, p->col_off, p->ent, p->wlo, p->wide, P, g, p->spread_big, p->spread_big_count);
     else
         k2_spread64<<<(P + 7) / 8, 256, 0, s>>>((const double2*)f, p->col_off, p->col_node, p->w64, P, g);
     count_launches(1);
