@@ -47,7 +47,6 @@ struct infft2d_plan_s {
     int32_t* cell_start = nullptr; // P + 1: node counts per cell, then their exclusive prefix
     int32_t* cursor = nullptr;     // P: scatter cursors
     int32_t* big_cells = nullptr;  // P: cells with more than 32 nodes (ordered by one CTA each)
-    int32_t* col_count = nullptr;  // P
     int32_t* col_off = nullptr;    // P + 1
     int32_t* col_node = nullptr;   // nnz_cap: caller index of each entry, column by column
     int32_t* lists = nullptr;      // 5 P: columns of the three shared-memory tiers and the two large tiers
@@ -1199,7 +1198,7 @@ void layout2(infft2d_plan_s* p, Carver2& c) {
     const size_t N = p->N, P = p->P, M = p->M1 * p->M2;
     c.take(p->x, N); c.take(p->xs, N); c.take(p->node_cell, N); c.take(p->perm, N);
     c.take(p->cell_start, P + 1); c.take(p->cursor, P); c.take(p->big_cells, P);
-    c.take(p->col_count, P); c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
+    c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
     c.take(p->lists, 5 * P); c.take(p->order, P); c.take(p->spread_big, P); c.take(p->hist, LARGE_NMAX + 2);
     c.take(p->counters, C2_N);
     c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->ent, p->nnz_cap); c.take(p->wlo, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
