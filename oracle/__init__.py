@@ -22,8 +22,9 @@ Layout (each function cites the passage it follows):
                   tier that forms Re(L_l^* L_l) directly.
 * ``infft``    -- the modified adjoint NFFT fhat ~ D^* F^* B_opt^* f
                   (eq:approx_ansatz2), its adjoint B_opt F D (Remark
-                  remark:ansatz2_adj), the Frobenius objective and the
-                  per-node error measures (eq:errors_per_node_lagrange).
+                  remark:ansatz2_adj), the Frobenius objective, the
+                  per-node error measures (eq:errors_per_node_lagrange) and
+                  the residual correction fhat += D^* F^* B_opt^* (f - A fhat).
 * ``infft2d``  -- the 2-D tensor-product reading of Sec. 3.2.2 (box pattern,
                   product kernel, 2-D F and D), naive and closed-form tiers.
 * ``under``    -- the underdetermined case of Sec. 3.2.1: one least-squares

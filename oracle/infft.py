@@ -3,7 +3,7 @@ Remark remark:ansatz2_adj), the Frobenius objective (eq:matrixnorm_opt_ansatz2)
 and the error measures (eq:errors_per_node_lagrange)."""
 import numpy as np
 
-from .nfft import matrix_A
+from .nfft import matrix_A, nfft_direct
 from .kernel import diag_D
 from .bopt import BOpt, bopt_closed, bopt_naive, matrix_F
 
@@ -93,3 +93,19 @@ def errors_per_node(fhat, fcheck, N):
 def rel_l2(a, b):
     """||a - b||_2 / ||b||_2."""
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def refine(B: BOpt, x, f, fhat, sweeps=1):
+    """Residual correction of an inverse-NFFT estimate, `sweeps` times:
+
+        fhat <- fhat + D^* F^* B_opt^* (f - A fhat),   A fhat by its direct sum (eq:nfft).
+
+    The modified adjoint NFFT (eq:approx_ansatz2) serves as an approximate left inverse of A
+    in a Richardson iteration for A fhat = f (eq:problem_infft; Sec. 1 surveys iterative
+    solvers of this system).  For data f = A fhat_true each sweep maps the error e to
+    (I - D^* F^* B_opt^* A) e."""
+    f = np.asarray(f, np.complex128)
+    fhat = np.asarray(fhat, np.complex128).copy()
+    for _ in range(sweeps):
+        fhat = fhat + infft_apply(B, f - nfft_direct(x, fhat))
+    return fhat

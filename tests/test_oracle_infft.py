@@ -69,3 +69,41 @@ def test_jittered_reconstruction_and_error_measures():
         assert e["rel_2"] <= e["abs_2"] / np.linalg.norm(p.fhat) * 1.0000001
     assert errs[1] < 1e-5
     assert errs[1] < errs[0]          # "errors ... decrease for large sizes of M"
+
+
+def test_refine_is_the_residual_error_map():
+    """One sweep maps the error e of noiseless data to (I - D^* F^* B_opt^* A) e, with every
+    matrix formed explicitly (eq:matrix_A, eq:matrix_F, eq:matrix_D, eq:matrix_B)."""
+    x = jittered(31, 64)
+    M, Ms = 16, 32
+    B = bopt.bopt_closed(x, M, 2.0, 3)
+    fh = complex_normal(32, M)
+    f = nfft.nfft_direct(x, fh)
+    Bt = np.diag(kernel.diag_D(M, Ms, "full")).conj().T @ bopt.matrix_F(M, Ms).conj().T @ B.dense().T
+    A = nfft.matrix_A(x, M)
+    start = infft.infft_apply(B, f) + 1e-3 * complex_normal(33, M)       # any starting estimate
+    e1 = infft.refine(B, x, f, start, 1) - fh
+    np.testing.assert_allclose(e1, (np.eye(M) - Bt @ A) @ (start - fh), atol=1e-13)
+    assert np.array_equal(infft.refine(B, x, f, start, 0), start)
+
+
+def test_refine_converges_on_jittered_nodes():
+    """Jittered nodes, N = 4M, m = 4: the inverse NFFT is accurate to ~1e-7, so each sweep
+    shrinks the error about 1e7-fold until fp64 rounding."""
+    x = jittered(34, 256)
+    fh = complex_normal(35, 64)
+    f = nfft.nfft_direct(x, fh)
+    B = bopt.bopt_closed(x, 64, 2.0, 4)
+    f0 = infft.infft_apply(B, f)
+    e = [infft.rel_l2(infft.refine(B, x, f, f0, k), fh) for k in range(3)]
+    assert 1e-9 < e[0] < 1e-5 and e[1] < 1e-12 and e[2] < 1e-14
+
+
+def test_refine_keeps_an_exact_inverse():
+    """sigma = 1, M = N equispaced, kernel full: the estimate fhat/(1 + tau) is corrected to
+    fhat up to tau^2."""
+    x = equispaced(32)
+    fh = complex_normal(36, 32)
+    f = nfft.nfft_direct(x, fh)
+    B = bopt.bopt_closed(x, 32, 1.0, 2, "full", 1e-12)
+    np.testing.assert_allclose(infft.refine(B, x, f, infft.infft_apply(B, f), 1), fh, atol=1e-14)
