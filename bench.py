@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--no-refine", action="store_true")
     return ap.parse_args()
 
 
@@ -483,6 +484,36 @@ def run_gpu(a):
                                       "bound": "hbm", "achieved": ach_b, "peak": peaks()[0], "unit": "GB/s",
                                       "frac": ach_b / peaks()[0], "algorithmic_bytes": ab_b}}
 
+    # ---- fp64 residual correction on the config-2 nodes: data of a trigonometric polynomial
+    # (the direct fp64 sum of random coefficients), the fp64 inverse NFFT and one or two sweeps
+    # fhat += D^* F^* B_opt^* (f - A fhat), errors against the true coefficients
+    refine = None
+    if not a.no_refine:
+        gen = torch.Generator(device=dev).manual_seed(31 + rank)
+        fh_true = torch.randn(a.M, dtype=torch.complex128, device=dev, generator=gen)
+        plan_r = g.infft_plan_create(a.M, a.N, 2.0, a.m)
+        g.infft_set_nodes(plan_r, x, stream)
+        g.infft_precompute(plan_r, stream)
+        f_true = g.infft_ndft_z(plan_r, fh_true, stream=stream)
+        est = g.infft_apply_z(plan_r, f_true, stream=stream)
+
+        def rel(v):
+            return float(torch.linalg.norm(v - fh_true) / torch.linalg.norm(fh_true))
+        errs = [rel(est)]
+        for _ in range(2):
+            g.infft_refine_z(plan_r, f_true, est, 1, stream)
+            errs.append(rel(est))
+        scratch = torch.empty_like(f_true)
+        t_ndft = timed(lambda: g.infft_ndft_z(plan_r, fh_true, out=scratch, stream=stream), reps=2, warm=1)
+        t_sweep = timed(lambda: g.infft_refine_z(plan_r, f_true, est, 1, stream), reps=2, warm=1)
+        t_apply_z = timed(lambda: g.infft_apply_z(plan_r, f_true, stream=stream), reps=10)
+        plan_r.close()
+        refine = {"workload": workload_name(a) + ", data f = A fhat of complex normal fhat (fp64 direct sum)",
+                  "rel_err_vs_true": {"fp64_infft": errs[0], "after_1_sweep": errs[1], "after_2_sweeps": errs[2]},
+                  "apply_z_ms": t_apply_z, "ndft_z_ms": t_ndft, "sweep_ms": t_sweep,
+                  "note": "A fhat by the direct fp64 sum (O(N M), fp64-pipe bound); a windowed fast NFFT would "
+                          "replace it"}
+
     # ---- 2-D tensor-product form (workload 4: radial trajectory of 512 spokes x 512
     # samples, M = 256 x 256, sigma = 2 per dimension, m = 4)
     two_d = None
@@ -576,6 +607,7 @@ def run_gpu(a):
         "underdetermined": under,
         "batched": batched,
         "two_d": two_d,
+        "refine": refine,
         "kernels": {name: {"launches": n, "ms_total": ms} for name, n, ms in kernels},
         "plan": {"nnz": info["nnz"], "max_column": info["max_column"], "fallback_columns": info["fallback_columns"]},
         "cpu_baseline": cpu,

@@ -379,6 +379,25 @@ infft_status infft2d_copy_plan_data(infft2d_plan_t plan, int32_t* col_offset, in
 /* Frees the plan (synchronises its device first). */
 infft_status infft2d_plan_destroy(infft2d_plan_t plan);
 
+/* ---- fp64 direct sum and residual correction ---------------------------------
+ * The trigonometric polynomial at the plan's nodes by its defining sum (eq:nfft),
+ *   f_j = sum_{k=-M/2}^{M/2-1} fhat_k e^{2 pi i k x_j},
+ * in fp64 (exponentials by complex rotation, restarted every 32 frequencies from an exactly
+ * reduced sincospi), O(N M) work.  fhat: M complex128, f: N complex128 in the caller's node
+ * order, both device pointers.  Requires infft_set_nodes. */
+infft_status infft_ndft_z(infft_plan_t plan, const double* fhat, double* f, infft_stream_t stream);
+
+/* Residual correction of an estimate fhat (in place), `sweeps` times (0 .. 64):
+ *   fhat <- fhat + D^* F^* B_opt^* (f - A fhat)
+ * with A fhat by infft_ndft_z and D^* F^* B_opt^* by infft_apply_z: the modified adjoint NFFT
+ * (eq:approx_ansatz2) as an approximate inverse of A in a Richardson iteration for A fhat = f
+ * (eq:problem_infft).  For data f = A fhat_true each sweep maps the error e to
+ * (I - D^* F^* B_opt^* A) e: on jittered nodes with N = 4M an estimate accurate to ~1e-7
+ * reaches ~1e-14 in one sweep.  f: N complex128, fhat: M complex128, device pointers; the
+ * plan's staging buffers hold the residual and the correction (no other call on the plan
+ * may run meanwhile).  Requires infft_precompute. */
+infft_status infft_refine_z(infft_plan_t plan, const double* f, double* fhat, int sweeps, infft_stream_t stream);
+
 /* Number of kernels this library has launched in the process so far. */
 int64_t infft_launch_count(void);
 

@@ -28,6 +28,7 @@ EXPORTED_SYMBOLS = (
     "infft_apply_many", "infft_apply_many_workspace",
     "infft2d_plan_create", "infft2d_set_nodes", "infft2d_precompute", "infft2d_apply", "infft2d_apply_z",
     "infft2d_get_info", "infft2d_copy_plan_data", "infft2d_plan_destroy",
+    "infft_ndft_z", "infft_refine_z",
 )
 
 
@@ -106,6 +107,8 @@ def library():
         "infft_batch_copy_problem": [P, I64, VP, VP, VP, VP, VP, VP],
         "infft_batch_destroy": [P],
         "infft_apply_many": [P, I64, VP, VP, VP, I64, VP],
+        "infft_ndft_z": [P, VP, VP, VP],
+        "infft_refine_z": [P, VP, VP, I32, VP],
         "infft2d_plan_create": [I64, I64, I64, D, I32, I32, D, ctypes.POINTER(P)],
         "infft2d_set_nodes": [P, VP, VP],
         "infft2d_precompute": [P, VP],
@@ -287,6 +290,24 @@ def infft_apply_z(plan, f, out=None, stream=None):
 
 def nfft_apply_z(plan, fhat, out=None, stream=None):
     return _apply(library().nfft_apply_z, plan, fhat, out, plan.N, "c128", stream)
+
+
+def infft_ndft_z(plan, fhat, out=None, stream=None):
+    """f = A fhat by the direct fp64 sum at the plan's nodes (device complex128 tensors)."""
+    keep = []
+    if out is None:
+        out = _empty_like(fhat, plan.N, "c128")
+    _check(library().infft_ndft_z(plan.handle, _as_ptr(fhat, "c128", keep), _as_ptr(out, "c128", keep),
+                                  _stream(stream, fhat, out)))
+    return out
+
+
+def infft_refine_z(plan, f, fhat, sweeps=1, stream=None):
+    """fhat <- fhat + D^* F^* B_opt^* (f - A fhat), `sweeps` times, in place (device complex128)."""
+    keep = []
+    _check(library().infft_refine_z(plan.handle, _as_ptr(f, "c128", keep), _as_ptr(fhat, "c128", keep),
+                                    int(sweeps), _stream(stream, f, fhat)))
+    return fhat
 
 
 def plan_destroy(plan):

@@ -332,6 +332,42 @@ infft_status infft_apply_many(infft_plan_t p, int64_t K, const float* f, float* 
     return INFFT_OK;
 }
 
+infft_status infft_ndft_z(infft_plan_t p, const double* fhat, double* f, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!fhat || !f) return fail(INFFT_EINVAL, "fhat and f must not be NULL");
+    if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_ndft_z before infft_set_nodes");
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(fhat) || !is_device_pointer(f))
+        return fail(INFFT_EINVAL, "infft_ndft_z takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = run_ndft_z(p, fhat, nullptr, f, s);
+    if (e != cudaSuccess) return cuda_fail(e, "direct sum");
+    return INFFT_OK;
+}
+
+infft_status infft_refine_z(infft_plan_t p, const double* f, double* fhat, int sweeps, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
+    if (sweeps < 0 || sweeps > 64) return fail(INFFT_EINVAL, "sweeps must be in [0, 64] (got %d)", sweeps);
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_refine_z before infft_precompute");
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(f) || !is_device_pointer(fhat))
+        return fail(INFFT_EINVAL, "infft_refine_z takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    double* r = (double*)p->stage_in;       // N complex128: the residual f - A fhat
+    double* d = (double*)p->stage_out;      // M complex128: its inverse NFFT
+    for (int it = 0; it < sweeps; ++it) {
+        cudaError_t e = run_ndft_z(p, fhat, f, r, s);
+        if (e != cudaSuccess) return cuda_fail(e, "residual");
+        const infft_status st = apply_impl<double>(p, r, d, stream);
+        if (st != INFFT_OK) return st;
+        if ((e = run_axpy_z(p, fhat, d, (int)p->M, s)) != cudaSuccess) return cuda_fail(e, "update");
+    }
+    return INFFT_OK;
+}
+
 infft_status nfft_apply(infft_plan_t p, const float* fhat, float* f, infft_stream_t stream) {
     return nfft_impl<float>(p, fhat, f, stream);
 }

@@ -175,3 +175,7 @@ cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cu
 bool fft2d_r8_supported(int log1, int log2, int M2);
 cudaError_t fft2d_adjoint_r8(const float2* g, float2* Y, float2* fhat, int log1, int log2, int M1, int M2, int sym,
                              cudaStream_t s);
+// refine.cu: out = A fhat by the direct fp64 sum over the plan's nodes (caller order), or
+// resid - A fhat when resid is given (N complex128 each); y += d (n complex128)
+cudaError_t run_ndft_z(Plan* p, const void* fhat, const void* resid, void* out, cudaStream_t s);
+cudaError_t run_axpy_z(Plan* p, void* y, const void* d, int n, cudaStream_t s);
