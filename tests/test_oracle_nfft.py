@@ -79,3 +79,24 @@ def test_dense_lsq_normal_equations():
     sol = nfft.dense_lsq_inverse(x, f, 12)
     A = nfft.matrix_A(x, 12)
     assert np.abs(A.conj().T @ (A @ sol - f)).max() < 1e-11
+
+
+def test_direct_sum_with_reduced_phases():
+    """The reduced-phase sum equals the plain one at small M and, at M = 2^16, a 50-digit
+    evaluation (mpmath) at a few nodes, where the plain sum's angles lose ~1e-11."""
+    mp = pytest.importorskip("mpmath")
+    x = iid_uniform(91, 40)
+    fh = complex_normal(92, 64)
+    np.testing.assert_allclose(nfft.nfft_direct_reduced(x, fh), nfft.nfft_direct(x, fh), rtol=0, atol=1e-13)
+    M = 1 << 16
+    fh = complex_normal(93, M)
+    xs = iid_uniform(94, 3)
+    mp.mp.dps = 50
+    ks = np.arange(-M // 2, M // 2)
+    for xj in xs:
+        X = mp.mpf(float(xj))
+        acc = mp.mpc(0)
+        for k, c in zip(ks[::256], fh[::256]):          # a strided subset of the terms keeps it fast
+            acc += mp.mpc(c.real, c.imag) * mp.expjpi(2 * k * X)
+        part = nfft.nfft_direct_reduced(np.array([xj]), np.where(np.arange(M) % 256 == 0, fh, 0))[0]
+        assert abs(complex(acc) - part) <= 1e-13 * max(1.0, abs(complex(acc)))
