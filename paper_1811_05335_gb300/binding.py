@@ -28,7 +28,7 @@ EXPORTED_SYMBOLS = (
     "infft_apply_many", "infft_apply_many_workspace",
     "infft2d_plan_create", "infft2d_set_nodes", "infft2d_precompute", "infft2d_apply", "infft2d_apply_z",
     "infft2d_get_info", "infft2d_copy_plan_data", "infft2d_plan_destroy",
-    "infft_ndft_z", "infft_refine_z",
+    "infft_ndft_z", "infft_refine_z", "infft_nfft_kb_z",
 )
 
 
@@ -109,6 +109,7 @@ def library():
         "infft_apply_many": [P, I64, VP, VP, VP, I64, VP],
         "infft_ndft_z": [P, VP, VP, VP],
         "infft_refine_z": [P, VP, VP, I32, VP],
+        "infft_nfft_kb_z": [P, VP, VP, VP],
         "infft2d_plan_create": [I64, I64, I64, D, I32, I32, D, ctypes.POINTER(P)],
         "infft2d_set_nodes": [P, VP, VP],
         "infft2d_precompute": [P, VP],
@@ -299,6 +300,16 @@ def infft_ndft_z(plan, fhat, out=None, stream=None):
         out = _empty_like(fhat, plan.N, "c128")
     _check(library().infft_ndft_z(plan.handle, _as_ptr(fhat, "c128", keep), _as_ptr(out, "c128", keep),
                                   _stream(stream, fhat, out)))
+    return out
+
+
+def infft_nfft_kb_z(plan, fhat, out=None, stream=None):
+    """f ~ A fhat by the windowed fp64 NFFT (Kaiser-Bessel, sigma >= 2; device complex128 tensors)."""
+    keep = []
+    if out is None:
+        out = _empty_like(fhat, plan.N, "c128")
+    _check(library().infft_nfft_kb_z(plan.handle, _as_ptr(fhat, "c128", keep), _as_ptr(out, "c128", keep),
+                                     _stream(stream, fhat, out)))
     return out
 
 

@@ -346,6 +346,23 @@ infft_status infft_ndft_z(infft_plan_t p, const double* fhat, double* f, infft_s
     return INFFT_OK;
 }
 
+infft_status infft_nfft_kb_z(infft_plan_t p, const double* fhat, double* f, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!fhat || !f) return fail(INFFT_EINVAL, "fhat and f must not be NULL");
+    if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_nfft_kb_z before infft_set_nodes");
+    if (!nfft_kb_supported(p))
+        return fail(INFFT_EUNSUPPORTED, "infft_nfft_kb_z needs sigma >= 2 and M_sigma >= 96 (M_sigma = %lld)",
+                    (long long)p->Ms);
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(fhat) || !is_device_pointer(f))
+        return fail(INFFT_EINVAL, "infft_nfft_kb_z takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = run_nfft_kb_z(p, fhat, nullptr, f, p->stage_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "windowed NFFT");
+    return INFFT_OK;
+}
+
 infft_status infft_refine_z(infft_plan_t p, const double* f, double* fhat, int sweeps, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
     if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
@@ -358,8 +375,9 @@ infft_status infft_refine_z(infft_plan_t p, const double* f, double* fhat, int s
     p->last_stream = s;
     double* r = (double*)p->stage_in;       // N complex128: the residual f - A fhat
     double* d = (double*)p->stage_out;      // M complex128: its inverse NFFT
+    const bool fast = nfft_kb_supported(p);
     for (int it = 0; it < sweeps; ++it) {
-        cudaError_t e = run_ndft_z(p, fhat, f, r, s);
+        cudaError_t e = fast ? run_nfft_kb_z(p, fhat, f, r, d, s) : run_ndft_z(p, fhat, f, r, s);
         if (e != cudaSuccess) return cuda_fail(e, "residual");
         const infft_status st = apply_impl<double>(p, r, d, stream);
         if (st != INFFT_OK) return st;

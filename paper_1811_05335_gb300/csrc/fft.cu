@@ -568,6 +568,10 @@ cudaError_t run_fft_full_forward_z(Plan* p, const void* in, void* out, double sc
     return fft_forward_on<double>(p, in, out, (int)p->Ms, scale, 0, s);
 }
 
+cudaError_t run_fft_forward_band_z(Plan* p, const void* in, void* out, cudaStream_t s) {
+    return fft_forward_on<double>(p, in, out, (int)p->M, 1.0, 0, s);
+}
+
 // D^* F^* of K grids (grid: K x M_sigma, work: K x M_sigma, fhat: K x M), fp32, M_sigma > 2048.
 cudaError_t run_fft_adjoint_many(Plan* p, const void* grid, void* work, void* fhat, int K, cudaStream_t s) {
     return fft_adjoint_r8((const float2*)grid, (float2*)work, (float2*)fhat, p->logMs, (int)p->M,

@@ -167,6 +167,8 @@ cudaError_t run_fft_adjoint_many(Plan* p, const void* grid, void* work, void* fh
 template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s);
 // fft.cu: out_p = scale * sum_{k=-Ms/2}^{Ms/2-1} in[k + Ms/2] exp(2 pi i k (p - Ms/2)/Ms), fp64, all bins
 cudaError_t run_fft_full_forward_z(Plan* p, const void* in, void* out, double scale, cudaStream_t s);
+// fft.cu: out_p = sum_{k=-M/2}^{M/2-1} in[k + M/2] exp(2 pi i k (p - Ms/2)/Ms), fp64, all Ms bins
+cudaError_t run_fft_forward_band_z(Plan* p, const void* in, void* out, cudaStream_t s);
 // grad.cu: gx = dL/dx (caller order) for f (complex64, device) and w = dL/dfhat (complex64, device)
 cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cudaStream_t s);
 // fft.cu: the fp32 2-D transform of the tensor-product plan: grid g (2^log1 x 2^log2 complex64,
@@ -178,4 +180,8 @@ cudaError_t fft2d_adjoint_r8(const float2* g, float2* Y, float2* fhat, int log1,
 // refine.cu: out = A fhat by the direct fp64 sum over the plan's nodes (caller order), or
 // resid - A fhat when resid is given (N complex128 each); y += d (n complex128)
 cudaError_t run_ndft_z(Plan* p, const void* fhat, const void* resid, void* out, cudaStream_t s);
+// refine.cu: the same with the windowed NFFT (Kaiser-Bessel, Sec. 2.1) when nfft_kb_supported(p);
+// scratch: p->grid, p->work and `coef` (M complex128)
+bool nfft_kb_supported(const Plan* p);
+cudaError_t run_nfft_kb_z(Plan* p, const void* fhat, const void* resid, void* out, void* coef, cudaStream_t s);
 cudaError_t run_axpy_z(Plan* p, void* y, const void* d, int n, cudaStream_t s);
