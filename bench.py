@@ -156,7 +156,7 @@ def peaks():
 
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_PER_SM = 4          # 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
-KAPPA_FLOPS = 40                       # fp64 flops of one closed-form kernel value
+KAPPA_FLOPS = 40                       # fp64 flops of one closed-form kernel value: a sincospi and a sinpi (~17 each), products, a division
 
 
 def sources_sha1(paths):
