@@ -607,6 +607,9 @@ INFFT_D void panel_step(double* __restrict__ A, double* __restrict__ r, int n, i
         const int a = e / PB, b = e % PB;
         if (a < w && b <= a) A[trow(kb + a) + kb + b] = D[a * (PB + 1) + b];
     }
+    // the diagonal block is read through a volatile view: loaded at each use from shared
+    // memory (a broadcast) rather than held in 136 registers across the row loop
+    const volatile double* Dv = D;
     for (int i = kb + w + tid; i < n; i += blockDim.x) {
         double v[PB];
         double* row = A + trow(i) + kb;
@@ -618,8 +621,8 @@ INFFT_D void panel_step(double* __restrict__ A, double* __restrict__ r, int n, i
             if (b < w) {
                 double s = v[b];
 #pragma unroll
-                for (int c = 0; c < b; ++c) s = fma(-v[c], D[b * (PB + 1) + c], s);
-                v[b] = s * D[b * (PB + 1) + b];
+                for (int c = 0; c < b; ++c) s = fma(-v[c], Dv[b * (PB + 1) + c], s);
+                v[b] = s * Dv[b * (PB + 1) + b];
                 acc = fma(-v[b], ypan[b], acc);
             }
         }
@@ -715,8 +718,8 @@ INFFT_D void back_solve(const double* __restrict__ A, double* __restrict__ r, in
 
 size_t large_smem(int nmax) { return (size_t)nmax * (sizeof(NodeK) + sizeof(double)); }
 
-// one CTA per column of 129 .. GIANT_N nodes, largest first (atomic ticket)
-__global__ void __launch_bounds__(LARGE_THREADS, 1)
+// one CTA per column of 129 .. GIANT_N nodes, largest first (atomic ticket), two CTAs per SM
+__global__ void __launch_bounds__(LARGE_THREADS, 2)
 k2_solve_large(const double2* __restrict__ x, const int32_t* __restrict__ col_off, const int32_t* __restrict__ col_node,
                const int32_t* __restrict__ order, int Ms1, int Ms2, K2 kp, double mu0, double* __restrict__ scratch,
                size_t slot_doubles, int32_t* __restrict__ ticket, double* __restrict__ w64, float* __restrict__ w32,
@@ -1401,7 +1404,7 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
         // the shared-memory layout keeps 16-byte alignment with an even nmax
         const int nmax = (std::min(p->max_column, GIANT_N) + 1) & ~1;
         const size_t slot = (size_t)nmax * (nmax + 1) / 2;
-        const int slots = std::max(1, std::min(sms, cnt[C2_LIST0 + 3]));
+        const int slots = std::max(1, std::min(2 * sms, cnt[C2_LIST0 + 3]));   // two CTAs per SM
         if (p->scratch_doubles < slot * slots) {
             if (p->scratch) cudaFree(p->scratch);
             p->scratch = nullptr;
