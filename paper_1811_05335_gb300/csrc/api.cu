@@ -143,6 +143,15 @@ template <typename T> infft_status nfft_impl(infft_plan_t p, const T* fhat, T* f
 
 }  // namespace
 
+int64_t first_bad_coordinate(const double* x, int64_t n) {
+    int64_t bad = 0;
+    for (int64_t j = 0; j < n; ++j) bad += !((x[j] >= -0.5) & (x[j] < 0.5));
+    if (!bad) return -1;
+    for (int64_t j = 0; j < n; ++j)
+        if (!(x[j] >= -0.5 && x[j] < 0.5)) return j;
+    return -1;
+}
+
 infft_status set_error(infft_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -253,10 +262,8 @@ infft_status infft_set_nodes(infft_plan_t p, const double* x, infft_stream_t str
     if (is_device_pointer(x)) {
         e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double), cudaMemcpyDeviceToDevice, s);
     } else {
-        for (int64_t j = 0; j < p->N; ++j) {
-            if (!(std::isfinite(x[j]) && x[j] >= -0.5 && x[j] < 0.5))
-                return fail(INFFT_EINVAL, "node x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
-        }
+        const int64_t j = first_bad_coordinate(x, p->N);
+        if (j >= 0) return fail(INFFT_EINVAL, "node x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
         e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "copy nodes");

@@ -788,9 +788,8 @@ infft_status infft_batch_set_nodes(infft_batch_t b, const double* x, infft_strea
     if (on_device(x)) {
         e = cudaMemcpyAsync(b->x_all, x, b->sumN * sizeof(double), cudaMemcpyDeviceToDevice, s);
     } else {
-        for (int64_t j = 0; j < b->sumN; ++j)
-            if (!(std::isfinite(x[j]) && x[j] >= -0.5 && x[j] < 0.5))
-                return set_error(INFFT_EINVAL, "node x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
+        const int64_t j = first_bad_coordinate(x, b->sumN);
+        if (j >= 0) return set_error(INFFT_EINVAL, "node x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
         e = cudaMemcpyAsync(b->x_all, x, b->sumN * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     if (e != cudaSuccess) return cuda_err(e, "copy nodes");

@@ -122,6 +122,11 @@ struct Carver {
 // single-problem applies, staging and node gradient.
 void plan_layout(Plan* p, Carver& c, bool batch_member);
 
+// Host check of node coordinates: the index of the first one outside [-1/2, 1/2) or not finite
+// (NaN fails both comparisons), or -1.  A branch-free count runs first, which the compiler
+// vectorises (a loop that exits at the first bad value does not vectorise).
+int64_t first_bad_coordinate(const double* x, int64_t n);
+
 // Records a failure for infft_last_error() and returns st.
 infft_status set_error(infft_status st, const char* fmt, ...);
 // Adds to the library's launch counter (infft_launch_count) for launches made without a plan.

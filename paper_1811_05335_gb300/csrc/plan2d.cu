@@ -1557,9 +1557,9 @@ infft_status infft2d_set_nodes(infft2d_plan_t p, const double* x, infft_stream_t
     if (on_device2(x)) {
         e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     } else {
-        for (int64_t j = 0; j < 2 * p->N; ++j)
-            if (!(std::isfinite(x[j]) && x[j] >= -0.5 && x[j] < 0.5))
-                return fail2(INFFT_EINVAL, "node coordinate x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
+        const int64_t j = first_bad_coordinate(x, 2 * p->N);
+        if (j >= 0)
+            return fail2(INFFT_EINVAL, "node coordinate x[%lld] = %.17g is not in [-1/2, 1/2)", (long long)j, x[j]);
         e = cudaMemcpyAsync(p->x, x, p->N * sizeof(double2), cudaMemcpyHostToDevice, s);
     }
     if (e != cudaSuccess) return cuda_fail2(e, "copy nodes");
