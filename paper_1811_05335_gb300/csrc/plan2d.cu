@@ -469,12 +469,18 @@ __global__ void __launch_bounds__(NMAX) k2_solve_small(const double2* __restrict
         double mu = mu0, ysq = 0.0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-            if (i < n) {
-                const NodeK xi = xl[i];
-                for (int j = 0; j < i; ++j) A[trow(i) + j] = re_kappa2(xi, xl[j], kp);
-                A[trow(i) + i] = kp.diag + mu;
-                r[i] = re_kappa2(cp, xi, kp);
+            // the packed triangle's entries are spread evenly over the CTA's threads (a thread
+            // per row would leave the short rows' threads idle); row of entry e by an fp32 square
+            // root, corrected exactly
+            const int ntri = n * (n + 1) / 2;
+            for (int e = i; e < ntri; e += NMAX) {
+                int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                while (trow(a + 1) <= e) ++a;
+                while (trow(a) > e) --a;
+                const int c = e - trow(a);
+                A[e] = (a == c) ? kp.diag + mu : re_kappa2(xl[a], xl[c], kp);
             }
+            if (i < n) r[i] = re_kappa2(cp, xl[i], kp);
             __syncthreads();
             ysq = 0.0;
             bool failed = false;
