@@ -154,7 +154,12 @@ def peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-SM_COUNT = 152
+def sm_count():
+    """Multiprocessor count of the current device (queried, not assumed)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 FP64_FLOP_PER_CLK_PER_SM = 4          # 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 KAPPA_FLOPS = 40                       # fp64 flops of one closed-form kernel value: a sincospi and a sinpi (~17 each), products, a division
 
@@ -446,7 +451,7 @@ def run_gpu(a):
         mom_ms = ukern.get("under_moments", float("nan"))
         # one term of a node moment: complex rotate (4 mul, 2 add) + complex accumulate (2 add)
         mom_flops = 8.0 * Nu * Mu
-        peak64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
+        peak64 = sm_count() * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
         ach = mom_flops / (mom_ms / 1e3) / 1e12
         under = {"workload": f"1D jittered nodes N={Nu} M={Mu} sigma=2 m=4 (underdetermined, M = 4N)",
                  "precompute_ms": t_pre, "apply_ms": t_app, "apply_nodes_per_s": Nu / (t_app / 1e3),
@@ -543,7 +548,7 @@ def run_gpu(a):
         cols2 = np.diff(g.infft2d_copy_plan_data(q2, weights=False)["col_offset"].astype(np.int64))
         q2.close()
         fl2 = lsq_flops_2d(cols2)
-        peak64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
+        peak64 = sm_count() * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
         ach_pre2 = fl2 / (t_pre2 / 1e3) / 1e12
         M2d = w2.M1 * w2.M2
         ab2 = 8 * w2.N + 4 * info2["nnz"] + 8 * M2d          # f, weights, fhat
@@ -577,7 +582,7 @@ def run_gpu(a):
         # all columns are solved by the warp tiers at this workload (|I(l)| <= 64)
         fl = lsq_flops(counts)
         lsq_ms = sum(ms for name, (n, ms) in ktab.items() if name.startswith("lsq")) / dom_n
-        peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+        peak = sm_count() * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
         ach = fl / (lsq_ms / 1e3) / 1e12
         roofline = {"kernel": "lsq (B_opt precompute, all tiers)", "bound": "alu", "achieved": ach,
                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,

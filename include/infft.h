@@ -121,6 +121,39 @@ infft_status infft_precompute(infft_plan_t plan, infft_stream_t stream);
  * Requires infft_precompute. */
 infft_status infft_apply(infft_plan_t plan, const float* f, float* fhat, infft_stream_t stream);
 
+/* infft_apply with the samples given in the plan's sorted node order: f_sorted[i] =
+ * f[perm[i]] (infft_sort_values forms it; infft_copy_plan_data exports perm).  The
+ * spreading then reads the samples without the permutation.  Device pointers only
+ * (host pointers: INFFT_EINVAL); result as infft_apply's (the same arithmetic in the same
+ * order).  Requires infft_precompute. */
+infft_status infft_apply_sorted(infft_plan_t plan, const float* f_sorted, float* fhat, infft_stream_t stream);
+
+/* f_sorted[i] = f[perm[i]], i = 0 .. N-1 (complex64, device pointers, distinct buffers):
+ * the samples in the order of the plan's sorted nodes.  Requires infft_set_nodes. */
+infft_status infft_sort_values(infft_plan_t plan, const float* f, float* f_sorted, infft_stream_t stream);
+
+/* Tile shapes of the fp32 apply for 2^12 <= M_sigma <= 2^21 (two launches: the spreading
+ * fused with pass A of the four-step FFT M_sigma = N1 N2, then pass B with D^*).  Shape
+ * `id` spreads, per CTA, runs of `columns_per_run` consecutive grid points at N1 =
+ * 2^log2_N1 positions.  All shapes compute the same fhat up to fp32 rounding.
+ * infft_set_apply_config(plan, -1) restores the default rule (512 grid points per CTA
+ * for m <= 6, 256 beyond); an id whose N2 = M_sigma / N1 lies outside [2^6, 2^12] returns
+ * INFFT_EINVAL.  infft_get_apply_config returns the shape the next apply uses (-1 when the
+ * plan's M_sigma takes the three-launch path: spreading, pass A, pass B). */
+int32_t infft_apply_config_count(void);
+infft_status infft_apply_config_shape(int32_t id, int32_t* log2_N1, int32_t* columns_per_run);
+infft_status infft_set_apply_config(infft_plan_t plan, int32_t id);
+int32_t infft_get_apply_config(infft_plan_t plan);
+
+/* Autotuning of the tile shape: times `repeats` applies (after two untimed ones) of every
+ * valid shape on the plan's own B_opt with CUDA events on `stream` (the data vector is
+ * the plan's zeroed staging buffer), keeps the fastest for the plan and returns it.
+ * ms_out, when not NULL, receives infft_apply_config_count() average times in ms (-1
+ * for shapes not valid at this M_sigma).  Synchronises `stream`; allocates nothing.
+ * Requires infft_precompute; plans on the three-launch path return INFFT_EUNSUPPORTED. */
+infft_status infft_tune_apply(infft_plan_t plan, int32_t repeats, float* ms_out, int32_t* best,
+                              infft_stream_t stream);
+
 /* infft_apply for K data vectors sampled at the plan's nodes (the "fixed nodes, several
  * problems" use of the precomputed B_opt, Sec. 1 and Sec. 3.2.2), in one launch per step:
  *   f    : K x N complex64 on the device, vector k at k N (caller's node order), read only;
@@ -297,13 +330,28 @@ infft_status infft_batch_destroy(infft_batch_t batch);
  *   return INFFT_EUNSUPPORTED; host pointers return INFFT_EINVAL).
  * Allocates nothing: its scratch is one static device array of 2^20 complex64
  * (8 MiB) that every GPU loading the library holds until the process exits.  The
- * first call on a device looks up that array's device address (once per device,
- * with the device current); make that first call before any stream capture.
+ * first call on a device looks up that array's device address (with the device
+ * current) and later calls reuse it; make that first call before any stream
+ * capture.  A call that finds a different context current on the device than the
+ * one the address was taken in (after cudaDeviceReset) looks the address up again,
+ * so that call, too, belongs outside a capture.
  * Every call shares the array, so calls that may overlap on the GPU (different
  * streams, or different host threads) race: serialise them.  The array needs no
  * clearing: each call overwrites every element it reads. */
 infft_status infft_fft_deconv_noalloc(const float* grid, int64_t M, int64_t M_sigma, int kernel,
                                       float* fhat, infft_stream_t stream);
+
+/* ---- diagnostics -------------------------------------------------------------
+ * The paper has no counterpart of these calls.  infft_fp64_fma_probe measures what the
+ * fp64-bound precompute is compared against: it launches 8 CTAs per SM of 256 threads,
+ * each advancing 8 independent fp64 FMA recurrences for `iters` steps, on `stream`, and
+ * stores one double per thread into `sink` (device memory, at least
+ * infft_fp64_fma_probe_sink_len() doubles, owned by the caller).  *flops receives the
+ * flop count of the launch (2 per FMA); time the launch with events on `stream` to get the
+ * rate.  infft_fp64_fma_probe_sink_len returns -1 when no device is usable. */
+infft_status infft_fp64_fma_probe(int64_t iters, double* sink, int64_t sink_len, double* flops,
+                                  infft_stream_t stream);
+int64_t infft_fp64_fma_probe_sink_len(void);
 
 /* ---- two-dimensional tensor-product form ----------------------------------
  * The paper treats one dimension and leaves higher dimensions open (Sec. 5).

@@ -9,7 +9,8 @@ from .binding import (  # noqa: F401
     infft_apply, nfft_apply, infft_apply_z, nfft_apply_z, plan_destroy, infft_get_info,
     infft_copy_plan_data, infft_profile, infft_profile_read, infft_launch_count, infft_version,
     infft_fft_deconv_noalloc, infft_grad_nodes, infft_plan_create_ansatz, infft_ndft_z, infft_refine_z,
-    infft_nfft_kb_z,
+    infft_nfft_kb_z, infft_apply_sorted, infft_sort_values, infft_apply_configs, infft_set_apply_config,
+    infft_get_apply_config, infft_tune_apply, infft_fp64_fma_probe, infft_fp64_fma_probe_sink_len,
     Batch, infft_batch_create, infft_batch_set_nodes, infft_batch_precompute, infft_batch_apply,
     infft_batch_get_info, infft_batch_copy_problem, infft_apply_many, infft_apply_many_workspace,
     EXPORTED_SYMBOLS, KERNEL_FULL, KERNEL_SYM, ANSATZ_UNDERDETERMINED, ANSATZ_OVERDETERMINED,

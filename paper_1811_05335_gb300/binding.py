@@ -29,6 +29,9 @@ EXPORTED_SYMBOLS = (
     "infft2d_plan_create", "infft2d_set_nodes", "infft2d_precompute", "infft2d_apply", "infft2d_apply_z",
     "infft2d_get_info", "infft2d_copy_plan_data", "infft2d_plan_destroy",
     "infft_ndft_z", "infft_refine_z", "infft_nfft_kb_z",
+    "infft_apply_sorted", "infft_sort_values", "infft_apply_config_count", "infft_apply_config_shape",
+    "infft_set_apply_config", "infft_get_apply_config", "infft_tune_apply",
+    "infft_fp64_fma_probe", "infft_fp64_fma_probe_sink_len",
 )
 
 
@@ -118,6 +121,12 @@ def library():
         "infft2d_get_info": [P, ctypes.POINTER(_Info2D)],
         "infft2d_copy_plan_data": [P, VP, VP, VP, VP],
         "infft2d_plan_destroy": [P],
+        "infft_apply_sorted": [P, VP, VP, VP],
+        "infft_sort_values": [P, VP, VP, VP],
+        "infft_apply_config_shape": [I32, ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "infft_set_apply_config": [P, I32],
+        "infft_tune_apply": [P, I32, VP, ctypes.POINTER(I32), VP],
+        "infft_fp64_fma_probe": [I64, VP, I64, ctypes.POINTER(D), VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -125,6 +134,12 @@ def library():
         fn.restype = ctypes.c_int
     lib.infft_apply_many_workspace.restype = ctypes.c_int64
     lib.infft_apply_many_workspace.argtypes = [P, I64]
+    lib.infft_fp64_fma_probe_sink_len.restype = ctypes.c_int64
+    lib.infft_fp64_fma_probe_sink_len.argtypes = []
+    lib.infft_apply_config_count.restype = ctypes.c_int
+    lib.infft_apply_config_count.argtypes = []
+    lib.infft_get_apply_config.restype = ctypes.c_int
+    lib.infft_get_apply_config.argtypes = [P]
     lib.infft_launch_count.restype = ctypes.c_int64
     lib.infft_launch_count.argtypes = []
     lib.infft_last_error.restype = ctypes.c_char_p
@@ -264,6 +279,48 @@ def nfft_apply(plan, fhat, out=None, stream=None):
     return _apply(library().nfft_apply, plan, fhat, out, plan.N, "c64", stream)
 
 
+def infft_apply_sorted(plan, f_sorted, out=None, stream=None):
+    """fhat = D^* F^* B_opt^* f from samples in the plan's sorted node order (complex64, device)."""
+    return _apply(library().infft_apply_sorted, plan, f_sorted, out, plan.M, "c64", stream)
+
+
+def infft_sort_values(plan, f, out=None, stream=None):
+    """f_sorted[i] = f[perm[i]] (complex64 device tensors)."""
+    return _apply(library().infft_sort_values, plan, f, out, plan.N, "c64", stream)
+
+
+def infft_apply_configs():
+    """[(log2 N1, columns per run)] of every tile shape of the fp32 apply, by id."""
+    lib = library()
+    out = []
+    for i in range(lib.infft_apply_config_count()):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib.infft_apply_config_shape(i, ctypes.byref(a), ctypes.byref(b)))
+        out.append((a.value, b.value))
+    return out
+
+
+def infft_set_apply_config(plan, config):
+    """Tile shape id for the plan's fp32 apply (-1: the default rule)."""
+    _check(library().infft_set_apply_config(plan.handle, int(config)))
+
+
+def infft_get_apply_config(plan):
+    """Tile shape id the next apply uses (-1: the three-launch path)."""
+    return int(library().infft_get_apply_config(plan.handle))
+
+
+def infft_tune_apply(plan, repeats=20, stream=None):
+    """Times every valid tile shape on the plan and keeps the fastest: (best id, [ms per id])."""
+    lib = library()
+    n = lib.infft_apply_config_count()
+    ms = (ctypes.c_float * n)()
+    best = ctypes.c_int(-1)
+    _check(lib.infft_tune_apply(plan.handle, int(repeats), ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best),
+                                _stream(stream)))
+    return best.value, [float(v) for v in ms]
+
+
 def infft_apply_many_workspace(plan, K):
     """Bytes of device workspace infft_apply_many needs for K vectors."""
     return int(library().infft_apply_many_workspace(plan.handle, int(K)))
@@ -368,12 +425,17 @@ def infft_profile_read(plan):
 def infft_fft_deconv_noalloc(grid, M, out=None, kernel="full", stream=None):
     """fhat = D^* F^* grid (complex64, device tensors) without any allocation in the
     library (see include/infft.h); `out` is allocated here by torch when not given."""
+    import torch
     keep = []
     if out is None:
         out = _empty_like(grid, M, "c64")
+    if isinstance(grid, torch.Tensor) and isinstance(out, torch.Tensor) and grid.device != out.device:
+        raise InfftError(1, f"grid ({grid.device}) and out ({out.device}) must be on the same device")
     k = _KERNELS.get(kernel, kernel)
-    _check(library().infft_fft_deconv_noalloc(_as_ptr(grid, "c64", keep), int(M), int(grid.shape[0]), int(k),
-                                              _as_ptr(out, "c64", keep), _stream(stream, grid, out)))
+    # the library takes its scratch array on the current device: make grid's device current
+    with torch.cuda.device(grid.device if isinstance(grid, torch.Tensor) and grid.is_cuda else None):
+        _check(library().infft_fft_deconv_noalloc(_as_ptr(grid, "c64", keep), int(M), int(grid.shape[0]), int(k),
+                                                  _as_ptr(out, "c64", keep), _stream(stream, grid, out)))
     return out
 
 
@@ -386,6 +448,20 @@ def infft_grad_nodes(plan, f, w, out=None, stream=None):
     _check(library().infft_grad_nodes(plan.handle, _as_ptr(f, "c64", keep), _as_ptr(w, "c64", keep),
                                       _as_ptr(out, "f64", keep), _stream(stream, f, w, out)))
     return out
+
+
+def infft_fp64_fma_probe(iters, sink, stream=None):
+    """Launches the fp64 FMA throughput probe on `stream` (sink: float64 CUDA tensor of at least
+    infft_fp64_fma_probe_sink_len() elements); returns the launch's flop count."""
+    keep = []
+    flops = ctypes.c_double()
+    _check(library().infft_fp64_fma_probe(int(iters), _as_ptr(sink, "f64", keep), int(sink.numel()),
+                                          ctypes.byref(flops), _stream(stream, sink)))
+    return flops.value
+
+
+def infft_fp64_fma_probe_sink_len():
+    return int(library().infft_fp64_fma_probe_sink_len())
 
 
 def infft_launch_count():

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIBNAME = "libinfft_gb300.so"
-SOURCES = ["api.cu", "pattern.cu", "lsq.cu", "under.cu", "spread.cu", "fft.cu", "grad.cu", "batch.cu", "plan2d.cu", "refine.cu"]
+SOURCES = ["api.cu", "pattern.cu", "lsq.cu", "under.cu", "spread.cu", "fft.cu", "apply.cu", "grad.cu", "batch.cu", "plan2d.cu", "refine.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default",
          "--expt-relaxed-constexpr"]

@@ -104,8 +104,14 @@ template <typename T> infft_status apply_impl(infft_plan_t p, const T* f, T* fha
     }
     const bool host_out = !is_device_pointer(fhat);
     void* fout = host_out ? p->stage_out : (void*)fhat;
-    if ((e = run_spread<T>(p, fin, s)) != cudaSuccess) return cuda_fail(e, "spread");
-    if ((e = run_fft_adjoint<T>(p, fout, s)) != cudaSuccess) return cuda_fail(e, "fft");
+    if (sizeof(T) == 4 && apply2_default_config(p) >= 0) {
+        // two launches: spreading fused with FFT pass A, then pass B with D
+        if ((e = run_apply2(p, (const float2*)fin, false, (float2*)fout, s)) != cudaSuccess)
+            return cuda_fail(e, "apply");
+    } else {
+        if ((e = run_spread<T>(p, fin, s)) != cudaSuccess) return cuda_fail(e, "spread");
+        if ((e = run_fft_adjoint<T>(p, fout, s)) != cudaSuccess) return cuda_fail(e, "fft");
+    }
     if (host_out) {
         if ((e = cudaMemcpyAsync(fhat, p->stage_out, p->M * csz, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_fail(e, "copy fhat to host");
@@ -177,6 +183,16 @@ void plan_layout(Plan* p, Carver& c, bool member) {
     c.take(p->w64, p->nnz_cap); c.take(p->w32, p->nnz_cap); c.take(p->J, Ms > N ? Ms : N); c.take(p->wide, Ms);
     if (member) return;
     c.take(p->gterm, p->nnz_cap);
+    c.take(p->wlo, p->nnz_cap);
+    {
+        const int64_t tiles = apply2_max_tiles(p) > 0 ? apply2_max_tiles(p) : 1;
+        c.take(p->lay_hdr, tiles);
+        c.take(p->lay_cdesc, Ms);
+        c.take(p->lay_w, p->nnz_cap + 4 * tiles);
+        c.take(p->lay_list, apply2_list_capacity(p));
+        c.take(p->lay_list_sorted, apply2_list_capacity(p));
+        c.take(p->lay_tmp, 5 * tiles);
+    }
     if (p->ansatz == INFFT_ANSATZ_UNDERDETERMINED) {
         double2 *ustep, *upart, *umom, *uS;
         c.take(ustep, N); c.take(upart, (int64_t)under_moment_chunks(N) * M); c.take(umom, M);
@@ -227,8 +243,15 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
                     ansatz);
     if (ansatz == INFFT_ANSATZ_UNDERDETERMINED && 2 * m + 1 > UNDER_NMAX)
         return fail(INFFT_EUNSUPPORTED, "underdetermined case: 2m+1 = %d exceeds %d", 2 * m + 1, UNDER_NMAX);
+    int dev = 0, sms = 0;
+    cudaError_t qe = cudaGetDevice(&dev);
+    if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (qe != cudaSuccess || sms <= 0)
+        return fail(INFFT_ECUDA, "cannot query the device's multiprocessor count: %s",
+                    qe != cudaSuccess ? cudaGetErrorString(qe) : "count <= 0");
     Plan* p = new Plan();
-    cudaGetDevice(&p->device);
+    p->device = dev;
+    p->sms = sms;
     p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
     p->ansatz = ansatz;
     p->logMs = logMs;
@@ -268,6 +291,8 @@ infft_status infft_set_nodes(infft_plan_t p, const double* x, infft_stream_t str
     }
     if (e != cudaSuccess) return cuda_fail(e, "copy nodes");
     p->precomputed = 0;
+    p->apply_clean = 0;
+    p->lay_cfg = -1;
     if ((e = run_pattern(p, s)) != cudaSuccess) return cuda_fail(e, "pattern");
     p->nodes_set = 1;
     return INFFT_OK;
@@ -297,7 +322,10 @@ infft_status infft_precompute(infft_plan_t p, infft_stream_t stream) {
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
+    p->apply_clean = 0;
+    p->lay_cfg = -1;
     cudaError_t e = p->ansatz == INFFT_ANSATZ_UNDERDETERMINED ? run_precompute_under(p, s) : run_precompute(p, s);
+    if (e == cudaSuccess) e = run_weights_lo(p, s);
     if (e != cudaSuccess) return cuda_fail(e, "precompute");
     p->precomputed = 1;
     return INFFT_OK;
@@ -309,6 +337,114 @@ infft_status infft_apply(infft_plan_t p, const float* f, float* fhat, infft_stre
 infft_status infft_apply_z(infft_plan_t p, const double* f, double* fhat, infft_stream_t stream) {
     return apply_impl<double>(p, f, fhat, stream);
 }
+infft_status infft_apply_sorted(infft_plan_t p, const float* f, float* fhat, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_apply_sorted before infft_precompute");
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(f) || !is_device_pointer(fhat))
+        return fail(INFFT_EINVAL, "infft_apply_sorted takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e;
+    if (apply2_default_config(p) >= 0) {
+        e = run_apply2(p, (const float2*)f, true, (float2*)fhat, s);
+    } else {
+        // the three-launch path reads through the permutation: undo the sorting into the
+        // plan's staging buffer first
+        e = run_unsort_values(p, (const float2*)f, (float2*)p->stage_in, s);
+        if (e == cudaSuccess) e = run_spread<float>(p, p->stage_in, s);
+        if (e == cudaSuccess) e = run_fft_adjoint<float>(p, fhat, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "apply");
+    return INFFT_OK;
+}
+
+infft_status infft_sort_values(infft_plan_t p, const float* f, float* f_sorted, infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (!f || !f_sorted || f == f_sorted) return fail(INFFT_EINVAL, "f and f_sorted must be distinct buffers");
+    if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_sort_values before infft_set_nodes");
+    DeviceGuard g(p->device);
+    if (!is_device_pointer(f) || !is_device_pointer(f_sorted))
+        return fail(INFFT_EINVAL, "infft_sort_values takes device pointers only");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = run_sort_values(p, (const float2*)f, (float2*)f_sorted, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sort values");
+    return INFFT_OK;
+}
+
+int32_t infft_apply_config_count(void) { return apply2_config_count(); }
+
+infft_status infft_apply_config_shape(int32_t id, int32_t* log2_N1, int32_t* columns_per_run) {
+    if (id < 0 || id >= apply2_config_count()) return fail(INFFT_EINVAL, "no apply config %d", id);
+    apply2_config_shape(id, log2_N1, columns_per_run);
+    return INFFT_OK;
+}
+
+infft_status infft_set_apply_config(infft_plan_t p, int32_t id) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (id != -1 && !apply2_config_valid(p, id))
+        return fail(INFFT_EINVAL, "apply config %d is not valid for M_sigma = %lld", id, (long long)p->Ms);
+    p->apply_cfg = id;
+    return INFFT_OK;
+}
+
+int32_t infft_get_apply_config(infft_plan_t p) {
+    if (!p || apply2_default_config(p) < 0) return -1;
+    return p->apply_cfg >= 0 ? p->apply_cfg : apply2_default_config(p);
+}
+
+infft_status infft_tune_apply(infft_plan_t p, int32_t repeats, float* ms_out, int32_t* best,
+                              infft_stream_t stream) {
+    if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (repeats < 1 || repeats > 10000) return fail(INFFT_EINVAL, "repeats must be in [1, 10000] (got %d)", repeats);
+    if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_tune_apply before infft_precompute");
+    if (apply2_default_config(p) < 0)
+        return fail(INFFT_EUNSUPPORTED, "M_sigma = %lld takes the three-launch apply (no tile shapes)",
+                    (long long)p->Ms);
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    const int n = apply2_config_count();
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->stage_in, 0, p->N * sizeof(float2), s);
+    const int keep = p->apply_cfg;
+    int best_id = -1;
+    float best_ms = 0.f;
+    for (int id = 0; id < n && e == cudaSuccess; ++id) {
+        if (ms_out) ms_out[id] = -1.f;
+        if (!apply2_config_valid(p, id)) continue;
+        p->apply_cfg = id;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            e = run_apply2(p, (const float2*)p->stage_in, false, (float2*)p->stage_out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        for (int r = 0; r < repeats && e == cudaSuccess; ++r)
+            e = run_apply2(p, (const float2*)p->stage_in, false, (float2*)p->stage_out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        ms /= (float)repeats;
+        if (ms_out) ms_out[id] = ms;
+        if (e == cudaSuccess && (best_id < 0 || ms < best_ms)) {
+            best_id = id;
+            best_ms = ms;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) {
+        p->apply_cfg = keep;
+        return cuda_fail(e, "tune apply");
+    }
+    p->apply_cfg = best_id;
+    if (best) *best = best_id;
+    return INFFT_OK;
+}
+
 int64_t infft_apply_many_workspace(infft_plan_t p, int64_t K) {
     if (!p || K < 1) return 0;
     return 2 * K * p->Ms * (int64_t)sizeof(float2) + 256;
@@ -334,6 +470,13 @@ infft_status infft_apply_many(infft_plan_t p, int64_t K, const float* f, float* 
     void* grid = ws;
     void* work = ws + K * p->Ms * sizeof(float2);
     cudaError_t e;
+    if (apply2_default_config(p) >= 0) {
+        // the single apply's two kernels with one CTA row per data vector: every vector's
+        // result equals infft_apply's (same kernels, same arithmetic order)
+        if ((e = run_apply2(p, (const float2*)f, false, (float2*)fhat, s, (int)K, (float2*)work)) != cudaSuccess)
+            return cuda_fail(e, "apply");
+        return INFFT_OK;
+    }
     if ((e = run_spread_many(p, f, grid, (int)K, s)) != cudaSuccess) return cuda_fail(e, "spread");
     if ((e = run_fft_adjoint_many(p, grid, work, fhat, (int)K, s)) != cudaSuccess) return cuda_fail(e, "fft");
     return INFFT_OK;

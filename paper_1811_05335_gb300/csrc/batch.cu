@@ -625,10 +625,15 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
             return set_error(INFFT_EUNSUPPORTED, "batch too large: sum N = %lld, sum M_sigma = %lld (each < 2^31)",
                              (long long)sn, (long long)sg);
     }
+    int dev = 0, sms = 0;
+    cudaError_t qe = cudaGetDevice(&dev);
+    if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (qe != cudaSuccess || sms <= 0)
+        return set_error(INFFT_ECUDA, "cannot query the device's multiprocessor count: %s",
+                         qe != cudaSuccess ? cudaGetErrorString(qe) : "count <= 0");
     infft_batch_t b = new infft_batch_s();
-    cudaGetDevice(&b->device);
-    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (b->sms <= 0) b->sms = 148;
+    b->device = dev;
+    b->sms = sms;
     b->P = P; b->sigma = sigma; b->m = m; b->kernel = kernel; b->tau = tau;
     b->M.assign(M, M + P);
     b->N.assign(N, N + P);

@@ -20,7 +20,7 @@
 #include <mutex>
 
 #include "plan.h"
-#include "fft_device.cuh"
+#include "fft_r8.cuh"
 
 namespace {
 
@@ -28,19 +28,6 @@ constexpr int FFT_THREADS = 256;
 constexpr int FFT_SMALL = 2048;
 
 template <typename T> INFFT_D cplx_t<T> czero() { return cmake((T)0, (T)0); }
-
-// frequency k of DFT bin q (or INT_MIN when q is pruned)
-INFFT_D int bin_to_k(int q, int Ms, int M) {
-    if (q < M / 2) return q;
-    if (q >= Ms - M / 2) return q - Ms;
-    return INT_MIN;
-}
-
-// (-1)^k d_k as a real factor (d_k = 1/M_sigma, 0 at k = -M/2 for kernel sym)
-template <typename T> INFFT_D T deconv(int k, int M, T inv_Ms, int sym) {
-    if (sym && k == -M / 2) return (T)0;
-    return (k & 1) ? -inv_Ms : inv_Ms;
-}
 
 // ---- single-CTA transform --------------------------------------------------
 
@@ -150,191 +137,6 @@ k_fft_passB(const cplx_t<T>* __restrict__ Y, cplx_t<T>* __restrict__ out, int lo
 template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// ---- register-resident radix-8 Stockham transforms (fp32 adjoint apply) -----
-//
-// A length n = 2^LOGN transform is held by n/8 threads, 8 values each.  Every
-// stage is a radix-R Stockham step (R = 8, and one final radix-4 or radix-2 step
-// when LOGN is not a multiple of 3): butterfly jj reads a[jj + r n/R], multiplies
-// value r by w^{r k n/(Ns R)} (k = jj mod Ns, w = e^{DIR 2 pi i/n}, Ns the length
-// already transformed), runs a length-R DFT in registers and stores value r to
-// a[(jj - k) R + k + r Ns].  The first stage takes its input from registers and
-// the last leaves its output there: value slot s = b R + r of thread j holds bin
-// j + b n/8 + r n/R.  Stages exchange values through shared memory (two
-// buffers, one padding slot per 8 entries, so the stride-8 stores of the first
-// stage hit distinct banks).  Twiddles come from a table of e^{DIR 2 pi i t/n}
-// evaluated by sincospif on exact arguments.
-
-INFFT_D int pad8(int i) { return i + (i >> 3); }
-
-// One radix-R stage over this thread's butterflies jj = j + b n/8 (b < 8/R);
-// dst == nullptr keeps the results in v (last stage).
-template <int LOGN, int R, int DIR>
-INFFT_D void r8_stage(float2 (&v)[8], const float2* src, float2* dst, const float2* tw, int j, int Ns) {
-    constexpr int n = 1 << LOGN;
-#pragma unroll
-    for (int b = 0; b < 8 / R; ++b) {
-        const int jj = j + b * (n / 8);
-        float2* x = v + b * R;
-#pragma unroll
-        for (int r = 0; r < R; ++r) x[r] = src[pad8(jj + r * (n / R))];
-        const int k = jj & (Ns - 1);
-        const int step = k * (n / (Ns * R));
-#pragma unroll
-        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw[r * step]);
-        dft_r<DIR>(x, int_constant_tag<R>());
-        if (dst) {
-            const int base = (jj - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) dst[pad8(base + r * Ns)] = x[r];
-        }
-    }
-}
-
-// bin held by value slot s of thread j after fft_r8<LOGN>
-template <int LOGN> INFFT_D int r8_bin(int j, int s) {
-    constexpr int n = 1 << LOGN, R = (LOGN % 3) ? (1 << (LOGN % 3)) : 8;
-    return j + (s / R) * (n / 8) + (s % R) * (n / R);
-}
-
-// In: v[r] = x[j + r n/8].  Out: v[s] = X[r8_bin<LOGN>(j, s)].  bufA/bufB hold
-// pad8(n) entries each; tw holds n twiddles.  Every thread of the CTA calls it.
-template <int LOGN, int DIR>
-INFFT_D void fft_r8(float2 (&v)[8], float2* bufA, float2* bufB, const float2* tw, int j) {
-    constexpr int S8 = LOGN / 3, REM = LOGN % 3;
-    static_assert(LOGN >= 6, "fft_r8 needs at least two stages");
-    dft_r<DIR>(v, int_constant_tag<8>());
-#pragma unroll
-    for (int r = 0; r < 8; ++r) bufA[pad8(8 * j + r)] = v[r];
-    float2* src = bufA;
-    float2* dst = bufB;
-    int Ns = 8;
-#pragma unroll
-    for (int st = 1; st < S8; ++st) {
-        __syncthreads();
-        const bool last = (st == S8 - 1) && REM == 0;
-        r8_stage<LOGN, 8, DIR>(v, src, last ? nullptr : dst, tw, j, Ns);
-        Ns *= 8;
-        float2* t = src; src = dst; dst = t;
-    }
-    if (REM) {
-        __syncthreads();
-        r8_stage<LOGN, (REM ? (1 << REM) : 8), DIR>(v, src, nullptr, tw, j, Ns);
-    }
-}
-
-// e^{-2 pi i t/n} for t < n (n a power of two >= 4): a quarter of the table by
-// sincospif on exact arguments, the rest by exact quarter turns.
-template <int n> INFFT_D void r8_twiddles(float2* tw, int t0, int stride) {
-    for (int i = t0; i < n / 4; i += stride) {
-        float sn, cs;
-        sincospif((float)(-2 * i) / (float)n, &sn, &cs);
-        tw[i] = make_float2(cs, sn);
-        tw[i + n / 4] = make_float2(sn, -cs);          // * e^{-i pi/2}
-        tw[i + n / 2] = make_float2(-cs, -sn);         // * e^{-i pi}
-        tw[i + 3 * n / 4] = make_float2(-sn, cs);      // * e^{-3 i pi/2}
-    }
-}
-
-// e^{-2 pi i t/Ms} for an integer t >= 0 (Ms a power of two), reduced exactly
-INFFT_D float2 expm2pi_frac(int t, int Ms) {
-    float sn, cs;
-    sincospif((float)(-2 * (t & (Ms - 1))) / (float)Ms, &sn, &cs);
-    return make_float2(cs, sn);
-}
-
-constexpr int R8_MIN_THREADS = 64;
-
-// threads of one length-2^logn transform, transforms per CTA, shared bytes per CTA
-struct R8Shape {
-    int threads_per, per_cta, smem;
-};
-
-INFFT_HD R8Shape r8_shape(int logn, int count, int K = 1) {
-    R8Shape s;
-    s.threads_per = (1 << logn) / 8;
-    s.per_cta = s.threads_per >= R8_MIN_THREADS ? 1 : R8_MIN_THREADS / s.threads_per;
-    // several data vectors fill the GPU anyway: wider CTAs read whole 32-byte sectors
-    // of the strided columns (4 consecutive complex64) and write longer output runs
-    if (K >= 4 && s.threads_per < 256 && s.per_cta * s.threads_per < 256) s.per_cta = 256 / s.threads_per;
-    if (s.per_cta > count) s.per_cta = count;
-    const int n = 1 << logn;
-    s.smem = (n + 2 * s.per_cta * (n + n / 8)) * (int)sizeof(float2);
-    return s;
-}
-
-// Pass A of the fp32 adjoint four-step: CTA owns p2 in [blockIdx.x CA, +CA)
-// (thread t: column c = t mod CA, j = t / CA); transforms g[p1 N2 + p2] over
-// p1 (length N1 = 2^LOG1), multiplies bin k1 by w^{p2 k1} (w = e^{-2 pi i/M_sigma})
-// and stores Y[k1 N2 + p2].
-template <int LOG1>
-__global__ void __launch_bounds__(512)
-k_fftA_r8(const float2* __restrict__ g, float2* __restrict__ Y, int log2, int CA) {
-    constexpr int N1 = 1 << LOG1, T1 = N1 / 8, RS = N1 + N1 / 8;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tw = (float2*)smem_raw;
-    const int t = threadIdx.x, c = t % CA, j = t / CA;
-    float2* bufA = tw + N1 + 2 * c * RS;
-    r8_twiddles<N1>(tw, t, blockDim.x);
-    griddep_wait();
-    griddep_launch();
-    const int p2 = blockIdx.x * CA + c;
-    const int Ms = N1 << log2;
-    g += (size_t)blockIdx.y * Ms;   // data vector blockIdx.y
-    Y += (size_t)blockIdx.y * Ms;
-    float2 v[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = g[((j + r * T1) << log2) + p2];
-    fft_r8<LOG1, -1>(v, bufA, bufA + RS, tw, j);
-    // w^{p2 k1} for the bins k1 = j + b N1/8 + r N1/R of this thread: three exact
-    // evaluations and products (at most 8 roundings)
-    constexpr int R = (LOG1 % 3) ? (1 << (LOG1 % 3)) : 8;
-    const float2 wj = expm2pi_frac(p2 * j, Ms), wb = expm2pi_frac(p2 * (N1 / 8), Ms),
-                 wr = expm2pi_frac(p2 * (N1 / R), Ms);
-    float2 rowb = wj;
-#pragma unroll
-    for (int b = 0; b < 8 / R; ++b) {
-        float2 w = rowb;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int s = b * R + r;
-            Y[(r8_bin<LOG1>(j, s) << log2) + p2] = cmul(v[s], w);
-            w = cmul(w, wr);
-        }
-        rowb = cmul(rowb, wb);
-    }
-}
-
-// Pass B: CTA owns rows k1 in [blockIdx.x CB, +CB) (thread t: row c = t / T2,
-// j = t mod T2); transforms Y[k1 N2 + p2] over p2 (length N2 = 2^LOG2) and writes
-// bin q = k1 + N1 k2 pruned to the M central frequencies with (-1)^k d_k applied.
-template <int LOG2>
-__global__ void __launch_bounds__(512)
-k_fftB_r8(const float2* __restrict__ Y, float2* __restrict__ fhat, int log1, int CB, int M, float inv_Ms,
-          int sym) {
-    constexpr int N2 = 1 << LOG2, T2 = N2 / 8, RS = N2 + N2 / 8;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tw = (float2*)smem_raw;
-    const int t = threadIdx.x, c = t / T2, j = t % T2;
-    float2* bufA = tw + N2 + 2 * c * RS;
-    r8_twiddles<N2>(tw, t, blockDim.x);
-    griddep_wait();
-    griddep_launch();
-    const int k1 = blockIdx.x * CB + c;
-    const int Ms = N2 << log1;
-    Y += (size_t)blockIdx.y * Ms;   // data vector blockIdx.y
-    fhat += (size_t)blockIdx.y * M;
-    float2 v[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = Y[(k1 << LOG2) + j + r * T2];
-    fft_r8<LOG2, -1>(v, bufA, bufA + RS, tw, j);
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const int q = k1 + (r8_bin<LOG2>(j, s) << log1);
-        const int k = bin_to_k(q, Ms, M);
-        if (k != INT_MIN) fhat[k + M / 2] = cscale(v[s], deconv<float>(k, M, inv_Ms, sym));
-    }
 }
 
 // Launches both passes for a length-2^(log1+log2) grid; the pass B launch is
@@ -490,6 +292,34 @@ template <typename T> Split choose_split(int logMs) {
 
 }  // namespace
 
+// Launches pass B alone (the apply's second launch): rows of Y of length 2^log2, pruned and
+// deconvolved output, programmatically dependent on the kernel before it.
+cudaError_t fft_passB_r8(const float2* work, float2* fhat, int log1, int log2, int M, int sym, cudaStream_t s,
+                         Plan* p, int K) {
+    const int Ms = 1 << (log1 + log2);
+    const float inv_Ms = 1.0f / (float)Ms;
+    const R8Shape b = r8_shape(log2, 1 << log1, K);
+    void (*kb)(const float2*, float2*, int, int, int, float, int) = nullptr;
+    switch (log2) {
+        case 6: kb = k_fftB_r8<6>; break;
+        case 7: kb = k_fftB_r8<7>; break;
+        case 8: kb = k_fftB_r8<8>; break;
+        case 9: kb = k_fftB_r8<9>; break;
+        case 10: kb = k_fftB_r8<10>; break;
+        case 11: kb = k_fftB_r8<11>; break;
+        case 12: kb = k_fftB_r8<12>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = allow_smem(kb, (size_t)b.smem);
+    if (e != cudaSuccess) return e;
+    if (p) launch_begin(p, "fft_passB_deconv", s);
+    e = launch_pdl(kb, dim3((1 << log1) / b.per_cta, K), dim3(b.per_cta * b.threads_per), (size_t)b.smem, s, work,
+                   fhat, log1, b.per_cta, M, inv_Ms, sym);
+    if (p) launch_end(p, s);
+    return e;
+}
+
+
 template <typename T>
 cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStream_t s) {
     using C = cplx_t<T>;
@@ -601,20 +431,51 @@ __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_MAX_MS];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mutex;
-float2* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+struct NoallocSlot {
+    void* ctx = nullptr;      // the context the address belongs to
+    float2* addr = nullptr;
+};
+NoallocSlot g_noalloc_slot[NOALLOC_MAX_DEVICES];
+
+// cuCtxGetCurrent, reached through the runtime's driver entry point query (the library
+// links no driver library); nullptr when the query fails.
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)ptr;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
 
 // The device address of the scratch array on the current device.  The host-side
 // symbol is only a stand-in: the address must come from cudaGetSymbolAddress,
-// looked up once per device with that device current.
+// looked up with the device current.  It is looked up on the first call on a device
+// and again whenever the device's current context differs from the one it was taken
+// in (after cudaDeviceReset the module is loaded anew and the array may move).
 cudaError_t noalloc_scratch(int dev, float2** out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    void* ctx = nullptr;
+    if (CtxGetCurrentFn get = ctx_get_current()) {
+        if (get(&ctx) != 0) ctx = nullptr;
+    }
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    if (!slot.addr || slot.ctx != ctx) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = (float2*)ptr;
+        slot.addr = (float2*)ptr;
+        slot.ctx = ctx;
     }
-    *out = g_noalloc_addr[dev];
+    *out = slot.addr;
     return cudaSuccess;
 }
 

@@ -274,10 +274,8 @@ cudaError_t run_pattern(Plan* p, cudaStream_t s) {
     launch_begin(p, "bucket_fixup", s);
     k_bucket_fixup<<<blocks_for(nkeys, 256), 256, 0, s>>>(p->bucket, nkeys, p->perm, p->seg_list, p->counters);
     launch_end(p, s);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     launch_begin(p, "bigseg_fixup", s);
-    k_bigseg_fixup<<<sms > 0 ? sms : 148, 256, 0, s>>>(p->seg_list, p->counters, p->bucket, p->perm, p->sort_tmp);
+    k_bigseg_fixup<<<p->sms, 256, 0, s>>>(p->seg_list, p->counters, p->bucket, p->perm, p->sort_tmp);
     launch_end(p, s);
     launch_begin(p, "gather_nodes", s);
     k_gather_nodes<<<blocks_for(N, 256), 256, 0, s>>>(p->x, p->perm, N, (double)p->M, p->xs, p->phase);

@@ -78,7 +78,8 @@ struct infft_plan_s {
     double* w64 = nullptr;      // nnz_cap
     float* w32 = nullptr;       // nnz_cap
     double* J = nullptr;        // Ms (overdetermined), N (underdetermined, caller order)
-    uint8_t* wide = nullptr;    // Ms: 1 if column l uses fp64 weights in the fp32 applies
+    uint8_t* wide = nullptr;    // Ms: 1 if column l spreads in float-float in the fp32 applies
+    float* wlo = nullptr;       // nnz_cap: fp32(w64 - w32), the low parts of the float-float weights
     double* gterm = nullptr;    // nnz_cap: per (column, node) terms of the node gradient
 
     // underdetermined case (Sec. 3.2.1)
@@ -96,6 +97,19 @@ struct infft_plan_s {
     void* arena = nullptr;      // the one device allocation holding the buffers above (owned)
     bool batch_member = false;  // buffers carved from a batch; big columns go to the batch's solver
     int nodes_set = 0, precomputed = 0;
+    int apply_clean = 0;        // 0 after set_nodes / precompute until the next apply has been launched
+    int apply_cfg = -1;         // tile shape of the fused apply (-1: the default rule)
+    int lay_cfg = -1;           // tile shape the apply layout below holds (-1: none, or stale)
+    int sms = 0;                // multiprocessors of the plan's device
+
+    // apply layout of the fused apply (apply.cu): per tile a header, per column a descriptor,
+    // the weights and node-window lists tile by tile
+    int4* lay_hdr = nullptr;          // max tiles
+    uint2* lay_cdesc = nullptr;       // Ms
+    float* lay_w = nullptr;           // nnz_cap + 4 max tiles
+    int32_t* lay_list = nullptr;      // apply2_list_capacity: caller indices
+    int32_t* lay_list_sorted = nullptr;   // the same windows as sorted positions
+    int32_t* lay_tmp = nullptr;       // 5 max tiles: block lengths, direct flags, block starts
     cudaStream_t last_stream = nullptr;
 
     bool profiling = false;
@@ -168,6 +182,26 @@ template <typename T> cudaError_t run_fft_adjoint(Plan* p, void* fhat, cudaStrea
 // fhat: K x M); the FFT requires M_sigma > 2048
 cudaError_t run_spread_many(Plan* p, const void* f, void* grid, int K, cudaStream_t s);
 cudaError_t run_fft_adjoint_many(Plan* p, const void* grid, void* work, void* fhat, int K, cudaStream_t s);
+// apply.cu: the fp32 apply in two launches (spreading fused with FFT pass A, then pass B with D);
+// sorted: f is given in the plan's sorted node order.  Tile shapes ("configs") are numbered
+// 0 .. apply2_config_count() - 1; valid ones depend on M_sigma.
+int apply2_config_count();
+bool apply2_config_valid(const Plan* p, int id);
+int apply2_default_config(const Plan* p);
+// K data vectors (f: K x N, fhat: K x M) with pass A's output in Y (K x M_sigma; nullptr: the
+// plan's work buffer, K = 1)
+cudaError_t run_apply2(Plan* p, const float2* f, bool sorted, float2* fhat, cudaStream_t s, int K = 1,
+                       float2* Y = nullptr);
+cudaError_t run_weights_lo(Plan* p, cudaStream_t s);
+int64_t apply2_max_tiles(const Plan* p);
+int64_t apply2_list_capacity(const Plan* p);
+void apply2_config_shape(int id, int* log1, int* C);
+// apply.cu: out[i] = f[perm[i]] (sort) and out[perm[i]] = f[i] (unsort), complex64
+cudaError_t run_sort_values(Plan* p, const float2* f, float2* out, cudaStream_t s);
+cudaError_t run_unsort_values(Plan* p, const float2* f, float2* out, cudaStream_t s);
+// fft.cu: pass B of the four-step FFT alone (rows of length 2^log2), D fused, pruned output
+cudaError_t fft_passB_r8(const float2* work, float2* fhat, int log1, int log2, int M, int sym, cudaStream_t s,
+                         Plan* p, int K = 1);
 // fft.cu: grid = F D fhat
 template <typename T> cudaError_t run_fft_forward(Plan* p, const void* fhat, cudaStream_t s);
 // fft.cu: out_p = scale * sum_{k=-Ms/2}^{Ms/2-1} in[k + Ms/2] exp(2 pi i k (p - Ms/2)/Ms), fp64, all bins

@@ -20,7 +20,7 @@ def built():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:infft_status|int64_t|const char\s*\*)\s*(\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:infft_status|int64_t|int32_t|const char\s*\*)\s*(\w+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declares_the_method_calls():

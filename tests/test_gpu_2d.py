@@ -251,6 +251,28 @@ def test_errors():
     plan.close()
 
 
+@pytest.mark.slow
+def test_mid_size_radial_dense_data():
+    """128 spokes x 128 samples, M = 64 x 64, sigma = 2, m = 4 (columns up to 1187 nodes): fhat
+    of dense trigonometric-polynomial data against the oracle's closed tier, every coefficient,
+    in the fp32 path (1e-5) and the fp64 path (1e-9)."""
+    x = radial(409, 128, 128, 1e-4)
+    M1 = M2 = 64
+    B = o2.bopt2_closed(x, M1, M2, 2.0, 4, "full")
+    fh = complex_normal(909, M1 * M2).reshape(M1, M2)
+    f = trig_poly_eval_2d(x, fh)
+    f32 = np.asarray(f, np.complex64).astype(np.complex128)
+    plan, fhat, data, info = run_gpu2(x, f32, M1, M2, 2.0, 4, "full")
+    assert info["max_column"] == np.diff(B.ptr).max() and info["fallback_columns"] == 0
+    err32 = rel_l2(fhat, o2.infft2_apply(B, f32))
+    plan.close()
+    plan, fhat64, _, _ = run_gpu2(x, f, M1, M2, 2.0, 4, "full", z=True)
+    err64 = rel_l2(fhat64, o2.infft2_apply(B, f))
+    plan.close()
+    print(f"radial 128 x 128, M = 64 x 64: rel l2 vs oracle fp32 {err32:.3e}, fp64 {err64:.3e}")
+    assert err32 <= FP32_TOL and err64 <= FP64_TOL
+
+
 def test_full_size_radial_sampled():
     """The full 2-D workload: 512 spokes x 512 samples, M = 256 x 256, sigma = 2, m = 4."""
     import torch

@@ -71,6 +71,21 @@ def test_jittered_reconstruction_and_error_measures():
     assert errs[1] < errs[0]          # "errors ... decrease for large sizes of M"
 
 
+def test_errors_per_node_golden(golden):
+    """Hand-worked values of eq:errors_per_node_lagrange (tests/golden/errors_per_node.txt):
+    a wrong divisor (N or the norm of fhat), a swapped norm or a squared norm fails them."""
+    rows = golden("errors_per_node.txt")
+    assert len(rows) % 3 == 0
+    for c in range(0, len(rows), 3):
+        N = int(rows[c][0])
+        fh = np.array(rows[c][1::2]) + 1j * np.array(rows[c][2::2])
+        fc = np.array(rows[c + 1][0::2]) + 1j * np.array(rows[c + 1][1::2])
+        want = dict(zip(("abs_2", "rel_2", "abs_inf", "rel_inf"), rows[c + 2]))
+        got = infft.errors_per_node(fh, fc, N)
+        for key, val in want.items():
+            assert abs(got[key] - val) <= 1e-15 * abs(val), (c // 3, key, got[key], val)
+
+
 def test_refine_is_the_residual_error_map():
     """One sweep maps the error e of noiseless data to (I - D^* F^* B_opt^* A) e, with every
     matrix formed explicitly (eq:matrix_A, eq:matrix_F, eq:matrix_D, eq:matrix_B)."""
