@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--M", type=int, default=2 ** 16)
     ap.add_argument("--N", type=int, default=2 ** 18)
     ap.add_argument("--m", type=int, default=4)
-    ap.add_argument("--apply-steps", type=int, default=200)
+    ap.add_argument("--apply-steps", type=int, default=50)
+    ap.add_argument("--rotating-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
@@ -183,17 +184,50 @@ def recorded_traffic(kernel):
             rec = json.load(fh).get(kernel)
         if not rec or sources_sha1(rec["sources"]) != rec["sha1"]:
             return None
-        return rec["bytes_per_launch"]
+        return rec["value"] if "value" in rec else rec["bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         return None
 
 
-def lsq_flops(counts):
+def lsq_flops(counts, kappa_values=None):
     """Algorithmic fp64 flops of the B_opt precompute: per column of n nodes, the
     Cholesky factorisation n^3/3, the two triangular solves 2n^2, and the
-    n(n-1)/2 + n closed-form kernel values of Re G_l and Re r_l."""
+    n(n-1)/2 + n closed-form kernel values of Re G_l and Re r_l (or, when given, the
+    number of kernel values the solver actually evaluates)."""
     n = counts.astype(np.float64)
-    return float(np.sum(n ** 3 / 3 + 2 * n ** 2 + (n * (n - 1) / 2 + n) * KAPPA_FLOPS))
+    kv = float(np.sum(n * (n - 1) / 2 + n)) if kappa_values is None else float(kappa_values)
+    return float(np.sum(n ** 3 / 3 + 2 * n ** 2)) + kv * KAPPA_FLOPS
+
+
+def kappa_values_executed(starts, counts, N, tile=32, nmax=17):
+    """Kernel values the one-thread-per-column solver evaluates: per tile of 32 consecutive
+    columns it evaluates each node pair (a, b), a < b, of the tile's union of sorted nodes once
+    if some column of the tile holds both (so consecutive columns share them), plus each
+    column's n right-hand-side values.  Only when every column is in that tier (n <= 17)."""
+    if counts.max() > nmax:
+        return None
+    total = 0
+    for t0 in range(0, len(counts), tile):
+        n = counts[t0:t0 + tile]
+        live = n > 0
+        if not live.any():
+            continue
+        s0 = starts[t0]
+        rs = (starts[t0:t0 + tile] - s0) % N
+        rs, n = rs[live], n[live]
+        end = rs + n                       # ranges [rs, end), both non-decreasing in the column
+        U = int(end.max())
+        a = np.arange(U)
+        last = np.searchsorted(rs, a, side="right") - 1      # last column starting at or before a
+        reach = np.where(last >= 0, np.maximum.accumulate(end)[np.maximum(last, 0)], 0)
+        total += int(np.sum(np.maximum(reach - a - 1, 0))) + int(n.sum())
+    return total
+
+
+def recorded_counter(name):
+    """A counter value recorded with its capture in profiles/traffic.json (None when the
+    kernel's sources changed since)."""
+    return recorded_traffic(name)
 
 
 KAPPA2_FLOPS = 2 * KAPPA_FLOPS + 17    # a 2-D kernel value: two 1-D Dirichlet ratios and the full kernel's cospi
@@ -209,6 +243,76 @@ def apply_bytes(N, M, nnz):
     """Algorithmic HBM bytes of one modified adjoint NFFT: read f (8N), read the
     fp32 weights (4 nnz), write fhat (8M); the grid stays in L2."""
     return 8 * N + 4 * nnz + 8 * M
+
+
+def rotating_applies(g, torch, a, dev, rank, stream, reps=200):
+    """The apply timed over R rotating plans: R plans (seeds differ), each precomputed, their
+    R applies captured back to back in one CUDA graph on one stream; the graph is replayed
+    `reps` times and the per-apply time is the median replay time over R.  R is chosen so that
+    R (8N + 4 nnz + 8M) >= 4 x L2.  Also timed: the same R applies issued one by one on the
+    stream (no graph)."""
+    L2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    plans, fs, outs = [], [], []
+    first = make_problem(2, M=a.M, N=a.N, m=a.m, with_data=False, seed=1811053352 + 1000 * rank)
+    pl = g.infft_plan_create(a.M, a.N, 2.0, a.m)
+    g.infft_set_nodes(pl, torch.tensor(first.x, dtype=torch.float64, device=dev), stream)
+    g.infft_precompute(pl, stream)
+    torch.cuda.synchronize()
+    nnz = g.infft_get_info(pl)["nnz"]
+    per = apply_bytes(a.N, a.M, nnz)
+    R = max(8, -(-4 * L2 // per))
+    plans.append(pl)
+    for r in range(1, R):
+        pr = make_problem(2, M=a.M, N=a.N, m=a.m, with_data=False, seed=1811053352 + 1000 * rank + 7919 * r)
+        q = g.infft_plan_create(a.M, a.N, 2.0, a.m)
+        g.infft_set_nodes(q, torch.tensor(pr.x, dtype=torch.float64, device=dev), stream)
+        g.infft_precompute(q, stream)
+        plans.append(q)
+    for r in range(R):
+        gen = torch.Generator(device=dev).manual_seed(100 + r)
+        fs.append(torch.randn(a.N, dtype=torch.complex64, device=dev, generator=gen))
+        outs.append(torch.empty(a.M, dtype=torch.complex64, device=dev))
+    for _ in range(3):
+        for r in range(R):
+            g.infft_apply(plans[r], fs[r], outs[r], stream)
+    torch.cuda.synchronize()
+    total_bytes = sum(apply_bytes(a.N, a.M, g.infft_get_info(q)["nnz"]) for q in plans)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for s0, s1 in ev:
+        s0.record(stream)
+        for r in range(R):
+            g.infft_apply(plans[r], fs[r], outs[r], stream)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    stream_ms = statistics.median(s0.elapsed_time(s1) for s0, s1 in ev) / R
+    gs = torch.cuda.Stream(dev)
+    gs.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        for r in range(R):
+            g.infft_apply(plans[r], fs[r], outs[r], gs)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        graph.replay()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for s0, s1 in ev:
+        s0.record(stream)
+        graph.replay()
+        s1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = statistics.median(s0.elapsed_time(s1) for s0, s1 in ev) / R
+    del graph
+    launches0 = g.infft_launch_count()
+    g.infft_apply(plans[0], fs[0], outs[0], stream)
+    per_apply_launches = g.infft_launch_count() - launches0
+    cfg = g.infft_get_apply_config(plans[0])
+    for q in plans:
+        q.close()
+    torch.cuda.synchronize()
+    return {"plans": R, "l2_bytes": L2, "bytes_per_apply": total_bytes / R, "footprint_over_l2": total_bytes / L2,
+            "replays": reps, "ms_per_apply_graph": graph_ms, "ms_per_apply_stream": stream_ms,
+            "launches_per_apply": per_apply_launches,
+            "tile_shape": list(g.infft_apply_configs()[cfg]) if cfg >= 0 else None}
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -245,7 +349,8 @@ def run_gpu(a):
         step()
     torch.cuda.synchronize()
     info = g.infft_get_info(plan)
-    counts = g.infft_copy_plan_data(plan, weights=False)["col_count"]
+    pdata = g.infft_copy_plan_data(plan, weights=False)
+    counts, col_starts = pdata["col_count"].astype(np.int64), pdata["col_start"].astype(np.int64)
 
     # ---- timed region: K whole-path steps, L2 flushed before each
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -280,7 +385,8 @@ def run_gpu(a):
     ms_step = ms_total / a.steps
     value = job_rate(a.N, a.steps, world, ms_total / 1e3)
 
-    # ---- apply only (fixed plan): the paper's "fixed nodes, several problems" regime
+    # ---- the modified adjoint NFFT alone (the paper's "fixed nodes, several problems" regime)
+    # (1) one apply at a time with the L2 cache flushed before each: single-apply latency
     k_app = a.apply_steps
     s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k_app)]
     e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k_app)]
@@ -290,7 +396,7 @@ def run_gpu(a):
         g.infft_apply(plan, f, fhat, stream)
         e_ev[i].record(stream)
     torch.cuda.synchronize()
-    app_ms = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) / k_app
+    app_ms = statistics.median(s.elapsed_time(e) for s, e in zip(s_ev, e_ev))
     g.infft_profile(plan, True)
     for i in range(k_app):
         flush.fill_(float(i))
@@ -298,32 +404,10 @@ def run_gpu(a):
     torch.cuda.synchronize()
     g.infft_profile(plan, False)
     app_kernels = g.infft_profile_read(plan)
-    # the same apply replayed from a captured CUDA graph (the calls are stream-ordered
-    # and allocate nothing, so they capture): the GPU time without the host's launch
-    # gaps; L2 still flushed before every replay
-    gstream = torch.cuda.Stream(dev)
-    gstream.wait_stream(stream)
-    with torch.cuda.stream(gstream):
-        for _ in range(3):
-            g.infft_apply(plan, f, fhat, gstream)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=gstream):
-        g.infft_apply(plan, f, fhat, gstream)
-    torch.cuda.synchronize()
-    gs_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k_app)]
-    ge_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k_app)]
-    for _ in range(3):
-        graph.replay()
-    for i in range(k_app):
-        flush.fill_(float(i))
-        gs_ev[i].record(stream)
-        graph.replay()
-        ge_ev[i].record(stream)
-    torch.cuda.synchronize()
-    app_graph_ms = sum(s.elapsed_time(e) for s, e in zip(gs_ev, ge_ev)) / k_app
-    del graph
-
+    # (2) the rotating-plan protocol: R plans of the same recipe (distinct nodes, B_opt and data)
+    # whose algorithmic bytes exceed 4x the L2 cache, their applies back to back in one
+    # captured CUDA graph, replayed; per-apply time = median replay time / R
+    rot = rotating_applies(g, torch, a, dev, rank, stream, reps=a.rotating_reps)
     # K data vectors on the same plan in one call (infft_apply_many): the weights are read
     # once for all K; algorithmic bytes K (8N + 8M) + 4 nnz
     K_many = 16
@@ -484,7 +568,7 @@ def run_gpu(a):
         nb = int(w.N.sum())
         ab_b = apply_bytes(nb, int(w.M.sum()), infob["nnz"])
         ach_b = ab_b / (t_app_b / 1e3) / 1e9
-        single_rate = world * a.N / (app_ms / 1e3)
+        single_rate = world * a.N / (rot["ms_per_apply_graph"] / 1e3)
         batched = {"workload": f"{w.M.size} problems, M log-uniform in [256, 8192] (sum {int(w.M.sum())}), "
                                f"N = 2-4 M (sum {nb}), Chebyshev-clustered nodes, sigma=2, m={w.m}",
                    "precompute_ms": t_pre_b, "apply_ms": t_app_b,
@@ -571,59 +655,92 @@ def run_gpu(a):
                                     "frac": ach2 / peaks()[0], "algorithmic_bytes": ab2,
                                     "index_bytes": idx2}}
 
-    # ---- roofline of the dominant kernel and of the apply
+    # ---- fp64 FMA throughput of this GPU (the precompute's roofline denominator), measured
+    sink = torch.empty(g.infft_fp64_fma_probe_sink_len(), dtype=torch.float64, device=dev)
+    probe_iters = 4096
+    g.infft_fp64_fma_probe(probe_iters, sink, stream)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for s0, s1 in pev:
+        s0.record(stream)
+        probe_flops = g.infft_fp64_fma_probe(probe_iters, sink, stream)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    fp64_peak = probe_flops / (statistics.median(s0.elapsed_time(s1) for s0, s1 in pev) / 1e3) / 1e12
+    del sink
+
+    # ---- rooflines: the modified adjoint NFFT (HBM) and the B_opt precompute (fp64 ALU)
     hbm, sm_max, src = peaks()
     ktab = {name: (n, ms) for name, n, ms in kernels}
-    dom = max(ktab, key=lambda k: ktab[k][1])
-    dom_n, dom_ms = ktab[dom]
-    dom_avg_s = dom_ms / dom_n / 1e3
-    roofline = None
-    if dom.startswith("lsq"):
-        # all columns are solved by the warp tiers at this workload (|I(l)| <= 64)
-        fl = lsq_flops(counts)
-        lsq_ms = sum(ms for name, (n, ms) in ktab.items() if name.startswith("lsq")) / dom_n
-        peak = sm_count() * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-        ach = fl / (lsq_ms / 1e3) / 1e12
-        roofline = {"kernel": "lsq (B_opt precompute, all tiers)", "bound": "alu", "achieved": ach,
-                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": recorded_traffic("k_lsq_thread<17, 5>"),
-                    "peak_source": "derived: 152 SMs x 4 fp64 flop/clk x max SM clock"}
+    ab = apply_bytes(a.N, a.M, info["nnz"])
+    graph_ms = rot["ms_per_apply_graph"]
+    ach_app = rot["bytes_per_apply"] / (graph_ms / 1e3) / 1e9
+    ach_single = ab / (app_ms / 1e3) / 1e9
+    traffic = recorded_traffic("apply")
+    roofline = {"kernel": f"modified adjoint NFFT D^*F^*B^*f: k_apply_spread_fftA + k_fftB_r8 "
+                          f"({rot['launches_per_apply']} launches per apply), {rot['plans']} applies over rotating "
+                          f"plans in one CUDA graph, median of {rot['replays']} replays",
+                "bound": "hbm", "achieved": ach_app, "peak": hbm, "unit": "GB/s", "frac": ach_app / hbm,
+                "traffic": traffic, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_apply": rot["bytes_per_apply"],
+                "algorithmic_bytes": "8N (f) + 4 nnz (fp32 weights) + 8M (fhat); the grid and the FFT "
+                                     "intermediate stay in L2",
+                "ms_per_apply": graph_ms, "footprint_over_l2": rot["footprint_over_l2"],
+                "tile_shape": rot["tile_shape"]}
+    lsq_names = [k for k in ktab if k.startswith("lsq")]
+    lsq_n = ktab[lsq_names[0]][0] if lsq_names else 1
+    lsq_ms = sum(ktab[k][1] for k in lsq_names) / lsq_n
+    fl = lsq_flops(counts)
+    ach64 = fl / (lsq_ms / 1e3) / 1e12
+    executed = kappa_values_executed(col_starts, counts, a.N)
+    fl_exec = None if executed is None else lsq_flops(counts, kappa_values=executed)
+    roofline_precompute = {
+        "kernel": "lsq (B_opt precompute, all solver tiers)", "bound": "alu", "achieved": ach64,
+        "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
+        "peak_source": f"measured in this run: fp64 FMA probe (8 independent FMA chains per thread, 8 CTAs of "
+                       f"256 threads per SM), {fp64_peak:.3f} TFLOP/s; nominal 152 SMs x 4 flop/clk x max clock = "
+                       f"{sm_count() * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12:.3f} TFLOP/s",
+        "traffic": recorded_traffic("k_lsq_thread<17, 5>"),
+        "flop_convention": f"per column of n nodes: n^3/3 + 2n^2 + (n(n-1)/2 + n) x {KAPPA_FLOPS} "
+                           f"(one closed-form kernel value = {KAPPA_FLOPS} flop)",
+        "kappa_values_per_column_definition": float(np.sum(counts * (counts - 1) / 2 + counts)),
+        "kappa_values_executed": executed,
+        "achieved_as_executed": None if fl_exec is None else fl_exec / (lsq_ms / 1e3) / 1e12,
+        "fp64_pipe_active": recorded_counter("lsq_fp64_pipe_active"),
+        "ms": lsq_ms}
     app_tab = {name: ms for name, n, ms in app_kernels}
     app_kernel_ms = sum(app_tab.values()) / k_app
-    ab = apply_bytes(a.N, a.M, info["nnz"])
-    ach_app = ab / (app_ms / 1e3) / 1e9
-    ach_app_graph = ab / (app_graph_ms / 1e3) / 1e9
-    roofline_apply = {"kernel": "spread + fft passes (one apply, event-timed as a whole)", "bound": "hbm",
-                      "achieved": ach_app,
-                      "peak": hbm, "unit": "GB/s", "frac": ach_app / hbm, "traffic": None,
-                      "peak_source": src, "algorithmic_bytes": ab,
-                      "graph_replay": {"ms_per_apply": app_graph_ms, "achieved": ach_app_graph,
-                                       "frac": ach_app_graph / hbm}}
 
     ab_many = K_many * (8 * a.N + 8 * a.M) + 4 * info["nnz"]
     ach_many = ab_many / (many_ms / 1e3) / 1e9
     apply_many = {"vectors": K_many, "ms_per_call": many_ms, "value": world * K_many * a.N / (many_ms / 1e3),
                   "unit": "nodes/s",
-                  "roofline": {"kernel": "spread + fft passes of 16 data vectors (infft_apply_many)", "bound": "hbm",
-                               "achieved": ach_many, "peak": hbm, "unit": "GB/s", "frac": ach_many / hbm,
-                               "algorithmic_bytes": ab_many, "peak_source": src}}
+                  "roofline": {"kernel": "the apply's two kernels over 16 data vectors (infft_apply_many)",
+                               "bound": "hbm", "achieved": ach_many, "peak": hbm, "unit": "GB/s",
+                               "frac": ach_many / hbm, "algorithmic_bytes": ab_many, "peak_source": src}}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(a)
+        cpu, accuracy = cpu_baseline(a, g, torch, dev, stream)
+    else:
+        accuracy = None
 
     out = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64 precompute, f32 apply", "data": "synthetic",
         "config": {"workload": workload_name(a), "M": a.M, "N": a.N, "sigma": 2.0, "m": a.m,
                    "step": "pattern + fp64 B_opt precompute + fp32 apply", "l2_flush": "256 MiB write before each step",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-        "roofline_apply": roofline_apply,
-        "apply_only": {"value": world * a.N / (app_ms / 1e3), "unit": "nodes/s", "ms_per_apply": app_ms,
-                       "kernel_ms_per_apply": app_kernel_ms, "steps": k_app,
-                       "graph_replay": {"value": world * a.N / (app_graph_ms / 1e3), "ms_per_apply": app_graph_ms}},
+        "roofline_precompute": roofline_precompute,
+        "accuracy": accuracy,
+        "apply_only": {"value": world * a.N / (graph_ms / 1e3), "unit": "nodes/s", "ms_per_apply": graph_ms,
+                       "protocol": "rotating plans, CUDA graph (the roofline's figure)",
+                       "stream_back_to_back": {"ms_per_apply": rot["ms_per_apply_stream"],
+                                               "value": world * a.N / (rot["ms_per_apply_stream"] / 1e3)},
+                       "single_apply_l2_flushed": {"ms": app_ms, "achieved_gbs": ach_single,
+                                                   "frac": ach_single / hbm, "kernel_ms": app_kernel_ms,
+                                                   "repeats": k_app}},
         "apply_many": apply_many,
         "fft_vs_cufft": {"own_fft_deconv_ms": own_fft_ms, "cufft_ms": cufft_ms, "length": plan.M_sigma,
                          "note": "own: pruned length-M_sigma FFT with D fused (M outputs); cuFFT: full FFT"},
@@ -652,16 +769,54 @@ def oracle_step(p, f):
     return oracle.infft.infft_apply(B, f)
 
 
-def cpu_baseline(a):
-    """The oracle as it stands, single-threaded, on one full problem of the workload."""
-    p = make_problem(2, M=a.M, N=a.N, m=a.m, with_data=False)
-    f = np.random.default_rng(7).standard_normal(a.N) + 0j
+def cpu_baseline(a, g, torch, dev, stream):
+    """CPU legs on the workload of the headline (rank 0, one GPU), outside every timed GPU region:
+
+    * the oracle as it stands (numpy, one thread): pattern, closed-form fp64 B_opt and
+      D^*F^*B^*f on one full problem with data f = A fhat + 1e-8 noise;
+    * the oracle's C apply (gather, radix-2 FFT, D; OpenMP on every host core), fp64 and fp32,
+      with the oracle's B_opt;
+    * the accuracy of the measured configuration: the GPU's fhat on the same data against the
+      oracle's (on the same complex64 input) and against the true coefficients."""
+    import oracle
+    from oracle import capply
+    p = make_problem(2, M=a.M, N=a.N, m=a.m)
     t0 = time.perf_counter()
-    oracle_step(p, f)
+    B = oracle.bopt.bopt_closed(p.x, p.M, 2.0, p.m)
+    fhat_o = oracle.infft.infft_apply(B, p.f)
     dt = time.perf_counter() - t0
-    return {"value": a.N / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
-            "sample": f"one full problem of the workload (M={a.M}, N={a.N}, m={a.m}): pattern, closed-form "
-                      f"fp64 B_opt and D^*F^*B^*f, {dt:.1f} s"}
+    cpu = {"value": a.N / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+           "sample": f"one full problem of the workload (M={a.M}, N={a.N}, m={a.m}): pattern, closed-form fp64 "
+                     f"B_opt and D^*F^*B^*f, {dt:.1f} s"}
+    # the oracle's C apply on all host cores
+    cores = os.cpu_count() or 1
+    capply.set_threads(cores)
+    c_apply = {}
+    for prec, dt_ in (("f64", np.complex128), ("f32", np.complex64)):
+        ca = capply.CApply(B, prec)
+        fin = p.f.astype(dt_)
+        ca(fin)
+        ts = []
+        for _ in range(5):
+            t1 = time.perf_counter()
+            ca(fin)
+            ts.append(time.perf_counter() - t1)
+        c_apply[prec] = {"ms_per_apply": 1e3 * statistics.median(ts), "nodes_per_s": a.N / statistics.median(ts)}
+    cpu["c_apply"] = dict(c_apply, cores=capply.threads(), nproc=cores,
+                          kind="oracle/capply.c: gather + radix-2 FFT + D, OpenMP, the oracle's B_opt")
+    # accuracy of the measured configuration
+    f32 = np.asarray(p.f, np.complex64)
+    plan = g.infft_plan_create(a.M, a.N, 2.0, a.m)
+    g.infft_set_nodes(plan, torch.tensor(p.x, dtype=torch.float64, device=dev), stream)
+    g.infft_precompute(plan, stream)
+    got = g.infft_apply(plan, torch.tensor(f32, device=dev), stream=stream).cpu().numpy().astype(np.complex128)
+    plan.close()
+    want = oracle.infft.infft_apply(B, f32.astype(np.complex128))
+    accuracy = {"data": "f = A fhat + complex noise of 1e-8 relative level (fp64 trigonometric sum)",
+                "rel_l2_vs_oracle": oracle.infft.rel_l2(got, want), "tolerance": 1e-5,
+                "rel_l2_vs_true_coefficients": oracle.infft.rel_l2(got, p.fhat),
+                "oracle_rel_l2_vs_true_coefficients": oracle.infft.rel_l2(fhat_o, p.fhat)}
+    return cpu, accuracy
 
 
 def run_reference(a):

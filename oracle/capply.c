@@ -30,6 +30,15 @@ int capply_threads(void) {
 #endif
 }
 
+/* threads of the following calls (n >= 1) */
+void capply_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static int64_t bit_reverse(int64_t v, int bits) {
     int64_t r = 0;
     for (int i = 0; i < bits; ++i) {

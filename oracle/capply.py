@@ -41,6 +41,8 @@ def library():
         lib.capply_twiddles.restype = None
         lib.capply_threads.argtypes = []
         lib.capply_threads.restype = ctypes.c_int
+        lib.capply_set_threads.argtypes = [ctypes.c_int]
+        lib.capply_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -48,6 +50,11 @@ def library():
 def threads():
     """OpenMP threads the C apply runs on."""
     return int(library().capply_threads())
+
+
+def set_threads(n):
+    """Sets the OpenMP threads of the following C applies."""
+    library().capply_set_threads(int(n))
 
 
 class CApply:

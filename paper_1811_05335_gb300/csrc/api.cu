@@ -181,14 +181,14 @@ void plan_layout(Plan* p, Carver& c, bool member) {
     c.take(p->phase, N);
     c.take(p->counters, CNT_N);
     c.take(p->w64, p->nnz_cap); c.take(p->w32, p->nnz_cap); c.take(p->J, Ms > N ? Ms : N); c.take(p->wide, Ms);
+    c.take(p->wlo, p->nnz_cap);
     if (member) return;
     c.take(p->gterm, p->nnz_cap);
-    c.take(p->wlo, p->nnz_cap);
     {
         const int64_t tiles = apply2_max_tiles(p) > 0 ? apply2_max_tiles(p) : 1;
         c.take(p->lay_hdr, tiles);
         c.take(p->lay_cdesc, Ms);
-        c.take(p->lay_w, p->nnz_cap + 4 * tiles);
+        c.take(p->lay_w, apply2_weight_capacity(p));
         c.take(p->lay_list, apply2_list_capacity(p));
         c.take(p->lay_list_sorted, apply2_list_capacity(p));
         c.take(p->lay_tmp, 5 * tiles);

@@ -11,7 +11,8 @@
 // sorted nodes.
 //
 // Apply layout.  After the precompute, a preparation pass lays each tile's data out
-// contiguously: its weights (column by column, in the tile's column order), the caller
+// contiguously: its weights (column by column, in the tile's column order, one unused slot
+// after each column so that a warp's columns start on different shared-memory banks), the caller
 // indices (and the sorted positions) of its runs' node windows, and one 8-byte descriptor
 // per column (weight offset and count, offset of its first node in the window list, the
 // float-float flag).  A tile header gives the block positions and lengths; tiles that
@@ -29,6 +30,7 @@
 // data.
 #include "plan.h"
 #include "fft_r8.cuh"
+#include "ffsum.cuh"
 
 namespace {
 
@@ -52,33 +54,6 @@ struct A1Args {
     float2* Y;                // M_sigma: Y[k1 N2 + p2]
     int N;
     int log2;                 // N2 = 2^log2
-};
-
-// s + e = a + b exactly (Knuth's two-sum; the _rn intrinsics keep the compiler from
-// reassociating or contracting)
-INFFT_D void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// sum_i w_i v_i over one column in float-float on the fp32 pipe: b = hi + lo, each product
-// split exactly by an FMA, the sum carried as an unevaluated pair through two-sum (about 44
-// significant bits).  For wide columns (||b_l||_1 > WIDE_COLUMN_L1), whose terms cancel.
-struct FFSum {
-    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    INFFT_D void add(float wh, float wl, float2 v) {
-        const float tr = __fmul_rn(wh, v.x), ti = __fmul_rn(wh, v.y);
-        const float lr = fmaf(wl, v.x, fmaf(wh, v.x, -tr)), li = fmaf(wl, v.y, fmaf(wh, v.y, -ti));
-        float t, err;
-        two_sum(sr, tr, t, err);
-        sr = t;
-        cr += err + lr;
-        two_sum(si, ti, t, err);
-        si = t;
-        ci += err + li;
-    }
-    INFFT_D float2 value() const { return make_float2(sr + cr, si + ci); }
 };
 
 // g_l of one column by direct global loads (tiles that do not fit the staging buffers)
@@ -153,7 +128,13 @@ k_apply_spread_fftA(A1Args a) {
     if (staged) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        for (int q = tid; q < h.w; q += A1_THREADS) cp_async8(fu + q, a.f + sl[q]);
+        for (int q = tid; q < h.w / 4; q += A1_THREADS) {
+            const int4 ix = ((const int4*)sl)[q];
+            cp_async8(fu + 4 * q, a.f + ix.x);
+            cp_async8(fu + 4 * q + 1, a.f + ix.y);
+            cp_async8(fu + 4 * q + 2, a.f + ix.z);
+            cp_async8(fu + 4 * q + 3, a.f + ix.w);
+        }
         cp_async_wait_all();
         __syncthreads();
 #pragma unroll
@@ -171,18 +152,27 @@ k_apply_spread_fftA(A1Args a) {
                 val[k] = s.value();
                 continue;
             }
-            // neighbouring threads' columns start about |I(l)| entries apart: walking each from
-            // a lane-dependent start spreads a warp's shared-memory accesses over the banks
-            float re = 0.f, im = 0.f;
-            int i = n ? (tid & 31) % n : 0;
-            for (int t = 0; t < n; ++t) {
+            float re = 0.f, im = 0.f, re2 = 0.f, im2 = 0.f;
+            int i = 0;
+            for (; i + 4 <= n; i += 4) {
+                const float w0 = wc[i], w1 = wc[i + 1], w2 = wc[i + 2], w3 = wc[i + 3];
+                const float2 v0 = fc[i], v1 = fc[i + 1], v2 = fc[i + 2], v3 = fc[i + 3];
+                re = fmaf(w0, v0.x, re);
+                im = fmaf(w0, v0.y, im);
+                re2 = fmaf(w1, v1.x, re2);
+                im2 = fmaf(w1, v1.y, im2);
+                re = fmaf(w2, v2.x, re);
+                im = fmaf(w2, v2.y, im);
+                re2 = fmaf(w3, v3.x, re2);
+                im2 = fmaf(w3, v3.y, im2);
+            }
+            for (; i < n; ++i) {
                 const float wi = wc[i];
                 const float2 v = fc[i];
                 re = fmaf(wi, v.x, re);
                 im = fmaf(wi, v.y, im);
-                i = (i + 1 == n) ? 0 : i + 1;
             }
-            val[k] = make_float2(re, im);
+            val[k] = make_float2(re + re2, im + im2);
         }
     } else {
 #pragma unroll
@@ -281,7 +271,7 @@ __global__ void k_layout_count(const int32_t* __restrict__ col_off, const int32_
     int w = 0, u = 0, bad = 0;
     for (int r = threadIdx.x; r < N1; r += blockDim.x) {
         const int p0 = (r << log2) + C * b;
-        w += col_off[p0 + C] - col_off[p0];
+        w += col_off[p0 + C] - col_off[p0] + C;   // + one skew slot per column
         const RunWindow rw = run_window(col_off, col_start, N, p0, C);
         u += rw.U;
         bad += !rw.ok;
@@ -304,20 +294,20 @@ k_layout_fill(const int32_t* __restrict__ col_off, const int32_t* __restrict__ c
               const float* __restrict__ w32, const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
               int N, int log1, int log2, int C, const int32_t* __restrict__ wstart, const int32_t* __restrict__ ustart,
               const int32_t* __restrict__ wlen, const int32_t* __restrict__ ulen, const int32_t* __restrict__ direct,
-              int64_t lcap, int4* __restrict__ hdr, uint2* __restrict__ cdesc, float* __restrict__ aw,
+              int64_t wcap, int64_t lcap, int4* __restrict__ hdr, uint2* __restrict__ cdesc, float* __restrict__ aw,
               int32_t* __restrict__ alist, int32_t* __restrict__ alist_sorted) {
     __shared__ int wrun[257], urun[257];   // per run: offsets within the tile's blocks (N1 <= 256)
     const int b = blockIdx.x, N1 = 1 << log1, NCOL = N1 * C;
-    // a tile whose node list would end beyond the lists' capacity is read directly (cannot
-    // happen for windows that are unions of their columns' ranges; a guard for the rest)
-    if (direct[b] || (int64_t)ustart[b] + ulen[b] > lcap) {
+    // a tile whose blocks would end beyond the buffers' capacities is read directly (cannot
+    // happen: the capacities bound the sums of all tiles' blocks; a guard all the same)
+    if (direct[b] || (int64_t)wstart[b] + wlen[b] > wcap || (int64_t)ustart[b] + ulen[b] > lcap) {
         if (threadIdx.x == 0) hdr[b] = make_int4(0, -1, 0, -1);
         return;
     }
     // prefix over the runs: lengths by all threads, then a sequential scan by thread 0
     for (int r = threadIdx.x; r < N1; r += blockDim.x) {
         const int p0 = (r << log2) + C * b;
-        wrun[r + 1] = col_off[p0 + C] - col_off[p0];
+        wrun[r + 1] = col_off[p0 + C] - col_off[p0] + C;
         urun[r + 1] = run_window(col_off, col_start, N, p0, C).U;
     }
     __syncthreads();
@@ -337,9 +327,16 @@ k_layout_fill(const int32_t* __restrict__ col_off, const int32_t* __restrict__ c
     for (int r = warp; r < N1; r += nw) {
         const int p0 = (r << log2) + C * b;
         const RunWindow rw = run_window(col_off, col_start, N, p0, C);
-        // the run's weights (columns p0 .. p0 + C - 1 are contiguous in w32)
+        // the run's weights (columns p0 .. p0 + C - 1 are contiguous in w32), column c shifted
+        // by c slots: each column is followed by one unused slot, so that the columns of a warp
+        // start on spread-out shared-memory banks
         const int o0 = col_off[p0], nrun = col_off[p0 + C] - o0;
-        for (int i = lane; i < nrun; i += 32) awb[wrun[r] + i] = w32[o0 + i];
+        for (int i = lane; i < nrun; i += 32) {
+            int c = 0;
+            while (c + 1 < C && col_off[p0 + c + 1] - o0 <= i) ++c;
+            awb[wrun[r] + i + c] = w32[o0 + i];
+        }
+        if (lane < C) awb[wrun[r] + (col_off[p0 + lane + 1] - o0) + lane] = 0.f;
         for (int i = lane; i < rw.U; i += 32) {
             int q = rw.S + i;
             if (q >= N) q -= N;
@@ -348,7 +345,7 @@ k_layout_fill(const int32_t* __restrict__ col_off, const int32_t* __restrict__ c
         }
         if (lane < C) {
             const int p = p0 + lane;
-            const int woff = wrun[r] + (col_off[p] - o0), n = col_off[p + 1] - col_off[p];
+            const int woff = wrun[r] + (col_off[p] - o0) + lane, n = col_off[p + 1] - col_off[p];
             int r0 = col_start[p] - rw.S;
             if (r0 < 0) r0 += N;
             const unsigned uoff = (unsigned)(urun[r] + (n ? r0 : 0));
@@ -451,6 +448,11 @@ int apply2_default_config(const Plan* p) {
 
 int64_t apply2_max_tiles(const Plan* p) { return p->Ms / 256; }
 
+int64_t apply2_weight_capacity(const Plan* p) {
+    // every weight once, one skew slot per grid point, 3 padding slots per tile
+    return p->nnz_cap + p->Ms + 4 * apply2_max_tiles(p);
+}
+
 int64_t apply2_list_capacity(const Plan* p) {
     // a node lies in the windows of at most (C + 2m)/C + 1 <= m + 2 runs (C >= 2), plus 3
     // padding entries per tile
@@ -487,8 +489,9 @@ cudaError_t run_apply_layout(Plan* p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     launch_begin(p, "layout_fill", s);
     k_layout_fill<<<tiles, 256, 0, s>>>(p->col_off, p->col_start, p->w32, p->wide, p->perm, (int)p->N, log1, log2, C,
-                                         wstart, ustart, wlen, ulen, direct, apply2_list_capacity(p), p->lay_hdr,
-                                         p->lay_cdesc, p->lay_w, p->lay_list, p->lay_list_sorted);
+                                         wstart, ustart, wlen, ulen, direct, apply2_weight_capacity(p),
+                                         apply2_list_capacity(p), p->lay_hdr, p->lay_cdesc, p->lay_w, p->lay_list,
+                                         p->lay_list_sorted);
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     p->lay_cfg = id;

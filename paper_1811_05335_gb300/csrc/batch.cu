@@ -51,6 +51,7 @@ constexpr int BATCH_STREAMS = 48;
 struct BatchProblem {
     const float* w32;
     const double* w64;
+    float* wlo;            // low parts fp32(w64 - w32) of the float-float spreading
     const uint8_t* wide;
     const int32_t* perm;
     const int32_t* col_start;
@@ -237,6 +238,15 @@ INFFT_D bool tile_start(const int32_t* __restrict__ col_off, int p) {
     return p % TILE_COLS == 0 || (col_off[p] / TILE_WEIGHTS) != (col_off[p - 1] / TILE_WEIGHTS);
 }
 
+// Per problem (one CTA): the low parts fp32(w64 - w32) of its weights, for the float-float
+// spreading of wide columns (the fp64 subtraction belongs to the precompute).
+__global__ void __launch_bounds__(TILE_SCAN_THREADS)
+k_batch_weights_lo(const BatchProblem* __restrict__ probs) {
+    const BatchProblem pr = probs[blockIdx.x];
+    const int nnz = pr.col_off[2 * pr.M];
+    for (int e = threadIdx.x; e < nnz; e += blockDim.x) pr.wlo[e] = (float)(pr.w64[e] - (double)pr.w32[e]);
+}
+
 // Per problem (one CTA): its number of tiles.
 __global__ void __launch_bounds__(TILE_SCAN_THREADS)
 k_tile_count(const BatchProblem* __restrict__ probs, int32_t* __restrict__ count) {
@@ -335,8 +345,8 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     float2* g = g_all + pr.g_off;
     const int wb = w0 & ~3, we = (w1 + 3) & ~3;
     if ((we - wb) > TILE_WMAX || U > TILE_UMAX || U > N) {   // block-uniform
-        spread_tile_segmented<TILE_COLS>(fp, pr.w32, pr.w64, pr.wide, pr.perm, pr.col_start, pr.col_off, N, p0, p1, w0, w1, g,
-                              (int*)ws, fu);
+        spread_tile_segmented<TILE_COLS>(fp, pr.w32, pr.wlo, pr.wide, pr.perm, pr.col_start, pr.col_off, N, p0, p1,
+                                         w0, w1, g, (int*)ws, fu);
         return;
     }
     const float* w32 = pr.w32;
@@ -367,7 +377,7 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     int r0 = s - S;
     if (r0 < 0) r0 += N;
     if (wide_col || (n > 0 && r0 + n > U)) {
-        g[p] = spread_direct<float>(fp, w32, pr.w64, wide_col, perm, n, s, off, N);
+        g[p] = spread_direct<float>(fp, w32, nullptr, pr.wlo, wide_col, perm, n, s, off, N);
         return;
     }
     // walk the column from a lane-dependent start (neighbouring columns sit |I(l)|
@@ -659,6 +669,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     for (int64_t i = 0; i < P; ++i) {
         Plan* p = new Plan();
         p->device = b->device;
+        p->sms = b->sms;
         p->M = M[i]; p->N = N[i]; p->Ms = 2 * M[i]; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
         p->ansatz = INFFT_ANSATZ_OVERDETERMINED;
         p->logMs = log2_ceil(p->Ms);
@@ -728,7 +739,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
         Plan* p = b->plans[i];
         p->x = b->x_all + b->noff[i];
         BatchProblem& d = hp[i];
-        d.w32 = p->w32; d.w64 = p->w64; d.wide = p->wide; d.perm = p->perm;
+        d.w32 = p->w32; d.w64 = p->w64; d.wlo = p->wlo; d.wide = p->wide; d.perm = p->perm;
         d.col_start = p->col_start; d.col_count = p->col_count; d.col_off = p->col_off;
         d.bhat = b->bhat + loff[i];
         d.f_off = b->noff[i]; d.fhat_off = b->moff[i]; d.g_off = goff[i];
@@ -829,6 +840,8 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
                                  b->huge_slots, b->huge_nmax, s)) !=
             cudaSuccess)
         return cuda_err(e, "large-column precompute");
+    k_batch_weights_lo<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs);
+    count_launches(1);
     // spreading tiles from the weight offsets
     k_tile_count<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, b->tile_count);
     k_tile_prefix<<<1, 1024, 0, s>>>(b->tile_count, (int)b->P, b->tile_off);

@@ -36,9 +36,9 @@ constexpr int LSQ_CTA_NMAX = 224;
 // largest |I(x_j)| = 2m + 1 of the underdetermined case
 constexpr int UNDER_NMAX = 17;
 
-// Columns whose ||b_l||_1 exceeds this are spread and interpolated with fp64
-// weights and fp64 accumulation: their terms cancel, and fp32 rounding of
-// O(||b_l||_1 |f|) terms would dominate the result.
+// Columns whose ||b_l||_1 exceeds this are spread and interpolated in float-float on the
+// fp32 pipe (weights as fp32 pairs hi + lo, exact products, compensated sums; ffsum.cuh):
+// their terms cancel, and fp32 rounding of O(||b_l||_1 |f|) terms would dominate the result.
 constexpr double WIDE_COLUMN_L1 = 32.0;
 
 struct ProfileRec {
@@ -106,7 +106,7 @@ struct infft_plan_s {
     // the weights and node-window lists tile by tile
     int4* lay_hdr = nullptr;          // max tiles
     uint2* lay_cdesc = nullptr;       // Ms
-    float* lay_w = nullptr;           // nnz_cap + 4 max tiles
+    float* lay_w = nullptr;           // apply2_weight_capacity
     int32_t* lay_list = nullptr;      // apply2_list_capacity: caller indices
     int32_t* lay_list_sorted = nullptr;   // the same windows as sorted positions
     int32_t* lay_tmp = nullptr;       // 5 max tiles: block lengths, direct flags, block starts
@@ -195,6 +195,7 @@ cudaError_t run_apply2(Plan* p, const float2* f, bool sorted, float2* fhat, cuda
 cudaError_t run_weights_lo(Plan* p, cudaStream_t s);
 int64_t apply2_max_tiles(const Plan* p);
 int64_t apply2_list_capacity(const Plan* p);
+int64_t apply2_weight_capacity(const Plan* p);
 void apply2_config_shape(int id, int* log1, int* C);
 // apply.cu: out[i] = f[perm[i]] (sort) and out[perm[i]] = f[i] (unsort), complex64
 cudaError_t run_sort_values(Plan* p, const float2* f, float2* out, cudaStream_t s);

@@ -7,17 +7,17 @@
 
 namespace {
 
-// Spreading of the fp32 path.  A CTA owns SPREAD_COLS consecutive grid points:
-// their weights are one contiguous block of B_opt's storage and their nodes one
-// contiguous (wrapping) range of sorted nodes, so both are staged in shared
-// memory with coalesced loads before each thread sums its own column.  Columns
-// with large ||b_l||_1 ("wide", cancelling terms) use the fp64 weights and an
-// fp64 accumulator.  A CTA whose block does not fit falls back to direct loads.
+// Spreading in the precision of T (the fp64 apply; the fp32 apply uses k_spread_f32 or the
+// fused kernel of apply.cu).  A CTA owns SPREAD_COLS consecutive grid points: their
+// weights are one contiguous block of B_opt's storage and their nodes one contiguous
+// (wrapping) range of sorted nodes, so both are staged in shared memory with coalesced
+// loads before each thread sums its own column (fp32 staging only; fp64 reads directly).
 
 template <typename T>
 __global__ void __launch_bounds__(SPREAD_COLS)
 k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32, const double* __restrict__ w64,
-         const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
+         const float* __restrict__ wlo, const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
+         const int32_t* __restrict__ col_start,
          const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
          cplx_t<T>* __restrict__ g) {
     __shared__ __align__(16) float ws[SPREAD_WMAX];
@@ -46,7 +46,7 @@ k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32, const d
     const bool staged = __syncthreads_and(inside) && sizeof(T) == 4 && (w1 - w0) <= SPREAD_WMAX &&
                         U <= SPREAD_UMAX && U <= N;
     if (!staged) {
-        if (live) g[p] = spread_direct<T>(f, w32, w64, wide_col, perm, n, s, off, N);
+        if (live) g[p] = spread_direct<T>(f, w32, w64, wlo, wide_col, perm, n, s, off, N);
         return;
     }
     // weights: 16-byte vector loads of the aligned part, scalar edges
@@ -73,7 +73,7 @@ k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32, const d
     __syncthreads();
     if (!live) return;
     if (wide_col) {
-        g[p] = spread_direct<T>(f, w32, w64, true, perm, n, s, off, N);
+        g[p] = spread_direct<T>(f, w32, w64, wlo, true, perm, n, s, off, N);
         return;
     }
     const float* wc = ws + (off - w0);
@@ -90,7 +90,7 @@ k_spread(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32, const d
 // The fp32 spreading of the apply (one tile of SPREAD_COLS grid points per CTA),
 // launched as a programmatically dependent kernel.
 __global__ void __launch_bounds__(SPREAD_COLS)
-k_spread_f32(const float2* __restrict__ f, const float* __restrict__ w32, const double* __restrict__ w64,
+k_spread_f32(const float2* __restrict__ f, const float* __restrict__ w32, const float* __restrict__ wlo,
              const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
              const int32_t* __restrict__ col_start, const int32_t* __restrict__ col_count,
              const int32_t* __restrict__ col_off, int N, int Ms, float2* __restrict__ g) {
@@ -100,14 +100,15 @@ k_spread_f32(const float2* __restrict__ f, const float* __restrict__ w32, const 
     griddep_launch();
     // data vector blockIdx.y: f and g of vector k at k N and k M_sigma
     const int p0 = blockIdx.x * SPREAD_COLS;
-    spread_tile_f32(f + (size_t)blockIdx.y * N, w32, w64, wide, perm, col_start, col_count, col_off, N, p0,
+    spread_tile_f32(f + (size_t)blockIdx.y * N, w32, wlo, wide, perm, col_start, col_count, col_off, N, p0,
                     min(p0 + SPREAD_COLS, Ms), g + (size_t)blockIdx.y * Ms, ws, fu);
 }
 
 // One thread per sorted node: gathers from the 2m (or 2m+1) grid points of I(x_j).
 template <typename T>
 __global__ void k_interp(const cplx_t<T>* __restrict__ g, const float* __restrict__ w32,
-                         const double* __restrict__ w64, const uint8_t* __restrict__ wide,
+                         const double* __restrict__ w64, const float* __restrict__ wlo,
+                         const uint8_t* __restrict__ wide,
                          const uint32_t* __restrict__ skey, const int32_t* __restrict__ perm,
                          const int32_t* __restrict__ col_start, const int32_t* __restrict__ col_off, int N,
                          int Ms, int m, cplx_t<T>* __restrict__ f) {
@@ -116,25 +117,41 @@ __global__ void k_interp(const cplx_t<T>* __restrict__ g, const float* __restric
     const uint32_t key = skey[i];
     const int cell = (int)(key >> 1);
     const int first = cell - m + (int)(key & 1u);   // integer nodes also meet cell - m
-    float re32 = 0, im32 = 0;
-    double re64 = 0, im64 = 0;
-    for (int c = first; c <= cell + m; ++c) {
-        int q = c;
-        if (q < 0) q += Ms; else if (q >= Ms) q -= Ms;
-        int pos = i - col_start[q];
-        if (pos < 0) pos += N;
-        const cplx_t<T> v = g[q];
-        if (sizeof(T) == 8 || wide[q]) {
+    if constexpr (sizeof(T) == 8) {
+        double re = 0, im = 0;
+        for (int c = first; c <= cell + m; ++c) {
+            int q = c;
+            if (q < 0) q += Ms; else if (q >= Ms) q -= Ms;
+            int pos = i - col_start[q];
+            if (pos < 0) pos += N;
+            const cplx_t<T> v = g[q];
             const double wi = w64[col_off[q] + pos];
-            re64 += wi * (double)v.x;
-            im64 += wi * (double)v.y;
-        } else {
-            const float wi = w32[col_off[q] + pos];
-            re32 += wi * (float)v.x;
-            im32 += wi * (float)v.y;
+            re += wi * (double)v.x;
+            im += wi * (double)v.y;
         }
+        f[perm[i]] = cmake((T)re, (T)im);
+    } else {
+        // fp32 terms, and the terms of wide columns in float-float (ffsum.cuh)
+        float re = 0, im = 0;
+        FFSum acc;
+        for (int c = first; c <= cell + m; ++c) {
+            int q = c;
+            if (q < 0) q += Ms; else if (q >= Ms) q -= Ms;
+            int pos = i - col_start[q];
+            if (pos < 0) pos += N;
+            const float2 v = make_float2((float)g[q].x, (float)g[q].y);
+            const int e = col_off[q] + pos;
+            if (wide[q]) {
+                acc.add(w32[e], wlo[e], v);
+            } else {
+                re = fmaf(w32[e], v.x, re);
+                im = fmaf(w32[e], v.y, im);
+            }
+        }
+        acc.add(1.0f, 0.0f, make_float2(re, im));
+        const float2 r = acc.value();
+        f[perm[i]] = cmake((T)r.x, (T)r.y);
     }
-    f[perm[i]] = cmake((T)(re64 + (double)re32), (T)(im64 + (double)im32));
 }
 
 }  // namespace
@@ -146,10 +163,10 @@ cudaError_t run_spread(Plan* p, const void* f, cudaStream_t s) {
     const int blocks = (Ms + SPREAD_COLS - 1) / SPREAD_COLS;
     cudaError_t e = cudaSuccess;
     if constexpr (sizeof(T) == 4) {
-        e = launch_pdl(k_spread_f32, dim3(blocks), dim3(SPREAD_COLS), 0, s, (const float2*)f, p->w32, p->w64,
+        e = launch_pdl(k_spread_f32, dim3(blocks), dim3(SPREAD_COLS), 0, s, (const float2*)f, p->w32, p->wlo,
                        p->wide, p->perm, p->col_start, p->col_count, p->col_off, (int)p->N, Ms, (float2*)p->grid);
     } else {
-        k_spread<T><<<blocks, SPREAD_COLS, 0, s>>>((const cplx_t<T>*)f, p->w32, p->w64, p->wide, p->perm,
+        k_spread<T><<<blocks, SPREAD_COLS, 0, s>>>((const cplx_t<T>*)f, p->w32, p->w64, p->wlo, p->wide, p->perm,
                                                    p->col_start, p->col_count, p->col_off, (int)p->N, Ms,
                                                    (cplx_t<T>*)p->grid);
     }
@@ -162,7 +179,8 @@ template <typename T>
 cudaError_t run_interp(Plan* p, void* f, cudaStream_t s) {
     const int N = (int)p->N;
     launch_begin(p, sizeof(T) == 4 ? "interp" : "interp_z", s);
-    k_interp<T><<<(N + 255) / 256, 256, 0, s>>>((const cplx_t<T>*)p->grid, p->w32, p->w64, p->wide, p->skey, p->perm,
+    k_interp<T><<<(N + 255) / 256, 256, 0, s>>>((const cplx_t<T>*)p->grid, p->w32, p->w64, p->wlo, p->wide, p->skey,
+                                                 p->perm,
                                                  p->col_start, p->col_off, N, (int)p->Ms, p->m,
                                                  (cplx_t<T>*)f);
     launch_end(p, s);
@@ -184,7 +202,7 @@ static constexpr int MANY_NB = 4;                   // buffers (prefetch depth M
 static constexpr size_t MANY_SMEM = SPREAD_WMAX * sizeof(float) + MANY_NB * MANY_UMAX * sizeof(float2);
 
 static __global__ void __launch_bounds__(SPREAD_COLS, 3)
-k_spread_many(const float2* __restrict__ f, int K, const float* __restrict__ w32, const double* __restrict__ w64,
+k_spread_many(const float2* __restrict__ f, int K, const float* __restrict__ w32, const float* __restrict__ wlo,
               const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
               const int32_t* __restrict__ col_start, const int32_t* __restrict__ col_count,
               const int32_t* __restrict__ col_off, int N, int Ms, float2* __restrict__ g) {
@@ -211,7 +229,7 @@ k_spread_many(const float2* __restrict__ f, int K, const float* __restrict__ w32
     const bool staged = __syncthreads_and(inside) && (we - wb) <= SPREAD_WMAX && U <= MANY_UMAX && U <= N;
     if (!staged) {
         for (int k = 0; k < K; ++k) {
-            spread_tile_f32(f + (size_t)k * N, w32, w64, wide, perm, col_start, col_count, col_off, N, p0, p1,
+            spread_tile_f32(f + (size_t)k * N, w32, wlo, wide, perm, col_start, col_count, col_off, N, p0, p1,
                             g + (size_t)k * Ms, ws, fu);
             __syncthreads();
         }
@@ -250,7 +268,7 @@ k_spread_many(const float2* __restrict__ f, int K, const float* __restrict__ w32
         if (live) {
             float2* gk = g + (size_t)k * Ms;
             if (wide_col) {
-                gk[p] = spread_direct<float>(f + (size_t)k * N, w32, w64, true, perm, n, s, off, N);
+                gk[p] = spread_direct<float>(f + (size_t)k * N, w32, nullptr, wlo, true, perm, n, s, off, N);
             } else {
                 // walk the column from a lane-dependent start (see spread_tile_f32)
                 const float* wc = ws + (off - wb);
@@ -277,7 +295,7 @@ cudaError_t run_spread_many(Plan* p, const void* f, void* grid, int K, cudaStrea
     if (e != cudaSuccess) return e;
     launch_begin(p, "spread_many", s);
     e = launch_pdl(k_spread_many, dim3((Ms + SPREAD_COLS - 1) / SPREAD_COLS), dim3(SPREAD_COLS), MANY_SMEM, s,
-                   (const float2*)f, K, p->w32, p->w64, p->wide, p->perm, p->col_start, p->col_count, p->col_off,
+                   (const float2*)f, K, p->w32, p->wlo, p->wide, p->perm, p->col_start, p->col_count, p->col_off,
                    (int)p->N, Ms, (float2*)grid);
     launch_end(p, s);
     if (e != cudaSuccess) return e;

@@ -4,6 +4,7 @@
 // nodes of I(l).
 #pragma once
 #include "plan.h"
+#include "ffsum.cuh"
 
 namespace {
 
@@ -11,12 +12,14 @@ constexpr int SPREAD_COLS = 256;
 constexpr int SPREAD_WMAX = 8192;     // staged weights per CTA (32 KB)
 constexpr int SPREAD_UMAX = 2048;     // staged node values per CTA (16 KB)
 
+// g_l of one column by direct loads: fp64 weights and accumulation for T = double; fp32 for
+// T = float, float-float (w32 + wlo, ffsum.cuh) for wide columns.
 template <typename T>
 INFFT_D cplx_t<T> spread_direct(const cplx_t<T>* __restrict__ f, const float* __restrict__ w32,
-                                const double* __restrict__ w64, bool wide_col, const int32_t* __restrict__ perm,
-                                int n, int s, int off, int N) {
+                                const double* __restrict__ w64, const float* __restrict__ wlo, bool wide_col,
+                                const int32_t* __restrict__ perm, int n, int s, int off, int N) {
     int q = s;
-    if (sizeof(T) == 8 || wide_col) {
+    if constexpr (sizeof(T) == 8) {
         double re = 0, im = 0;
         for (int i = 0; i < n; ++i) {
             const double wi = w64[off + i];
@@ -26,16 +29,25 @@ INFFT_D cplx_t<T> spread_direct(const cplx_t<T>* __restrict__ f, const float* __
             if (++q == N) q = 0;
         }
         return cmake((T)re, (T)im);
+    } else {
+        if (wide_col) {
+            FFSum acc;
+            for (int i = 0; i < n; ++i) {
+                acc.add(w32[off + i], wlo[off + i], f[perm[q]]);
+                if (++q == N) q = 0;
+            }
+            return acc.value();
+        }
+        float re = 0, im = 0;
+        for (int i = 0; i < n; ++i) {
+            const float wi = w32[off + i];
+            const cplx_t<T> v = f[perm[q]];
+            re += wi * (float)v.x;
+            im += wi * (float)v.y;
+            if (++q == N) q = 0;
+        }
+        return cmake((T)re, (T)im);
     }
-    float re = 0, im = 0;
-    for (int i = 0; i < n; ++i) {
-        const float wi = w32[off + i];
-        const cplx_t<T> v = f[perm[q]];
-        re += wi * (float)v.x;
-        im += wi * (float)v.y;
-        if (++q == N) q = 0;
-    }
-    return cmake((T)re, (T)im);
 }
 
 // Spreads grid points [p0, p1) whose weights [w0, w1) do not fit a staging buffer
@@ -43,12 +55,12 @@ INFFT_D cplx_t<T> spread_direct(const cplx_t<T>* __restrict__ f, const float* __
 // time (coalesced weight and index loads); each thread follows its entry's column
 // with a running pointer over the tile's offsets, a warp-level segmented sum
 // combines neighbouring entries of one column and the segment's last lane adds it
-// to the column's sum in shared memory.  fp64 ("wide") columns are summed per
+// to the column's sum in shared memory.  Wide columns (float-float) are summed per
 // thread afterwards.  iw: 2 COLS + 1 ints, gs: COLS float2 of shared
 // memory.  Every thread of the CTA calls it.
 template <int COLS = SPREAD_COLS>
 INFFT_D void spread_tile_segmented(const float2* __restrict__ f, const float* __restrict__ w32,
-                                   const double* __restrict__ w64, const uint8_t* __restrict__ wide,
+                                   const float* __restrict__ wlo, const uint8_t* __restrict__ wide,
                                    const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
                                    const int32_t* __restrict__ col_off, int N, int p0, int p1, int w0, int w1,
                                    float2* __restrict__ g, int* iw, float2* gs) {
@@ -96,7 +108,7 @@ INFFT_D void spread_tile_segmented(const float2* __restrict__ f, const float* __
     __syncthreads();
     const int p = p0 + threadIdx.x;
     if (p < p1) {
-        if (wide[p]) g[p] = spread_direct<float>(f, w32, w64, true, perm, col_off[p + 1] - col_off[p], col_start[p],
+        if (wide[p]) g[p] = spread_direct<float>(f, w32, nullptr, wlo, true, perm, col_off[p + 1] - col_off[p], col_start[p],
                                                   col_off[p], N);
         else g[p] = gs[threadIdx.x];
     }
@@ -107,13 +119,13 @@ INFFT_D void spread_tile_segmented(const float2* __restrict__ f, const float* __
 // memory by 16-byte asynchronous copies of the 16-byte aligned span around them,
 // the node indices of the window come to registers and the node values follow by
 // 8-byte asynchronous copies, so every load of the tile is in flight at once.
-// Columns with large ||b_l||_1 use the fp64 weights; a tile whose block does not
+// Columns with large ||b_l||_1 spread in float-float; a tile whose block does not
 // fit the staging buffers falls back to direct loads.  One thread per grid point;
 // every thread of the CTA calls it.
 constexpr int SPREAD_UPT = SPREAD_UMAX / SPREAD_COLS;   // staged node values per thread
 
 INFFT_D void spread_tile_f32(const float2* __restrict__ f, const float* __restrict__ w32,
-                             const double* __restrict__ w64, const uint8_t* __restrict__ wide,
+                             const float* __restrict__ wlo, const uint8_t* __restrict__ wide,
                              const int32_t* __restrict__ perm, const int32_t* __restrict__ col_start,
                              const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N,
                              int p0, int p1, float2* __restrict__ g, float* ws, float2* fu) {
@@ -134,7 +146,7 @@ INFFT_D void spread_tile_f32(const float2* __restrict__ f, const float* __restri
     const int inside = !live || n == 0 || (r0 + n <= U);
     const bool staged = __syncthreads_and(inside) && (we - wb) <= SPREAD_WMAX && U <= SPREAD_UMAX && U <= N;
     if (!staged) {
-        spread_tile_segmented(f, w32, w64, wide, perm, col_start, col_off, N, p0, p1, w0, w1, g, (int*)ws, fu);
+        spread_tile_segmented(f, w32, wlo, wide, perm, col_start, col_off, N, p0, p1, w0, w1, g, (int*)ws, fu);
         return;
     }
     for (int v = threadIdx.x; v < (we - wb) / 4; v += SPREAD_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
@@ -155,7 +167,7 @@ INFFT_D void spread_tile_f32(const float2* __restrict__ f, const float* __restri
     __syncthreads();
     if (!live) return;
     if (wide_col) {
-        g[p] = spread_direct<float>(f, w32, w64, true, perm, n, s, off, N);
+        g[p] = spread_direct<float>(f, w32, nullptr, wlo, true, perm, n, s, off, N);
         return;
     }
     // Neighbouring threads' columns start about |I(l)| weights (and N/M_sigma nodes)
