@@ -325,7 +325,6 @@ infft_status infft_precompute(infft_plan_t p, infft_stream_t stream) {
     p->apply_clean = 0;
     p->lay_cfg = -1;
     cudaError_t e = p->ansatz == INFFT_ANSATZ_UNDERDETERMINED ? run_precompute_under(p, s) : run_precompute(p, s);
-    if (e == cudaSuccess) e = run_weights_lo(p, s);
     if (e != cudaSuccess) return cuda_fail(e, "precompute");
     p->precomputed = 1;
     return INFFT_OK;

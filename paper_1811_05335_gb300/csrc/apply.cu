@@ -288,74 +288,101 @@ __global__ void k_layout_count(const int32_t* __restrict__ col_off, const int32_
 }
 
 // Pass 2 (wstart, ustart: exclusive prefix sums of the lengths): header, weights, node lists
-// and column descriptors of tile b, one warp per run.
-__global__ void __launch_bounds__(256)
+// and column descriptors of tile b.  The tile's column offsets and starts are staged in
+// shared memory once; the runs' offsets within the tile's blocks come from a block scan.
+__global__ void __launch_bounds__(1024)
 k_layout_fill(const int32_t* __restrict__ col_off, const int32_t* __restrict__ col_start,
               const float* __restrict__ w32, const uint8_t* __restrict__ wide, const int32_t* __restrict__ perm,
               int N, int log1, int log2, int C, const int32_t* __restrict__ wstart, const int32_t* __restrict__ ustart,
               const int32_t* __restrict__ wlen, const int32_t* __restrict__ ulen, const int32_t* __restrict__ direct,
               int64_t wcap, int64_t lcap, int4* __restrict__ hdr, uint2* __restrict__ cdesc, float* __restrict__ aw,
               int32_t* __restrict__ alist, int32_t* __restrict__ alist_sorted) {
-    __shared__ int wrun[257], urun[257];   // per run: offsets within the tile's blocks (N1 <= 256)
-    const int b = blockIdx.x, N1 = 1 << log1, NCOL = N1 * C;
+    __shared__ int s_off[A1_NCOL_MAX + 256];   // N1 (C + 1) column offsets (N1 <= 256, N1 C <= 512)
+    __shared__ int s_st[A1_NCOL_MAX];          // N1 C column starts
+    __shared__ int wrun[257], urun[257], rS[256], red[64];
+    const int b = blockIdx.x, N1 = 1 << log1, NCOL = N1 * C, tid = threadIdx.x;
     // a tile whose blocks would end beyond the buffers' capacities is read directly (cannot
     // happen: the capacities bound the sums of all tiles' blocks; a guard all the same)
     if (direct[b] || (int64_t)wstart[b] + wlen[b] > wcap || (int64_t)ustart[b] + ulen[b] > lcap) {
-        if (threadIdx.x == 0) hdr[b] = make_int4(0, -1, 0, -1);
+        if (tid == 0) hdr[b] = make_int4(0, -1, 0, -1);
         return;
     }
-    // prefix over the runs: lengths by all threads, then a sequential scan by thread 0
-    for (int r = threadIdx.x; r < N1; r += blockDim.x) {
-        const int p0 = (r << log2) + C * b;
-        wrun[r + 1] = col_off[p0 + C] - col_off[p0] + C;
-        urun[r + 1] = run_window(col_off, col_start, N, p0, C).U;
+    for (int i = tid; i < N1 * (C + 1); i += blockDim.x) {
+        const int r = i / (C + 1), c = i - r * (C + 1);
+        s_off[i] = col_off[(r << log2) + C * b + c];
+    }
+    for (int i = tid; i < NCOL; i += blockDim.x) {
+        const int r = i / C, c = i - r * C;
+        s_st[i] = col_start[(r << log2) + C * b + c];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // per run (thread r): weights incl. one skew slot per column, window start and length
+    int W = 0, U = 0;
+    if (tid < N1) {
+        const int* o = s_off + tid * (C + 1);
+        W = o[C] - o[0] + C;
+        const int S = s_st[tid * C];
+        U = s_st[tid * C + C - 1] + (o[C] - o[C - 1]) - S;
+        if (U < 0) U += N;
+        rS[tid] = S;
+    }
+    // inclusive block scans of W and U (blockDim.x = 1024 = 32 warps)
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    int wi = W, ui = U;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, wi, o), c = __shfl_up_sync(0xffffffffu, ui, o);
+        if (lane >= o) { wi += a; ui += c; }
+    }
+    if (lane == 31) { red[warp] = wi; red[32 + warp] = ui; }
+    __syncthreads();
+    int wbase = 0, ubase = 0;
+    for (int w = 0; w < warp; ++w) { wbase += red[w]; ubase += red[32 + w]; }
+    if (tid < N1) {
+        wrun[tid + 1] = wbase + wi;
+        urun[tid + 1] = ubase + ui;
+    }
+    if (tid == 0) {
         wrun[0] = urun[0] = 0;
-        for (int r = 0; r < N1; ++r) {
-            wrun[r + 1] += wrun[r];
-            urun[r + 1] += urun[r];
-        }
         hdr[b] = make_int4(wstart[b], wlen[b], ustart[b], ulen[b]);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float* awb = aw + wstart[b];
     int32_t* alb = alist + ustart[b];
     int32_t* asb = alist_sorted + ustart[b];
     for (int r = warp; r < N1; r += nw) {
-        const int p0 = (r << log2) + C * b;
-        const RunWindow rw = run_window(col_off, col_start, N, p0, C);
-        // the run's weights (columns p0 .. p0 + C - 1 are contiguous in w32), column c shifted
-        // by c slots: each column is followed by one unused slot, so that the columns of a warp
-        // start on spread-out shared-memory banks
-        const int o0 = col_off[p0], nrun = col_off[p0 + C] - o0;
+        const int* o = s_off + r * (C + 1);
+        const int o0 = o[0], nrun = o[C] - o0;
+        // the run's weights (its columns are contiguous in w32), column c shifted by c slots:
+        // each column is followed by one unused slot, so that the columns of a warp start on
+        // spread-out shared-memory banks
         for (int i = lane; i < nrun; i += 32) {
             int c = 0;
-            while (c + 1 < C && col_off[p0 + c + 1] - o0 <= i) ++c;
+            while (c + 1 < C && o[c + 1] - o0 <= i) ++c;
             awb[wrun[r] + i + c] = w32[o0 + i];
         }
-        if (lane < C) awb[wrun[r] + (col_off[p0 + lane + 1] - o0) + lane] = 0.f;
-        for (int i = lane; i < rw.U; i += 32) {
-            int q = rw.S + i;
+        if (lane < C) awb[wrun[r] + (o[lane + 1] - o0) + lane] = 0.f;
+        const int S = rS[r], Ur = urun[r + 1] - urun[r];
+        for (int i = lane; i < Ur; i += 32) {
+            int q = S + i;
             if (q >= N) q -= N;
             alb[urun[r] + i] = perm[q];
             asb[urun[r] + i] = q;
         }
-        if (lane < C) {
-            const int p = p0 + lane;
-            const int woff = wrun[r] + (col_off[p] - o0) + lane, n = col_off[p + 1] - col_off[p];
-            int r0 = col_start[p] - rw.S;
-            if (r0 < 0) r0 += N;
-            const unsigned uoff = (unsigned)(urun[r] + (n ? r0 : 0));
-            cdesc[(size_t)b * NCOL + r * C + lane] =
-                make_uint2((unsigned)woff | ((unsigned)n << 16), uoff | ((unsigned)(wide[p] != 0) << 31));
-        }
+    }
+    for (int j = tid; j < NCOL; j += blockDim.x) {
+        const int r = j / C, c = j - r * C;
+        const int* o = s_off + r * (C + 1);
+        const int woff = wrun[r] + (o[c] - o[0]) + c, n = o[c + 1] - o[c];
+        int r0 = s_st[j] - rS[r];
+        if (r0 < 0) r0 += N;
+        const unsigned uoff = (unsigned)(urun[r] + (n ? r0 : 0));
+        const int p = (r << log2) + C * b + c;
+        cdesc[(size_t)b * NCOL + j] = make_uint2((unsigned)woff | ((unsigned)n << 16),
+                                                 uoff | ((unsigned)(wide[p] != 0) << 31));
     }
     // zero the padding at the blocks' ends
-    if (threadIdx.x < 4) {
-        const int w = wrun[N1] + (int)threadIdx.x, u = urun[N1] + (int)threadIdx.x;
+    if (tid < 4) {
+        const int w = wrun[N1] + tid, u = urun[N1] + tid;
         if (w < wlen[b]) awb[w] = 0.f;
         if (u < ulen[b]) {
             alb[u] = 0;
@@ -374,15 +401,6 @@ __global__ void k_permute_values(const float2* __restrict__ f, const int32_t* __
         if (SORT) out[i] = f[perm[i]];
         else out[perm[i]] = f[i];
     }
-}
-
-// low parts of the weights: wlo = fp32(w64 - fp32(w64)) for the float-float spreading of
-// wide columns (the fp64 subtraction belongs to the precompute, not to the apply)
-__global__ void k_weights_lo(const double* __restrict__ w64, const float* __restrict__ w32,
-                             const int32_t* __restrict__ col_off, int Ms, float* __restrict__ wlo) {
-    const int nnz = col_off[Ms];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
-        wlo[e] = (float)(w64[e] - (double)w32[e]);
 }
 
 using A1Fn = void (*)(A1Args);
@@ -459,13 +477,6 @@ int64_t apply2_list_capacity(const Plan* p) {
     return p->N * ((int64_t)p->m + 2) + 4 * apply2_max_tiles(p);
 }
 
-cudaError_t run_weights_lo(Plan* p, cudaStream_t s) {
-    launch_begin(p, "weights_lo", s);
-    k_weights_lo<<<2 * p->sms, 256, 0, s>>>(p->w64, p->w32, p->col_off, (int)p->Ms, p->wlo);
-    launch_end(p, s);
-    return cudaGetLastError();
-}
-
 // Lays out the tiles of the current shape (after precompute or a change of shape).
 cudaError_t run_apply_layout(Plan* p, cudaStream_t s) {
     int n;
@@ -488,7 +499,7 @@ cudaError_t run_apply_layout(Plan* p, cudaStream_t s) {
     if (e == cudaSuccess) e = run_exclusive_scan(p, ulen, ustart, tiles, s);
     if (e != cudaSuccess) return e;
     launch_begin(p, "layout_fill", s);
-    k_layout_fill<<<tiles, 256, 0, s>>>(p->col_off, p->col_start, p->w32, p->wide, p->perm, (int)p->N, log1, log2, C,
+    k_layout_fill<<<tiles, 1024, 0, s>>>(p->col_off, p->col_start, p->w32, p->wide, p->perm, (int)p->N, log1, log2, C,
                                          wstart, ustart, wlen, ulen, direct, apply2_weight_capacity(p),
                                          apply2_list_capacity(p), p->lay_hdr, p->lay_cdesc, p->lay_w, p->lay_list,
                                          p->lay_list_sorted);

@@ -238,15 +238,6 @@ INFFT_D bool tile_start(const int32_t* __restrict__ col_off, int p) {
     return p % TILE_COLS == 0 || (col_off[p] / TILE_WEIGHTS) != (col_off[p - 1] / TILE_WEIGHTS);
 }
 
-// Per problem (one CTA): the low parts fp32(w64 - w32) of its weights, for the float-float
-// spreading of wide columns (the fp64 subtraction belongs to the precompute).
-__global__ void __launch_bounds__(TILE_SCAN_THREADS)
-k_batch_weights_lo(const BatchProblem* __restrict__ probs) {
-    const BatchProblem pr = probs[blockIdx.x];
-    const int nnz = pr.col_off[2 * pr.M];
-    for (int e = threadIdx.x; e < nnz; e += blockDim.x) pr.wlo[e] = (float)(pr.w64[e] - (double)pr.w32[e]);
-}
-
 // Per problem (one CTA): its number of tiles.
 __global__ void __launch_bounds__(TILE_SCAN_THREADS)
 k_tile_count(const BatchProblem* __restrict__ probs, int32_t* __restrict__ count) {
@@ -840,8 +831,6 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
                                  b->huge_slots, b->huge_nmax, s)) !=
             cudaSuccess)
         return cuda_err(e, "large-column precompute");
-    k_batch_weights_lo<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs);
-    count_launches(1);
     // spreading tiles from the weight offsets
     k_tile_count<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, b->tile_count);
     k_tile_prefix<<<1, 1024, 0, s>>>(b->tile_count, (int)b->P, b->tile_off);

@@ -226,8 +226,7 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
         if (i < n) {
-            w64[off + i] = v[i];
-            w32[off + i] = (float)v[i];
+            store_b(w64, w32, kp.wlo, off + i, v[i]);
             bsq = fma(v[i], v[i], bsq);
             babs += fabs(v[i]);
         }
@@ -570,8 +569,7 @@ k_lsq_group(const double* __restrict__ xs, const double2* __restrict__ ph, const
             for (int t = 0; t < R; ++t) {
                 const int k = NMAX - g - G * t;
                 if (write && k >= 0 && k < n) {
-                    w64[off + k] = bacc[t];
-                    w32[off + k] = (float)bacc[t];
+                    store_b(w64, w32, kp.wlo, off + k, bacc[t]);
                     bsq = fma(bacc[t], bacc[t], bsq);
                     babs += fabs(bacc[t]);
                 }
@@ -714,8 +712,7 @@ k_lsq_warp(const double* __restrict__ xs, const double2* __restrict__ ph, const 
         double bsq = 0.0, babs = 0.0;
         for (int i = lane; i < n; i += 32) {
             const double b = r[i];
-            w64[off + i] = b;
-            w32[off + i] = (float)b;
+            store_b(w64, w32, kp.wlo, off + i, b);
             bsq = fma(b, b, bsq);
             babs += fabs(b);
         }
@@ -835,8 +832,7 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
         double bsq = 0.0, babs = 0.0;
         for (int i = threadIdx.x; i < n; i += CTA_THREADS) {
             const double b = r[i];
-            w64[off + i] = b;
-            w32[off + i] = (float)b;
+            store_b(w64, w32, kp.wlo, off + i, b);
             bsq = fma(b, b, bsq);
             babs += fabs(b);
         }
@@ -1119,8 +1115,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
         double bsq = 0.0, babs = 0.0;
         for (int i = tid; i < n; i += HUGE_THREADS) {
             const double b = r[i];
-            pr.w64[off + i] = b;
-            pr.w32[off + i] = (float)b;
+            store_b(pr.w64, pr.w32, pr.kp.wlo, off + i, b);
             bsq = fma(b, b, bsq);
             babs += fabs(b);
         }

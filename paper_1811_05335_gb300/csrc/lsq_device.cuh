@@ -31,7 +31,17 @@ struct KernelParams {
     double cs[9];
     int short_cot;   // 1: |pi t| of every near pair is so small that terms beyond cx[2] drop below 2^-56
     unsigned long long near_bits;   // bit pattern of 0.25 / M (|t| below it: sin(z)/z series)
+    float* wlo;      // nnz_cap: low parts fp32(b - fp32(b)) of the float-float applies (or nullptr)
 };
+
+// Stores coefficient b of entry e in fp64, in fp32 and, when lo is given, the fp32 low part
+// fp32(b - fp32(b)) that the fp32 applies use for wide columns (float-float).
+INFFT_D void store_b(double* w64, float* w32, float* lo, int e, double b) {
+    w64[e] = b;
+    const float h = (float)b;
+    w32[e] = h;
+    if (lo) lo[e] = (float)(b - (double)h);
+}
 
 constexpr double PI = 3.141592653589793238462643383279502884;
 constexpr double SMALL_T = 1.0 / 32.0;    // Taylor path for cot(pi t) below this |t|
@@ -255,6 +265,7 @@ struct HugeProblem {
 inline KernelParams make_kernel_params(const Plan* p) {
     const int64_t Ms = p->Ms;
     KernelParams kp;
+    kp.wlo = p->wlo;
     kp.M = (double)p->M;
     kp.inv_Ms = 1.0 / (double)Ms;
     kp.sym = (p->kernel == INFFT_KERNEL_SYM);

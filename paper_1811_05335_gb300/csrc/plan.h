@@ -192,7 +192,6 @@ int apply2_default_config(const Plan* p);
 // plan's work buffer, K = 1)
 cudaError_t run_apply2(Plan* p, const float2* f, bool sorted, float2* fhat, cudaStream_t s, int K = 1,
                        float2* Y = nullptr);
-cudaError_t run_weights_lo(Plan* p, cudaStream_t s);
 int64_t apply2_max_tiles(const Plan* p);
 int64_t apply2_list_capacity(const Plan* p);
 int64_t apply2_weight_capacity(const Plan* p);

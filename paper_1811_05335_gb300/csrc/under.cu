@@ -197,8 +197,7 @@ k_under_lsq(const double* __restrict__ xs, const double2* __restrict__ ph, const
             if (pos < 0) pos += N;
             const double wv = ok ? b[a] * invM : 0.0;
             if (pos < col_count[q]) {
-                w64[col_off[q] + pos] = wv;
-                w32[col_off[q] + pos] = (float)wv;
+                store_b(w64, w32, kp.wlo, col_off[q] + pos, wv);
             } else {
                 atomicAdd(&counters[CNT_UNSUPPORTED], 1);   // the pattern and the key disagree
             }
