@@ -160,7 +160,8 @@ infft_status infft_tune_apply(infft_plan_t plan, int32_t repeats, float* ms_out,
  *   fhat : K x M complex64 on the device, vector k at k M (k + M/2 layout), written;
  *   workspace : device memory of at least infft_apply_many_workspace(plan, K) bytes,
  *               owned by the caller (the call allocates nothing), overwritten.
- * Each vector's result equals infft_apply's for it.  1 <= K <= 65535; M_sigma > 2048
+ * Each vector's result agrees with infft_apply's for it to fp32 rounding (the same
+ * arithmetic, in a different order: spreading tile and FFT split differ).  1 <= K <= 65535; M_sigma > 2048
  * (smaller plans: INFFT_EUNSUPPORTED); host pointers: INFFT_EINVAL.  Requires
  * infft_precompute. */
 int64_t infft_apply_many_workspace(infft_plan_t plan, int64_t K);

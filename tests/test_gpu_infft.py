@@ -311,8 +311,8 @@ def test_full_size_config2(m):
 
 
 def test_apply_many_equals_single_applies():
-    """K data vectors in one call give, vector by vector, what infft_apply gives (same
-    kernels, same summation order: identical values), and match the oracle."""
+    """K data vectors in one call give, vector by vector, what infft_apply gives (to fp32
+    rounding: spreading tiles and FFT split differ), and match the oracle."""
     import torch
     import paper_1811_05335_gb300 as g
     p = make_problem(2, M=4096, N=16384, m=4, with_data=False)
@@ -327,7 +327,7 @@ def test_apply_many_equals_single_applies():
     B = oracle.bopt.bopt_closed(p.x, p.M, 2.0, 4)
     for k in range(K):
         one = g.infft_apply(plan, ft[k].contiguous()).cpu().numpy()
-        assert np.array_equal(many[k], one)
+        assert np.linalg.norm(many[k] - one) <= 1e-6 * np.linalg.norm(one)
         assert oracle.infft.rel_l2(many[k].astype(np.complex128), oracle.infft.infft_apply(B, c64(fs[k]))) <= FP32_TOL
     with pytest.raises(g.InfftError):     # workspace too small
         g.infft_apply_many(plan, ft, workspace=torch.empty(16, dtype=torch.uint8, device=dev))
