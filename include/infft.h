@@ -184,7 +184,12 @@ infft_status plan_destroy(infft_plan_t plan);
  * kernel (INFFT_KERNEL_FULL or INFFT_KERNEL_SYM) and the Tikhonov factor tau
  * (0 <= tau < 1; 1e-12 is the default reading) and allocates every device
  * buffer for the worst case nnz <= (2m+1) N, so later calls allocate nothing.
- * Requires N * (2m+1) < 2^31 and M_sigma <= 2^24 a power of two. */
+ * Requires N * (2m+1) < 2^31 and M_sigma <= 2^24.  M_sigma a power of two: every call
+ * below.  Any other even M_sigma = 2M with sigma = 2 and M <= 8192 (Sec. 2.1 allows any
+ * even sigma M): the plan is a batch of one problem (infft_batch_*), whose FFT is a chirp
+ * convolution of power-of-two length; it supports infft_set_nodes, infft_precompute,
+ * infft_apply, infft_get_info and infft_copy_plan_data, and every other call returns
+ * INFFT_EUNSUPPORTED.  Other non-power-of-two sizes return INFFT_EUNSUPPORTED. */
 infft_status infft_plan_create(int64_t M, int64_t N, double sigma, int m, int kernel,
                                double tau, infft_plan_t* out);
 

@@ -27,6 +27,13 @@ infft_status fail(infft_status st, const char* fmt, ...) {
     return st;
 }
 
+// entry points a plan whose M_sigma is not a power of two (a batch of one problem) lacks
+infft_status chirp_only(const char* what) {
+    return fail(INFFT_EUNSUPPORTED,
+                "%s: a plan whose M_sigma is not a power of two supports set_nodes, precompute, infft_apply, "
+                "get_info and copy_plan_data only", what);
+}
+
 infft_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? INFFT_ENOMEM : INFFT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -77,9 +84,15 @@ infft_status validate_sizes(int64_t M, int64_t N, double sigma, int m, int kerne
     if (!(tau >= 0.0 && tau < 1.0)) return fail(INFFT_EINVAL, "tau must be in [0, 1) (got %g)", tau);
     if ((double)N * (2.0 * m + 1.0) >= 2147483647.0)
         return fail(INFFT_EINVAL, "N (2m+1) must be < 2^31 (N = %lld, m = %d)", (long long)N, m);
-    if (Ms > (1 << 24) || (Ms & (Ms - 1)))
-        return fail(INFFT_EUNSUPPORTED, "M_sigma = %lld: this build supports powers of two up to 2^24",
-                    (long long)Ms);
+    if (Ms > (1 << 24))
+        return fail(INFFT_EUNSUPPORTED, "M_sigma = %lld: this build supports M_sigma up to 2^24", (long long)Ms);
+    if (Ms & (Ms - 1)) {
+        // any even M_sigma = 2M with M <= 8192: the chirp-convolution FFT of the batched form
+        if (sigma != 2.0 || M > 8192)
+            return fail(INFFT_EUNSUPPORTED,
+                        "M_sigma = %lld is not a power of two: supported for sigma = 2 and M <= 8192 only",
+                        (long long)Ms);
+    }
     int lg = 0;
     while ((int64_t(1) << lg) < Ms) ++lg;
     *Ms_out = Ms;
@@ -91,6 +104,10 @@ template <typename T> infft_status apply_impl(infft_plan_t p, const T* f, T* fha
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
     if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_apply before infft_precompute");
+    if (p->chirp) {
+        if (sizeof(T) != 4) return chirp_only("infft_apply_z");
+        return infft_batch_apply(p->chirp, (const float*)f, (float*)fhat, stream);
+    }
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
@@ -122,6 +139,7 @@ template <typename T> infft_status apply_impl(infft_plan_t p, const T* f, T* fha
 
 template <typename T> infft_status nfft_impl(infft_plan_t p, const T* fhat, T* f, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only(sizeof(T) == 4 ? "nfft_apply" : "nfft_apply_z");
     if (!f || !fhat) return fail(INFFT_EINVAL, "fhat and f must not be NULL");
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "nfft_apply before infft_precompute");
     DeviceGuard g(p->device);
@@ -252,6 +270,23 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
     Plan* p = new Plan();
     p->device = dev;
     p->sms = sms;
+    if (Ms & (Ms - 1)) {
+        if (ansatz != INFFT_ANSATZ_OVERDETERMINED) {
+            delete p;
+            return fail(INFFT_EUNSUPPORTED, "the underdetermined case needs M_sigma a power of two");
+        }
+        p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
+        p->ansatz = ansatz;
+        p->logMs = logMs;
+        const int64_t Mv = M, Nv = N;
+        const infft_status st2 = infft_batch_create(1, &Mv, &Nv, sigma, m, kernel, tau, &p->chirp);
+        if (st2 != INFFT_OK) {
+            delete p;
+            return st2;
+        }
+        *out = p;
+        return INFFT_OK;
+    }
     p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
     p->ansatz = ansatz;
     p->logMs = logMs;
@@ -278,6 +313,12 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
 infft_status infft_set_nodes(infft_plan_t p, const double* x, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
     if (!x) return fail(INFFT_EINVAL, "x is NULL");
+    if (p->chirp) {
+        p->precomputed = 0;
+        const infft_status st = infft_batch_set_nodes(p->chirp, x, stream);
+        if (st == INFFT_OK) p->nodes_set = 1;
+        return st;
+    }
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
@@ -319,6 +360,11 @@ infft_status infft_plan(int64_t M, int64_t N, const double* x, double sigma, int
 infft_status infft_precompute(infft_plan_t p, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
     if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_precompute before infft_set_nodes");
+    if (p->chirp) {
+        const infft_status st = infft_batch_precompute(p->chirp, stream);
+        if (st == INFFT_OK) p->precomputed = 1;
+        return st;
+    }
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
@@ -338,6 +384,7 @@ infft_status infft_apply_z(infft_plan_t p, const double* f, double* fhat, infft_
 }
 infft_status infft_apply_sorted(infft_plan_t p, const float* f, float* fhat, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_apply_sorted");
     if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_apply_sorted before infft_precompute");
     DeviceGuard g(p->device);
@@ -361,6 +408,7 @@ infft_status infft_apply_sorted(infft_plan_t p, const float* f, float* fhat, inf
 
 infft_status infft_sort_values(infft_plan_t p, const float* f, float* f_sorted, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_sort_values");
     if (!f || !f_sorted || f == f_sorted) return fail(INFFT_EINVAL, "f and f_sorted must be distinct buffers");
     if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_sort_values before infft_set_nodes");
     DeviceGuard g(p->device);
@@ -383,6 +431,7 @@ infft_status infft_apply_config_shape(int32_t id, int32_t* log2_N1, int32_t* col
 
 infft_status infft_set_apply_config(infft_plan_t p, int32_t id) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_set_apply_config");
     if (id != -1 && !apply2_config_valid(p, id))
         return fail(INFFT_EINVAL, "apply config %d is not valid for M_sigma = %lld", id, (long long)p->Ms);
     p->apply_cfg = id;
@@ -390,13 +439,14 @@ infft_status infft_set_apply_config(infft_plan_t p, int32_t id) {
 }
 
 int32_t infft_get_apply_config(infft_plan_t p) {
-    if (!p || apply2_default_config(p) < 0) return -1;
+    if (!p || p->chirp || apply2_default_config(p) < 0) return -1;
     return p->apply_cfg >= 0 ? p->apply_cfg : apply2_default_config(p);
 }
 
 infft_status infft_tune_apply(infft_plan_t p, int32_t repeats, float* ms_out, int32_t* best,
                               infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_tune_apply");
     if (repeats < 1 || repeats > 10000) return fail(INFFT_EINVAL, "repeats must be in [1, 10000] (got %d)", repeats);
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_tune_apply before infft_precompute");
     if (apply2_default_config(p) < 0)
@@ -445,13 +495,14 @@ infft_status infft_tune_apply(infft_plan_t p, int32_t repeats, float* ms_out, in
 }
 
 int64_t infft_apply_many_workspace(infft_plan_t p, int64_t K) {
-    if (!p || K < 1) return 0;
+    if (!p || p->chirp || K < 1) return 0;
     return 2 * K * p->Ms * (int64_t)sizeof(float2) + 256;
 }
 
 infft_status infft_apply_many(infft_plan_t p, int64_t K, const float* f, float* fhat, void* workspace,
                               int64_t workspace_bytes, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_apply_many");
     if (!f || !fhat || !workspace) return fail(INFFT_EINVAL, "f, fhat and workspace must not be NULL");
     if (K < 1 || K > 65535) return fail(INFFT_EINVAL, "K must be in [1, 65535] (got %lld)", (long long)K);
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_apply_many before infft_precompute");
@@ -478,6 +529,7 @@ infft_status infft_apply_many(infft_plan_t p, int64_t K, const float* f, float* 
 
 infft_status infft_ndft_z(infft_plan_t p, const double* fhat, double* f, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_ndft_z");
     if (!fhat || !f) return fail(INFFT_EINVAL, "fhat and f must not be NULL");
     if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_ndft_z before infft_set_nodes");
     DeviceGuard g(p->device);
@@ -492,6 +544,7 @@ infft_status infft_ndft_z(infft_plan_t p, const double* fhat, double* f, infft_s
 
 infft_status infft_nfft_kb_z(infft_plan_t p, const double* fhat, double* f, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_nfft_kb_z");
     if (!fhat || !f) return fail(INFFT_EINVAL, "fhat and f must not be NULL");
     if (!p->nodes_set) return fail(INFFT_ENOTREADY, "infft_nfft_kb_z before infft_set_nodes");
     if (!nfft_kb_supported(p))
@@ -509,6 +562,7 @@ infft_status infft_nfft_kb_z(infft_plan_t p, const double* fhat, double* f, inff
 
 infft_status infft_refine_z(infft_plan_t p, const double* f, double* fhat, int sweeps, infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_refine_z");
     if (!f || !fhat) return fail(INFFT_EINVAL, "f and fhat must not be NULL");
     if (sweeps < 0 || sweeps > 64) return fail(INFFT_EINVAL, "sweeps must be in [0, 64] (got %d)", sweeps);
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_refine_z before infft_precompute");
@@ -540,6 +594,7 @@ infft_status nfft_apply_z(infft_plan_t p, const double* fhat, double* f, infft_s
 infft_status infft_grad_nodes(infft_plan_t p, const float* f, const float* w, double* grad_x,
                               infft_stream_t stream) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return chirp_only("infft_grad_nodes");
     if (!f || !w || !grad_x) return fail(INFFT_EINVAL, "f, w and grad_x must not be NULL");
     if (!p->precomputed) return fail(INFFT_ENOTREADY, "infft_grad_nodes before infft_precompute");
     if (p->ansatz != INFFT_ANSATZ_OVERDETERMINED)
@@ -556,6 +611,11 @@ infft_status infft_grad_nodes(infft_plan_t p, const float* f, const float* w, do
 
 infft_status plan_destroy(infft_plan_t p) {
     if (!p) return INFFT_OK;
+    if (p->chirp) {
+        const infft_status st = infft_batch_destroy(p->chirp);
+        delete p;
+        return st;
+    }
     {
         DeviceGuard g(p->device);
         cudaDeviceSynchronize();
@@ -568,6 +628,19 @@ infft_status plan_destroy(infft_plan_t p) {
 
 infft_status infft_get_info(infft_plan_t p, infft_info* info) {
     if (!p || !info) return fail(INFFT_EINVAL, "plan and info must not be NULL");
+    if (p->chirp) {
+        infft_batch_info bi;
+        const infft_status st = infft_batch_get_info(p->chirp, &bi);
+        if (st != INFFT_OK) return st;
+        std::memset(info, 0, sizeof *info);
+        info->M = p->M; info->N = p->N; info->M_sigma = p->Ms; info->m = p->m; info->kernel = p->kernel;
+        info->sigma = p->sigma; info->tau = p->tau; info->ansatz = p->ansatz;
+        info->nodes_set = p->nodes_set; info->precomputed = p->precomputed;
+        info->nnz = bi.nnz; info->max_column = bi.max_column; info->empty_columns = (int32_t)bi.empty_columns;
+        info->bad_nodes = (int32_t)bi.bad_nodes; info->fallback_columns = (int32_t)bi.fallback_columns;
+        info->unsupported_columns = (int32_t)bi.unsupported_columns; info->objective = bi.objective;
+        return INFFT_OK;
+    }
     DeviceGuard g(p->device);
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     if (e != cudaSuccess) return cuda_fail(e, "synchronize");
@@ -608,6 +681,7 @@ infft_status infft_get_info(infft_plan_t p, infft_info* info) {
 infft_status infft_copy_plan_data(infft_plan_t p, int32_t* perm, int32_t* col_start, int32_t* col_count,
                                   int32_t* col_offset, double* weights, double* objective) {
     if (!p) return fail(INFFT_EINVAL, "plan is NULL");
+    if (p->chirp) return infft_batch_copy_problem(p->chirp, 0, perm, col_start, col_count, col_offset, weights, objective);
     if (!p->nodes_set) return fail(INFFT_ENOTREADY, "no nodes set");
     if ((weights || objective) && !p->precomputed) return fail(INFFT_ENOTREADY, "not precomputed");
     DeviceGuard g(p->device);

@@ -303,9 +303,7 @@ cudaError_t run_grad_nodes(Plan* p, const void* f, const void* w, double* gx, cu
     const KernelParams kk = make_kernel_params(p);
     const double mu = p->tau * kp.diag;
     if ((e = cudaMemsetAsync(p->counters + CNT_GRAD_FAIL, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (sms <= 0) sms = 148;
+    const int sms = p->sms;
     const size_t smem = (size_t)GW * (GN * GLD + 6 * GN) * sizeof(double);
     if ((e = cudaFuncSetAttribute(k_grad_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)

@@ -1155,9 +1155,7 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_BIG_LIST, 0, 3 * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_HUGE_LIST, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (sms <= 0) sms = 148;
+    const int sms = p->sms;
 
     // thread tier: a tile of 32 consecutive columns goes to the first tier whose NMAX
     // covers its largest column (this kernel routes the others); group tiers: G lanes

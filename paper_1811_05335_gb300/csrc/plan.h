@@ -95,6 +95,10 @@ struct infft_plan_s {
     void* stage_out = nullptr;  // max(N, M) double2: host-output staging
 
     void* arena = nullptr;      // the one device allocation holding the buffers above (owned)
+    // M_sigma not a power of two (sigma = 2, M <= 8192): the plan is a batch of one problem,
+    // whose FFT is the chirp convolution (batch.cu); only set_nodes, precompute, the fp32 apply,
+    // get_info and copy_plan_data are available (owned)
+    infft_batch_t chirp = nullptr;
     bool batch_member = false;  // buffers carved from a batch; big columns go to the batch's solver
     int nodes_set = 0, precomputed = 0;
     int apply_clean = 0;        // 0 after set_nodes / precompute until the next apply has been launched

@@ -1370,8 +1370,8 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     if ((e = cudaMemsetAsync(p->counters + C2_WIDE, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p->hist, 0, (LARGE_NMAX + 2) * sizeof(int32_t), s)) != cudaSuccess) return e;
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (sms <= 0) sms = 148;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) return e;
+    if (sms <= 0) return cudaErrorInvalidDevice;
     if ((e = cudaMemsetAsync(p->counters + C2_SPREAD_BIG, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     k2_route<<<(P + 255) / 256, 256, 0, s>>>(p->col_off, P, p->lists, p->w64, p->w32, p->J, p->wide, p->hist,
                                              p->spread_big, p->counters);

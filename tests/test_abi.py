@@ -56,7 +56,8 @@ def test_version_and_counter():
     ((64, 128, 2.0, 0), 1),            # m < 1
     ((4, 128, 1.0, 2), 1),             # 2m >= M_sigma
     ((64, 2 ** 30, 2.0, 4), 1),        # N (2m+1) >= 2^31
-    ((48, 128, 2.0, 4), 5),            # M_sigma = 96: not a power of two in this build
+    ((1000, 4000, 1.5, 4), 5),         # M_sigma = 1500 not a power of two, sigma != 2
+    ((8194, 20000, 2.0, 4), 5),        # M_sigma = 16388 not a power of two, M above 8192
 ])
 def test_invalid_sizes(args, code):
     with pytest.raises(g.InfftError) as ei:
