@@ -261,6 +261,8 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
                     ansatz);
     if (ansatz == INFFT_ANSATZ_UNDERDETERMINED && 2 * m + 1 > UNDER_NMAX)
         return fail(INFFT_EUNSUPPORTED, "underdetermined case: 2m+1 = %d exceeds %d", 2 * m + 1, UNDER_NMAX);
+    if (ansatz == INFFT_ANSATZ_UNDERDETERMINED && (Ms & (Ms - 1)))
+        return fail(INFFT_EUNSUPPORTED, "the underdetermined case needs M_sigma a power of two");
     int dev = 0, sms = 0;
     cudaError_t qe = cudaGetDevice(&dev);
     if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -271,10 +273,6 @@ infft_status infft_plan_create_ansatz(int64_t M, int64_t N, double sigma, int m,
     p->device = dev;
     p->sms = sms;
     if (Ms & (Ms - 1)) {
-        if (ansatz != INFFT_ANSATZ_OVERDETERMINED) {
-            delete p;
-            return fail(INFFT_EUNSUPPORTED, "the underdetermined case needs M_sigma a power of two");
-        }
         p->M = M; p->N = N; p->Ms = Ms; p->m = m; p->kernel = kernel; p->sigma = sigma; p->tau = tau;
         p->ansatz = ansatz;
         p->logMs = logMs;
