@@ -2,10 +2,13 @@
 // one plan, the paper's overdetermined direct inversion (Sec. 3.2.2) for each.
 //
 // Pattern and precompute: every problem is a plan of its own whose buffers are
-// carved from one allocation; their launches are spread over a pool of streams
-// (stream-ordered after the caller's stream, so the whole precompute can be
-// captured in a CUDA graph), and the columns of more than 64 nodes of all
-// problems go to one launch of the blocked solver.
+// carved from one allocation, and each step is one launch over all problems: the
+// pattern one CTA per problem (pattern.cu, k_batch_pattern), each solver tier one
+// launch over the work items of all problems, numbered by a device prefix of the
+// problems' counts (lsq.cu, run_precompute_batch), and the columns of more than 64
+// nodes of all problems one launch of the blocked solver.  Everything is
+// stream-ordered on the caller's stream, so the whole precompute can be captured in
+// a CUDA graph.
 //
 // Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of at
 // most 128 grid points of one problem (staged like the single-problem apply's
@@ -46,7 +49,6 @@ constexpr int TW_LOG = 14;
 constexpr int TW_N = 1 << TW_LOG;                 // twiddle table e^{-2 pi i t / TW_N}
 constexpr int BATCH_MMAX = TW_N / 2;              // 2M - 1 <= TW_N
 constexpr int BATCH_STASH = BATCH_MMAX / BATCH_FFT_THREADS;
-constexpr int BATCH_STREAMS = 48;
 
 struct BatchProblem {
     const float* w32;
@@ -529,13 +531,17 @@ struct infft_batch_s {
     int32_t* tile_count = nullptr;  // P counts, then P + 1 offsets
     int32_t* tile_off = nullptr;
     int64_t max_tiles = 0;
+    PatternArgs* pat_args = nullptr;   // P pattern descriptors (one launch for every problem's pattern)
+    void* tier_args = nullptr;         // P solver-tier descriptors (one launch per tier)
+    int32_t* pat_order = nullptr;      // problems by decreasing N (the pattern's CTAs take them in order)
+    int32_t* tier_tile_off = nullptr;  // P + 1: prefix of the problems' 32-column tiles
+    int32_t* tier_work = nullptr;      // 3 (P + 1): prefixes of the routed lists
+    int64_t total_tiles32 = 0;
     const int32_t** d_counters = nullptr;
     const int32_t** d_col_off = nullptr;
     const double** d_J = nullptr;
     int32_t* d_Ms = nullptr;
     double* d_info = nullptr;       // 8 P
-    cudaStream_t streams[BATCH_STREAMS] = {};
-    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
     int nodes_set = 0, precomputed = 0;
     cudaStream_t last_stream = nullptr;
 };
@@ -546,14 +552,10 @@ void batch_free(infft_batch_t b) {
     for (Plan* p : b->plans) delete p;
     void* bufs[] = {b->arena, b->x_all, b->g_all, b->bhat, b->tw, b->stage_f, b->stage_fhat, b->probs,
                     b->huge_probs, b->job_off, b->job_order, b->job_work, b->huge_scratch, b->order, b->ticket, b->tiles, b->tile_count, b->tile_off,
+                    (void*)b->pat_args, b->tier_args, b->pat_order, b->tier_tile_off, b->tier_work,
                     (void*)b->d_counters, (void*)b->d_col_off, (void*)b->d_J, b->d_Ms, b->d_info};
     for (void* p : bufs)
         if (p) cudaFree(p);
-    for (int i = 0; i < BATCH_STREAMS; ++i) {
-        if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
-        if (b->join[i]) cudaEventDestroy(b->join[i]);
-    }
-    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -572,23 +574,6 @@ struct DevGuard {
 infft_status cuda_err(cudaError_t e, const char* what) {
     return set_error(e == cudaErrorMemoryAllocation ? INFFT_ENOMEM : INFFT_ECUDA, "%s: %s", what,
                      cudaGetErrorString(e));
-}
-
-// Makes every pool stream wait for the caller's stream s.
-cudaError_t fork_streams(infft_batch_t b, cudaStream_t s) {
-    cudaError_t e = cudaEventRecord(b->fork, s);
-    for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-    return e;
-}
-
-// Makes the caller's stream s wait for every pool stream.
-cudaError_t join_streams(infft_batch_t b, cudaStream_t s) {
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) {
-        e = cudaEventRecord(b->join[i], b->streams[i]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
-    }
-    return e;
 }
 
 }  // namespace
@@ -691,6 +676,11 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     alloc(&b->job_off, (P + 1) * sizeof(int32_t));
     alloc(&b->order, P * sizeof(int32_t));
     alloc(&b->ticket, sizeof(int32_t));
+    alloc(&b->pat_args, P * sizeof(PatternArgs));
+    alloc(&b->tier_args, P * tier_args_bytes());
+    alloc(&b->pat_order, P * sizeof(int32_t));
+    alloc(&b->tier_tile_off, (P + 1) * sizeof(int32_t));
+    alloc(&b->tier_work, 3 * (P + 1) * sizeof(int32_t));
     alloc(&b->d_counters, P * sizeof(void*));
     alloc(&b->d_col_off, P * sizeof(void*));
     alloc(&b->d_J, P * sizeof(void*));
@@ -712,11 +702,6 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     alloc(&b->tiles, 2 * b->max_tiles * sizeof(int4));
     alloc(&b->tile_count, P * sizeof(int32_t));
     alloc(&b->tile_off, (P + 1) * sizeof(int32_t));
-    for (int i = 0; i < BATCH_STREAMS && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         batch_free(b);
         return cuda_err(e, "allocate batch");
@@ -740,6 +725,23 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     }
     std::vector<char> hh(P * huge_problem_bytes());
     huge_problems_fill(b->plans.data(), (int)P, hh.data());
+    // batch-wide pattern and solver tiers: descriptors, order and tile prefix
+    std::vector<PatternArgs> hpat(P);
+    std::vector<int32_t> htoff(P + 1, 0), pord(P);
+    for (int64_t i = 0; i < P; ++i) {
+        Plan* p = b->plans[i];
+        PatternArgs& a = hpat[i];
+        a.x = p->x; a.xs = p->xs; a.phase = p->phase; a.skey = p->skey; a.perm = p->perm; a.bucket = p->bucket;
+        a.cursor = p->cursor; a.seg_list = p->seg_list; a.sort_tmp = p->sort_tmp; a.col_start = p->col_start;
+        a.col_count = p->col_count; a.col_off = p->col_off; a.counters = p->counters;
+        a.N = (int)p->N; a.Ms = (int)p->Ms; a.m = p->m; a.M = (double)p->M;
+        htoff[i + 1] = htoff[i] + (int32_t)((p->Ms + 31) / 32);
+    }
+    b->total_tiles32 = htoff[P];
+    std::iota(pord.begin(), pord.end(), 0);
+    std::stable_sort(pord.begin(), pord.end(), [&](int32_t a, int32_t c) { return N[a] + 2 * M[a] > N[c] + 2 * M[c]; });
+    std::vector<char> htier(P * tier_args_bytes());
+    tier_args_fill(b->plans.data(), (int)P, htier.data());
     std::vector<int32_t> ord(P);
     std::iota(ord.begin(), ord.end(), 0);
     // largest first: grid reads plus transform work (2 or 4 transforms of length L)
@@ -757,6 +759,11 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     if (e == cudaSuccess) e = cudaMemcpy(b->huge_probs, hh.data(), hh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->order, ord.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->tw, htw.data(), TW_N * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->pat_args, hpat.data(), P * sizeof(PatternArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tier_args, htier.data(), htier.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->pat_order, pord.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->tier_tile_off, htoff.data(), (P + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_counters, hc.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_col_off, ho.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_J, hj.data(), P * sizeof(void*), cudaMemcpyHostToDevice);
@@ -801,13 +808,10 @@ infft_status infft_batch_set_nodes(infft_batch_t b, const double* x, infft_strea
     }
     if (e != cudaSuccess) return cuda_err(e, "copy nodes");
     b->precomputed = 0;
-    if ((e = fork_streams(b, s)) != cudaSuccess) return cuda_err(e, "fork");
-    for (int64_t i = 0; i < b->P; ++i) {
-        if ((e = run_pattern(b->plans[i], b->streams[i % BATCH_STREAMS])) != cudaSuccess)
-            return cuda_err(e, "pattern");
-        b->plans[i]->nodes_set = 1;
-    }
-    if ((e = join_streams(b, s)) != cudaSuccess) return cuda_err(e, "join");
+    // every problem's pattern in one launch (a CTA per problem)
+    if ((e = run_pattern_batch(b->pat_args, b->pat_order, (int)b->P, b->sms, s)) != cudaSuccess)
+        return cuda_err(e, "pattern");
+    for (int64_t i = 0; i < b->P; ++i) b->plans[i]->nodes_set = 1;
     b->nodes_set = 1;
     return INFFT_OK;
 }
@@ -819,13 +823,11 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     b->last_stream = s;
     cudaError_t e;
-    if ((e = fork_streams(b, s)) != cudaSuccess) return cuda_err(e, "fork");
-    for (int64_t i = 0; i < b->P; ++i) {
-        if ((e = run_precompute(b->plans[i], b->streams[i % BATCH_STREAMS])) != cudaSuccess)
-            return cuda_err(e, "precompute");
-        b->plans[i]->precomputed = 1;
-    }
-    if ((e = join_streams(b, s)) != cudaSuccess) return cuda_err(e, "join");
+    // every problem's columns up to 64 nodes: one launch per solver tier over all problems
+    if ((e = run_precompute_batch(b->tier_args, (int)b->P, b->tier_tile_off, (int)b->total_tiles32, b->tier_work,
+                                  b->sms, s)) != cudaSuccess)
+        return cuda_err(e, "precompute");
+    for (int64_t i = 0; i < b->P; ++i) b->plans[i]->precomputed = 1;
     if (b->huge_slots &&
         (e = run_precompute_huge(b->huge_probs, (int)b->P, b->job_off, b->job_order, b->job_work, b->huge_scratch,
                                  b->huge_slots, b->huge_nmax, s)) !=

@@ -65,14 +65,14 @@ INFFT_D void fill_gram(double* T, const double* __restrict__ xs, const double2* 
 // pair of the union once and scatter the value into the triangle of every column
 // that contains both nodes; a tile whose union does not fit falls back to
 // per-column evaluation.
-template <int NMAX, int WARPS>
+template <int NMAX, int WARPS, bool BATCH = false>
 __global__ void __launch_bounds__(WARPS * 32)
-k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
-             const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
-             KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-             double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ tiles_in,
-             int tiles_counter, int32_t* __restrict__ route_mid, int32_t* __restrict__ route_big,
-             int32_t* __restrict__ col_list, int32_t* __restrict__ counters) {
+k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, const int32_t* __restrict__ col_start_,
+             const int32_t* __restrict__ col_count_, const int32_t* __restrict__ col_off_, int N_, int Ms_,
+             KernelParams kp_, double mu0_, double* __restrict__ w64_, float* __restrict__ w32_,
+             double* __restrict__ Jout_, uint8_t* __restrict__ wide_, const int32_t* __restrict__ tiles_in,
+             int tiles_counter, int32_t* __restrict__ route_mid_, int32_t* __restrict__ route_big_,
+             int32_t* __restrict__ col_list_, int32_t* __restrict__ counters_, TierBatch tb) {
     extern __shared__ double lsq_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* wbase = (double*)((char*)lsq_smem + (size_t)wid * tile_warp_bytes<NMAX>());
@@ -85,12 +85,31 @@ k_lsq_thread(const double* __restrict__ xs, const double2* __restrict__ ph, cons
     int* clst = cfst + TILE_UMAX;                               // per union node: last candidate column
 
     // tiles_in == nullptr: every tile, one per warp, routing the tiles this tier cannot
-    // take; otherwise the tiles of the list (persistent warps)
-    const int ntiles = tiles_in ? counters[tiles_counter] : (Ms + 31) / 32;
+    // take; otherwise the tiles of the list (persistent warps).  Batch mode (BATCH, routing
+    // only): the tiles of all problems, numbered by the prefix tb.off.
+    const int ntiles = BATCH ? tb.off[tb.P] : tiles_in ? counters_[tiles_counter] : (Ms_ + 31) / 32;
     const int first = blockIdx.x * WARPS + wid, stride = tiles_in ? gridDim.x * WARPS : ntiles;
     for (int it = first; it < ntiles; it += stride) {
     __syncwarp();
-    const int tile = tiles_in ? tiles_in[it] : it;
+    const int pb = BATCH ? batch_problem(tb.off, tb.P, it) : 0;
+    const TierArgs* pa = BATCH ? tb.probs + pb : nullptr;
+    const double* __restrict__ xs = BATCH ? pa->xs : xs_;
+    const double2* __restrict__ ph = BATCH ? pa->ph : ph_;
+    const int32_t* __restrict__ col_start = BATCH ? pa->col_start : col_start_;
+    const int32_t* __restrict__ col_count = BATCH ? pa->col_count : col_count_;
+    const int32_t* __restrict__ col_off = BATCH ? pa->col_off : col_off_;
+    const int N = BATCH ? pa->N : N_, Ms = BATCH ? pa->Ms : Ms_;
+    const KernelParams& kp = BATCH ? pa->kp : kp_;
+    const double mu0 = BATCH ? pa->mu0 : mu0_;
+    double* __restrict__ w64 = BATCH ? pa->w64 : w64_;
+    float* __restrict__ w32 = BATCH ? pa->w32 : w32_;
+    double* __restrict__ Jout = BATCH ? pa->J : Jout_;
+    uint8_t* __restrict__ wide = BATCH ? pa->wide : wide_;
+    int32_t* __restrict__ route_mid = BATCH ? pa->tiles_mid : route_mid_;
+    int32_t* __restrict__ route_big = BATCH ? pa->tiles_big : route_big_;
+    int32_t* __restrict__ col_list = BATCH ? pa->list_a : col_list_;
+    int32_t* __restrict__ counters = BATCH ? pa->counters : counters_;
+    const int tile = BATCH ? it - tb.off[pb] : tiles_in ? tiles_in[it] : it;
     const int p = tile * 32 + lane;
     const bool live = p < Ms;
     const int n = live ? col_count[p] : 0;
@@ -383,13 +402,13 @@ INFFT_D void group_fill_direct(double* Tc, int g, int n, int Dw, int s, const do
     }
 }
 
-template <int NMAX, int G>
+template <int NMAX, int G, bool BATCH = false>
 __global__ void __launch_bounds__(G * 32, 1)
-k_lsq_group(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
-            const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
-            KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-            double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ tiles,
-            int tiles_counter, int32_t* __restrict__ counters) {
+k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, const int32_t* __restrict__ col_start_,
+            const int32_t* __restrict__ col_count_, const int32_t* __restrict__ col_off_, int N_, int Ms_,
+            KernelParams kp_, double mu0_, double* __restrict__ w64_, float* __restrict__ w32_,
+            double* __restrict__ Jout_, uint8_t* __restrict__ wide_, const int32_t* __restrict__ tiles_,
+            int tiles_counter, int32_t* __restrict__ counters_, TierBatch tb) {
     constexpr int C = 32 / G;          // columns per warp
     constexpr int R = (NMAX + G) / G;  // row slots per lane: rows 0 .. NMAX, from the bottom
     constexpr int NT = 32 * G;         // threads per CTA
@@ -417,10 +436,28 @@ k_lsq_group(const double* __restrict__ xs, const double2* __restrict__ ph, const
         colo[t] = i * GS;
     }
 
-    const int ntiles = counters[tiles_counter];
+    // batch mode (BATCH): the listed tiles of all problems, numbered by the prefix tb.off
+    const int ntiles = BATCH ? tb.off[tb.P] : counters_[tiles_counter];
     for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
         __syncthreads();                  // the previous tile is done with shared memory
-        const int tile = tiles[it];
+        const int pb = BATCH ? batch_problem(tb.off, tb.P, it) : 0;
+        const TierArgs* pa = BATCH ? tb.probs + pb : nullptr;
+        const double* __restrict__ xs = BATCH ? pa->xs : xs_;
+        const double2* __restrict__ ph = BATCH ? pa->ph : ph_;
+        const int32_t* __restrict__ col_start = BATCH ? pa->col_start : col_start_;
+        const int32_t* __restrict__ col_count = BATCH ? pa->col_count : col_count_;
+        const int32_t* __restrict__ col_off = BATCH ? pa->col_off : col_off_;
+        const int N = BATCH ? pa->N : N_, Ms = BATCH ? pa->Ms : Ms_;
+        const KernelParams& kp = BATCH ? pa->kp : kp_;
+        const double mu0 = BATCH ? pa->mu0 : mu0_;
+        double* __restrict__ w64 = BATCH ? pa->w64 : w64_;
+        float* __restrict__ w32 = BATCH ? pa->w32 : w32_;
+        double* __restrict__ Jout = BATCH ? pa->J : Jout_;
+        uint8_t* __restrict__ wide = BATCH ? pa->wide : wide_;
+        int32_t* __restrict__ counters = BATCH ? pa->counters : counters_;
+        const int32_t* __restrict__ tiles =
+            BATCH ? (tiles_counter == CNT_TILES_MID ? pa->tiles_mid : pa->tiles_big) : tiles_;
+        const int tile = tiles[BATCH ? it - tb.off[pb] : it];
         if (wid == 0) {
             const int p = tile * 32 + lane;
             const bool live = p < Ms;
@@ -603,13 +640,14 @@ k_lsq_group(const double* __restrict__ xs, const double2* __restrict__ ph, const
 
 // One warp per column; lane t owns rows t, t + 32, ... (NMAX / 32 rows).  Columns
 // come from `list` (count at counters[list_counter]).
-template <int NMAX, int WARPS>
+template <int NMAX, int WARPS, bool BATCH = false>
 __global__ void __launch_bounds__(WARPS * 32)
-k_lsq_warp(const double* __restrict__ xs, const double2* __restrict__ ph, const int32_t* __restrict__ col_start,
-           const int32_t* __restrict__ col_count, const int32_t* __restrict__ col_off, int N, int Ms,
-           KernelParams kp, double mu0, double* __restrict__ w64, float* __restrict__ w32,
-           double* __restrict__ Jout, uint8_t* __restrict__ wide, const int32_t* __restrict__ list,
-           int list_counter, int32_t* __restrict__ next_list, int next_counter, int32_t* __restrict__ counters) {
+k_lsq_warp(const double* __restrict__ xs_, const double2* __restrict__ ph_, const int32_t* __restrict__ col_start_,
+           const int32_t* __restrict__ col_count_, const int32_t* __restrict__ col_off_, int N_, int Ms_,
+           KernelParams kp_, double mu0_, double* __restrict__ w64_, float* __restrict__ w32_,
+           double* __restrict__ Jout_, uint8_t* __restrict__ wide_, const int32_t* __restrict__ list_,
+           int list_counter, int32_t* __restrict__ next_list_, int next_counter, int32_t* __restrict__ counters_,
+           TierBatch tb) {
     constexpr int ROWS = NMAX / 32;
     constexpr int LD = NMAX + 1;     // padded row stride: conflict-free column access
     extern __shared__ double lsq_smem[];
@@ -618,9 +656,27 @@ k_lsq_warp(const double* __restrict__ xs, const double2* __restrict__ ph, const 
     double* r = A + NMAX * LD;
     double* xl = r + NMAX;
     double2* pv = (double2*)(xl + NMAX);
-    const int total = counters[list_counter];
+    // batch mode (BATCH): the listed columns of all problems, numbered by the prefix tb.off
+    const int total = BATCH ? tb.off[tb.P] : counters_[list_counter];
     for (int it = blockIdx.x * WARPS + wid; it < total; it += gridDim.x * WARPS) {
-        const int p = list[it];
+        const int pb = BATCH ? batch_problem(tb.off, tb.P, it) : 0;
+        const TierArgs* pa = BATCH ? tb.probs + pb : nullptr;
+        const double* __restrict__ xs = BATCH ? pa->xs : xs_;
+        const double2* __restrict__ ph = BATCH ? pa->ph : ph_;
+        const int32_t* __restrict__ col_start = BATCH ? pa->col_start : col_start_;
+        const int32_t* __restrict__ col_count = BATCH ? pa->col_count : col_count_;
+        const int32_t* __restrict__ col_off = BATCH ? pa->col_off : col_off_;
+        const int N = BATCH ? pa->N : N_, Ms = BATCH ? pa->Ms : Ms_;
+        const KernelParams& kp = BATCH ? pa->kp : kp_;
+        const double mu0 = BATCH ? pa->mu0 : mu0_;
+        double* __restrict__ w64 = BATCH ? pa->w64 : w64_;
+        float* __restrict__ w32 = BATCH ? pa->w32 : w32_;
+        double* __restrict__ Jout = BATCH ? pa->J : Jout_;
+        uint8_t* __restrict__ wide = BATCH ? pa->wide : wide_;
+        int32_t* __restrict__ counters = BATCH ? pa->counters : counters_;
+        int32_t* __restrict__ next_list = BATCH ? pa->big_list : next_list_;
+        const int32_t* __restrict__ list = BATCH ? pa->list_a : list_;
+        const int p = list[BATCH ? it - tb.off[pb] : it];
         const int n = col_count[p];
         if (n > NMAX) {
             if (lane == 0) next_list[atomicAdd(&counters[next_counter], 1)] = p;
@@ -1184,22 +1240,24 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     launch_begin(p, "lsq_thread17", s);
     t1<<<(tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
                                                   kp, mu, p->w64, p->w32, p->J, p->wide, nullptr, 0, p->tiles_mid,
-                                                  p->tiles_big, p->list_a, p->counters);
+                                                  p->tiles_big, p->list_a, p->counters, TierBatch{});
     launch_end(p, s);
     launch_begin(p, "lsq_group25", s);
     t2<<<occ2 * sms, G2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                       p->w64, p->w32, p->J, p->wide, p->tiles_mid, CNT_TILES_MID, p->counters);
+                                       p->w64, p->w32, p->J, p->wide, p->tiles_mid, CNT_TILES_MID, p->counters,
+                                       TierBatch{});
     launch_end(p, s);
     launch_begin(p, "lsq_group33", s);
     t3<<<occ3 * sms, G3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
-                                       p->w64, p->w32, p->J, p->wide, p->tiles_big, CNT_TILES_BIG, p->counters);
+                                       p->w64, p->w32, p->J, p->wide, p->tiles_big, CNT_TILES_BIG, p->counters,
+                                       TierBatch{});
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // warp tier: columns of tiles whose largest column exceeds the thread tiers, |I(l)| <= 64
     launch_begin(p, "lsq_warp64", s);
     k4<<<2 * sms, W4 * 32, s4, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
                                     p->w64, p->w32, p->J, p->wide, p->list_a, CNT_LIST_A, p->big_list,
-                                    CNT_BIG_LIST, p->counters);
+                                    CNT_BIG_LIST, p->counters, TierBatch{});
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // CTA tier: the big list, one CTA per column, |I(l)| <= 224.  Batch members leave
@@ -1251,5 +1309,113 @@ cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int3
     k_job_scatter<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist, order);
     k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, order, ticket, scratch, nmax);
     count_launches(5);
+    return cudaGetLastError();
+}
+
+// ---- every problem of a batch in one launch per solver tier ----------------------------
+
+namespace {
+
+// The precompute counters of every problem (as run_precompute clears them for one).
+__global__ void k_batch_clear_counters(const TierArgs* __restrict__ probs, int P) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int32_t* c = probs[p].counters;
+    c[CNT_FALLBACK] = 0;
+    c[CNT_UNSUPPORTED] = 0;
+    c[CNT_LIST_A] = 0;
+    c[CNT_BIG_LIST] = 0;
+    c[CNT_TILES_MID] = 0;
+    c[CNT_TILES_BIG] = 0;
+    c[CNT_HUGE_LIST] = 0;
+}
+
+// off[p] = sum_{q < p} probs[q].counters[idx], off[P] = the total (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024)
+k_batch_count_prefix(const TierArgs* __restrict__ probs, int P, int idx, int32_t* __restrict__ off) {
+    __shared__ int32_t part[1024];
+    const int per = (P + 1023) / 1024;
+    const int a = min((int)threadIdx.x * per, P), b = min(a + per, P);
+    int32_t sum = 0;
+    for (int i = a; i < b; ++i) sum += probs[i].counters[idx];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = a; i < b; ++i) {
+        off[i] = run;
+        run += probs[i].counters[idx];
+    }
+    if (threadIdx.x == 1023) off[P] = part[1023];
+}
+
+}  // namespace
+
+static TierArgs tier_args(const Plan* p) {
+    TierArgs a;
+    a.xs = p->xs; a.ph = p->phase; a.col_start = p->col_start; a.col_count = p->col_count; a.col_off = p->col_off;
+    a.N = (int)p->N; a.Ms = (int)p->Ms;
+    a.kp = make_kernel_params(p);
+    a.mu0 = p->tau * a.kp.diag;
+    a.w64 = p->w64; a.w32 = p->w32; a.J = p->J; a.wide = p->wide;
+    a.tiles_mid = p->tiles_mid; a.tiles_big = p->tiles_big; a.list_a = p->list_a; a.big_list = p->big_list;
+    a.counters = p->counters;
+    return a;
+}
+
+size_t tier_args_bytes() { return sizeof(TierArgs); }
+
+void tier_args_fill(Plan* const* plans, int P, void* host) {
+    TierArgs* h = (TierArgs*)host;
+    for (int i = 0; i < P; ++i) h[i] = tier_args(plans[i]);
+}
+
+cudaError_t run_precompute_batch(const void* probs_v, int P, const int32_t* tile_off, int total_tiles,
+                                 int32_t* off_work, int sms, cudaStream_t s) {
+    const TierArgs* probs = (const TierArgs*)probs_v;
+    constexpr int A1 = LSQ_THREAD_NMAX1, A2 = LSQ_THREAD_NMAX2, A3 = LSQ_THREAD_NMAX3;
+    constexpr int W1 = 5, G2 = LSQ_GROUP_G2, G3 = LSQ_GROUP_G3, W4 = 4;
+    auto t1 = k_lsq_thread<A1, W1, true>;
+    auto t2 = k_lsq_group<A2, G2, true>;
+    auto t3 = k_lsq_group<A3, G3, true>;
+    auto k4 = k_lsq_warp<LSQ_WARP2_NMAX, W4, true>;
+    const size_t s1 = W1 * tile_warp_bytes<A1>(), s2 = group_smem_bytes<A2>(), s3 = group_smem_bytes<A3>();
+    const size_t s4 = warp_smem_bytes<LSQ_WARP2_NMAX, W4>();
+    cudaError_t e;
+    if ((e = set_smem(t1, s1)) != cudaSuccess) return e;
+    if ((e = set_smem(t2, s2)) != cudaSuccess) return e;
+    if ((e = set_smem(t3, s3)) != cudaSuccess) return e;
+    if ((e = set_smem(k4, s4)) != cudaSuccess) return e;
+    int occ2 = 1, occ3 = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, t2, G2 * 32, s2)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, t3, G3 * 32, s3)) != cudaSuccess) return e;
+    occ2 = std::max(occ2, 1);
+    occ3 = std::max(occ3, 1);
+    int32_t* off_mid = off_work;
+    int32_t* off_big = off_work + (P + 1);
+    int32_t* off_a = off_work + 2 * (P + 1);
+    const KernelParams kp0 = {};
+    k_batch_clear_counters<<<(P + 255) / 256, 256, 0, s>>>(probs, P);
+    // routing tier: every tile of every problem, one warp each
+    t1<<<(total_tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0,
+                                                         nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
+                                                         nullptr, nullptr, nullptr, TierBatch{probs, tile_off, P});
+    // group tiers and warp tier: the problems' routed lists, numbered by device prefixes
+    k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_TILES_MID, off_mid);
+    t2<<<occ2 * sms, G2 * 32, s2, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0, nullptr, nullptr,
+                                       nullptr, nullptr, nullptr, CNT_TILES_MID, nullptr, TierBatch{probs, off_mid, P});
+    k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_TILES_BIG, off_big);
+    t3<<<occ3 * sms, G3 * 32, s3, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0, nullptr, nullptr,
+                                       nullptr, nullptr, nullptr, CNT_TILES_BIG, nullptr, TierBatch{probs, off_big, P});
+    k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_LIST_A, off_a);
+    k4<<<2 * sms, W4 * 32, s4, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0, nullptr, nullptr,
+                                    nullptr, nullptr, nullptr, CNT_LIST_A, nullptr, CNT_BIG_LIST, nullptr,
+                                    TierBatch{probs, off_a, P});
+    count_launches(8);
     return cudaGetLastError();
 }

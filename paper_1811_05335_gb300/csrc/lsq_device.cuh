@@ -243,6 +243,46 @@ INFFT_D bool chol_solve(double* T, int n, double (&v)[NMAX], double& ysq) {
     return ok;
 }
 
+// One problem's buffers for the batch mode of the solver tiers (lsq.cu): one launch of a tier
+// covers the work items of all problems of a batch.
+struct TierArgs {
+    const double* xs;
+    const double2* ph;
+    const int32_t* col_start;
+    const int32_t* col_count;
+    const int32_t* col_off;
+    int N, Ms;
+    KernelParams kp;
+    double mu0;
+    double* w64;
+    float* w32;
+    double* J;
+    uint8_t* wide;
+    int32_t* tiles_mid;
+    int32_t* tiles_big;
+    int32_t* list_a;
+    int32_t* big_list;
+    int32_t* counters;
+};
+
+// Batch mode of a tier launch: probs == nullptr for a single-problem launch; otherwise P
+// problems whose work items are numbered by the prefix off (P + 1 entries on the device).
+struct TierBatch {
+    const TierArgs* probs;
+    const int32_t* off;
+    int P;
+};
+
+// The problem of global work item `it`: the largest p with off[p] <= it (off non-decreasing).
+INFFT_D int batch_problem(const int32_t* __restrict__ off, int P, int it) {
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Kernel constants of a plan (host side).
 // Device view of one plan for the large-column tier (lsq.cu).
 struct HugeProblem {

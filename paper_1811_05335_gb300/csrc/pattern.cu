@@ -12,6 +12,7 @@
 // so the result -- and every later result -- is deterministic.  A last pass
 // gathers the sorted nodes and their phases (sin, cos)(pi M x) used by the
 // precompute.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -286,4 +287,135 @@ cudaError_t run_pattern(Plan* p, cudaStream_t s) {
                                                      p->counters);
     launch_end(p, s);
     return run_exclusive_scan(p, p->col_count, p->col_off, Ms, s);
+}
+
+// ---- the pattern of every problem of a batch in one launch ----------------------------
+//
+// One CTA per problem (persistent CTAs take problems in the order given, largest first): the
+// same steps as run_pattern -- clear, key histogram, its exclusive scan (the bucket offsets),
+// scatter, ordering of each bucket by caller index, sorted nodes and phases, column ranges and
+// their scan -- separated by CTA barriers instead of kernel boundaries.  The results are those
+// of run_pattern on each problem.
+
+namespace {
+
+constexpr int BP_THREADS = 1024;
+
+// out[i] = sum_{q < i} in[q] for i < n and out[n] = the total (out may alias in); every thread
+// of the CTA calls it.  Thread t scans the contiguous range [t per, (t + 1) per).
+INFFT_D void cta_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_t* red) {
+    const int per = (n + BP_THREADS - 1) / BP_THREADS;
+    const int a = min((int)threadIdx.x * per, n), b = min(a + per, n);
+    int32_t loc = 0;
+    for (int i = a; i < b; ++i) loc += in[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t inc = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) red[w] = inc;
+    __syncthreads();
+    int32_t run = inc - loc;
+    for (int ww = 0; ww < w; ++ww) run += red[ww];
+    for (int i = a; i < b; ++i) {
+        const int32_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == BP_THREADS - 1) out[n] = run;
+    __syncthreads();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(BP_THREADS)
+k_batch_pattern(const PatternArgs* __restrict__ probs, const int32_t* __restrict__ order, int P) {
+    __shared__ int32_t red[BP_THREADS / 32];
+    const int tid = threadIdx.x;
+    for (int k = blockIdx.x; k < P; k += gridDim.x) {
+        const PatternArgs a = probs[order[k]];
+        const int N = a.N, Ms = a.Ms, nkeys = 2 * Ms;
+        // clear
+        for (int i = tid; i <= nkeys; i += BP_THREADS) a.bucket[i] = 0;
+        for (int i = tid; i < nkeys; i += BP_THREADS) a.cursor[i] = 0;
+        if (tid < CNT_N) a.counters[tid] = 0;
+        __syncthreads();
+        // key histogram (bad nodes counted, and keyed as x = 0)
+        for (int j = tid; j < N; j += BP_THREADS) {
+            const double xj = a.x[j];
+            if (!(isfinite(xj) && xj >= -0.5 && xj < 0.5)) atomicAdd(&a.counters[CNT_BAD_NODES], 1);
+            atomicAdd(&a.bucket[node_key(checked_node(a.x, j), Ms)], 1);
+        }
+        __syncthreads();
+        cta_exclusive_scan(a.bucket, a.bucket, nkeys, red);
+        // scatter
+        for (int j = tid; j < N; j += BP_THREADS) {
+            const uint32_t key = node_key(checked_node(a.x, j), Ms);
+            const int pos = a.bucket[key] + atomicAdd(&a.cursor[key], 1);
+            a.perm[pos] = j;
+            a.skey[pos] = key;
+        }
+        __syncthreads();
+        // order each bucket by caller index: small ones by one thread, large ones by the CTA
+        for (int b = tid; b < nkeys; b += BP_THREADS) {
+            const int s0 = a.bucket[b], s1 = a.bucket[b + 1], c = s1 - s0;
+            if (c <= 1) continue;
+            if (c > SMALL_BUCKET) {
+                a.seg_list[atomicAdd(&a.counters[CNT_BIG_SEGMENTS], 1)] = b;
+                continue;
+            }
+            for (int i = s0 + 1; i < s1; ++i) {
+                const int v = a.perm[i];
+                int q = i - 1;
+                while (q >= s0 && a.perm[q] > v) {
+                    a.perm[q + 1] = a.perm[q];
+                    --q;
+                }
+                a.perm[q + 1] = v;
+            }
+        }
+        __syncthreads();
+        const int nbig = a.counters[CNT_BIG_SEGMENTS];
+        for (int it = 0; it < nbig; ++it) {
+            const int b = a.seg_list[it];
+            const int s0 = a.bucket[b], c = a.bucket[b + 1] - s0;
+            for (int i = tid; i < c; i += BP_THREADS) {
+                const int v = a.perm[s0 + i];
+                int rank = 0;
+                for (int q = 0; q < c; ++q) rank += a.perm[s0 + q] < v;
+                a.sort_tmp[s0 + rank] = v;
+            }
+            __syncthreads();
+            for (int i = tid; i < c; i += BP_THREADS) a.perm[s0 + i] = a.sort_tmp[s0 + i];
+            __syncthreads();
+        }
+        // sorted nodes and their phases
+        for (int i = tid; i < N; i += BP_THREADS) {
+            const double xi = checked_node(a.x, a.perm[i]);
+            a.xs[i] = xi;
+            a.phase[i] = node_phase(a.M, xi);
+        }
+        // column ranges: keys [2(p-m), 2(p+m)] (mod 2 M_sigma)
+        for (int p = tid; p < Ms; p += BP_THREADS) {
+            int lo = p - a.m; if (lo < 0) lo += Ms;
+            int hi = p + a.m; if (hi >= Ms) hi -= Ms;
+            const int klo = 2 * lo, khi = 2 * hi + 1;
+            const int s0 = a.bucket[klo], s1 = a.bucket[khi];
+            const int c = (klo < khi) ? (s1 - s0) : (N - s0) + s1;
+            a.col_start[p] = (s0 == N) ? 0 : s0;
+            a.col_count[p] = c;
+            if (c == 0) atomicAdd(&a.counters[CNT_EMPTY], 1);
+            atomicMax(&a.counters[CNT_MAX_COLUMN], c);
+        }
+        __syncthreads();
+        cta_exclusive_scan(a.col_count, a.col_off, Ms, red);
+    }
+}
+
+cudaError_t run_pattern_batch(const PatternArgs* probs, const int32_t* order, int P, int sms, cudaStream_t s) {
+    const int ctas = std::min(P, 2 * sms);
+    k_batch_pattern<<<ctas, BP_THREADS, 0, s>>>(probs, order, P);
+    count_launches(1);
+    return cudaGetLastError();
 }

@@ -157,6 +157,26 @@ void launch_end(Plan* p, cudaStream_t s);
 
 // pattern.cu
 cudaError_t run_pattern(Plan* p, cudaStream_t s);
+// pattern.cu: the pattern of every problem of a batch in one launch (one CTA per problem,
+// problems in `order`, largest first); PatternArgs on the device
+struct PatternArgs {
+    const double* x;
+    double* xs;
+    double2* phase;
+    uint32_t* skey;
+    int32_t* perm;
+    int32_t* bucket;
+    int32_t* cursor;
+    int32_t* seg_list;
+    int32_t* sort_tmp;
+    int32_t* col_start;
+    int32_t* col_count;
+    int32_t* col_off;
+    int32_t* counters;
+    int N, Ms, m;
+    double M;
+};
+cudaError_t run_pattern_batch(const PatternArgs* probs, const int32_t* order, int P, int sms, cudaStream_t s);
 // pattern.cu: fills the node-phase table on the current device (once; synchronous, so it is
 // called when a plan or batch is created, not inside a stream capture)
 cudaError_t phase_table_init();
@@ -173,6 +193,14 @@ size_t huge_scratch_doubles(int slots, int nmax);
 // order: one int per possible job (sum of the problems' M_sigma); work: nmax + 2 ints
 cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int32_t* order, int32_t* work,
                                 double* scratch, int slots, int nmax, cudaStream_t s);
+// lsq.cu: the solver tiers of every problem of a batch, one launch per tier.  probs: P device
+// descriptors (tier_args of each member, tier_args_bytes() each); tile_off: P + 1 device
+// prefix of the problems' 32-column tiles; off_work: 3 (P + 1) ints of device scratch.  Columns
+// above 64 nodes stay in the members' big lists (run_precompute_huge).
+size_t tier_args_bytes();
+void tier_args_fill(Plan* const* plans, int P, void* host);
+cudaError_t run_precompute_batch(const void* probs, int P, const int32_t* tile_off, int total_tiles,
+                                 int32_t* off_work, int sms, cudaStream_t s);
 // under.cu: the underdetermined case; under_moment_chunks = partial-sum blocks of the node moments
 cudaError_t run_precompute_under(Plan* p, cudaStream_t s);
 int under_moment_chunks(int64_t N);
