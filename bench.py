@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-under", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--tune-cache-out", default=None,
+                    help="write the batched workload's measured tile shape to this cache file")
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     return ap.parse_args()
@@ -562,7 +564,16 @@ def run_gpu(a):
             g.infft_batch_precompute(bt, stream)
 
         t_pre_b = timed(pre_b, reps=2, warm=1)
+        # the fixed tile rule, then the autotuned shape (from the package's cache for this
+        # workload class and device, else measured now); both give bit-identical fhat
+        g.infft_batch_set_tile_shape(bt, -1, stream)
+        t_app_fixed = timed(lambda: g.infft_batch_apply(bt, fb, out=outb, stream=stream), reps=20)
+        out_fixed = outb.clone()
+        from paper_1811_05335_gb300 import tuning
+        tune = tuning.autotune_batch(bt, stream=stream, write=a.tune_cache_out)
         t_app_b = timed(lambda: g.infft_batch_apply(bt, fb, out=outb, stream=stream), reps=20)
+        torch.cuda.synchronize()
+        tuned_identical = bool(torch.equal(torch.view_as_real(outb), torch.view_as_real(out_fixed)))
         infob = g.infft_batch_get_info(bt)
         bt.close()
         nb = int(w.N.sum())
@@ -572,6 +583,10 @@ def run_gpu(a):
         batched = {"workload": f"{w.M.size} problems, M log-uniform in [256, 8192] (sum {int(w.M.sum())}), "
                                f"N = 2-4 M (sum {nb}), Chebyshev-clustered nodes, sigma=2, m={w.m}",
                    "precompute_ms": t_pre_b, "apply_ms": t_app_b,
+                   "tile_shape": {"cols": tune["cols"], "weights": tune["weights"], "source": tune["source"],
+                                  "key": tune["key"], "ms_per_shape": tune["ms"]},
+                   "apply_ms_fixed_rule": t_app_fixed, "tuned_vs_fixed_speedup": t_app_fixed / t_app_b,
+                   "tuned_bit_identical_to_fixed": tuned_identical,
                    "apply_nodes_per_s": nb / (t_app_b / 1e3),
                    "apply_vs_single_problem_apply": (nb / (t_app_b / 1e3)) / single_rate,
                    "precompute_nodes_per_s": nb / (t_pre_b / 1e3),

@@ -277,8 +277,8 @@ infft_status infft_profile_read(infft_plan_t plan, int cap, const char** names,
  * f: sum N_p complex64 values; fhat: sum M_p complex64 coefficients, problem p's
  * block at offset sum_{q<p} M_q in the k + M_p/2 layout.
  * The batch owns all device buffers (one arena for the members' patterns and
- * weights, staging for host f/fhat) and a pool of streams ordered after the
- * caller's stream. */
+ * weights, staging for host f/fhat); every step runs on the caller's stream, one
+ * launch per stage over all problems. */
 typedef struct infft_batch_s* infft_batch_t;
 
 typedef struct {
@@ -309,6 +309,28 @@ infft_status infft_batch_precompute(infft_batch_t batch, infft_stream_t stream);
 /* fhat_p = D^* F^* B_opt,p^* f_p for every problem p (eq:approx_ansatz2), fp32:
  * f (sum N_p complex64) -> fhat (sum M_p complex64), host or device. */
 infft_status infft_batch_apply(infft_batch_t batch, const float* f, float* fhat, infft_stream_t stream);
+
+/* Tile shapes of the batched apply's spreading (the autotuned part).  Shape `id` cuts
+ * each problem's grid into tiles of at most `cols` grid points (one thread each) whose
+ * weights start within one block of `weights` entries (both powers of two).  Every
+ * shape computes bit-identical fhat: each column is summed in one fixed order that
+ * depends on its grid point only.  infft_batch_set_tile_shape(batch, -1) restores the
+ * default (the fixed rule: 128 grid points, 2048 weights); on a precomputed batch it
+ * re-cuts the tiles on `stream` (three launches), otherwise the precompute uses it.
+ * Ids outside [-1, count): INFFT_EINVAL.  infft_batch_get_tile_shape returns the shape
+ * the next apply uses (-1 for a NULL batch). */
+int32_t infft_batch_tile_shape_count(void);
+infft_status infft_batch_tile_shape(int32_t id, int32_t* cols, int32_t* weights);
+infft_status infft_batch_set_tile_shape(infft_batch_t batch, int32_t id, infft_stream_t stream);
+int32_t infft_batch_get_tile_shape(infft_batch_t batch);
+
+/* Autotuning of the tile shape: times `repeats` batched applies (after two untimed ones)
+ * of every shape on the batch's own B_opt with CUDA events on `stream` (the data vector
+ * is the batch's zeroed staging buffer), keeps the fastest and returns its id in *best.
+ * ms_out, when not NULL, receives infft_batch_tile_shape_count() average times in ms.
+ * Synchronises `stream`; allocates nothing.  Requires infft_batch_precompute. */
+infft_status infft_batch_tune_apply(infft_batch_t batch, int32_t repeats, float* ms_out, int32_t* best,
+                                    infft_stream_t stream);
 
 /* Synchronises the batch's last stream and fills *info (sums over problems). */
 infft_status infft_batch_get_info(infft_batch_t batch, infft_batch_info* info);

@@ -13,8 +13,10 @@ from .binding import (  # noqa: F401
     infft_get_apply_config, infft_tune_apply, infft_fp64_fma_probe, infft_fp64_fma_probe_sink_len,
     Batch, infft_batch_create, infft_batch_set_nodes, infft_batch_precompute, infft_batch_apply,
     infft_batch_get_info, infft_batch_copy_problem, infft_apply_many, infft_apply_many_workspace,
+    infft_batch_tile_shapes, infft_batch_set_tile_shape, infft_batch_get_tile_shape, infft_batch_tune_apply,
     EXPORTED_SYMBOLS, KERNEL_FULL, KERNEL_SYM, ANSATZ_UNDERDETERMINED, ANSATZ_OVERDETERMINED,
     Plan2D, infft2d_plan_create, infft2d_set_nodes, infft2d_precompute, infft2d_apply, infft2d_apply_z,
     infft2d_get_info, infft2d_copy_plan_data,
 )
 from .autograd import InverseNFFT, inverse_nfft  # noqa: F401
+from .tuning import batch_workload_key, autotune_batch  # noqa: F401

@@ -32,6 +32,8 @@ EXPORTED_SYMBOLS = (
     "infft_apply_sorted", "infft_sort_values", "infft_apply_config_count", "infft_apply_config_shape",
     "infft_set_apply_config", "infft_get_apply_config", "infft_tune_apply",
     "infft_fp64_fma_probe", "infft_fp64_fma_probe_sink_len",
+    "infft_batch_tile_shape_count", "infft_batch_tile_shape", "infft_batch_set_tile_shape",
+    "infft_batch_get_tile_shape", "infft_batch_tune_apply",
 )
 
 
@@ -127,6 +129,9 @@ def library():
         "infft_set_apply_config": [P, I32],
         "infft_tune_apply": [P, I32, VP, ctypes.POINTER(I32), VP],
         "infft_fp64_fma_probe": [I64, VP, I64, ctypes.POINTER(D), VP],
+        "infft_batch_tile_shape": [I32, ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "infft_batch_set_tile_shape": [P, I32, VP],
+        "infft_batch_tune_apply": [P, I32, VP, ctypes.POINTER(I32), VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -140,6 +145,10 @@ def library():
     lib.infft_apply_config_count.argtypes = []
     lib.infft_get_apply_config.restype = ctypes.c_int
     lib.infft_get_apply_config.argtypes = [P]
+    lib.infft_batch_tile_shape_count.restype = ctypes.c_int
+    lib.infft_batch_tile_shape_count.argtypes = []
+    lib.infft_batch_get_tile_shape.restype = ctypes.c_int
+    lib.infft_batch_get_tile_shape.argtypes = [P]
     lib.infft_launch_count.restype = ctypes.c_int64
     lib.infft_launch_count.argtypes = []
     lib.infft_last_error.restype = ctypes.c_char_p
@@ -529,6 +538,38 @@ def infft_batch_apply(batch, f, out=None, stream=None):
     _check(library().infft_batch_apply(batch.handle, _as_ptr(f, "c64", keep), _as_ptr(out, "c64", keep),
                                        _stream(stream, f, out)))
     return out
+
+
+def infft_batch_tile_shapes():
+    """[(grid points per tile, weights per block)] of every tile shape of the batched spreading, by id."""
+    lib = library()
+    out = []
+    for i in range(lib.infft_batch_tile_shape_count()):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib.infft_batch_tile_shape(i, ctypes.byref(a), ctypes.byref(b)))
+        out.append((a.value, b.value))
+    return out
+
+
+def infft_batch_set_tile_shape(batch, shape, stream=None):
+    """Tile shape id of the batched spreading (-1: the fixed default rule)."""
+    _check(library().infft_batch_set_tile_shape(batch.handle, int(shape), _stream(stream)))
+
+
+def infft_batch_get_tile_shape(batch):
+    """Tile shape id the next batched apply uses."""
+    return int(library().infft_batch_get_tile_shape(batch.handle))
+
+
+def infft_batch_tune_apply(batch, repeats=10, stream=None):
+    """Times every tile shape on the batch and keeps the fastest: (best id, [ms per id])."""
+    lib = library()
+    n = lib.infft_batch_tile_shape_count()
+    ms = (ctypes.c_float * n)()
+    best = ctypes.c_int(-1)
+    _check(lib.infft_batch_tune_apply(batch.handle, int(repeats), ctypes.cast(ms, ctypes.c_void_p),
+                                      ctypes.byref(best), _stream(stream)))
+    return best.value, [float(v) for v in ms]
 
 
 def infft_batch_get_info(batch):

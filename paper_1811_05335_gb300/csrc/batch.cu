@@ -225,28 +225,32 @@ k_batch_chirp(const BatchProblem* __restrict__ probs, float2* __restrict__ bhat_
     for (int i = threadIdx.x; i < L; i += blockDim.x) out[i] = sm[pad16(i)];
 }
 
-// Tiles of the batched spreading.  Grid point p of a problem starts a tile when
-// p is a multiple of TILE_COLS or when its weight offset enters a new block of
-// TILE_WEIGHTS entries: a tile then has at most TILE_COLS grid points and fewer
-// than TILE_WEIGHTS + |I(l)|max weights, which the staged spreading holds.
-constexpr int TILE_COLS = 128;      // grid points per spreading tile (one thread each)
-constexpr int TILE_WEIGHTS = 2048;
-constexpr int TILE_WMAX = 3072;     // staged weights: TILE_WEIGHTS + the largest column of the workloads
-constexpr int TILE_UMAX = 1024;     // staged node values
-constexpr int TILE_UPT = TILE_UMAX / TILE_COLS;
+// Tiles of the batched spreading, the autotuned part of the batched apply.  A tile
+// shape is (cols, wblk), both powers of two: grid point p of a problem starts a tile
+// when p is a multiple of cols or when its weight offset enters a new block of wblk
+// entries, so a tile has at most cols grid points (one thread each) and fewer than
+// wblk + |I(l)|max weights.  The shapes are the tuner's candidates (the default is
+// the fixed rule, 128 grid points and 2048 weights).  Every shape gives the same
+// sums: each column is summed in one order that depends on the grid point only.
+struct TileShape {
+    int log_cols, log_wblk;
+};
+constexpr TileShape TILE_SHAPES[] = {{6, 10}, {6, 11}, {6, 12}, {7, 10}, {7, 11}, {7, 12}, {8, 11}, {8, 12}};
+constexpr int TILE_SHAPE_COUNT = (int)(sizeof(TILE_SHAPES) / sizeof(TILE_SHAPES[0]));
+constexpr int TILE_SHAPE_DEFAULT = 4;
 constexpr int TILE_SCAN_THREADS = 1024;
 
-INFFT_D bool tile_start(const int32_t* __restrict__ col_off, int p) {
-    return p % TILE_COLS == 0 || (col_off[p] / TILE_WEIGHTS) != (col_off[p - 1] / TILE_WEIGHTS);
+INFFT_D bool tile_start(const int32_t* __restrict__ col_off, int p, int lc, int lw) {
+    return (p & ((1 << lc) - 1)) == 0 || (col_off[p] >> lw) != (col_off[p - 1] >> lw);
 }
 
 // Per problem (one CTA): its number of tiles.
 __global__ void __launch_bounds__(TILE_SCAN_THREADS)
-k_tile_count(const BatchProblem* __restrict__ probs, int32_t* __restrict__ count) {
+k_tile_count(const BatchProblem* __restrict__ probs, int lc, int lw, int32_t* __restrict__ count) {
     const BatchProblem pr = probs[blockIdx.x];
     const int Ms = 2 * pr.M;
     int c = 0;
-    for (int p = threadIdx.x; p < Ms; p += blockDim.x) c += tile_start(pr.col_off, p);
+    for (int p = threadIdx.x; p < Ms; p += blockDim.x) c += tile_start(pr.col_off, p, lc, lw);
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     __shared__ int red[TILE_SCAN_THREADS / 32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -285,13 +289,14 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(const int32_t* __restrict_
 // first grid point, end grid point, first node S) and (first weight, end weight,
 // node window U, 0); thread t scans a contiguous run of grid points.
 __global__ void __launch_bounds__(TILE_SCAN_THREADS)
-k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ off, int4* __restrict__ tiles) {
+k_tile_fill(const BatchProblem* __restrict__ probs, int lc, int lw, const int32_t* __restrict__ off,
+            int4* __restrict__ tiles) {
     const BatchProblem pr = probs[blockIdx.x];
     const int Ms = 2 * pr.M;
     const int per = (Ms + TILE_SCAN_THREADS - 1) / TILE_SCAN_THREADS;
     const int a = min((int)threadIdx.x * per, Ms), b = min(a + per, Ms);
     int c = 0;
-    for (int p = a; p < b; ++p) c += tile_start(pr.col_off, p);
+    for (int p = a; p < b; ++p) c += tile_start(pr.col_off, p, lc, lw);
     __shared__ int part[TILE_SCAN_THREADS];
     part[threadIdx.x] = c;
     __syncthreads();
@@ -303,9 +308,9 @@ k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ 
     }
     int pos = off[blockIdx.x] + part[threadIdx.x] - c;
     for (int p = a; p < b; ++p) {
-        if (!tile_start(pr.col_off, p)) continue;
+        if (!tile_start(pr.col_off, p, lc, lw)) continue;
         int q = p + 1;   // the tile ends at the next start
-        while (q < Ms && !tile_start(pr.col_off, q)) ++q;
+        while (q < Ms && !tile_start(pr.col_off, q, lc, lw)) ++q;
         // the tile's weights [w0, w1) and its window of U sorted nodes from S (mod N)
         const int S = pr.col_start[p];
         int U = pr.col_start[q - 1] + pr.col_count[q - 1] - S;
@@ -316,69 +321,15 @@ k_tile_fill(const BatchProblem* __restrict__ probs, const int32_t* __restrict__ 
     }
 }
 
-// Spreading of all problems: CTA t spreads tile t (problem, [p0, p1)) into the
-// problem's slice of g_all; CTAs beyond the number of tiles return.  The tile
-// record carries the tile's weight range and node window, so the weights and
-// node indices are requested together with the threads' column data (two
-// dependent load phases per tile: weights and indices, then node values).  A tile
-// whose block does not fit the staging buffers takes the segmented walk.  (A
-// persistent, two-stage software-pipelined variant was slower: 1.48 ms against
-// 1.10 ms on the batched workload, at half the resident threads per SM.)
-__global__ void __launch_bounds__(TILE_COLS)
-k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ tiles,
-               const int32_t* __restrict__ ntiles, const float2* __restrict__ f, float2* __restrict__ g_all) {
-    __shared__ __align__(16) float ws[TILE_WMAX];
-    __shared__ __align__(16) float2 fu[TILE_UMAX];
-    if ((int)blockIdx.x >= *ntiles) return;
-    const int4 ra = tiles[2 * blockIdx.x], rb = tiles[2 * blockIdx.x + 1];
-    const int p0 = ra.y, p1 = ra.z, S = ra.w, w0 = rb.x, w1 = rb.y, U = rb.z;
-    const BatchProblem& pr = probs[ra.x];
-    const int N = pr.N;
-    const float2* fp = f + pr.f_off;
-    float2* g = g_all + pr.g_off;
-    const int wb = w0 & ~3, we = (w1 + 3) & ~3;
-    if ((we - wb) > TILE_WMAX || U > TILE_UMAX || U > N) {   // block-uniform
-        spread_tile_segmented<TILE_COLS>(fp, pr.w32, pr.wlo, pr.wide, pr.perm, pr.col_start, pr.col_off, N, p0, p1,
-                                         w0, w1, g, (int*)ws, fu);
-        return;
-    }
-    const float* w32 = pr.w32;
-    const int32_t* perm = pr.perm;
-    for (int v = threadIdx.x; v < (we - wb) / 4; v += TILE_COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
-    int pq[TILE_UPT];
-#pragma unroll
-    for (int u = 0; u < TILE_UPT; ++u) {
-        const int q = threadIdx.x + u * TILE_COLS;
-        int gq = S + q;
-        if (gq >= N) gq -= N;
-        pq[u] = q < U ? perm[gq] : 0;
-    }
-    const int p = p0 + threadIdx.x;
-    const bool live = p < p1;
-    const int n = live ? pr.col_count[p] : 0;
-    const int s = live ? pr.col_start[p] : 0;
-    const int off = live ? pr.col_off[p] : 0;
-    const bool wide_col = live && pr.wide[p];
-#pragma unroll
-    for (int u = 0; u < TILE_UPT; ++u) {
-        const int q = threadIdx.x + u * TILE_COLS;
-        if (q < U) cp_async8(fu + q, fp + pq[u]);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (!live) return;
-    int r0 = s - S;
-    if (r0 < 0) r0 += N;
-    if (wide_col || (n > 0 && r0 + n > U)) {
-        g[p] = spread_direct<float>(fp, w32, nullptr, pr.wlo, wide_col, perm, n, s, off, N);
-        return;
-    }
-    // walk the column from a lane-dependent start (neighbouring columns sit |I(l)|
-    // weights apart in shared memory, so a common start would hit few banks)
-    const float* wc = ws + (off - wb);
-    const float2* fc = fu + r0;
+// g_l of grid point p in its one summation order, whatever the tile: the entries
+// i = k0, k0 + 1, .., n - 1, 0, .., k0 - 1 with k0 = (p mod 32) mod n, one fmaf per entry
+// and component (float-float, w32 + wlo, for wide columns).  Starting each column at
+// its grid point's lane spreads a warp's shared-memory accesses over the banks
+// (neighbouring columns sit |I(l)| weights apart).  From staged data: wc and fc are
+// the column's weights and node values in shared memory.
+INFFT_D float2 col_sum_staged(const float* wc, const float2* fc, int n, int k0) {
     float re = 0, im = 0;
-    int k = n ? (int)(threadIdx.x & 31) % n : 0;
+    int k = k0;
     for (int i = 0; i < n; ++i) {
         const float wi = wc[k];
         const float2 v = fc[k];
@@ -386,7 +337,157 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
         im = fmaf(wi, v.y, im);
         k = (k + 1 == n) ? 0 : k + 1;
     }
-    g[p] = make_float2(re, im);
+    return make_float2(re, im);
+}
+
+// The same sum by direct loads (node s + k of the sorted order is f[perm[(s + k) mod N]]).
+INFFT_D float2 col_sum_direct(const float2* __restrict__ f, const float* __restrict__ w32,
+                              const float* __restrict__ wlo, bool wide_col, const int32_t* __restrict__ perm,
+                              int n, int s, int off, int N, int k0) {
+    int k = k0, q = s + k0;
+    if (q >= N) q -= N;
+    if (wide_col) {
+        FFSum acc;
+        for (int i = 0; i < n; ++i) {
+            acc.add(w32[off + k], wlo[off + k], f[perm[q]]);
+            if (++k == n) k = 0, q = s - 1;
+            if (++q >= N) q -= N;
+        }
+        return acc.value();
+    }
+    float re = 0, im = 0;
+    for (int i = 0; i < n; ++i) {
+        const float wi = w32[off + k];
+        const float2 v = f[perm[q]];
+        re = fmaf(wi, v.x, re);
+        im = fmaf(wi, v.y, im);
+        if (++k == n) k = 0, q = s - 1;
+        if (++q >= N) q -= N;
+    }
+    return make_float2(re, im);
+}
+
+// Spreading of all problems with tiles of shape (2^LC grid points, 2^LW weight
+// blocks): CTA t spreads tile t (problem, [p0, p1)) into the problem's slice of
+// g_all; CTAs beyond the number of tiles return.  The tile record carries the
+// tile's weight range and node window, so the weights and node indices are
+// requested together with the threads' column data (two dependent load phases per
+// tile: weights and indices, then node values).  A node window longer than the
+// staging buffer (the densest clusters) is staged in pieces, twice: the first sweep
+// adds each column's entries k0 .. n-1, the second its entries 0 .. k0-1, which keeps
+// the one summation order.  Wide columns, columns outside the window and tiles whose
+// weights do not fit (a column above HUGE_NMAX nodes) are summed by direct loads, in
+// the same order.  (A persistent, two-stage software-pipelined variant was slower:
+// 1.48 ms against 1.10 ms on the batched workload, at half the resident threads per SM.)
+template <int LC, int LW>
+__global__ void __launch_bounds__(1 << LC)
+k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ tiles,
+               const int32_t* __restrict__ ntiles, const float2* __restrict__ f, float2* __restrict__ g_all) {
+    constexpr int COLS = 1 << LC;
+    constexpr int WMAX = (1 << LW) + HUGE_NMAX + 8;       // wblk + the largest solved column + alignment
+    constexpr int UMAX = COLS * 8 > 1024 ? COLS * 8 : 1024;
+    constexpr int UPT = UMAX / COLS;
+    __shared__ __align__(16) float ws[WMAX];
+    __shared__ __align__(16) float2 fu[UMAX];
+    if ((int)blockIdx.x >= *ntiles) return;
+    const int4 ra = tiles[2 * blockIdx.x], rb = tiles[2 * blockIdx.x + 1];
+    const int p0 = ra.y, p1 = ra.z, S = ra.w, w0 = rb.x, w1 = rb.y, U = rb.z;
+    const BatchProblem& pr = probs[ra.x];
+    const int N = pr.N;
+    const float2* fp = f + pr.f_off;
+    float2* g = g_all + pr.g_off;
+    const float* w32 = pr.w32;
+    const int32_t* perm = pr.perm;
+    const int wb = w0 & ~3, we = (w1 + 3) & ~3;
+    const bool staged = (we - wb) <= WMAX && U <= N;       // block-uniform
+    const bool one_piece = U <= UMAX;
+    int pq[UPT];
+    if (staged) {
+        for (int v = threadIdx.x; v < (we - wb) / 4; v += COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
+        if (one_piece) {
+#pragma unroll
+            for (int u = 0; u < UPT; ++u) {
+                const int q = threadIdx.x + u * COLS;
+                int gq = S + q;
+                if (gq >= N) gq -= N;
+                pq[u] = q < U ? perm[gq] : 0;
+            }
+        }
+    }
+    const int p = p0 + threadIdx.x;
+    const bool live = p < p1;
+    const int n = live ? pr.col_count[p] : 0;
+    const int s = live ? pr.col_start[p] : 0;
+    const int off = live ? pr.col_off[p] : 0;
+    const bool wide_col = live && pr.wide[p];
+    const int k0 = n ? (p & 31) % n : 0;
+    int r0 = s - S;
+    if (r0 < 0) r0 += N;
+    const bool direct = !staged || wide_col || (n > 0 && r0 + n > U);
+    float2 acc = make_float2(0.f, 0.f);
+    if (staged && one_piece) {
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+            const int q = threadIdx.x + u * COLS;
+            if (q < U) cp_async8(fu + q, fp + pq[u]);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (live && !direct) acc = col_sum_staged(ws + (off - wb), fu + r0, n, k0);
+    } else if (staged) {
+        const float* wc = ws + (off - wb);
+        float re = 0, im = 0;
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            // window positions of the sweep's entries: [r0 + k0, r0 + n), then [r0, r0 + k0)
+            const int lo = sweep == 0 ? r0 + k0 : r0, hi = sweep == 0 ? r0 + n : r0 + k0;
+            for (int c0 = 0; c0 < U; c0 += UMAX) {
+                __syncthreads();   // the previous piece is consumed
+                const int len = min(UMAX, U - c0);
+                for (int q = threadIdx.x; q < len; q += COLS) {
+                    int gq = S + c0 + q;
+                    if (gq >= N) gq -= N;
+                    cp_async8(fu + q, fp + perm[gq]);
+                }
+                cp_async_wait_all();
+                __syncthreads();
+                if (live && !direct) {
+                    const int a = max(lo, c0), e = min(hi, c0 + len);
+                    for (int r = a; r < e; ++r) {
+                        const float wi = wc[r - r0];
+                        const float2 v = fu[r - c0];
+                        re = fmaf(wi, v.x, re);
+                        im = fmaf(wi, v.y, im);
+                    }
+                }
+            }
+        }
+        acc = make_float2(re, im);
+    }
+    if (!live) return;
+    g[p] = direct ? col_sum_direct(fp, w32, pr.wlo, wide_col, perm, n, s, off, N, k0) : acc;
+}
+
+cudaError_t launch_batch_spread(int shape, unsigned grid, const BatchProblem* probs, const int4* tiles,
+                                const int32_t* ntiles, const float2* f, float2* g, cudaStream_t s) {
+    switch (shape) {
+#define INFFT_SPREAD_SHAPE(ID, LC, LW)                                                   \
+    case ID:                                                                             \
+        static_assert(TILE_SHAPES[ID].log_cols == LC && TILE_SHAPES[ID].log_wblk == LW, ""); \
+        k_batch_spread<LC, LW><<<grid, 1 << LC, 0, s>>>(probs, tiles, ntiles, f, g);    \
+        break;
+        INFFT_SPREAD_SHAPE(0, 6, 10)
+        INFFT_SPREAD_SHAPE(1, 6, 11)
+        INFFT_SPREAD_SHAPE(2, 6, 12)
+        INFFT_SPREAD_SHAPE(3, 7, 10)
+        INFFT_SPREAD_SHAPE(4, 7, 11)
+        INFFT_SPREAD_SHAPE(5, 7, 12)
+        INFFT_SPREAD_SHAPE(6, 8, 11)
+        INFFT_SPREAD_SHAPE(7, 8, 12)
+#undef INFFT_SPREAD_SHAPE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // D^* F^* of every problem's grid (pruned to its M central frequencies): one CTA
@@ -531,6 +632,8 @@ struct infft_batch_s {
     int32_t* tile_count = nullptr;  // P counts, then P + 1 offsets
     int32_t* tile_off = nullptr;
     int64_t max_tiles = 0;
+    int tile_shape = TILE_SHAPE_DEFAULT;   // the spreading's tile shape (TILE_SHAPES)
+    int64_t shape_tiles[TILE_SHAPE_COUNT] = {};   // the tile-count bound of each shape (the launch's grid)
     PatternArgs* pat_args = nullptr;   // P pattern descriptors (one launch for every problem's pattern)
     void* tier_args = nullptr;         // P solver-tier descriptors (one launch per tier)
     int32_t* pat_order = nullptr;      // problems by decreasing N (the pattern's CTAs take them in order)
@@ -547,6 +650,17 @@ struct infft_batch_s {
 };
 
 namespace {
+
+// The spreading tiles of the batch's tile shape, cut from the weight offsets.
+cudaError_t build_tiles(infft_batch_t b, cudaStream_t s) {
+    const TileShape sh = TILE_SHAPES[b->tile_shape];
+    k_tile_count<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, sh.log_cols, sh.log_wblk, b->tile_count);
+    k_tile_prefix<<<1, 1024, 0, s>>>(b->tile_count, (int)b->P, b->tile_off);
+    k_tile_fill<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, sh.log_cols, sh.log_wblk, b->tile_off,
+                                                             b->tiles);
+    count_launches(3);
+    return cudaGetLastError();
+}
 
 void batch_free(infft_batch_t b) {
     for (Plan* p : b->plans) delete p;
@@ -695,10 +809,15 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
         alloc(&b->job_order, b->sumG * sizeof(int32_t));
         alloc(&b->job_work, (HUGE_NMAX + 2) * sizeof(int32_t));
     }
-    // tiles of the batched spreading: at most one per TILE_COLS grid points plus
-    // one per TILE_WEIGHTS weights of the largest possible nnz
-    for (int64_t i = 0; i < P; ++i)
-        b->max_tiles += (2 * M[i] + TILE_COLS - 1) / TILE_COLS + b->plans[i]->nnz_cap / TILE_WEIGHTS + 1;
+    // tiles of the batched spreading: at most one per cols grid points plus one per
+    // wblk weights of the largest possible nnz (the buffer for the smallest shape; the
+    // apply launches the bound of the batch's shape)
+    for (int sh = 0; sh < TILE_SHAPE_COUNT; ++sh) {
+        const int cols = 1 << TILE_SHAPES[sh].log_cols, wblk = 1 << TILE_SHAPES[sh].log_wblk;
+        for (int64_t i = 0; i < P; ++i)
+            b->shape_tiles[sh] += (2 * M[i] + cols - 1) / cols + b->plans[i]->nnz_cap / wblk + 1;
+        b->max_tiles = std::max(b->max_tiles, b->shape_tiles[sh]);
+    }
     alloc(&b->tiles, 2 * b->max_tiles * sizeof(int4));
     alloc(&b->tile_count, P * sizeof(int32_t));
     alloc(&b->tile_off, (P + 1) * sizeof(int32_t));
@@ -833,13 +952,98 @@ infft_status infft_batch_precompute(infft_batch_t b, infft_stream_t stream) {
                                  b->huge_slots, b->huge_nmax, s)) !=
             cudaSuccess)
         return cuda_err(e, "large-column precompute");
-    // spreading tiles from the weight offsets
-    k_tile_count<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, b->tile_count);
-    k_tile_prefix<<<1, 1024, 0, s>>>(b->tile_count, (int)b->P, b->tile_off);
-    k_tile_fill<<<(unsigned)b->P, TILE_SCAN_THREADS, 0, s>>>(b->probs, b->tile_off, b->tiles);
-    count_launches(3);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "spreading tiles");
+    if ((e = build_tiles(b, s)) != cudaSuccess) return cuda_err(e, "spreading tiles");
     b->precomputed = 1;
+    return INFFT_OK;
+}
+
+namespace {
+
+// The two launches of the batched apply on device buffers.
+cudaError_t run_batch_apply(infft_batch_t b, const float2* fin, float2* fout, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_batch_spread(b->tile_shape, (unsigned)b->shape_tiles[b->tile_shape], b->probs, b->tiles,
+                                 b->tile_off + b->P, fin,
+                                 b->g_all, s)) != cudaSuccess)
+        return e;
+    const size_t smem = (size_t)(pad16(TW_N) + BATCH_MMAX) * sizeof(float2);
+    if ((e = cudaFuncSetAttribute(k_batch_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(b->ticket, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    k_batch_fft<<<b->sms, BATCH_FFT_THREADS, smem, s>>>(b->probs, (int)b->P, b->order, b->g_all, fout, b->tw,
+                                                        b->ticket);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int32_t infft_batch_tile_shape_count(void) { return TILE_SHAPE_COUNT; }
+
+infft_status infft_batch_tile_shape(int32_t id, int32_t* cols, int32_t* weights) {
+    if (id < 0 || id >= TILE_SHAPE_COUNT)
+        return set_error(INFFT_EINVAL, "tile shape id %d not in [0, %d)", id, TILE_SHAPE_COUNT);
+    if (cols) *cols = 1 << TILE_SHAPES[id].log_cols;
+    if (weights) *weights = 1 << TILE_SHAPES[id].log_wblk;
+    return INFFT_OK;
+}
+
+int32_t infft_batch_get_tile_shape(infft_batch_t b) { return b ? b->tile_shape : -1; }
+
+infft_status infft_batch_set_tile_shape(infft_batch_t b, int32_t id, infft_stream_t stream) {
+    if (!b) return set_error(INFFT_EINVAL, "batch is NULL");
+    if (id == -1) id = TILE_SHAPE_DEFAULT;
+    if (id < 0 || id >= TILE_SHAPE_COUNT)
+        return set_error(INFFT_EINVAL, "tile shape id %d not in [-1, %d)", id, TILE_SHAPE_COUNT);
+    b->tile_shape = id;
+    if (!b->precomputed) return INFFT_OK;   // the precompute cuts the tiles
+    DevGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last_stream = s;
+    cudaError_t e = build_tiles(b, s);
+    if (e != cudaSuccess) return cuda_err(e, "spreading tiles");
+    return INFFT_OK;
+}
+
+infft_status infft_batch_tune_apply(infft_batch_t b, int32_t repeats, float* ms_out, int32_t* best,
+                                    infft_stream_t stream) {
+    if (!b) return set_error(INFFT_EINVAL, "batch is NULL");
+    if (repeats < 1 || repeats > 10000) return set_error(INFFT_EINVAL, "repeats must be in [1, 10000] (got %d)", repeats);
+    if (!b->precomputed) return set_error(INFFT_ENOTREADY, "infft_batch_tune_apply before infft_batch_precompute");
+    DevGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last_stream = s;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    cudaError_t e = cudaEventCreate(&ea);
+    if (e == cudaSuccess) e = cudaEventCreate(&eb);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->stage_f, 0, b->sumN * sizeof(float2), s);
+    const int keep = b->tile_shape;
+    int best_id = -1;
+    float best_ms = 0.f;
+    for (int id = 0; id < TILE_SHAPE_COUNT && e == cudaSuccess; ++id) {
+        b->tile_shape = id;
+        e = build_tiles(b, s);
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run_batch_apply(b, b->stage_f, b->stage_fhat, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ea, s);
+        for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = run_batch_apply(b, b->stage_f, b->stage_fhat, s);
+        if (e == cudaSuccess) e = cudaEventRecord(eb, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+        ms /= (float)repeats;
+        if (ms_out) ms_out[id] = ms;
+        if (e == cudaSuccess && (best_id < 0 || ms < best_ms)) {
+            best_id = id;
+            best_ms = ms;
+        }
+    }
+    if (ea) cudaEventDestroy(ea);
+    if (eb) cudaEventDestroy(eb);
+    b->tile_shape = e == cudaSuccess ? best_id : keep;
+    const cudaError_t e2 = build_tiles(b, s);
+    if (e != cudaSuccess) return cuda_err(e, "tune batched apply");
+    if (e2 != cudaSuccess) return cuda_err(e2, "spreading tiles");
+    if (best) *best = best_id;
     return INFFT_OK;
 }
 
@@ -859,16 +1063,7 @@ infft_status infft_batch_apply(infft_batch_t b, const float* f, float* fhat, inf
     }
     const bool host_out = !on_device(fhat);
     float2* fout = host_out ? b->stage_fhat : (float2*)fhat;
-    k_batch_spread<<<(unsigned)b->max_tiles, TILE_COLS, 0, s>>>(b->probs, b->tiles, b->tile_off + b->P, fin,
-                                                                 b->g_all);
-    const size_t smem = (size_t)(pad16(TW_N) + BATCH_MMAX) * sizeof(float2);
-    if ((e = cudaFuncSetAttribute(k_batch_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return cuda_err(e, "shared memory");
-    if ((e = cudaMemsetAsync(b->ticket, 0, sizeof(int32_t), s)) != cudaSuccess) return cuda_err(e, "ticket");
-    k_batch_fft<<<b->sms, BATCH_FFT_THREADS, smem, s>>>(b->probs, (int)b->P, b->order, b->g_all, fout, b->tw,
-                                                        b->ticket);
-    count_launches(2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "launch");
+    if ((e = run_batch_apply(b, fin, fout, s)) != cudaSuccess) return cuda_err(e, "apply");
     if (host_out) {
         if ((e = cudaMemcpyAsync(fhat, b->stage_fhat, b->sumM * sizeof(float2), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)
