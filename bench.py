@@ -509,6 +509,19 @@ def run_gpu(a):
                 "forward_ms": t_f, "backward_ms": t_b, "backward_over_forward": t_b / t_f,
                 "unit_note": "forward: pattern + fp64 B_opt + apply; backward: nfft_apply + node gradient"}
 
+    # ---- fp64 FMA throughput of this GPU (the precompute's roofline denominator), measured
+    sink = torch.empty(g.infft_fp64_fma_probe_sink_len(), dtype=torch.float64, device=dev)
+    probe_iters = 4096
+    g.infft_fp64_fma_probe(probe_iters, sink, stream)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for s0, s1 in pev:
+        s0.record(stream)
+        probe_flops = g.infft_fp64_fma_probe(probe_iters, sink, stream)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    fp64_peak = probe_flops / (statistics.median(s0.elapsed_time(s1) for s0, s1 in pev) / 1e3) / 1e12
+    del sink
+
     # ---- underdetermined case (Sec. 3.2.1): jittered nodes, M = 4N (the ratio of the paper's
     # Example ex:trig_poly_ansatz1), N = 2^14, M = 2^16, sigma = 2, m = 4
     under = None
@@ -537,7 +550,7 @@ def run_gpu(a):
         mom_ms = ukern.get("under_moments", float("nan"))
         # one term of a node moment: complex rotate (4 mul, 2 add) + complex accumulate (2 add)
         mom_flops = 8.0 * Nu * Mu
-        peak64 = sm_count() * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
+        peak64 = fp64_peak
         ach = mom_flops / (mom_ms / 1e3) / 1e12
         under = {"workload": f"1D jittered nodes N={Nu} M={Mu} sigma=2 m=4 (underdetermined, M = 4N)",
                  "precompute_ms": t_pre, "apply_ms": t_app, "apply_nodes_per_s": Nu / (t_app / 1e3),
@@ -545,7 +558,7 @@ def run_gpu(a):
                  "roofline_moments": {"kernel": "k_moments (node moments, O(N M) fp64)", "bound": "alu",
                                       "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
                                       "algorithmic_flops": mom_flops,
-                                      "peak_source": "derived: 152 SMs x 4 fp64 flop/clk x max SM clock"}}
+                                      "peak_source": "measured in this run: fp64 FMA probe"}}
 
     # ---- batched form (workload 3: P problems, M log-uniform in [256, 8192], N = 2-4 M,
     # Chebyshev-clustered nodes, m = 6) against the plain single-problem form
@@ -647,7 +660,7 @@ def run_gpu(a):
         cols2 = np.diff(g.infft2d_copy_plan_data(q2, weights=False)["col_offset"].astype(np.int64))
         q2.close()
         fl2 = lsq_flops_2d(cols2)
-        peak64 = sm_count() * FP64_FLOP_PER_CLK_PER_SM * peaks()[1] * 1e6 / 1e12
+        peak64 = fp64_peak
         ach_pre2 = fl2 / (t_pre2 / 1e3) / 1e12
         M2d = w2.M1 * w2.M2
         ab2 = 8 * w2.N + 4 * info2["nnz"] + 8 * M2d          # f, weights, fhat
@@ -664,24 +677,11 @@ def run_gpu(a):
                  "roofline_precompute": {"kernel": "2-D B_opt precompute, all tiers (fp64 Cholesky of every column)",
                                          "bound": "alu", "achieved": ach_pre2, "peak": peak64, "unit": "TFLOP/s",
                                          "frac": ach_pre2 / peak64, "algorithmic_flops": fl2,
-                                         "peak_source": "derived: 152 SMs x 4 fp64 flop/clk x max SM clock"},
+                                         "peak_source": "measured in this run: fp64 FMA probe"},
                  "roofline_apply": {"kernel": "2-D spread + row and column FFT passes (one apply)", "bound": "hbm",
                                     "achieved": ach2, "peak": peaks()[0], "unit": "GB/s",
                                     "frac": ach2 / peaks()[0], "algorithmic_bytes": ab2,
                                     "index_bytes": idx2}}
-
-    # ---- fp64 FMA throughput of this GPU (the precompute's roofline denominator), measured
-    sink = torch.empty(g.infft_fp64_fma_probe_sink_len(), dtype=torch.float64, device=dev)
-    probe_iters = 4096
-    g.infft_fp64_fma_probe(probe_iters, sink, stream)
-    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-    for s0, s1 in pev:
-        s0.record(stream)
-        probe_flops = g.infft_fp64_fma_probe(probe_iters, sink, stream)
-        s1.record(stream)
-    torch.cuda.synchronize()
-    fp64_peak = probe_flops / (statistics.median(s0.elapsed_time(s1) for s0, s1 in pev) / 1e3) / 1e12
-    del sink
 
     # ---- rooflines: the modified adjoint NFFT (HBM) and the B_opt precompute (fp64 ALU)
     hbm, sm_max, src = peaks()

@@ -412,9 +412,11 @@ typedef struct {
     int32_t fallback_columns;     /* columns whose Cholesky needed a larger regulariser */
     int32_t unsupported_columns;  /* columns above 8192 nodes (b_l = 0) */
     int32_t large_columns;        /* columns solved by the blocked solver (above 128 nodes) */
-    int32_t wide_columns;         /* columns spread with fp64 weights (||b_l||_1 > 32) */
+    int32_t wide_columns;         /* columns spread in float-float (||b_l||_1 > 32) */
     int32_t nodes_set, precomputed;
     double objective;             /* sum_l J_l = ||F D A^* B_opt - I||_F^2 */
+    int32_t indexed_columns;      /* columns the fp32 spread reads through node indices (a node on
+                                     a grid line); the others as 2m cell-row runs of sorted nodes */
 } infft2d_info;
 
 /* Creates a 2-D plan (sizes as above; kernel FULL or SYM; tau >= 0 the regulariser
@@ -437,8 +439,10 @@ infft_status infft2d_precompute(infft2d_plan_t plan, infft_stream_t stream);
 
 /* fhat = D^* F^* B_opt^* f: spreading onto the grid, the 2-D FFT pruned to the
  * M1 x M2 central frequencies with D^* fused into its last pass.  fp32 arithmetic
- * and accumulation (columns with ||b_l||_1 > 32 spread in fp64).  f and fhat host
- * or device; with a host fhat the call returns after the result is copied. */
+ * and accumulation (columns with ||b_l||_1 > 32 spread in float-float on the fp32 pipe).
+ * The data is first copied into sorted node order, so the spread reads each column as
+ * 2m cell-row runs of consecutive nodes (no node index per entry).  f and fhat host or
+ * device; with a host fhat the call returns after the result is copied. */
 infft_status infft2d_apply(infft2d_plan_t plan, const float* f, float* fhat, infft_stream_t stream);
 /* The same in fp64 throughout (complex128 f and fhat). */
 infft_status infft2d_apply_z(infft2d_plan_t plan, const double* f, double* fhat, infft_stream_t stream);

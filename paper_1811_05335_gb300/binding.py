@@ -70,7 +70,7 @@ class _Info2D(ctypes.Structure):
                 ("bad_nodes", ctypes.c_int32), ("fallback_columns", ctypes.c_int32),
                 ("unsupported_columns", ctypes.c_int32), ("large_columns", ctypes.c_int32),
                 ("wide_columns", ctypes.c_int32), ("nodes_set", ctypes.c_int32), ("precomputed", ctypes.c_int32),
-                ("objective", ctypes.c_double)]
+                ("objective", ctypes.c_double), ("indexed_columns", ctypes.c_int32)]
 
 
 _lib = None

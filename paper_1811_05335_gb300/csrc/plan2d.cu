@@ -56,7 +56,8 @@ struct infft2d_plan_s {
     int32_t* hist = nullptr;       // LARGE_NMAX + 2: size buckets, then offsets / cursors; ticket
     int32_t* counters = nullptr;   // C2_N
     float* w32 = nullptr;          // nnz_cap
-    int2* ent = nullptr;           // nnz_cap: (caller node index, fp32 weight bits) for the fp32 spread
+    uint8_t* kind = nullptr;       // P: column kinds of the fp32 spread (K2_WIDE, K2_INDEXED)
+    float2* fsort = nullptr;       // N: the data in sorted node order (fp32 spread of run columns)
     float* wlo = nullptr;          // nnz_cap: fp32(b - fp32(b)), the low part of wide columns' weights
     double* w64 = nullptr;         // nnz_cap
     double* J = nullptr;           // P
@@ -85,7 +86,8 @@ enum {
     C2_LIST0 = 5,   // C2_LIST0 + t: length of the list of tier t (0..2 shared memory, 3 one CTA, 4 many CTAs)
     C2_BIG_CELLS = 10, C2_WIDE = 11,
     C2_SPREAD_BIG = 12,   // columns above SPREAD_BIG entries, spread by a whole CTA each
-    C2_N = 13
+    C2_INDEXED = 13,      // columns the fp32 spread reads through node indices
+    C2_N = 14
 };
 
 constexpr int TIER_NMAX[3] = {32, 64, 128};
@@ -98,7 +100,7 @@ constexpr int TBP = TB + 2;        // shared-memory row stride of the staged pan
 constexpr int LARGE_THREADS = 256;
 constexpr int CELL_SORT_MAX = 4096;
 constexpr int FFT2_THREADS = 256;
-constexpr int SPREAD_LPC = 16;    // lanes per column of the fp32 spread
+constexpr int SPREAD_LPC = 8;     // lanes per column of the fp32 spread (the width of a cell-row run at m = 4)
 constexpr int SPREAD_BIG = 512;   // longer columns are spread by one CTA each
 
 thread_local std::string g_err2;
@@ -913,15 +915,100 @@ __global__ void k2g_give_up(const GiantCol* __restrict__ gs, const int32_t* __re
 
 // ---- apply ---------------------------------------------------------------------
 
-// the entries of the fp32 spread: node index and fp32 weight in one 8-byte load, and the
-// low part of each weight for the columns that spread in float-float
-__global__ void k2_pack(const int32_t* __restrict__ col_node, const float* __restrict__ w32,
-                        const double* __restrict__ w64, int nnz, int2* __restrict__ ent, float* __restrict__ wlo) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
-        const float hi = w32[e];
-        ent[e] = make_int2(col_node[e], __float_as_int(hi));
-        wlo[e] = (float)(w64[e] - (double)hi);
+// The fp32 spread reads no node index per entry.  The entries of column (a1, a2) are
+// the nodes of I(l) in candidate order: the cells (a1 + d1, a2 - m .. a2 + m) for
+// d1 = -m .. m, sorted nodes inside each, filtered by the exact test of eq:set_xj.  That
+// test keeps every node of the cells with c_t in [a_t - m, a_t + m - 1] and, of the cells
+// with c_t = a_t + m, only nodes with an integer u_t = fl(M_sigma,t x_t).  A column with no
+// such node (nearly all: an integer u_t needs a node on a grid line) is therefore 2m
+// cell-row runs of consecutive sorted nodes, d1 = -m .. m - 1, each the cells a2 - m ..
+// a2 + m - 1 (two runs where they wrap), whose bounds the spread reads from cell_start
+// (L2-resident) and whose node values it reads from the sorted copy of f.  The others are
+// spread through their node indices.  Column kinds: bit 0 wide (||b_l||_1 > 32: float-float
+// on the fp32 pipe), bit 1 indexed.
+constexpr int K2_WIDE = 1, K2_INDEXED = 2;
+constexpr int K2_RUNS_MAX = 64;   // 2m rows, two runs each where they wrap: m <= 16
+
+// the cell ranges [c0[r], c1[r]] of the runs of a row (nr = 1, or 2 where a2 - m .. a2 + m - 1
+// wraps); returns nr
+INFFT_D int k2_row_ranges(int a2, int m, int Ms2, int (&c0)[2], int (&c1)[2]) {
+    const int lo = a2 - m, hi = a2 + m - 1;
+    if (lo < 0) { c0[0] = lo + Ms2; c1[0] = Ms2 - 1; c0[1] = 0; c1[1] = hi; return 2; }
+    if (hi >= Ms2) { c0[0] = lo; c1[0] = Ms2 - 1; c0[1] = 0; c1[1] = hi - Ms2; return 2; }
+    c0[0] = lo; c1[0] = hi;
+    return 1;
+}
+
+// sorted-node range [s, e) of run j (row d1 = -m + j / nr, range j % nr) of column (a1, .)
+INFFT_D void k2_run_bounds(const int32_t* __restrict__ cell_start, int Ms1, int Ms2, int a1, int m, int nr,
+                           const int (&c0)[2], const int (&c1)[2], int j, int& s, int& e) {
+    int r1 = a1 - m + j / nr;
+    if (r1 < 0) r1 += Ms1;
+    else if (r1 >= Ms1) r1 -= Ms1;
+    const int r = j % nr;
+    const int base = r1 * Ms2;
+    s = cell_start[base + c0[r]];
+    e = cell_start[base + c1[r] + 1];
+}
+
+// Low parts of the weights, fp32(b - fp32(b)), for the float-float spread of wide columns
+__global__ void k2_lowparts(const float* __restrict__ w32, const double* __restrict__ w64, int nnz,
+                            float* __restrict__ wlo) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
+        wlo[e] = (float)(w64[e] - (double)w32[e]);
+}
+
+// The kind of every column (after the weights are final): a run column when its 2m runs
+// hold exactly its |I(l)| entries
+__global__ void k2_kinds(const int32_t* __restrict__ cell_start, const int32_t* __restrict__ col_off,
+                         const uint8_t* __restrict__ wide, int Ms1, int Ms2, int m, int P,
+                         uint8_t* __restrict__ kind, int32_t* __restrict__ counters) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int a1 = p / Ms2, a2 = p - a1 * Ms2;
+        int c0[2], c1[2];
+        const int nr = k2_row_ranges(a2, m, Ms2, c0, c1);
+        int cnt = 0;
+        for (int j = 0; j < 2 * m * nr; ++j) {
+            int sj, ej;
+            k2_run_bounds(cell_start, Ms1, Ms2, a1, m, nr, c0, c1, j, sj, ej);
+            cnt += ej - sj;
+        }
+        const bool runs = m <= K2_RUNS_MAX / 4 && cnt == col_off[p + 1] - col_off[p];
+        kind[p] = (uint8_t)((wide[p] ? K2_WIDE : 0) | (runs ? 0 : K2_INDEXED));
+        if (!runs) atomicAdd(&counters[C2_INDEXED], 1);
     }
+}
+
+// f in the order of the sorted nodes: fs[i] = f[perm[i]]
+__global__ void k2_sort_values(const float2* __restrict__ f, const int32_t* __restrict__ perm, int N,
+                               float2* __restrict__ fs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) fs[i] = f[perm[i]];
+}
+
+// The run table of column (a1, a2) built by warp 0 of a CTA: rt[j] = (first sorted node,
+// first entry) of run j, rt[R] = (0, number of entries).  Returns R.
+INFFT_D int k2_build_runs(const int32_t* __restrict__ cell_start, int Ms1, int Ms2, int a1, int a2, int m, int lane,
+                          int2* rt) {
+    int c0[2], c1[2];
+    const int nr = k2_row_ranges(a2, m, Ms2, c0, c1);
+    const int R = 2 * m * nr;
+    int run = 0;
+    for (int j0 = 0; j0 < R; j0 += 32) {
+        const int j = j0 + lane;
+        int sj = 0, ej = 0;
+        if (j < R) k2_run_bounds(cell_start, Ms1, Ms2, a1, m, nr, c0, c1, j, sj, ej);
+        const int len = ej - sj;
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (j < R) rt[j] = make_int2(sj, run + inc - len);
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) rt[R] = make_int2(0, run);
+    return R;
 }
 
 // s + e = a + b exactly (Knuth's two-sum; the _rn intrinsics keep the compiler from
@@ -932,61 +1019,26 @@ INFFT_D void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// fp32 apply: g_p = sum_{e in column p} b_e f_{node(e)}, LPC lanes per column (the lanes of
-// a column walk its entries LPC apart, four loads in flight each).  Ordinary columns: fp32
-// weights and accumulation.  Wide columns (||b_l||_1 > 32, whose terms cancel): float-float --
-// b = hi + lo, each product split exactly by an FMA, sums carried as (s, c) pairs through
-// two-sum -- about 44 significant bits on the fp32 pipe, which runs 64 times as many lanes
-// per clock as the fp64 pipe.
-// one column by the whole CTA (256 threads): per-thread sums, warp shuffles, then the
-// eight warp partials in shared memory
-INFFT_D void spread_column_cta(int p, const float2* __restrict__ f, const int32_t* __restrict__ col_off,
-                               const int2* __restrict__ ent, const float* __restrict__ wlo,
-                               const uint8_t* __restrict__ wide, float2* __restrict__ g) {
-    __shared__ float red[4][8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int s = col_off[p], e = col_off[p + 1];
-    if (!wide[p]) {
-        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-        int q = s + tid;
-        for (; q + 3 * 256 < e; q += 4 * 256) {
-            int2 en[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) en[u] = ent[q + u * 256];
-            float2 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = f[en[u].x];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ar[u] = fmaf(__int_as_float(en[u].y), v[u].x, ar[u]);
-                ai[u] = fmaf(__int_as_float(en[u].y), v[u].y, ai[u]);
-            }
-        }
-        for (; q < e; q += 256) {
-            const int2 en = ent[q];
-            const float2 v = f[en.x];
-            ar[0] = fmaf(__int_as_float(en.y), v.x, ar[0]);
-            ai[0] = fmaf(__int_as_float(en.y), v.y, ai[0]);
-        }
-        float r = (ar[0] + ar[1]) + (ar[2] + ar[3]), i = (ai[0] + ai[1]) + (ai[2] + ai[3]);
-        for (int o = 16; o; o >>= 1) {
-            r += __shfl_xor_sync(0xffffffffu, r, o);
-            i += __shfl_xor_sync(0xffffffffu, i, o);
-        }
-        if (lane == 0) { red[0][warp] = r; red[1][warp] = i; }
-        __syncthreads();
-        if (tid == 0) {
-            float a = 0.f, b = 0.f;
-            for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; }
-            g[p] = make_float2(a, b);
-        }
-        return;
+// A thread's partial sum of a column: fp32 (four accumulator pairs, one per unrolled
+// entry) or float-float ((s, c) pairs through two-sum, each product split exactly by an
+// FMA: about 44 significant bits on the fp32 pipe, which runs 64 times as many lanes per
+// clock as the fp64 pipe).
+template <bool WIDE> struct K2Acc;
+
+template <> struct K2Acc<false> {
+    float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+    INFFT_D void add(int u, float w, float, float2 v) {
+        ar[u] = fmaf(w, v.x, ar[u]);
+        ai[u] = fmaf(w, v.y, ai[u]);
     }
+    INFFT_D float4 total() const {
+        return make_float4((ar[0] + ar[1]) + (ar[2] + ar[3]), 0.f, (ai[0] + ai[1]) + (ai[2] + ai[3]), 0.f);
+    }
+};
+
+template <> struct K2Acc<true> {
     float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    for (int q = s + tid; q < e; q += 256) {
-        const int2 en = ent[q];
-        const float wh = __int_as_float(en.y), wl = wlo[q];
-        const float2 v = f[en.x];
+    INFFT_D void add(int, float wh, float wl, float2 v) {
         const float tr = __fmul_rn(wh, v.x), ti = __fmul_rn(wh, v.y);
         const float lr = fmaf(wl, v.x, fmaf(wh, v.x, -tr)), li = fmaf(wl, v.y, fmaf(wh, v.y, -ti));
         float t, err;
@@ -997,108 +1049,182 @@ INFFT_D void spread_column_cta(int p, const float2* __restrict__ f, const int32_
         si = t;
         ci += err + li;
     }
-    for (int o = 16; o; o >>= 1) {
-        float t, err;
-        const float osr = __shfl_xor_sync(0xffffffffu, sr, o), ocr = __shfl_xor_sync(0xffffffffu, cr, o);
-        const float osi = __shfl_xor_sync(0xffffffffu, si, o), oci = __shfl_xor_sync(0xffffffffu, ci, o);
-        two_sum(sr, osr, t, err);
-        sr = t;
-        cr += ocr + err;
-        two_sum(si, osi, t, err);
-        si = t;
-        ci += oci + err;
-    }
-    if (lane == 0) { red[0][warp] = sr; red[1][warp] = cr; red[2][warp] = si; red[3][warp] = ci; }
-    __syncthreads();
-    if (tid == 0) {
-        float a = red[0][0], ac = red[1][0], b = red[2][0], bc = red[3][0];
-        for (int w = 1; w < 8; ++w) {
-            float t, err;
-            two_sum(a, red[0][w], t, err);
-            a = t;
-            ac += red[1][w] + err;
-            two_sum(b, red[2][w], t, err);
-            b = t;
-            bc += red[3][w] + err;
-        }
-        g[p] = make_float2(a + ac, b + bc);
-    }
+    INFFT_D float4 total() const { return make_float4(sr, cr, si, ci); }
+};
+
+// (s, c) pairs of two float-float sums combined (plain sums: c = 0 stays 0)
+template <bool WIDE> INFFT_D float4 k2_combine(float4 a, float4 b) {
+    if (!WIDE) return make_float4(a.x + b.x, 0.f, a.z + b.z, 0.f);
+    float t, err;
+    two_sum(a.x, b.x, t, err);
+    a.x = t;
+    a.y += b.y + err;
+    two_sum(a.z, b.z, t, err);
+    a.z = t;
+    a.w += b.w + err;
+    return a;
 }
 
+template <bool WIDE> INFFT_D float4 k2_reduce(unsigned mask, float4 v, int width) {
+    for (int o = width / 2; o; o >>= 1) {
+        const float4 u = make_float4(__shfl_xor_sync(mask, v.x, o), WIDE ? __shfl_xor_sync(mask, v.y, o) : 0.f,
+                                     __shfl_xor_sync(mask, v.z, o), WIDE ? __shfl_xor_sync(mask, v.w, o) : 0.f);
+        v = k2_combine<WIDE>(v, u);
+    }
+    return v;
+}
+
+// entries o0, o0 + step, .. < len of one run (weights w, low parts wl, node values v), four
+// loads in flight
+template <bool WIDE>
+INFFT_D void k2_sum_run(K2Acc<WIDE>& acc, const float* __restrict__ w, const float* __restrict__ wl,
+                        const float2* __restrict__ v, int o0, int step, int len) {
+    int o = o0;
+    for (; o + 3 * step < len; o += 4 * step) {
+        float wq[4], lq[4];
+        float2 vq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            wq[u] = w[o + u * step];
+            lq[u] = WIDE ? wl[o + u * step] : 0.f;
+            vq[u] = v[o + u * step];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc.add(u, wq[u], lq[u], vq[u]);
+    }
+    for (; o < len; o += step) acc.add(0, w[o], WIDE ? wl[o] : 0.f, v[o]);
+}
+
+// entries q = q0, q0 + step, .. < n of an indexed column (node values through node[q])
+template <bool WIDE>
+INFFT_D void k2_sum_indexed(K2Acc<WIDE>& acc, const float* __restrict__ w, const float* __restrict__ wl,
+                            const float2* __restrict__ f, const int32_t* __restrict__ node, int q0, int step, int n) {
+    int q = q0;
+    for (; q + 3 * step < n; q += 4 * step) {
+        int nq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) nq[u] = node[q + u * step];
+        float wq[4], lq[4];
+        float2 vq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            wq[u] = w[q + u * step];
+            lq[u] = WIDE ? wl[q + u * step] : 0.f;
+            vq[u] = f[nq[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc.add(u, wq[u], lq[u], vq[u]);
+    }
+    for (; q < n; q += step) acc.add(0, w[q], WIDE ? wl[q] : 0.f, f[node[q]]);
+}
+
+// One column by a group of LPC lanes (sub = lane in the group).  Run columns: lane sub takes
+// runs sub, sub + LPC, .. whole (their first entries from a scan of the run lengths over the
+// group), so a lane's loads walk consecutive weights and consecutive sorted node values;
+// indexed columns: the lanes walk the entries LPC apart.  Returns the group's total on every lane.
+template <int LPC, bool WIDE>
+INFFT_D float4 k2_column_group(int p, int sub, unsigned mask, int s, int n, bool runs, const float2* __restrict__ f,
+                               const float2* __restrict__ fs, const int32_t* __restrict__ cell_start,
+                               const int32_t* __restrict__ col_node, const float* __restrict__ w32,
+                               const float* __restrict__ wlo, int Ms1, int Ms2, int m) {
+    K2Acc<WIDE> acc;
+    const float* w = w32 + s;
+    const float* wl = wlo + s;
+    if (runs) {
+        const int a1 = p / Ms2, a2 = p - a1 * Ms2;
+        int c0[2], c1[2];
+        const int nr = k2_row_ranges(a2, m, Ms2, c0, c1);
+        const int R = 2 * m * nr;
+        int base = 0;
+        for (int j0 = 0; j0 < R; j0 += LPC) {
+            const int j = j0 + sub;
+            int sj = 0, ej = 0;
+            if (j < R) k2_run_bounds(cell_start, Ms1, Ms2, a1, m, nr, c0, c1, j, sj, ej);
+            const int len = ej - sj;
+            int inc = len;
+#pragma unroll
+            for (int o = 1; o < LPC; o <<= 1) {
+                const int v = __shfl_up_sync(mask, inc, o, LPC);
+                if (sub >= o) inc += v;
+            }
+            const int eo = base + inc - len;
+            base += __shfl_sync(mask, inc, LPC - 1, LPC);
+            k2_sum_run<WIDE>(acc, w + eo, wl + eo, fs + sj, 0, 1, len);
+        }
+    } else {
+        k2_sum_indexed<WIDE>(acc, w, wl, f, col_node + s, sub, LPC, n);
+    }
+    return k2_reduce<WIDE>(mask, acc.total(), LPC);
+}
+
+// One column by a CTA of 256 threads (columns above SPREAD_BIG entries): run columns take the
+// runs one after another, all threads over each run's entries.
+template <bool WIDE>
+INFFT_D float4 k2_column_cta(int p, int s, int n, bool runs, const float2* __restrict__ f,
+                             const float2* __restrict__ fs, const int32_t* __restrict__ cell_start,
+                             const int32_t* __restrict__ col_node, const float* __restrict__ w32,
+                             const float* __restrict__ wlo, int Ms1, int Ms2, int m, int2* rt, float4* red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    K2Acc<WIDE> acc;
+    const float* w = w32 + s;
+    const float* wl = wlo + s;
+    if (runs) {
+        const int a1 = p / Ms2, a2 = p - a1 * Ms2;
+        if (warp == 0) k2_build_runs(cell_start, Ms1, Ms2, a1, a2, m, lane, rt);
+        int c0[2], c1[2];
+        const int R = 2 * m * k2_row_ranges(a2, m, Ms2, c0, c1);
+        __syncthreads();
+        for (int j = 0; j < R; ++j) {
+            const int2 r = rt[j];
+            k2_sum_run<WIDE>(acc, w + r.y, wl + r.y, fs + r.x, tid, 256, rt[j + 1].y - r.y);
+        }
+    } else {
+        k2_sum_indexed<WIDE>(acc, w, wl, f, col_node + s, tid, 256, n);
+    }
+    const float4 v = k2_reduce<WIDE>(0xffffffffu, acc.total(), 32);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float4 t = red[0];
+    for (int i = 1; i < 8; ++i) t = k2_combine<WIDE>(t, red[i]);
+    return t;
+}
+
+// fp32 apply: g_p = sum_{e in column p} b_e f_{node(e)}, LPC lanes per column; columns above
+// SPREAD_BIG entries (the first nbig CTAs, listed in big) take a whole CTA.  Ordinary columns:
+// fp32 weights and accumulation; wide columns: float-float.
 template <int LPC>
-__global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f, const int32_t* __restrict__ col_off,
-                                                   const int2* __restrict__ ent, const float* __restrict__ wlo,
-                                                   const uint8_t* __restrict__ wide, int P, float2* __restrict__ g,
+__global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f, const float2* __restrict__ fs,
+                                                   const int32_t* __restrict__ col_off,
+                                                   const int32_t* __restrict__ cell_start,
+                                                   const int32_t* __restrict__ col_node, const float* __restrict__ w32,
+                                                   const float* __restrict__ wlo, const uint8_t* __restrict__ kind,
+                                                   int Ms1, int Ms2, int m, int P, float2* __restrict__ g,
                                                    const int32_t* __restrict__ big, int nbig) {
-    if ((int)blockIdx.x < nbig) {                          // the columns above SPREAD_BIG entries
-        spread_column_cta(big[blockIdx.x], f, col_off, ent, wlo, wide, g);
+    __shared__ int2 rt[K2_RUNS_MAX + 1];
+    __shared__ float4 red[8];
+    if ((int)blockIdx.x < nbig) {                          // a column above SPREAD_BIG entries
+        const int p = big[blockIdx.x];
+        const int s = col_off[p], n = col_off[p + 1] - s;
+        const int k = kind[p];
+        const bool runs = !(k & K2_INDEXED);
+        const float4 t = (k & K2_WIDE)
+            ? k2_column_cta<true>(p, s, n, runs, f, fs, cell_start, col_node, w32, wlo, Ms1, Ms2, m, rt, red)
+            : k2_column_cta<false>(p, s, n, runs, f, fs, cell_start, col_node, w32, wlo, Ms1, Ms2, m, rt, red);
+        if (threadIdx.x == 0) g[p] = make_float2(t.x + t.y, t.z + t.w);
         return;
     }
     const int sub = threadIdx.x & (LPC - 1);
     const int p = (blockIdx.x - nbig) * (256 / LPC) + threadIdx.x / LPC;
     const unsigned mask = LPC == 32 ? 0xffffffffu : ((1u << LPC) - 1) << ((threadIdx.x & 31) & ~(LPC - 1));
     if (p >= P) return;                                    // uniform over the column's lanes
-    const int s = col_off[p], e = col_off[p + 1];
-    if (e - s > SPREAD_BIG) return;                        // spread by its own CTA
-    if (!wide[p]) {
-        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-        int q = s + sub;
-        for (; q + 3 * LPC < e; q += 4 * LPC) {
-            int2 en[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) en[u] = ent[q + u * LPC];
-            float2 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = f[en[u].x];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ar[u] = fmaf(__int_as_float(en[u].y), v[u].x, ar[u]);
-                ai[u] = fmaf(__int_as_float(en[u].y), v[u].y, ai[u]);
-            }
-        }
-        for (; q < e; q += LPC) {
-            const int2 en = ent[q];
-            const float2 v = f[en.x];
-            ar[0] = fmaf(__int_as_float(en.y), v.x, ar[0]);
-            ai[0] = fmaf(__int_as_float(en.y), v.y, ai[0]);
-        }
-        float r = (ar[0] + ar[1]) + (ar[2] + ar[3]), i = (ai[0] + ai[1]) + (ai[2] + ai[3]);
-#pragma unroll
-        for (int o = LPC / 2; o; o >>= 1) {
-            r += __shfl_xor_sync(mask, r, o);
-            i += __shfl_xor_sync(mask, i, o);
-        }
-        if (sub == 0) g[p] = make_float2(r, i);
-        return;
-    }
-    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    for (int q = s + sub; q < e; q += LPC) {
-        const int2 en = ent[q];
-        const float wh = __int_as_float(en.y), wl = wlo[q];
-        const float2 v = f[en.x];
-        const float tr = __fmul_rn(wh, v.x), ti = __fmul_rn(wh, v.y);
-        const float lr = fmaf(wl, v.x, fmaf(wh, v.x, -tr)), li = fmaf(wl, v.y, fmaf(wh, v.y, -ti));
-        float t, err;
-        two_sum(sr, tr, t, err);
-        sr = t;
-        cr += err + lr;
-        two_sum(si, ti, t, err);
-        si = t;
-        ci += err + li;
-    }
-#pragma unroll
-    for (int o = LPC / 2; o; o >>= 1) {
-        float t, err;
-        const float osr = __shfl_xor_sync(mask, sr, o), ocr = __shfl_xor_sync(mask, cr, o);
-        const float osi = __shfl_xor_sync(mask, si, o), oci = __shfl_xor_sync(mask, ci, o);
-        two_sum(sr, osr, t, err);
-        sr = t;
-        cr += ocr + err;
-        two_sum(si, osi, t, err);
-        si = t;
-        ci += oci + err;
-    }
-    if (sub == 0) g[p] = make_float2(sr + cr, si + ci);
+    const int s = col_off[p], n = col_off[p + 1] - s;
+    if (n > SPREAD_BIG) return;                            // spread by its own CTA
+    const int k = kind[p];
+    const bool runs = !(k & K2_INDEXED);
+    const float4 t = (k & K2_WIDE)
+        ? k2_column_group<LPC, true>(p, sub, mask, s, n, runs, f, fs, cell_start, col_node, w32, wlo, Ms1, Ms2, m)
+        : k2_column_group<LPC, false>(p, sub, mask, s, n, runs, f, fs, cell_start, col_node, w32, wlo, Ms1, Ms2, m);
+    if (sub == 0) g[p] = make_float2(t.x + t.y, t.z + t.w);
 }
 
 // fp64 apply: fp64 weights, inputs and accumulation, one warp per column
@@ -1210,7 +1336,8 @@ void layout2(infft2d_plan_s* p, Carver2& c) {
     c.take(p->col_off, P + 1); c.take(p->col_node, p->nnz_cap);
     c.take(p->lists, 5 * P); c.take(p->order, P); c.take(p->spread_big, P); c.take(p->hist, LARGE_NMAX + 2);
     c.take(p->counters, C2_N);
-    c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->ent, p->nnz_cap); c.take(p->wlo, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
+    c.take(p->w32, p->nnz_cap); c.take(p->w64, p->nnz_cap); c.take(p->wlo, p->nnz_cap); c.take(p->J, P); c.take(p->wide, P);
+    c.take(p->kind, P); c.take(p->fsort, N);
     double2 *grid, *work, *si, *so;
     c.take(grid, P); c.take(work, (size_t)p->M2 * p->Ms1);
     const size_t stage = std::max(N, M);
@@ -1368,6 +1495,7 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     if ((e = cudaMemsetAsync(p->counters + C2_FALLBACK, 0, 2 * sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p->counters + C2_LIST0, 0, 5 * sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p->counters + C2_WIDE, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->counters + C2_INDEXED, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p->hist, 0, (LARGE_NMAX + 2) * sizeof(int32_t), s)) != cudaSuccess) return e;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) return e;
@@ -1431,10 +1559,14 @@ cudaError_t run_precompute2(infft2d_plan_s* p, cudaStream_t s) {
     }
     if (G > 0 && (e = run_giants(p, G, kp, mu, sms, s)) != cudaSuccess) return e;
     if (p->nnz > 0) {
-        k2_pack<<<(int)std::min<int64_t>((p->nnz + 255) / 256, 16 * sms), 256, 0, s>>>(
-            p->col_node, p->w32, p->w64, (int)p->nnz, p->ent, p->wlo);
+        k2_lowparts<<<(int)std::min<int64_t>((p->nnz + 255) / 256, 16 * sms), 256, 0, s>>>(p->w32, p->w64,
+                                                                                       (int)p->nnz, p->wlo);
         count_launches(1);
     }
+    k2_kinds<<<(int)std::min<int64_t>((P + 255) / 256, 16 * sms), 256, 0, s>>>(p->cell_start, p->col_off, p->wide,
+                                                                              Ms1, Ms2, p->m, P, p->kind,
+                                                                              p->counters);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -1443,12 +1575,17 @@ template <typename T> cudaError_t run_apply2(infft2d_plan_s* p, const void* f, v
     const int P = (int)p->P;
     Cx* g = (Cx*)p->grid;
     Cx* Y = (Cx*)p->work;
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4) {
+        const int N = (int)p->N;
+        k2_sort_values<<<(N + 255) / 256, 256, 0, s>>>((const float2*)f, p->perm, N, p->fsort);
         k2_spread32<SPREAD_LPC><<<p->spread_big_count + (P + 256 / SPREAD_LPC - 1) / (256 / SPREAD_LPC), 256, 0, s>>>(
-            (const float2*)f, p->col_off, p->ent, p->wlo, p->wide, P, g, p->spread_big, p->spread_big_count);
-    else
+            (const float2*)f, p->fsort, p->col_off, p->cell_start, p->col_node, p->w32, p->wlo, p->kind,
+            (int)p->Ms1, (int)p->Ms2, p->m, P, g, p->spread_big, p->spread_big_count);
+        count_launches(2);
+    } else {
         k2_spread64<<<(P + 7) / 8, 256, 0, s>>>((const double2*)f, p->col_off, p->col_node, p->w64, P, g);
-    count_launches(1);
+        count_launches(1);
+    }
     if constexpr (sizeof(T) == 4) {
         if (fft2d_r8_supported(p->log1, p->log2, (int)p->M2))
             return fft2d_adjoint_r8((const float2*)g, (float2*)Y, (float2*)fhat, p->log1, p->log2, (int)p->M1,
@@ -1637,6 +1774,7 @@ infft_status infft2d_get_info(infft2d_plan_t p, infft2d_info* info) {
         info->unsupported_columns = cnt[C2_UNSUPPORTED];
         info->large_columns = cnt[C2_LIST0 + 3] + cnt[C2_LIST0 + 4];
         info->wide_columns = cnt[C2_WIDE];
+        info->indexed_columns = cnt[C2_INDEXED];
         std::string buf(p->P * sizeof(double), '\0');
         if ((e = cudaMemcpy(&buf[0], p->J, p->P * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail2(e, "read objective");

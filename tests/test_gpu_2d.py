@@ -156,6 +156,19 @@ def test_apply_fp32(name):
     plan.close()
 
 
+def test_spread_kinds_run_and_indexed():
+    """The fp32 spread reads a column as 2m cell-row runs of sorted nodes unless a node of its
+    box lies on a grid line (integer M_sigma,t x_t), which only the exact test of eq:set_xj
+    decides: such columns go through node indices.  Both kinds meet in the "edge" case; the
+    perturbed radial trajectory has none on a grid line."""
+    for name, want_indexed in (("edge", True), ("radial_m4", False)):
+        x, M1, M2, sigma, m, kernel, B, f = solved(name)
+        plan, fhat, _, info = run_gpu2(x, np.asarray(f, np.complex64), M1, M2, sigma, m, kernel)
+        assert (info["indexed_columns"] > 0) == want_indexed, (name, info["indexed_columns"])
+        assert info["indexed_columns"] < B.Ms1 * B.Ms2
+        plan.close()
+
+
 def oracle_ambiguity(name):
     """How far the oracle's own fhat moves when its columns are solved by a second
     backward-stable method (Cholesky instead of LU) on the same closed-form systems:
