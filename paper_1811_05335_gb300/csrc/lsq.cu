@@ -1109,11 +1109,19 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                     int bi, bj;
                     tri_index(bk, bi, bj);
                     const int i0 = w + 4 * bi, j0 = w + 4 * bj;   // panel row indices
-                    double acc[4][4];
+                    // the block's entries are requested first, so that their latency passes
+                    // under the 256 multiply-adds
+                    double old[4][4], acc[4][4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = kb + i0 + a;
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+                        for (int b = 0; b < 4; ++b) {
+                            const int j = kb + j0 + b;
+                            old[a][b] = (i < n && j <= i) ? A[trow(i) + j] : 0.0;
+                            acc[a][b] = 0.0;
+                        }
+                    }
 #pragma unroll 4
                     for (int c = 0; c < HUGE_PB; ++c) {
                         double li[4], lj[4];
@@ -1134,7 +1142,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const int j = kb + j0 + b;
-                            if (j <= i) A[trow(i) + j] -= acc[a][b];
+                            if (j <= i) A[trow(i) + j] = old[a][b] - acc[a][b];
                         }
                     }
                 }
