@@ -194,7 +194,7 @@ void plan_layout(Plan* p, Carver& c, bool member) {
     c.take(p->bucket, 2 * Ms + 1); c.take(p->cursor, 2 * Ms); c.take(p->seg_list, N / 32 + 2);
     c.take(p->col_start, Ms); c.take(p->col_count, Ms); c.take(p->col_off, Ms + 1);
     c.take(p->big_list, Ms); c.take(p->list_a, Ms); c.take(p->tiles_mid, Ms / 32 + 2);
-    c.take(p->tiles_big, Ms / 32 + 2);
+    c.take(p->tiles_big, Ms / 32 + 2); c.take(p->tiles_48, Ms / 32 + 2); c.take(p->tiles_64, Ms / 32 + 2);
     c.take(p->scan_sums, (2 * Ms + 1 + 4095) / 4096 + 2);
     c.take(p->phase, N);
     c.take(p->counters, CNT_N);

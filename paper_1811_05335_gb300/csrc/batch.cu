@@ -638,7 +638,7 @@ struct infft_batch_s {
     void* tier_args = nullptr;         // P solver-tier descriptors (one launch per tier)
     int32_t* pat_order = nullptr;      // problems by decreasing N (the pattern's CTAs take them in order)
     int32_t* tier_tile_off = nullptr;  // P + 1: prefix of the problems' 32-column tiles
-    int32_t* tier_work = nullptr;      // 3 (P + 1): prefixes of the routed lists
+    int32_t* tier_work = nullptr;      // 5 (P + 1): prefixes of the routed lists
     int64_t total_tiles32 = 0;
     const int32_t** d_counters = nullptr;
     const int32_t** d_col_off = nullptr;
@@ -794,7 +794,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     alloc(&b->tier_args, P * tier_args_bytes());
     alloc(&b->pat_order, P * sizeof(int32_t));
     alloc(&b->tier_tile_off, (P + 1) * sizeof(int32_t));
-    alloc(&b->tier_work, 3 * (P + 1) * sizeof(int32_t));
+    alloc(&b->tier_work, 5 * (P + 1) * sizeof(int32_t));
     alloc(&b->d_counters, P * sizeof(void*));
     alloc(&b->d_col_off, P * sizeof(void*));
     alloc(&b->d_J, P * sizeof(void*));

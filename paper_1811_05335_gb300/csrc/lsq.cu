@@ -72,6 +72,7 @@ k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, co
              KernelParams kp_, double mu0_, double* __restrict__ w64_, float* __restrict__ w32_,
              double* __restrict__ Jout_, uint8_t* __restrict__ wide_, const int32_t* __restrict__ tiles_in,
              int tiles_counter, int32_t* __restrict__ route_mid_, int32_t* __restrict__ route_big_,
+             int32_t* __restrict__ route_48_, int32_t* __restrict__ route_64_,
              int32_t* __restrict__ col_list_, int32_t* __restrict__ counters_, TierBatch tb) {
     extern __shared__ double lsq_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -107,6 +108,8 @@ k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, co
     uint8_t* __restrict__ wide = BATCH ? pa->wide : wide_;
     int32_t* __restrict__ route_mid = BATCH ? pa->tiles_mid : route_mid_;
     int32_t* __restrict__ route_big = BATCH ? pa->tiles_big : route_big_;
+    int32_t* __restrict__ route_48 = BATCH ? pa->tiles_48 : route_48_;
+    int32_t* __restrict__ route_64 = BATCH ? pa->tiles_64 : route_64_;
     int32_t* __restrict__ col_list = BATCH ? pa->list_a : col_list_;
     int32_t* __restrict__ counters = BATCH ? pa->counters : counters_;
     const int tile = BATCH ? it - tb.off[pb] : tiles_in ? tiles_in[it] : it;
@@ -120,6 +123,10 @@ k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, co
             if (lane == 0) route_mid[atomicAdd(&counters[CNT_TILES_MID], 1)] = tile;
         } else if (D <= LSQ_THREAD_NMAX3) {
             if (lane == 0) route_big[atomicAdd(&counters[CNT_TILES_BIG], 1)] = tile;
+        } else if (D <= LSQ_GROUP_NMAX4) {
+            if (lane == 0) route_48[atomicAdd(&counters[CNT_TILES_48], 1)] = tile;
+        } else if (D <= LSQ_WARP2_NMAX) {
+            if (lane == 0) route_64[atomicAdd(&counters[CNT_TILES_64], 1)] = tile;
         } else if (n > 0) {
             col_list[atomicAdd(&counters[CNT_LIST_A], 1)] = p;
         } else if (live) {                 // empty columns of a tile sent to the warp tier end here
@@ -273,13 +280,15 @@ k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, co
 // sit in the high slots, which drop out of the loop as j passes them, so few issued
 // multiply-adds fall on finished rows, and which lane and slot hold a row is known
 // at compile time.
-constexpr int GS = 33;   // element stride of the interleaved triangles (32 columns + 1 pad)
+// A CTA may also take its 32-column tile as 32 / TC sub-tiles of TC columns (TC = 16 and 8 for
+// the 48- and 64-node tiers, whose triangles of 32 columns would not fit shared memory); the
+// triangles of a sub-tile are interleaved with element stride TC + 1.
 
 template <int NMAX> constexpr int aug_doubles() { return (NMAX + 1) * (NMAX + 2) / 2; }
 // the triangles' region rounded up to 16 bytes, so that the double2 phases after it are aligned
-template <int NMAX> constexpr int group_tri_doubles() { return (aug_doubles<NMAX>() * GS + 1) & ~1; }
-template <int NMAX> constexpr size_t group_smem_bytes() {
-    return (size_t)group_tri_doubles<NMAX>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
+template <int NMAX, int TC = 32> constexpr int group_tri_doubles() { return (aug_doubles<NMAX>() * (TC + 1) + 1) & ~1; }
+template <int NMAX, int TC = 32> constexpr size_t group_smem_bytes() {
+    return (size_t)group_tri_doubles<NMAX, TC>() * sizeof(double) + (size_t)TILE_UMAX * 3 * sizeof(double) +
            (size_t)(64 + 2 * TILE_UMAX + 8) * sizeof(int);
 }
 
@@ -309,7 +318,7 @@ INFFT_D double rsqrt_pivot(double d, bool& ok) {
 // of one column, G lanes per column.  rowo[t]: element offset of row NMAX - g - G t
 // (row 0 where that is negative).  Rows of L overwrite the matrix, reciprocal pivots
 // the diagonal.  Returns false on a failed pivot (the same on all lanes of a group).
-template <int NMAX, int G, int R>
+template <int NMAX, int G, int R, int GS>
 INFFT_D bool group_factor(double* Tc, int g, int gbase, int Dw, const int (&rowo)[R]) {
     bool ok = true;
 #pragma unroll
@@ -347,7 +356,7 @@ INFFT_D bool group_factor(double* Tc, int g, int gbase, int Dw, const int (&rowo
 
 // Backward solve L^T b = y by columns of L^T: bacc[t] holds y of row NMAX - g - G t
 // on entry and b on exit; colo[t] = max(NMAX - g - G t, 0) * GS.
-template <int NMAX, int G, int R>
+template <int NMAX, int G, int R, int GS>
 INFFT_D void group_backsolve(const double* Tc, int g, int gbase, int Dw, const int (&colo)[R], double (&bacc)[R]) {
 #pragma unroll
     for (int i = NMAX - 1; i >= 0; --i) {
@@ -370,7 +379,7 @@ INFFT_D void group_backsolve(const double* Tc, int g, int gbase, int Dw, const i
 // A column's augmented system evaluated directly from the sorted nodes (tiles whose
 // union does not fit, and retries with a larger mu), rows and r entries split over
 // the G lanes: Re G_l + mu I for rows < n, identity rows for n <= i < Dw, r in row NMAX.
-template <int NMAX, int G>
+template <int NMAX, int G, int GS>
 INFFT_D void group_fill_direct(double* Tc, int g, int n, int Dw, int s, const double* __restrict__ xs,
                                const double2* __restrict__ ph, int N, double tl, double2 pl, double mu,
                                const KernelParams& kp) {
@@ -402,8 +411,8 @@ INFFT_D void group_fill_direct(double* Tc, int g, int n, int Dw, int s, const do
     }
 }
 
-template <int NMAX, int G, bool BATCH = false>
-__global__ void __launch_bounds__(G * 32, 1)
+template <int NMAX, int G, bool BATCH = false, int TC = 32>
+__global__ void __launch_bounds__(TC * G, 1)
 k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, const int32_t* __restrict__ col_start_,
             const int32_t* __restrict__ col_count_, const int32_t* __restrict__ col_off_, int N_, int Ms_,
             KernelParams kp_, double mu0_, double* __restrict__ w64_, float* __restrict__ w32_,
@@ -411,12 +420,13 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
             int tiles_counter, int32_t* __restrict__ counters_, TierBatch tb) {
     constexpr int C = 32 / G;          // columns per warp
     constexpr int R = (NMAX + G) / G;  // row slots per lane: rows 0 .. NMAX, from the bottom
-    constexpr int NT = 32 * G;         // threads per CTA
-    static_assert(32 % G == 0, "G divides the warp");
-    static_assert(group_tri_doubles<NMAX>() % 2 == 0 && TILE_UMAX % 2 == 0, "double2 phases 16-byte aligned");
+    constexpr int NT = TC * G;         // threads per CTA
+    constexpr int GS = TC + 1;         // element stride of the interleaved triangles
+    static_assert(32 % G == 0 && 32 % TC == 0 && NT % 32 == 0, "G and TC divide the warp; whole warps");
+    static_assert(group_tri_doubles<NMAX, TC>() % 2 == 0 && TILE_UMAX % 2 == 0, "double2 phases 16-byte aligned");
     extern __shared__ double lsq_smem[];
     double* T = lsq_smem;                                       // element e of column c at T[e * GS + c]
-    double* ux = T + group_tri_doubles<NMAX>();                 // union x      [TILE_UMAX]
+    double* ux = T + group_tri_doubles<NMAX, TC>();             // union x      [TILE_UMAX]
     double2* up = (double2*)(ux + TILE_UMAX);                   // union phases [TILE_UMAX]
     int* crs = (int*)(up + TILE_UMAX);                          // tile-relative start per column [32]
     int* cnn = crs + 32;                                        // size per column [32]
@@ -456,11 +466,17 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
         uint8_t* __restrict__ wide = BATCH ? pa->wide : wide_;
         int32_t* __restrict__ counters = BATCH ? pa->counters : counters_;
         const int32_t* __restrict__ tiles =
-            BATCH ? (tiles_counter == CNT_TILES_MID ? pa->tiles_mid : pa->tiles_big) : tiles_;
+            BATCH ? (tiles_counter == CNT_TILES_MID ? pa->tiles_mid
+                     : tiles_counter == CNT_TILES_BIG ? pa->tiles_big
+                     : tiles_counter == CNT_TILES_48 ? pa->tiles_48 : pa->tiles_64) : tiles_;
         const int tile = tiles[BATCH ? it - tb.off[pb] : it];
+        for (int sub = 0; sub < 32 / TC; ++sub) {
+        const int cb = tile * 32 + sub * TC;   // the sub-tile's first column
+        if (cb >= Ms) break;                   // uniform over the CTA
+        __syncthreads();                       // the previous sub-tile is done with shared memory
         if (wid == 0) {
-            const int p = tile * 32 + lane;
-            const bool live = p < Ms;
+            const int p = cb + lane;
+            const bool live = lane < TC && p < Ms;
             const int n = live ? col_count[p] : 0;
             const int s = live ? col_start[p] : 0;
             const int S = __shfl_sync(0xffffffffu, s, 0);
@@ -490,7 +506,7 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
             if (threadIdx.x == 0) atomicAdd(&counters[CNT_UNSUPPORTED], 1);
             continue;
         }
-        const int p = tile * 32 + c;
+        const int p = cb + c;
         const bool live = p < Ms;
         const int n = cnn[c], rs = crs[c];
         const double tl = col_t(p, Ms);
@@ -505,9 +521,9 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
             }
             __syncthreads();
             for (int q = threadIdx.x; q < U; q += NT) {
-                int cf = 32, cl = -1;
-                for (int cc = 0; cc < 32; ++cc) {
-                    if (cnn[cc] > 0 && crs[cc] + cnn[cc] > q && cf == 32) cf = cc;
+                int cf = TC, cl = -1;
+                for (int cc = 0; cc < TC; ++cc) {
+                    if (cnn[cc] > 0 && crs[cc] + cnn[cc] > q && cf == TC) cf = cc;
                     if (cnn[cc] > 0 && crs[cc] <= q) cl = cc;
                 }
                 cfst[q] = cf;
@@ -517,7 +533,7 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
                 // the near path needs the union and the columns' grid points to lie
                 // within 1/64 of each other without crossing the seam
                 const double x0 = ux[0], x1 = ux[U - 1];
-                const double tq = col_t(tile * 32 + lane, Ms);
+                const double tq = col_t(cb + lane, Ms);
                 const bool mine = cnn[lane] > 0;
                 const bool nr = !kp.sym && x1 >= x0 && x1 - x0 <= 1.0 / 64.0 &&
                                 __all_sync(0xffffffffu, !mine || (tq >= x0 - 1.0 / 64.0 && tq <= x1 + 1.0 / 64.0));
@@ -578,7 +594,7 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
                 Tc[(trow(NMAX) + k) * GS] = r;
             }
         } else {
-            group_fill_direct<NMAX, G>(Tc, g, n, Dw, s, xs, ph, N, tl, pl, mu, kp);
+            group_fill_direct<NMAX, G, GS>(Tc, g, n, Dw, s, xs, ph, N, tl, pl, mu, kp);
         }
         bool need = n > 0;
         const int off = live ? col_off[p] : 0;
@@ -587,11 +603,11 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
                 if (!__any_sync(0xffffffffu, need)) break;
                 if (need) {
                     mu *= 1e3;
-                    group_fill_direct<NMAX, G>(Tc, g, n, Dw, s, xs, ph, N, tl, pl, mu, kp);
+                    group_fill_direct<NMAX, G, GS>(Tc, g, n, Dw, s, xs, ph, N, tl, pl, mu, kp);
                 }
             }
             __syncwarp();
-            const bool ok = group_factor<NMAX, G, R>(Tc, g, gbase, Dw, rowo);
+            const bool ok = group_factor<NMAX, G, R, GS>(Tc, g, gbase, Dw, rowo);
             double bacc[R], ysq = 0.0;
 #pragma unroll
             for (int t = 0; t < R; ++t) {
@@ -599,7 +615,7 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
                 const int k = NMAX - g - G * t;
                 if (k >= 0 && k < n) ysq = fma(bacc[t], bacc[t], ysq);
             }
-            group_backsolve<NMAX, G, R>(Tc, g, gbase, Dw, colo, bacc);
+            group_backsolve<NMAX, G, R, GS>(Tc, g, gbase, Dw, colo, bacc);
             const bool write = need && ok;
             double bsq = 0.0, babs = 0.0;
 #pragma unroll
@@ -633,6 +649,7 @@ k_lsq_group(const double* __restrict__ xs_, const double2* __restrict__ ph_, con
                 atomicAdd(&counters[CNT_FALLBACK], 1);
             }
         }
+        }   // sub-tiles
     }
 }
 
@@ -1218,6 +1235,7 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_LIST_A, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_BIG_LIST, 0, 3 * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_HUGE_LIST, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->counters + CNT_TILES_48, 0, 2 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int sms = p->sms;
 
@@ -1229,13 +1247,19 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     auto t1 = k_lsq_thread<A1, W1>;
     auto t2 = k_lsq_group<A2, G2>;
     auto t3 = k_lsq_group<A3, G3>;
+    auto t4 = k_lsq_group<LSQ_GROUP_NMAX4, LSQ_GROUP_G4, false, LSQ_GROUP_TC4>;
+    auto t5 = k_lsq_group<LSQ_WARP2_NMAX, LSQ_GROUP_G5, false, LSQ_GROUP_TC5>;
     auto k4 = k_lsq_warp<LSQ_WARP2_NMAX, W4>;
     const size_t s1 = W1 * tile_warp_bytes<A1>(), s2 = group_smem_bytes<A2>(), s3 = group_smem_bytes<A3>();
+    const size_t st4 = group_smem_bytes<LSQ_GROUP_NMAX4, LSQ_GROUP_TC4>();
+    const size_t st5 = group_smem_bytes<LSQ_WARP2_NMAX, LSQ_GROUP_TC5>();
     const size_t s4 = warp_smem_bytes<LSQ_WARP2_NMAX, W4>();
     const size_t s5 = (size_t)(CN * (CN + 1) / 2 + 4 * CN) * sizeof(double);
     if ((e = set_smem(t1, s1)) != cudaSuccess) return e;
     if ((e = set_smem(t2, s2)) != cudaSuccess) return e;
     if ((e = set_smem(t3, s3)) != cudaSuccess) return e;
+    if ((e = set_smem(t4, st4)) != cudaSuccess) return e;
+    if ((e = set_smem(t5, st5)) != cudaSuccess) return e;
     if ((e = set_smem(k4, s4)) != cudaSuccess) return e;
     if ((e = set_smem(k_lsq_cta, s5)) != cudaSuccess) return e;
     const int tiles = (Ms + 31) / 32;
@@ -1248,7 +1272,8 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     launch_begin(p, "lsq_thread17", s);
     t1<<<(tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
                                                   kp, mu, p->w64, p->w32, p->J, p->wide, nullptr, 0, p->tiles_mid,
-                                                  p->tiles_big, p->list_a, p->counters, TierBatch{});
+                                                  p->tiles_big, p->tiles_48, p->tiles_64, p->list_a, p->counters,
+                                                  TierBatch{});
     launch_end(p, s);
     launch_begin(p, "lsq_group25", s);
     t2<<<occ2 * sms, G2 * 32, s2, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
@@ -1259,6 +1284,16 @@ cudaError_t run_precompute(Plan* p, cudaStream_t s) {
     t3<<<occ3 * sms, G3 * 32, s3, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms, kp, mu,
                                        p->w64, p->w32, p->J, p->wide, p->tiles_big, CNT_TILES_BIG, p->counters,
                                        TierBatch{});
+    launch_end(p, s);
+    launch_begin(p, "lsq_group48", s);
+    t4<<<sms, LSQ_GROUP_TC4 * LSQ_GROUP_G4, st4, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+                                                      kp, mu, p->w64, p->w32, p->J, p->wide, p->tiles_48, CNT_TILES_48,
+                                                      p->counters, TierBatch{});
+    launch_end(p, s);
+    launch_begin(p, "lsq_group64", s);
+    t5<<<sms, LSQ_GROUP_TC5 * LSQ_GROUP_G5, st5, s>>>(p->xs, p->phase, p->col_start, p->col_count, p->col_off, N, Ms,
+                                                      kp, mu, p->w64, p->w32, p->J, p->wide, p->tiles_64, CNT_TILES_64,
+                                                      p->counters, TierBatch{});
     launch_end(p, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // warp tier: columns of tiles whose largest column exceeds the thread tiers, |I(l)| <= 64
@@ -1335,6 +1370,8 @@ __global__ void k_batch_clear_counters(const TierArgs* __restrict__ probs, int P
     c[CNT_BIG_LIST] = 0;
     c[CNT_TILES_MID] = 0;
     c[CNT_TILES_BIG] = 0;
+    c[CNT_TILES_48] = 0;
+    c[CNT_TILES_64] = 0;
     c[CNT_HUGE_LIST] = 0;
 }
 
@@ -1371,7 +1408,8 @@ static TierArgs tier_args(const Plan* p) {
     a.kp = make_kernel_params(p);
     a.mu0 = p->tau * a.kp.diag;
     a.w64 = p->w64; a.w32 = p->w32; a.J = p->J; a.wide = p->wide;
-    a.tiles_mid = p->tiles_mid; a.tiles_big = p->tiles_big; a.list_a = p->list_a; a.big_list = p->big_list;
+    a.tiles_mid = p->tiles_mid; a.tiles_big = p->tiles_big; a.tiles_48 = p->tiles_48; a.tiles_64 = p->tiles_64;
+    a.list_a = p->list_a; a.big_list = p->big_list;
     a.counters = p->counters;
     return a;
 }
@@ -1391,13 +1429,19 @@ cudaError_t run_precompute_batch(const void* probs_v, int P, const int32_t* tile
     auto t1 = k_lsq_thread<A1, W1, true>;
     auto t2 = k_lsq_group<A2, G2, true>;
     auto t3 = k_lsq_group<A3, G3, true>;
+    auto t4 = k_lsq_group<LSQ_GROUP_NMAX4, LSQ_GROUP_G4, true, LSQ_GROUP_TC4>;
+    auto t5 = k_lsq_group<LSQ_WARP2_NMAX, LSQ_GROUP_G5, true, LSQ_GROUP_TC5>;
     auto k4 = k_lsq_warp<LSQ_WARP2_NMAX, W4, true>;
     const size_t s1 = W1 * tile_warp_bytes<A1>(), s2 = group_smem_bytes<A2>(), s3 = group_smem_bytes<A3>();
+    const size_t st4 = group_smem_bytes<LSQ_GROUP_NMAX4, LSQ_GROUP_TC4>();
+    const size_t st5 = group_smem_bytes<LSQ_WARP2_NMAX, LSQ_GROUP_TC5>();
     const size_t s4 = warp_smem_bytes<LSQ_WARP2_NMAX, W4>();
     cudaError_t e;
     if ((e = set_smem(t1, s1)) != cudaSuccess) return e;
     if ((e = set_smem(t2, s2)) != cudaSuccess) return e;
     if ((e = set_smem(t3, s3)) != cudaSuccess) return e;
+    if ((e = set_smem(t4, st4)) != cudaSuccess) return e;
+    if ((e = set_smem(t5, st5)) != cudaSuccess) return e;
     if ((e = set_smem(k4, s4)) != cudaSuccess) return e;
     int occ2 = 1, occ3 = 1;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, t2, G2 * 32, s2)) != cudaSuccess) return e;
@@ -1407,12 +1451,15 @@ cudaError_t run_precompute_batch(const void* probs_v, int P, const int32_t* tile
     int32_t* off_mid = off_work;
     int32_t* off_big = off_work + (P + 1);
     int32_t* off_a = off_work + 2 * (P + 1);
+    int32_t* off_48 = off_work + 3 * (P + 1);
+    int32_t* off_64 = off_work + 4 * (P + 1);
     const KernelParams kp0 = {};
     k_batch_clear_counters<<<(P + 255) / 256, 256, 0, s>>>(probs, P);
     // routing tier: every tile of every problem, one warp each
     t1<<<(total_tiles + W1 - 1) / W1, W1 * 32, s1, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0,
                                                          nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
-                                                         nullptr, nullptr, nullptr, TierBatch{probs, tile_off, P});
+                                                         nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                         TierBatch{probs, tile_off, P});
     // group tiers and warp tier: the problems' routed lists, numbered by device prefixes
     k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_TILES_MID, off_mid);
     t2<<<occ2 * sms, G2 * 32, s2, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0, nullptr, nullptr,
@@ -1420,10 +1467,18 @@ cudaError_t run_precompute_batch(const void* probs_v, int P, const int32_t* tile
     k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_TILES_BIG, off_big);
     t3<<<occ3 * sms, G3 * 32, s3, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0, nullptr, nullptr,
                                        nullptr, nullptr, nullptr, CNT_TILES_BIG, nullptr, TierBatch{probs, off_big, P});
+    k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_TILES_48, off_48);
+    t4<<<sms, LSQ_GROUP_TC4 * LSQ_GROUP_G4, st4, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0,
+                                                      nullptr, nullptr, nullptr, nullptr, nullptr, CNT_TILES_48, nullptr,
+                                                      TierBatch{probs, off_48, P});
+    k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_TILES_64, off_64);
+    t5<<<sms, LSQ_GROUP_TC5 * LSQ_GROUP_G5, st5, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0,
+                                                      nullptr, nullptr, nullptr, nullptr, nullptr, CNT_TILES_64, nullptr,
+                                                      TierBatch{probs, off_64, P});
     k_batch_count_prefix<<<1, 1024, 0, s>>>(probs, P, CNT_LIST_A, off_a);
     k4<<<2 * sms, W4 * 32, s4, s>>>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, kp0, 0.0, nullptr, nullptr,
                                     nullptr, nullptr, nullptr, CNT_LIST_A, nullptr, CNT_BIG_LIST, nullptr,
                                     TierBatch{probs, off_a, P});
-    count_launches(8);
+    count_launches(12);
     return cudaGetLastError();
 }

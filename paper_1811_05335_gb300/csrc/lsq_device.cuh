@@ -260,6 +260,8 @@ struct TierArgs {
     uint8_t* wide;
     int32_t* tiles_mid;
     int32_t* tiles_big;
+    int32_t* tiles_48;
+    int32_t* tiles_64;
     int32_t* list_a;
     int32_t* big_list;
     int32_t* counters;

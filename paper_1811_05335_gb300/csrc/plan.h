@@ -22,7 +22,9 @@ enum {
     CNT_TILES_BIG = 9,     // tiles routed to the 33-node thread tier
     CNT_GRAD_FAIL = 10,    // columns the node gradient could not factor (or too large)
     CNT_HUGE_LIST = 11,    // batch members: columns above 224 nodes solved by the batch's blocked solver
-    CNT_N = 12
+    CNT_TILES_48 = 12,     // tiles routed to the 48-node group tier
+    CNT_TILES_64 = 13,     // tiles routed to the 64-node group tier
+    CNT_N = 14
 };
 
 // largest column handled by the thread, warp and CTA solver tiers
@@ -32,6 +34,11 @@ constexpr int LSQ_THREAD_NMAX3 = 33;
 constexpr int LSQ_WARP2_NMAX = 64;
 constexpr int LSQ_GROUP_G2 = 4;      // lanes per column in the <= 25 tier
 constexpr int LSQ_GROUP_G3 = 8;      // lanes per column in the <= 33 tier
+constexpr int LSQ_GROUP_NMAX4 = 48;  // tiles of columns up to 48 nodes: 16 lanes per column, sub-tiles of 16
+constexpr int LSQ_GROUP_G4 = 16;
+constexpr int LSQ_GROUP_TC4 = 16;
+constexpr int LSQ_GROUP_G5 = 32;     // up to 64 nodes (LSQ_WARP2_NMAX): a warp per column, sub-tiles of 8
+constexpr int LSQ_GROUP_TC5 = 8;
 constexpr int LSQ_CTA_NMAX = 224;
 // largest |I(x_j)| = 2m + 1 of the underdetermined case
 constexpr int UNDER_NMAX = 17;
@@ -70,6 +77,8 @@ struct infft_plan_s {
     int32_t* list_a = nullptr;      // Ms (columns for the 32-row warp solver)
     int32_t* tiles_mid = nullptr;   // Ms/32 + 1 (tiles for the 25-node thread tier)
     int32_t* tiles_big = nullptr;   // Ms/32 + 1 (tiles for the 33-node thread tier)
+    int32_t* tiles_48 = nullptr;    // Ms/32 + 1 (tiles for the 48-node group tier)
+    int32_t* tiles_64 = nullptr;    // Ms/32 + 1 (tiles for the 64-node group tier)
     int32_t* big_list = nullptr;    // Ms (columns for the CTA solver)
     int32_t* scan_sums = nullptr;   // per-block partial sums of the scans
     int32_t* counters = nullptr;    // CNT_N
