@@ -943,6 +943,8 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
 constexpr int HUGE_PB = 16;
 constexpr int HUGE_PS = HUGE_PB + 1;   // panel row stride: rows 4 apart hit different banks
 constexpr int HUGE_THREADS = 256;
+constexpr int HUGE_MED = 256;        // columns up to this many nodes: the two-CTAs-per-SM part
+constexpr int HUGE_MED_MINB = 2;
 
 __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int32_t* __restrict__ job_off) {
     __shared__ int32_t part[1024];
@@ -1018,25 +1020,39 @@ __global__ void k_job_scatter(const HugeProblem* __restrict__ probs, int P, cons
         order[atomicAdd(&cursor[nmax - job_size(probs, P, job_off, j, nmax)], 1)] = j;
 }
 
-__global__ void __launch_bounds__(HUGE_THREADS, 1)
+// The number of jobs above HUGE_MED nodes (the first ones of the largest-first order):
+// after k_job_scatter each bucket's cursor holds the bucket's end.
+__global__ void k_job_split(const int32_t* __restrict__ cursor, int nmax, int32_t* __restrict__ split) {
+    *split = nmax > HUGE_MED ? cursor[nmax - HUGE_MED - 1] : 0;
+}
+
+// The jobs of one part of the order: PMAX = HUGE_NMAX, one CTA per SM, the jobs before
+// the split (columns above HUGE_MED nodes); PMAX = HUGE_MED, two CTAs per SM (their
+// latency-bound panel and back-solve steps overlap), the jobs after it.
+template <int PMAX, int MINB>
+__global__ void __launch_bounds__(HUGE_THREADS, MINB)
 k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
-           const int32_t* __restrict__ order, int32_t* __restrict__ ticket, double* __restrict__ scratch, int nmax) {
+           const int32_t* __restrict__ order, int32_t* __restrict__ ticket, const int32_t* __restrict__ split,
+           double* __restrict__ scratch, size_t slot_doubles, int nmax) {
     extern __shared__ double smem[];
-    double* pan = smem;                          // HUGE_NMAX x HUGE_PB panel (row stride HUGE_PS)
-    double* r = pan + HUGE_NMAX * HUGE_PS;       // HUGE_NMAX
-    double* xl = r + HUGE_NMAX;                  // HUGE_NMAX
-    double2* pv = (double2*)(xl + HUGE_NMAX);    // HUGE_NMAX
+    double* pan = smem;                          // PMAX x HUGE_PB panel (row stride HUGE_PS)
+    double* r = pan + PMAX * HUGE_PS;            // PMAX
+    double* xl = r + PMAX;                       // PMAX
+    double2* pv = (double2*)(xl + PMAX);         // PMAX
     __shared__ double s_red[2 * (HUGE_THREADS / 32)];
+    __shared__ double s_y[HUGE_PB];              // b of the current block of rows (back solve)
     __shared__ int s_t;
-    double* A = scratch + (size_t)blockIdx.x * ((size_t)nmax * (nmax + 1) / 2);
-    const int total = job_off[P];
+    double* A = scratch + (size_t)blockIdx.x * slot_doubles;
+    const bool large = PMAX == HUGE_NMAX;
+    const int first = large ? 0 : *split;
+    const int last = large ? *split : job_off[P];
     const int tid = threadIdx.x;
     for (;;) {
-        if (tid == 0) s_t = atomicAdd(ticket, 1);
+        if (tid == 0) s_t = first + atomicAdd(ticket, 1);
         __syncthreads();
         const int t = s_t;
         __syncthreads();
-        if (t >= total) break;
+        if (t >= last) break;
         const int job = order[t];   // largest columns first
         int lo = 0, hi = P - 1;   // problem: the last i with job_off[i] <= job
         while (lo < hi) {
@@ -1182,17 +1198,31 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
             const int hb = min(HUGE_PB, n - kb);
             __syncthreads();
             for (int c = 0; c < hb; ++c)
-                for (int i = tid; i <= kb + c; i += HUGE_THREADS) pan[c * HUGE_NMAX + i] = A[trow(kb + c) + i];
+                for (int i = tid; i <= kb + c; i += HUGE_THREADS) pan[c * PMAX + i] = A[trow(kb + c) + i];
             __syncthreads();
-            for (int c = hb - 1; c >= 0; --c) {
-                const int k = kb + c;
-                const double bk = r[k] * pan[c * HUGE_NMAX + k];
-                __syncthreads();
-                if (tid == 0) r[k] = bk;
-                for (int i = tid; i < k; i += HUGE_THREADS) r[i] = fma(-pan[c * HUGE_NMAX + i], bk, r[i]);
-                __syncthreads();
+            // the block's own rows by warp 0 (lane c holds y_{kb+c}, then b), b_k for k from
+            // the block's last row down; then every row above the block takes the block's b
+            // out of r at once (three barriers per block instead of two per row)
+            if (tid < 32) {
+                double v = tid < hb ? r[kb + tid] : 0.0;
+                for (int c = hb - 1; c >= 0; --c) {
+                    const double bc = __shfl_sync(0xffffffffu, v, c) * pan[c * PMAX + kb + c];
+                    if (tid == c) v = bc;
+                    else if (tid < c) v = fma(-pan[c * PMAX + kb + tid], bc, v);
+                }
+                if (tid < hb) {
+                    r[kb + tid] = v;
+                    s_y[tid] = v;
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < kb; i += HUGE_THREADS) {
+                double acc = r[i];
+                for (int c = hb - 1; c >= 0; --c) acc = fma(-pan[c * PMAX + i], s_y[c], acc);
+                r[i] = acc;
             }
         }
+        __syncthreads();
         double bsq = 0.0, babs = 0.0;
         for (int i = tid; i < n; i += HUGE_THREADS) {
             const double b = r[i];
@@ -1334,24 +1364,41 @@ void huge_problems_fill(Plan* const* plans, int P, void* host) {
     for (int i = 0; i < P; ++i) h[i] = huge_problem(plans[i]);
 }
 
-size_t huge_scratch_doubles(int slots, int nmax) { return (size_t)slots * ((size_t)nmax * (nmax + 1) / 2); }
+// the triangles of the large part's slots (one per SM), then the medium part's
+size_t huge_scratch_doubles(int slots, int nmax) {
+    const size_t med = (size_t)std::min(nmax, HUGE_MED);
+    return (size_t)slots * ((size_t)nmax * (nmax + 1) / 2) + (size_t)HUGE_MED_MINB * slots * (med * (med + 1) / 2);
+}
 
 cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int32_t* order, int32_t* work,
                                 double* scratch, int slots, int nmax, cudaStream_t s) {
-    const size_t smem = (size_t)(HUGE_NMAX * HUGE_PS + 2 * HUGE_NMAX) * sizeof(double) +
-                        (size_t)HUGE_NMAX * sizeof(double2);
-    cudaError_t e = set_smem(k_lsq_huge, smem);
+    auto big = k_lsq_huge<HUGE_NMAX, 1>;
+    auto med = k_lsq_huge<HUGE_MED, HUGE_MED_MINB>;
+    auto smem_of = [](int pmax) {
+        return (size_t)(pmax * HUGE_PS + 2 * pmax) * sizeof(double) + (size_t)pmax * sizeof(double2);
+    };
+    cudaError_t e = set_smem(big, smem_of(HUGE_NMAX));
+    if (e == cudaSuccess) e = set_smem(med, smem_of(HUGE_MED));
     if (e != cudaSuccess) return e;
     const HugeProblem* hp = (const HugeProblem*)probs;
     int32_t* hist = work;                  // nmax + 1 buckets (then their offsets, then cursors)
-    int32_t* ticket = work + nmax + 1;
-    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 2) * sizeof(int32_t), s)) != cudaSuccess) return e;
+    int32_t* ticket = work + nmax + 1;     // the two parts' tickets, then the split
+    int32_t* split = work + nmax + 3;
+    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 4) * sizeof(int32_t), s)) != cudaSuccess) return e;
     k_huge_prefix<<<1, 1024, 0, s>>>(hp, P, job_off);
     k_job_hist<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist);
     k_job_scan<<<1, 1024, 0, s>>>(hist, nmax + 1);
     k_job_scatter<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist, order);
-    k_lsq_huge<<<slots, HUGE_THREADS, smem, s>>>(hp, P, job_off, order, ticket, scratch, nmax);
-    count_launches(5);
+    k_job_split<<<1, 1, 0, s>>>(hist, nmax, split);
+    const size_t big_slot = (size_t)nmax * (nmax + 1) / 2;
+    const size_t mn = (size_t)std::min(nmax, HUGE_MED);
+    if (nmax > HUGE_MED)
+        big<<<slots, HUGE_THREADS, smem_of(HUGE_NMAX), s>>>(hp, P, job_off, order, ticket, split, scratch, big_slot,
+                                                            nmax);
+    med<<<HUGE_MED_MINB * slots, HUGE_THREADS, smem_of(HUGE_MED), s>>>(hp, P, job_off, order, ticket + 1, split,
+                                                                      scratch + (size_t)slots * big_slot,
+                                                                      mn * (mn + 1) / 2, nmax);
+    count_launches(nmax > HUGE_MED ? 7 : 6);
     return cudaGetLastError();
 }
 
