@@ -942,9 +942,10 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
 
 constexpr int HUGE_PB = 16;
 constexpr int HUGE_PS = HUGE_PB + 1;   // panel row stride: rows 4 apart hit different banks
-constexpr int HUGE_THREADS = 256;
-constexpr int HUGE_MED = 256;        // columns up to this many nodes: the two-CTAs-per-SM part
-constexpr int HUGE_MED_MINB = 2;
+// the blocked solver's parts: largest column of each (panel capacity), threads and CTAs per SM
+constexpr int HUGE_PART_LIMIT[3] = {HUGE_NMAX, 512, 256};
+constexpr int HUGE_PART_THREADS[3] = {256, 256, 128};
+constexpr int HUGE_PART_MINB[3] = {1, 2, 4};
 
 __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int32_t* __restrict__ job_off) {
     __shared__ int32_t part[1024];
@@ -1020,32 +1021,34 @@ __global__ void k_job_scatter(const HugeProblem* __restrict__ probs, int P, cons
         order[atomicAdd(&cursor[nmax - job_size(probs, P, job_off, j, nmax)], 1)] = j;
 }
 
-// The number of jobs above HUGE_MED nodes (the first ones of the largest-first order):
-// after k_job_scatter each bucket's cursor holds the bucket's end.
+// The jobs are solved in three parts of the largest-first order, each by its own
+// launch: columns above 512 nodes (panel capacity 1024 rows, one CTA of 256 threads per
+// SM), 257 .. 512 nodes (two CTAs per SM) and up to 256 nodes (four CTAs of 128 threads
+// per SM): smaller columns need less shared memory, and more CTAs per SM overlap their
+// latency-bound panel, fill and back-solve steps.  split[k]: the number of jobs above
+// HUGE_PART_LIMIT[k + 1] nodes; after k_job_scatter each bucket's cursor holds its end.
 __global__ void k_job_split(const int32_t* __restrict__ cursor, int nmax, int32_t* __restrict__ split) {
-    *split = nmax > HUGE_MED ? cursor[nmax - HUGE_MED - 1] : 0;
+    constexpr int L1 = HUGE_PART_LIMIT[1], L2 = HUGE_PART_LIMIT[2];
+    split[0] = nmax > L1 ? cursor[nmax - L1 - 1] : 0;
+    split[1] = nmax > L2 ? cursor[nmax - L2 - 1] : 0;
 }
 
-// The jobs of one part of the order: PMAX = HUGE_NMAX, one CTA per SM, the jobs before
-// the split (columns above HUGE_MED nodes); PMAX = HUGE_MED, two CTAs per SM (their
-// latency-bound panel and back-solve steps overlap), the jobs after it.
-template <int PMAX, int MINB>
-__global__ void __launch_bounds__(HUGE_THREADS, MINB)
+template <int PMAX, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB)
 k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restrict__ job_off,
            const int32_t* __restrict__ order, int32_t* __restrict__ ticket, const int32_t* __restrict__ split,
-           double* __restrict__ scratch, size_t slot_doubles, int nmax) {
+           int part, double* __restrict__ scratch, size_t slot_doubles, int nmax) {
     extern __shared__ double smem[];
     double* pan = smem;                          // PMAX x HUGE_PB panel (row stride HUGE_PS)
     double* r = pan + PMAX * HUGE_PS;            // PMAX
     double* xl = r + PMAX;                       // PMAX
     double2* pv = (double2*)(xl + PMAX);         // PMAX
-    __shared__ double s_red[2 * (HUGE_THREADS / 32)];
+    __shared__ double s_red[2 * (NTH / 32)];
     __shared__ double s_y[HUGE_PB];              // b of the current block of rows (back solve)
     __shared__ int s_t;
     double* A = scratch + (size_t)blockIdx.x * slot_doubles;
-    const bool large = PMAX == HUGE_NMAX;
-    const int first = large ? 0 : *split;
-    const int last = large ? *split : job_off[P];
+    const int first = part == 0 ? 0 : split[part - 1];
+    const int last = part == 2 ? job_off[P] : split[part];
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_t = first + atomicAdd(ticket, 1);
@@ -1064,14 +1067,14 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
         const int n = pr.col_count[p], s = pr.col_start[p], off = pr.col_off[p], N = pr.N;
         if (tid == 0 && n > LSQ_CTA_NMAX) atomicAdd(&pr.counters[CNT_HUGE_LIST], 1);
         if (n > nmax) {
-            for (int i = tid; i < n; i += HUGE_THREADS) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
+            for (int i = tid; i < n; i += NTH) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
             if (tid == 0) { pr.J[p] = 1.0; pr.wide[p] = 0; atomicAdd(&pr.counters[CNT_UNSUPPORTED], 1); }
             continue;
         }
         const KernelParams& kp = pr.kp;
         const double tl = col_t(p, pr.Ms);
         const double2 pl = phase_of(kp.M, tl);
-        for (int i = tid; i < n; i += HUGE_THREADS) {
+        for (int i = tid; i < n; i += NTH) {
             int q = s + i;
             if (q >= N) q -= N;
             xl[i] = pr.xs[q];
@@ -1082,9 +1085,9 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
         double ysq = 0.0;
         bool ok = false;
         for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
-            for (int i = tid; i < n; i += HUGE_THREADS) r[i] = re_kappa(tl, xl[i], pl, pv[i], kp);
+            for (int i = tid; i < n; i += NTH) r[i] = re_kappa(tl, xl[i], pl, pv[i], kp);
             const int ntri = n * (n + 1) / 2;
-            for (int e = tid; e < ntri; e += HUGE_THREADS) {   // packed row-major: entry e is (i, j)
+            for (int e = tid; e < ntri; e += NTH) {   // packed row-major: entry e is (i, j)
                 int i, j;
                 tri_index(e, i, j);
                 A[e] = (i == j) ? kp.diag + mu : re_kappa(xl[i], xl[j], pv[i], pv[j], kp);
@@ -1094,7 +1097,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
             bool failed = false;   // block-uniform: decided on shared values
             for (int kb = 0; kb < n && !failed; kb += HUGE_PB) {
                 const int w = min(HUGE_PB, n - kb), R = n - kb;
-                for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
+                for (int e = tid; e < R * HUGE_PB; e += NTH) {
                     const int i = e / HUGE_PB, c = e % HUGE_PB;
                     pan[i * HUGE_PS + c] = (c < w && c <= i) ? A[trow(kb + i) + kb + c] : 0.0;
                 }
@@ -1107,12 +1110,12 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                     }
                     const double rp = rsqrt(akk);
                     __syncthreads();
-                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) pan[i * HUGE_PS + c] *= rp;
+                    for (int i = c + 1 + tid; i < R; i += NTH) pan[i * HUGE_PS + c] *= rp;
                     if (tid == 0) pan[c * HUGE_PS + c] = rp;
                     __syncthreads();
                     // rank-1 update of the panel's remaining columns c' in (c, w), rows i >= c'
                     const int nc = w - c - 1;
-                    for (int e = tid; e < (R - c - 1) * nc; e += HUGE_THREADS) {
+                    for (int e = tid; e < (R - c - 1) * nc; e += NTH) {
                         const int i = c + 1 + e / nc, cc = c + 1 + e % nc;
                         if (cc <= i) pan[i * HUGE_PS + cc] = fma(-pan[i * HUGE_PS + c], pan[cc * HUGE_PS + c],
                                                                  pan[i * HUGE_PS + cc]);
@@ -1127,10 +1130,10 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                     ysq = fma(yc, yc, ysq);
                     __syncthreads();
                     if (tid == 0) r[kb + c] = yc;
-                    for (int i = c + 1 + tid; i < R; i += HUGE_THREADS) r[kb + i] = fma(-pan[i * HUGE_PS + c], yc, r[kb + i]);
+                    for (int i = c + 1 + tid; i < R; i += NTH) r[kb + i] = fma(-pan[i * HUGE_PS + c], yc, r[kb + i]);
                     __syncthreads();
                 }
-                for (int e = tid; e < R * HUGE_PB; e += HUGE_THREADS) {
+                for (int e = tid; e < R * HUGE_PB; e += NTH) {
                     const int i = e / HUGE_PB, c = e % HUGE_PB;
                     if (c < w && c <= i) A[trow(kb + i) + kb + c] = pan[i * HUGE_PS + c];
                 }
@@ -1138,7 +1141,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                 const int T = n - kb - w;
                 const int nb = (T + 3) >> 2;
                 const int nblk = nb * (nb + 1) / 2;
-                for (int bk = tid; bk < nblk; bk += HUGE_THREADS) {
+                for (int bk = tid; bk < nblk; bk += NTH) {
                     int bi, bj;
                     tri_index(bk, bi, bj);
                     const int i0 = w + 4 * bi, j0 = w + 4 * bj;   // panel row indices
@@ -1186,7 +1189,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
             if (!ok) mu *= 1e3;
         }
         if (!ok) {
-            for (int i = tid; i < n; i += HUGE_THREADS) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
+            for (int i = tid; i < n; i += NTH) { pr.w64[off + i] = 0.0; pr.w32[off + i] = 0.0f; }
             if (tid == 0) { pr.J[p] = 1.0; pr.wide[p] = 0; atomicAdd(&pr.counters[CNT_FALLBACK], 1); }
             __syncthreads();
             continue;
@@ -1198,7 +1201,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
             const int hb = min(HUGE_PB, n - kb);
             __syncthreads();
             for (int c = 0; c < hb; ++c)
-                for (int i = tid; i <= kb + c; i += HUGE_THREADS) pan[c * PMAX + i] = A[trow(kb + c) + i];
+                for (int i = tid; i <= kb + c; i += NTH) pan[c * PMAX + i] = A[trow(kb + c) + i];
             __syncthreads();
             // the block's own rows by warp 0 (lane c holds y_{kb+c}, then b), b_k for k from
             // the block's last row down; then every row above the block takes the block's b
@@ -1216,7 +1219,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
                 }
             }
             __syncthreads();
-            for (int i = tid; i < kb; i += HUGE_THREADS) {
+            for (int i = tid; i < kb; i += NTH) {
                 double acc = r[i];
                 for (int c = hb - 1; c >= 0; --c) acc = fma(-pan[c * PMAX + i], s_y[c], acc);
                 r[i] = acc;
@@ -1224,7 +1227,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
         }
         __syncthreads();
         double bsq = 0.0, babs = 0.0;
-        for (int i = tid; i < n; i += HUGE_THREADS) {
+        for (int i = tid; i < n; i += NTH) {
             const double b = r[i];
             store_b(pr.w64, pr.w32, pr.kp.wlo, off + i, b);
             bsq = fma(b, b, bsq);
@@ -1236,12 +1239,12 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
         }
         if ((tid & 31) == 0) {
             s_red[tid >> 5] = bsq;
-            s_red[HUGE_THREADS / 32 + (tid >> 5)] = babs;
+            s_red[NTH / 32 + (tid >> 5)] = babs;
         }
         __syncthreads();
         if (tid == 0) {
             double t = 0.0, a = 0.0;
-            for (int w = 0; w < HUGE_THREADS / 32; ++w) { t += s_red[w]; a += s_red[HUGE_THREADS / 32 + w]; }
+            for (int w = 0; w < NTH / 32; ++w) { t += s_red[w]; a += s_red[NTH / 32 + w]; }
             pr.J[p] = 1.0 - ysq - mu * t;
             pr.wide[p] = a > WIDE_COLUMN_L1;
         }
@@ -1364,41 +1367,54 @@ void huge_problems_fill(Plan* const* plans, int P, void* host) {
     for (int i = 0; i < P; ++i) h[i] = huge_problem(plans[i]);
 }
 
-// the triangles of the large part's slots (one per SM), then the medium part's
+// the triangles of every part's slots (HUGE_PART_MINB[k] per SM, of the part's largest column)
 size_t huge_scratch_doubles(int slots, int nmax) {
-    const size_t med = (size_t)std::min(nmax, HUGE_MED);
-    return (size_t)slots * ((size_t)nmax * (nmax + 1) / 2) + (size_t)HUGE_MED_MINB * slots * (med * (med + 1) / 2);
+    size_t tot = 0;
+    for (int k = 0; k < 3; ++k) {
+        const size_t c = (size_t)std::min(nmax, HUGE_PART_LIMIT[k]);
+        tot += (size_t)HUGE_PART_MINB[k] * slots * (c * (c + 1) / 2);
+    }
+    return tot;
 }
 
 cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int32_t* order, int32_t* work,
                                 double* scratch, int slots, int nmax, cudaStream_t s) {
-    auto big = k_lsq_huge<HUGE_NMAX, 1>;
-    auto med = k_lsq_huge<HUGE_MED, HUGE_MED_MINB>;
+    auto k0 = k_lsq_huge<HUGE_PART_LIMIT[0], HUGE_PART_THREADS[0], HUGE_PART_MINB[0]>;
+    auto k1 = k_lsq_huge<HUGE_PART_LIMIT[1], HUGE_PART_THREADS[1], HUGE_PART_MINB[1]>;
+    auto k2 = k_lsq_huge<HUGE_PART_LIMIT[2], HUGE_PART_THREADS[2], HUGE_PART_MINB[2]>;
     auto smem_of = [](int pmax) {
         return (size_t)(pmax * HUGE_PS + 2 * pmax) * sizeof(double) + (size_t)pmax * sizeof(double2);
     };
-    cudaError_t e = set_smem(big, smem_of(HUGE_NMAX));
-    if (e == cudaSuccess) e = set_smem(med, smem_of(HUGE_MED));
+    cudaError_t e = set_smem(k0, smem_of(HUGE_PART_LIMIT[0]));
+    if (e == cudaSuccess) e = set_smem(k1, smem_of(HUGE_PART_LIMIT[1]));
+    if (e == cudaSuccess) e = set_smem(k2, smem_of(HUGE_PART_LIMIT[2]));
     if (e != cudaSuccess) return e;
     const HugeProblem* hp = (const HugeProblem*)probs;
     int32_t* hist = work;                  // nmax + 1 buckets (then their offsets, then cursors)
-    int32_t* ticket = work + nmax + 1;     // the two parts' tickets, then the split
-    int32_t* split = work + nmax + 3;
-    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 4) * sizeof(int32_t), s)) != cudaSuccess) return e;
+    int32_t* ticket = work + nmax + 1;     // the three parts' tickets, then the two splits
+    int32_t* split = work + nmax + 4;
+    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 6) * sizeof(int32_t), s)) != cudaSuccess) return e;
     k_huge_prefix<<<1, 1024, 0, s>>>(hp, P, job_off);
     k_job_hist<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist);
     k_job_scan<<<1, 1024, 0, s>>>(hist, nmax + 1);
     k_job_scatter<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist, order);
     k_job_split<<<1, 1, 0, s>>>(hist, nmax, split);
-    const size_t big_slot = (size_t)nmax * (nmax + 1) / 2;
-    const size_t mn = (size_t)std::min(nmax, HUGE_MED);
-    if (nmax > HUGE_MED)
-        big<<<slots, HUGE_THREADS, smem_of(HUGE_NMAX), s>>>(hp, P, job_off, order, ticket, split, scratch, big_slot,
-                                                            nmax);
-    med<<<HUGE_MED_MINB * slots, HUGE_THREADS, smem_of(HUGE_MED), s>>>(hp, P, job_off, order, ticket + 1, split,
-                                                                      scratch + (size_t)slots * big_slot,
-                                                                      mn * (mn + 1) / 2, nmax);
-    count_launches(nmax > HUGE_MED ? 7 : 6);
+    int launches = 5;
+    double* base = scratch;
+    for (int k = 0; k < 3; ++k) {
+        const int lim = HUGE_PART_LIMIT[k];
+        const size_t c = (size_t)std::min(nmax, lim);
+        const size_t slot = c * (c + 1) / 2;
+        const int ctas = HUGE_PART_MINB[k] * slots;
+        if (k == 2 || nmax > HUGE_PART_LIMIT[k + 1]) {   // a part above nmax has no jobs
+            if (k == 0) k0<<<ctas, HUGE_PART_THREADS[0], smem_of(lim), s>>>(hp, P, job_off, order, ticket, split, 0, base, slot, nmax);
+            if (k == 1) k1<<<ctas, HUGE_PART_THREADS[1], smem_of(lim), s>>>(hp, P, job_off, order, ticket + 1, split, 1, base, slot, nmax);
+            if (k == 2) k2<<<ctas, HUGE_PART_THREADS[2], smem_of(lim), s>>>(hp, P, job_off, order, ticket + 2, split, 2, base, slot, nmax);
+            ++launches;
+        }
+        base += (size_t)ctas * slot;
+    }
+    count_launches(launches);
     return cudaGetLastError();
 }
 
