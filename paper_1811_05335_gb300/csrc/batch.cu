@@ -624,7 +624,7 @@ struct infft_batch_s {
     void* huge_probs = nullptr;     // P large-column descriptors
     int32_t* job_off = nullptr;     // P + 1
     int32_t* job_order = nullptr;   // sum M_sigma: blocked-solver jobs, largest first
-    int32_t* job_work = nullptr;    // HUGE_NMAX + 6: size buckets, three tickets and two splits
+    int32_t* job_work = nullptr;    // HUGE_NMAX + 8: size buckets, four tickets and three splits
     double* huge_scratch = nullptr;
     int32_t* order = nullptr;       // problems by decreasing size
     int32_t* ticket = nullptr;
@@ -807,7 +807,7 @@ infft_status infft_batch_create(int64_t P, const int64_t* M, const int64_t* N, d
     if (b->huge_slots) {
         alloc(&b->huge_scratch, huge_scratch_doubles(b->huge_slots, b->huge_nmax) * sizeof(double));
         alloc(&b->job_order, b->sumG * sizeof(int32_t));
-        alloc(&b->job_work, (HUGE_NMAX + 6) * sizeof(int32_t));
+        alloc(&b->job_work, (HUGE_NMAX + 8) * sizeof(int32_t));
     }
     // tiles of the batched spreading: at most one per cols grid points plus one per
     // wblk weights of the largest possible nnz (the buffer for the smallest shape; the

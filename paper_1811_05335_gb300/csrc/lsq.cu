@@ -943,9 +943,10 @@ k_lsq_cta(const double* __restrict__ xs, const double2* __restrict__ ph, const i
 constexpr int HUGE_PB = 16;
 constexpr int HUGE_PS = HUGE_PB + 1;   // panel row stride: rows 4 apart hit different banks
 // the blocked solver's parts: largest column of each (panel capacity), threads and CTAs per SM
-constexpr int HUGE_PART_LIMIT[3] = {HUGE_NMAX, 512, 256};
-constexpr int HUGE_PART_THREADS[3] = {256, 256, 128};
-constexpr int HUGE_PART_MINB[3] = {1, 2, 4};
+constexpr int HUGE_PARTS = 4;
+constexpr int HUGE_PART_LIMIT[HUGE_PARTS] = {HUGE_NMAX, 512, 256, 128};
+constexpr int HUGE_PART_THREADS[HUGE_PARTS] = {256, 256, 128, 64};
+constexpr int HUGE_PART_MINB[HUGE_PARTS] = {1, 2, 4, 8};
 
 __global__ void k_huge_prefix(const HugeProblem* __restrict__ probs, int P, int32_t* __restrict__ job_off) {
     __shared__ int32_t part[1024];
@@ -1021,16 +1022,18 @@ __global__ void k_job_scatter(const HugeProblem* __restrict__ probs, int P, cons
         order[atomicAdd(&cursor[nmax - job_size(probs, P, job_off, j, nmax)], 1)] = j;
 }
 
-// The jobs are solved in three parts of the largest-first order, each by its own
+// The jobs are solved in four parts of the largest-first order, each by its own
 // launch: columns above 512 nodes (panel capacity 1024 rows, one CTA of 256 threads per
-// SM), 257 .. 512 nodes (two CTAs per SM) and up to 256 nodes (four CTAs of 128 threads
-// per SM): smaller columns need less shared memory, and more CTAs per SM overlap their
-// latency-bound panel, fill and back-solve steps.  split[k]: the number of jobs above
-// HUGE_PART_LIMIT[k + 1] nodes; after k_job_scatter each bucket's cursor holds its end.
+// SM), 257 .. 512 nodes (two CTAs per SM), 129 .. 256 nodes (four CTAs of 128 threads)
+// and up to 128 nodes (eight CTAs of 64 threads): smaller columns need less shared
+// memory, and more CTAs per SM overlap their latency-bound panel, fill and back-solve
+// steps.  split[k]: the number of jobs above HUGE_PART_LIMIT[k + 1] nodes; after
+// k_job_scatter each bucket's cursor holds its end.
 __global__ void k_job_split(const int32_t* __restrict__ cursor, int nmax, int32_t* __restrict__ split) {
-    constexpr int L1 = HUGE_PART_LIMIT[1], L2 = HUGE_PART_LIMIT[2];
+    constexpr int L1 = HUGE_PART_LIMIT[1], L2 = HUGE_PART_LIMIT[2], L3 = HUGE_PART_LIMIT[3];
     split[0] = nmax > L1 ? cursor[nmax - L1 - 1] : 0;
     split[1] = nmax > L2 ? cursor[nmax - L2 - 1] : 0;
+    split[2] = nmax > L3 ? cursor[nmax - L3 - 1] : 0;
 }
 
 template <int PMAX, int NTH, int MINB>
@@ -1048,7 +1051,7 @@ k_lsq_huge(const HugeProblem* __restrict__ probs, int P, const int32_t* __restri
     __shared__ int s_t;
     double* A = scratch + (size_t)blockIdx.x * slot_doubles;
     const int first = part == 0 ? 0 : split[part - 1];
-    const int last = part == 2 ? job_off[P] : split[part];
+    const int last = part == HUGE_PARTS - 1 ? job_off[P] : split[part];
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_t = first + atomicAdd(ticket, 1);
@@ -1370,7 +1373,7 @@ void huge_problems_fill(Plan* const* plans, int P, void* host) {
 // the triangles of every part's slots (HUGE_PART_MINB[k] per SM, of the part's largest column)
 size_t huge_scratch_doubles(int slots, int nmax) {
     size_t tot = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < HUGE_PARTS; ++k) {
         const size_t c = (size_t)std::min(nmax, HUGE_PART_LIMIT[k]);
         tot += (size_t)HUGE_PART_MINB[k] * slots * (c * (c + 1) / 2);
     }
@@ -1382,18 +1385,21 @@ cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int3
     auto k0 = k_lsq_huge<HUGE_PART_LIMIT[0], HUGE_PART_THREADS[0], HUGE_PART_MINB[0]>;
     auto k1 = k_lsq_huge<HUGE_PART_LIMIT[1], HUGE_PART_THREADS[1], HUGE_PART_MINB[1]>;
     auto k2 = k_lsq_huge<HUGE_PART_LIMIT[2], HUGE_PART_THREADS[2], HUGE_PART_MINB[2]>;
+    auto k3 = k_lsq_huge<HUGE_PART_LIMIT[3], HUGE_PART_THREADS[3], HUGE_PART_MINB[3]>;
     auto smem_of = [](int pmax) {
         return (size_t)(pmax * HUGE_PS + 2 * pmax) * sizeof(double) + (size_t)pmax * sizeof(double2);
     };
     cudaError_t e = set_smem(k0, smem_of(HUGE_PART_LIMIT[0]));
     if (e == cudaSuccess) e = set_smem(k1, smem_of(HUGE_PART_LIMIT[1]));
     if (e == cudaSuccess) e = set_smem(k2, smem_of(HUGE_PART_LIMIT[2]));
+    if (e == cudaSuccess) e = set_smem(k3, smem_of(HUGE_PART_LIMIT[3]));
     if (e != cudaSuccess) return e;
     const HugeProblem* hp = (const HugeProblem*)probs;
     int32_t* hist = work;                  // nmax + 1 buckets (then their offsets, then cursors)
-    int32_t* ticket = work + nmax + 1;     // the three parts' tickets, then the two splits
-    int32_t* split = work + nmax + 4;
-    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 6) * sizeof(int32_t), s)) != cudaSuccess) return e;
+    int32_t* ticket = work + nmax + 1;     // the parts' tickets, then the splits
+    int32_t* split = work + nmax + 1 + HUGE_PARTS;
+    if ((e = cudaMemsetAsync(work, 0, (size_t)(nmax + 2 * HUGE_PARTS) * sizeof(int32_t), s)) != cudaSuccess)
+        return e;
     k_huge_prefix<<<1, 1024, 0, s>>>(hp, P, job_off);
     k_job_hist<<<4 * slots, 256, 0, s>>>(hp, P, job_off, nmax, hist);
     k_job_scan<<<1, 1024, 0, s>>>(hist, nmax + 1);
@@ -1401,15 +1407,16 @@ cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int3
     k_job_split<<<1, 1, 0, s>>>(hist, nmax, split);
     int launches = 5;
     double* base = scratch;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < HUGE_PARTS; ++k) {
         const int lim = HUGE_PART_LIMIT[k];
         const size_t c = (size_t)std::min(nmax, lim);
         const size_t slot = c * (c + 1) / 2;
         const int ctas = HUGE_PART_MINB[k] * slots;
-        if (k == 2 || nmax > HUGE_PART_LIMIT[k + 1]) {   // a part above nmax has no jobs
+        if (k == HUGE_PARTS - 1 || nmax > HUGE_PART_LIMIT[k + 1]) {   // a part above nmax has no jobs
             if (k == 0) k0<<<ctas, HUGE_PART_THREADS[0], smem_of(lim), s>>>(hp, P, job_off, order, ticket, split, 0, base, slot, nmax);
             if (k == 1) k1<<<ctas, HUGE_PART_THREADS[1], smem_of(lim), s>>>(hp, P, job_off, order, ticket + 1, split, 1, base, slot, nmax);
             if (k == 2) k2<<<ctas, HUGE_PART_THREADS[2], smem_of(lim), s>>>(hp, P, job_off, order, ticket + 2, split, 2, base, slot, nmax);
+            if (k == 3) k3<<<ctas, HUGE_PART_THREADS[3], smem_of(lim), s>>>(hp, P, job_off, order, ticket + 3, split, 3, base, slot, nmax);
             ++launches;
         }
         base += (size_t)ctas * slot;

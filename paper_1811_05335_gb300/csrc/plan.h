@@ -199,7 +199,7 @@ constexpr int HUGE_NMAX = 1024;
 size_t huge_problem_bytes();                                   // size of one device descriptor
 void huge_problems_fill(Plan* const* plans, int P, void* host); // P descriptors into host memory
 size_t huge_scratch_doubles(int slots, int nmax);
-// order: one int per possible job (sum of the problems' M_sigma); work: nmax + 6 ints
+// order: one int per possible job (sum of the problems' M_sigma); work: nmax + 8 ints
 cudaError_t run_precompute_huge(const void* probs, int P, int32_t* job_off, int32_t* order, int32_t* work,
                                 double* scratch, int slots, int nmax, cudaStream_t s);
 // lsq.cu: the solver tiers of every problem of a batch, one launch per tier.  probs: P device
