@@ -1193,7 +1193,7 @@ INFFT_D float4 k2_column_cta(int p, int s, int n, bool runs, const float2* __res
 // SPREAD_BIG entries (the first nbig CTAs, listed in big) take a whole CTA.  Ordinary columns:
 // fp32 weights and accumulation; wide columns: float-float.
 template <int LPC>
-__global__ void __launch_bounds__(256) k2_spread32(const float2* __restrict__ f, const float2* __restrict__ fs,
+__global__ void __launch_bounds__(256, 6) k2_spread32(const float2* __restrict__ f, const float2* __restrict__ fs,
                                                    const int32_t* __restrict__ col_off,
                                                    const int32_t* __restrict__ cell_start,
                                                    const int32_t* __restrict__ col_node, const float* __restrict__ w32,
