@@ -14,11 +14,16 @@
 //
 // GB300 executes fp64 at 1/64 of the fp32 rate, so the kernels are organised to
 // minimise fp64 warp instructions:
-//   * thread tiers: one THREAD per column (tiles whose largest |I(l)| is <= 17,
-//     25 or 33), a private packed triangle in shared memory (lane-interleaved),
-//     Gram entries shared across the 32 columns of a warp tile;
-//   * warp tier: one warp per column, lanes own rows (|I(l)| <= 64);
-//   * CTA tier: one CTA per column (|I(l)| <= 224), packed triangle.
+//   * thread tier: one THREAD per column (tiles whose largest |I(l)| is <= 17), a
+//     private packed triangle in shared memory (lane-interleaved), Gram entries
+//     shared across the 32 columns of a warp tile;
+//   * group tiers: G lanes per column (tiles whose largest |I(l)| is <= 25, 33, 48
+//     or 64; the last two in sub-tiles of 16 and 8 columns), Gram entries shared
+//     across the (sub-)tile;
+//   * warp tier: one warp per column, lanes own rows (|I(l)| <= 64, columns of tiles
+//     holding a larger one);
+//   * CTA tier: one CTA per column (|I(l)| <= 224), packed triangle; in a batch, the
+//     blocked solver in four parts by column size instead (k_lsq_huge).
 // Columns too large for a tier go to a device-side work list for the next one.
 //
 // The kernel values and the thread tier's register Cholesky are in lsq_device.cuh.
