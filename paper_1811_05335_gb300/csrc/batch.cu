@@ -329,13 +329,17 @@ k_tile_fill(const BatchProblem* __restrict__ probs, int lc, int lw, const int32_
 // the column's weights and node values in shared memory.
 INFFT_D float2 col_sum_staged(const float* wc, const float2* fc, int n, int k0) {
     float re = 0, im = 0;
-    int k = k0;
-    for (int i = 0; i < n; ++i) {
+    for (int k = k0; k < n; ++k) {   // the same order as one walk from k0 with wrap-around
         const float wi = wc[k];
         const float2 v = fc[k];
         re = fmaf(wi, v.x, re);
         im = fmaf(wi, v.y, im);
-        k = (k + 1 == n) ? 0 : k + 1;
+    }
+    for (int k = 0; k < k0; ++k) {
+        const float wi = wc[k];
+        const float2 v = fc[k];
+        re = fmaf(wi, v.x, re);
+        im = fmaf(wi, v.y, im);
     }
     return make_float2(re, im);
 }
@@ -402,15 +406,20 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     const bool staged = (we - wb) <= WMAX && U <= N;       // block-uniform
     const bool one_piece = U <= UMAX;
     int pq[UPT];
+    // the staging rounds this warp takes part in (warp-uniform: its lanes' first q is the warp's base)
+    const int wbase = threadIdx.x & ~31;
+    const int nu = U > wbase ? min(UPT, (U - wbase + COLS - 1) / COLS) : 0;
     if (staged) {
         for (int v = threadIdx.x; v < (we - wb) / 4; v += COLS) cp_async16(ws + 4 * v, w32 + wb + 4 * v);
         if (one_piece) {
 #pragma unroll
             for (int u = 0; u < UPT; ++u) {
-                const int q = threadIdx.x + u * COLS;
-                int gq = S + q;
-                if (gq >= N) gq -= N;
-                pq[u] = q < U ? perm[gq] : 0;
+                if (u < nu) {
+                    const int q = threadIdx.x + u * COLS;
+                    int gq = S + q;
+                    if (gq >= N) gq -= N;
+                    pq[u] = q < U ? perm[gq] : 0;
+                }
             }
         }
     }
@@ -420,7 +429,9 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     const int s = live ? pr.col_start[p] : 0;
     const int off = live ? pr.col_off[p] : 0;
     const bool wide_col = live && pr.wide[p];
-    const int k0 = n ? (p & 31) % n : 0;
+    int k0 = p & 31;                  // (p mod 32) mod n, by subtraction (n is mostly above 31)
+    if (n == 0) k0 = 0;
+    else while (k0 >= n) k0 -= n;
     int r0 = s - S;
     if (r0 < 0) r0 += N;
     const bool direct = !staged || wide_col || (n > 0 && r0 + n > U);
@@ -429,7 +440,7 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
 #pragma unroll
         for (int u = 0; u < UPT; ++u) {
             const int q = threadIdx.x + u * COLS;
-            if (q < U) cp_async8(fu + q, fp + pq[u]);
+            if (u < nu && q < U) cp_async8(fu + q, fp + pq[u]);
         }
         cp_async_wait_all();
         __syncthreads();
