@@ -235,7 +235,8 @@ k_batch_chirp(const BatchProblem* __restrict__ probs, float2* __restrict__ bhat_
 struct TileShape {
     int log_cols, log_wblk;
 };
-constexpr TileShape TILE_SHAPES[] = {{6, 10}, {6, 11}, {6, 12}, {7, 10}, {7, 11}, {7, 12}, {8, 11}, {8, 12}};
+constexpr TileShape TILE_SHAPES[] = {{6, 10}, {6, 11}, {6, 12}, {7, 10}, {7, 11}, {7, 12},
+                                     {8, 11}, {8, 12}, {8, 13}, {9, 12}, {9, 13}};
 constexpr int TILE_SHAPE_COUNT = (int)(sizeof(TILE_SHAPES) / sizeof(TILE_SHAPES[0]));
 constexpr int TILE_SHAPE_DEFAULT = 4;
 constexpr int TILE_SCAN_THREADS = 1024;
@@ -391,8 +392,9 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     constexpr int WMAX = (1 << LW) + HUGE_NMAX + 8;       // wblk + the largest solved column + alignment
     constexpr int UMAX = COLS * 8 > 1024 ? COLS * 8 : 1024;
     constexpr int UPT = UMAX / COLS;
-    __shared__ __align__(16) float ws[WMAX];
-    __shared__ __align__(16) float2 fu[UMAX];
+    extern __shared__ __align__(16) unsigned char bsp_smem[];
+    float* ws = (float*)bsp_smem;                       // WMAX weights (a multiple of 16 bytes)
+    float2* fu = (float2*)(bsp_smem + WMAX * 4);        // UMAX node values
     if ((int)blockIdx.x >= *ntiles) return;
     const int4 ra = tiles[2 * blockIdx.x], rb = tiles[2 * blockIdx.x + 1];
     const int p0 = ra.y, p1 = ra.z, S = ra.w, w0 = rb.x, w1 = rb.y, U = rb.z;
@@ -478,14 +480,29 @@ k_batch_spread(const BatchProblem* __restrict__ probs, const int4* __restrict__ 
     g[p] = direct ? col_sum_direct(fp, w32, pr.wlo, wide_col, perm, n, s, off, N, k0) : acc;
 }
 
+// shared memory of shape (LC, LW): the staged weights and node values
+template <int LC, int LW> constexpr size_t batch_spread_smem() {
+    return (size_t)((1 << LW) + HUGE_NMAX + 8) * 4 + (size_t)((1 << LC) * 8 > 1024 ? (1 << LC) * 8 : 1024) * 8;
+}
+
+template <int LC, int LW>
+cudaError_t launch_spread_shape(unsigned grid, const BatchProblem* probs, const int4* tiles, const int32_t* ntiles,
+                                const float2* f, float2* g, cudaStream_t s) {
+    constexpr size_t sm = batch_spread_smem<LC, LW>();
+    static_assert(((1 << LW) + HUGE_NMAX + 8) * 4 % 16 == 0, "node values 16-byte aligned");
+    cudaError_t e = cudaFuncSetAttribute(k_batch_spread<LC, LW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_batch_spread<LC, LW><<<grid, 1 << LC, sm, s>>>(probs, tiles, ntiles, f, g);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_spread(int shape, unsigned grid, const BatchProblem* probs, const int4* tiles,
                                 const int32_t* ntiles, const float2* f, float2* g, cudaStream_t s) {
     switch (shape) {
 #define INFFT_SPREAD_SHAPE(ID, LC, LW)                                                   \
     case ID:                                                                             \
         static_assert(TILE_SHAPES[ID].log_cols == LC && TILE_SHAPES[ID].log_wblk == LW, ""); \
-        k_batch_spread<LC, LW><<<grid, 1 << LC, 0, s>>>(probs, tiles, ntiles, f, g);    \
-        break;
+        return launch_spread_shape<LC, LW>(grid, probs, tiles, ntiles, f, g, s);
         INFFT_SPREAD_SHAPE(0, 6, 10)
         INFFT_SPREAD_SHAPE(1, 6, 11)
         INFFT_SPREAD_SHAPE(2, 6, 12)
@@ -494,11 +511,13 @@ cudaError_t launch_batch_spread(int shape, unsigned grid, const BatchProblem* pr
         INFFT_SPREAD_SHAPE(5, 7, 12)
         INFFT_SPREAD_SHAPE(6, 8, 11)
         INFFT_SPREAD_SHAPE(7, 8, 12)
+        INFFT_SPREAD_SHAPE(8, 8, 13)
+        INFFT_SPREAD_SHAPE(9, 9, 12)
+        INFFT_SPREAD_SHAPE(10, 9, 13)
 #undef INFFT_SPREAD_SHAPE
         default:
             return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // D^* F^* of every problem's grid (pruned to its M central frequencies): one CTA

@@ -41,7 +41,7 @@ def test_cache_roundtrip_and_version(tmp_path):
 def test_committed_cache_is_valid():
     entries = tuning.load_cache(tuning.DEFAULT_CACHE)
     shapes = g.infft_batch_tile_shapes()
-    assert len(shapes) == 8 and shapes[4] == (128, 2048)          # the default: the fixed rule
+    assert len(shapes) == 11 and shapes[4] == (128, 2048)         # the default: the fixed rule
     for key, e in entries.items():
         assert 0 <= e["shape"] < len(shapes)
         assert (e["cols"], e["weights"]) == shapes[e["shape"]]
