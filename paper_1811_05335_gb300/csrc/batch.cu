@@ -11,9 +11,11 @@
 // a CUDA graph.
 //
 // Apply: two launches for the whole batch.  (1) Spreading, one CTA per tile of at
-// most 128 grid points of one problem (staged like the single-problem apply's
-// tiles); tiles are cut after the precompute so that each holds fewer than
-// 2048 + |I(l)|max weights (clustered nodes make some columns hundreds of nodes long).
+// most `cols` grid points of one problem, staged in shared memory; tiles are cut after
+// the precompute so that each holds fewer than wblk + |I(l)|max weights (clustered
+// nodes make some columns hundreds of nodes long).  (cols, wblk) is the batch's tile
+// shape, chosen by measurement (infft_batch_tune_apply); every shape sums each column
+// in the same order, so the shape changes the time and never the result.
 // (2) One persistent CTA per SM takes problems by size: D^* F^* on the problem's
 // grid of M_sigma = 2M points.  M is any even number, so the pruned DFT
 //   h_k = sum_{l=-M}^{M-1} g_l w^{kl},  w = e^{-2 pi i/(2M)},  k = -M/2 .. M/2-1,
