@@ -115,7 +115,9 @@ k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, co
     int32_t* __restrict__ route_big = BATCH ? pa->tiles_big : route_big_;
     int32_t* __restrict__ route_48 = BATCH ? pa->tiles_48 : route_48_;
     int32_t* __restrict__ route_64 = BATCH ? pa->tiles_64 : route_64_;
-    int32_t* __restrict__ col_list = BATCH ? pa->list_a : col_list_;
+    // in a batch, the columns of tiles above 64 nodes go straight to the big list, which the
+    // blocked solver takes (its smallest part has eight CTAs per SM); alone, to the warp tier
+    int32_t* __restrict__ col_list = BATCH ? pa->big_list : col_list_;
     int32_t* __restrict__ counters = BATCH ? pa->counters : counters_;
     const int tile = BATCH ? it - tb.off[pb] : tiles_in ? tiles_in[it] : it;
     const int p = tile * 32 + lane;
@@ -133,7 +135,7 @@ k_lsq_thread(const double* __restrict__ xs_, const double2* __restrict__ ph_, co
         } else if (D <= LSQ_WARP2_NMAX) {
             if (lane == 0) route_64[atomicAdd(&counters[CNT_TILES_64], 1)] = tile;
         } else if (n > 0) {
-            col_list[atomicAdd(&counters[CNT_LIST_A], 1)] = p;
+            col_list[atomicAdd(&counters[BATCH ? CNT_BIG_LIST : CNT_LIST_A], 1)] = p;
         } else if (live) {                 // empty columns of a tile sent to the warp tier end here
             Jout[p] = 1.0;
             wide[p] = 0;
