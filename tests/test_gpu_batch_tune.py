@@ -1,9 +1,10 @@
 """Autotuned tiles of the batched spreading (through the C ABI).
 
 * Every tile shape gives a bit-identical fhat: each column is summed in one order that depends
-  on its grid point only, whichever tile holds it and whether the tile is staged in shared
-  memory or read directly (a problem of about 900 nodes per column makes some tiles of the
-  64-point shapes too large to stage) or spread in float-float (wide columns).
+  on its grid point only, whichever tile holds it and whether the tile's node window is staged
+  in shared memory in one piece or in several (a problem of about 900 nodes per column makes
+  some windows longer than the staging buffer) or the column is spread in float-float (wide
+  columns) by direct loads.
 * The tuner returns the shape it measured fastest and leaves the batch on it; the cache
   returns a stored choice without measuring.
 The default shape's fhat is held against the FP64 oracle in test_gpu_batch.py, so equality with
