@@ -100,7 +100,7 @@ constexpr int TBP = TB + 2;        // shared-memory row stride of the staged pan
 constexpr int LARGE_THREADS = 256;
 constexpr int CELL_SORT_MAX = 4096;
 constexpr int FFT2_THREADS = 256;
-constexpr int SPREAD_LPC = 8;     // lanes per column of the fp32 spread (the width of a cell-row run at m = 4)
+constexpr int SPREAD_LPC = 4;     // lanes per column of the fp32 spread (each takes every fourth cell-row run)
 constexpr int SPREAD_BIG = 512;   // longer columns are spread by one CTA each
 
 thread_local std::string g_err2;
