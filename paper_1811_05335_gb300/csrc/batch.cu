@@ -6,7 +6,7 @@
 // pattern one CTA per problem (pattern.cu, k_batch_pattern), each solver tier one
 // launch over the work items of all problems, numbered by a device prefix of the
 // problems' counts (lsq.cu, run_precompute_batch), and the columns of more than 64
-// nodes of all problems one launch of the blocked solver.  Everything is
+// nodes of all problems the blocked solver, four launches by column size.  Everything is
 // stream-ordered on the caller's stream, so the whole precompute can be captured in
 // a CUDA graph.
 //
